@@ -1,0 +1,27 @@
+"""FP64 CPU oracle of the nonlinear-damage ADER-DG step.
+
+TEST INFRASTRUCTURE ONLY.  This package is a plain, slow, independent
+restatement of the method (arXiv 2502.09714, Sec. 2 and Appendix A) in numpy
+FP64.  Only the test-suite, the smoke check and the CPU-baseline leg of the
+benchmark may import it; the CUDA library never does, and it shares no code,
+tables or helpers with the CUDA path (both only consume the seeded arrays of
+the `synthetic` package).
+
+Pins (see tests/test_oracle_*.py): quadrature exactness on monomials,
+orthonormality/span of the basis, the stress as the strain gradient of an
+energy, hand-derived damage rates of special strain states, the uniform-strain
+closed form of damage growth, design-order convergence on the elastic plane
+wave, energy decay, the brute-force monomial-basis re-derivation of one step,
+invariance under relabelling/rotation/translation and monotone damage.
+"""
+from .basis import eval_basis, mode_list, n_modes
+from .quadrature import gauss_jacobi, gauss_legendre_01, tet_rule, tri_rule
+from .rheology import (cdm_damage_rate, cdm_energy, cdm_stress, effective_lame, flux,
+                       invariants, jacobian_eff)
+from .solver import MeshError, Oracle, from_abi, stf_integral, to_abi
+
+__all__ = [
+    "eval_basis", "mode_list", "n_modes", "gauss_jacobi", "gauss_legendre_01", "tet_rule",
+    "tri_rule", "cdm_damage_rate", "cdm_energy", "cdm_stress", "effective_lame", "flux",
+    "invariants", "jacobian_eff", "MeshError", "Oracle", "from_abi", "to_abi", "stf_integral",
+]

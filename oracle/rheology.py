@@ -1,0 +1,124 @@
+"""Pointwise CDM (Lyakhovsky continuum damage) law of the oracle (test
+infrastructure only).  All arrays carry the 10 conservative variables in the
+last axis: (eps_xx, eps_yy, eps_zz, eps_xy, eps_yz, eps_zx, v_x, v_y, v_z, alpha)
+(Eq. "nonlinear hyper pdes"), tensor shear strains.
+
+Material arrays `mat` have last axis (rho, lambda0, mu0, gamma_r, xi0, C_d).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+I2_FLOOR = 1e-30   # reading R7: below this I2 counts as zero strain (xi = 0)
+
+# (i, j) component -> index of the strain entry in u
+SYM = np.array([[0, 3, 5],
+                [3, 1, 4],
+                [5, 4, 2]])
+
+
+def strain_tensor(u):
+    """3x3 strain tensor from u[..., 0:6]."""
+    return u[..., SYM]
+
+
+def invariants(u):
+    """I1 = eps_kk, I2 = eps_ij eps_ij (sum over all 9 entries), sqrt(I2), xi
+    (Sec. 2.1, text after Eq. "ivm-model" and Eq. "cdb-model"); xi = 0 where
+    I2 is below the floor (reading R7)."""
+    e = strain_tensor(u)
+    I1 = e[..., 0, 0] + e[..., 1, 1] + e[..., 2, 2]
+    I2 = np.einsum("...ij,...ij->...", e, e)
+    zero = I2 <= I2_FLOOR
+    s = np.where(zero, 0.0, np.sqrt(np.where(zero, 1.0, I2)))
+    xi = np.where(zero, 0.0, I1 / np.where(zero, 1.0, s))
+    return I1, I2, s, xi
+
+
+def cdm_stress(u, mat):
+    """Stress tensor [...,3,3] of Eq. "cdb-model":
+    sigma = lambda0 I1 delta - alpha gamma_r sqrt(I2) delta
+            + [2 (mu0 + alpha xi0 gamma_r) - alpha gamma_r xi] eps."""
+    lam0, mu0, gr, xi0 = mat[..., 1], mat[..., 2], mat[..., 3], mat[..., 4]
+    alpha = u[..., 9]
+    e = strain_tensor(u)
+    I1, I2, s, xi = invariants(u)
+    iso = lam0 * I1 - alpha * gr * s
+    shear = 2.0 * (mu0 + alpha * xi0 * gr) - alpha * gr * xi
+    return iso[..., None, None] * np.eye(3) + shear[..., None, None] * e
+
+
+def cdm_damage_rate(u, mat):
+    """r_alpha of Eq. "cdb-model": C_d gamma_r I2 (xi - xi0) where xi > xi0,
+    else 0.  Written as C_d gamma_r max(0, I1 sqrt(I2) - xi0 I2), which equals
+    it for I2 > 0 and needs no division (reading R7)."""
+    gr, xi0, cd = mat[..., 3], mat[..., 4], mat[..., 5]
+    I1, I2, s, xi = invariants(u)
+    return cd * gr * np.maximum(0.0, I1 * s - xi0 * I2)
+
+
+def cdm_energy(u, mat):
+    """Elastic energy density W with sigma = dW/d eps (derived, not printed):
+    W = lambda0/2 I1^2 + (mu0 + alpha xi0 gamma_r) I2 - alpha gamma_r I1 sqrt(I2)."""
+    lam0, mu0, gr, xi0 = mat[..., 1], mat[..., 2], mat[..., 3], mat[..., 4]
+    alpha = u[..., 9]
+    I1, I2, s, xi = invariants(u)
+    return 0.5 * lam0 * I1 * I1 + (mu0 + alpha * xi0 * gr) * I2 - alpha * gr * I1 * s
+
+
+def effective_lame(u, mat):
+    """Effective Lame parameters of the CDM (Eq. "effective-cdb") under readings
+    R2/R7: lambda_eff = lambda0 - alpha gamma_r (I1/3)/sqrt(I2)
+                      = lambda0 - alpha gamma_r xi / 3,
+    mu_eff = mu0 + alpha xi0 gamma_r - alpha gamma_r xi / 2 (sign of the xi0 term
+    taken from the stress law of Eq. "cdb-model")."""
+    lam0, mu0, gr, xi0 = mat[..., 1], mat[..., 2], mat[..., 3], mat[..., 4]
+    alpha = u[..., 9]
+    _, _, _, xi = invariants(u)
+    lam = lam0 - alpha * gr * xi / 3.0
+    mu = mu0 + alpha * xi0 * gr - 0.5 * alpha * gr * xi
+    return lam, mu
+
+
+def flux(u, mat):
+    """Physical flux F^d_p [...,3(d),10(p)] of Eq. "nonlinear hyper pdes" under the
+    rheology (follows from Eq. "nonlinear damage models"):
+      F^d_{eps_ij} = -(v_i delta_jd + v_j delta_id)/2,
+      F^d_{v_i}    = -sigma_id / rho,
+      F^d_alpha    = 0."""
+    rho = mat[..., 0]
+    v = u[..., 6:9]
+    sig = cdm_stress(u, mat)
+    F = np.zeros(u.shape[:-1] + (3, 10))
+    for p, (i, j) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (2, 0))):
+        # -(v_i delta_jd + v_j delta_id)/2: the d = j entry gets -v_i/2, the d = i entry -v_j/2
+        F[..., j, p] += -0.5 * v[..., i]
+        F[..., i, p] += -0.5 * v[..., j]
+    F[..., :, 6:9] = -np.swapaxes(sig, -1, -2) / rho[..., None, None]   # F[d, v_i] = -sigma_{i d}/rho
+    return F
+
+
+def jacobian_eff(lam, mu, rho):
+    """Effective isotropic flux Jacobians B^{d,eff} [...,3,10,10] (Appendix A,
+    Eqs. "matrix_Beff_1..3") rebuilt from the linear isotropic flux
+    (reading T1: the printed B^2/B^3 rows have misplaced entries) with a zero
+    alpha row (reading T2: F_alpha = 0, Lambda's last eigenvalue is 0)."""
+    shape = np.shape(lam)
+    B = np.zeros(shape + (3, 10, 10))
+    pairs = ((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (2, 0))
+    for d in range(3):
+        for p, (i, j) in enumerate(pairs):
+            # dF^d_{eps_ij}/d v_m = -(delta_im delta_jd + delta_jm delta_id)/2
+            for m in range(3):
+                val = -0.5 * ((i == m) * (j == d) + (j == m) * (i == d))
+                if val != 0.0:
+                    B[..., d, p, 6 + m] += val
+        for i in range(3):
+            row = 6 + i
+            # sigma_id = lam I1 delta_id + 2 mu eps_id ; F = -sigma_id/rho
+            if i == d:
+                for q in range(3):
+                    B[..., d, row, q] += -lam / rho
+            q = SYM[i, d]
+            B[..., d, row, q] += -2.0 * mu / rho
+    return B

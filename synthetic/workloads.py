@@ -1,0 +1,115 @@
+"""Seeded workload descriptions (materials, point sources, receivers).
+
+Material rows are (rho, lambda0, mu0, gamma_r, xi0, C_d) in SI units, C_d in
+1/(Pa s).  Field order of the state vector u is
+(eps_xx, eps_yy, eps_zz, eps_xy, eps_yz, eps_zx, v_x, v_y, v_z, alpha), with
+tensor (not engineering) shear strains.
+
+Workloads:
+  c1  periodic 4 km cube, 4^3 x 6 = 384 tets, N=2, homogeneous rock, plane P-wave.
+  c2  periodic 4 km cube, 32^3 x 6 = 196,608 tets, +-10% jitter (seed 1), N=4,
+      soft 600 m top layer over a halfspace, 45-degree dip-slip point source
+      with a 2 Hz Ricker moment rate, 64 receivers on a jittered 8x8 grid (seed 2).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .mesh import periodic_cube_mesh
+
+FIELD_NAMES = ("exx", "eyy", "ezz", "exy", "eyz", "ezx", "vx", "vy", "vz", "alpha")
+
+# damage parameters of the rock (config c1): gamma_r, xi0, C_d [1/(Pa s)]
+ROCK_GAMMA_R = 3.7e10
+ROCK_XI0 = -0.8
+ROCK_CD = 1.0e-4
+
+
+def rock_material(n_elem, rho=2700.0, lam=32e9, mu=32e9, gamma_r=ROCK_GAMMA_R,
+                  xi0=ROCK_XI0, cd=ROCK_CD):
+    m = np.empty((n_elem, 6))
+    m[:] = (rho, lam, mu, gamma_r, xi0, cd)
+    return m
+
+
+def uniform_material(n_elem, rho, lam, mu, gamma_r, xi0, cd):
+    return rock_material(n_elem, rho, lam, mu, gamma_r, xi0, cd)
+
+
+def lame_from_speeds(vp, vs, rho):
+    mu = rho * vs * vs
+    lam = rho * vp * vp - 2.0 * mu
+    return lam, mu
+
+
+def two_layer_material(centroid_z, z_top, layer_thickness, soft=(1500.0, 500.0, 2000.0),
+                       hard=(6000.0, 3500.0, 2700.0), xi0=ROCK_XI0, cd=ROCK_CD,
+                       gamma_over_mu=ROCK_GAMMA_R / 32e9):
+    """Per-element material of a soft top layer over a halfspace, chosen by the
+    element centroid depth.  gamma_r scales with each layer's mu0 so that the
+    soft layer keeps hyperbolicity at the damage levels of the run."""
+    n = centroid_z.shape[0]
+    m = np.empty((n, 6))
+    for (vp, vs, rho), mask in ((hard, centroid_z < z_top - layer_thickness),
+                                (soft, centroid_z >= z_top - layer_thickness)):
+        lam, mu = lame_from_speeds(vp, vs, rho)
+        m[mask] = (rho, lam, mu, gamma_over_mu * mu, xi0, cd)
+    return m
+
+
+def dip_slip_source(x, m0, f0=2.0, t0=0.45):
+    """45-degree dip-slip double couple (fault normal (1,0,1)/sqrt2, slip
+    (-1,0,1)/sqrt2): moment tensor m0*diag(-1,0,1).  Ricker moment rate with
+    peak frequency f0 centred at t0; m0 is the peak moment rate [N m / s]."""
+    return {"x": np.asarray(x, dtype=np.float64),
+            "m": np.array([-m0, 0.0, m0, 0.0, 0.0, 0.0]),
+            "stf": 0, "f0": float(f0), "t0": float(t0)}
+
+
+def receiver_grid(nx, ny, extent_xy, z, jitter, seed=2):
+    rng = np.random.default_rng(seed)
+    xs = (np.arange(nx) + 0.5) * extent_xy[0] / nx
+    ys = (np.arange(ny) + 0.5) * extent_xy[1] / ny
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), np.full(nx * ny, float(z))], axis=1)
+    pts[:, :2] += rng.uniform(-jitter, jitter, size=(nx * ny, 2))
+    return pts
+
+
+def workload_c1(damage=True, sort_by_vid=False):
+    """384-tet periodic cube, N=2, homogeneous rock; plane P-wave along x with
+    strain amplitude 1e-4 and wavelength equal to the 4 km cube."""
+    mesh = periodic_cube_mesh(4, 4000.0, jitter=0.0, sort_by_vid=sort_by_vid)
+    mat = rock_material(mesh.n_elem, cd=ROCK_CD if damage else 0.0)
+    return {"name": "c1 periodic cube 384 tets N=2", "mesh": mesh, "material": mat,
+            "order": 2, "cfl": 0.5, "steps": 20,
+            "plane_wave": {"amplitude": 1e-4, "k": 2.0 * np.pi / 4000.0, "kind": "P"}}
+
+
+# peak moment rate of the c2 point source [N m/s]; sets the peak strain near
+# the source to the 1e-3 range on the 125 m mesh
+C2_M0 = 4.0e14
+
+
+def workload_c2(n=32, side=4000.0, order=4, m0=C2_M0, sort_by_vid=True):
+    """The 196,608-tet (n=32) jittered two-layer cube with a point source and
+    64 receivers.  Smaller n gives the same workload at a smaller size."""
+    mesh = periodic_cube_mesh(n, side, jitter=0.1, seed=1, sort_by_vid=sort_by_vid)
+    cz = mesh.centroids()[:, 2]
+    mat = two_layer_material(cz, z_top=side, layer_thickness=600.0 * side / 4000.0)
+    src = dip_slip_source([0.5 * side, 0.5 * side, 0.75 * side], m0)
+    h = side / n
+    rec = receiver_grid(8, 8, (side, side), z=0.975 * side, jitter=0.5 * h, seed=2)
+    return {"name": f"c2 jittered two-layer cube {mesh.n_elem} tets N={order}",
+            "mesh": mesh, "material": mat, "order": order, "cfl": 0.5, "steps": 500,
+            "sources": [src], "receivers": rec}
+
+
+def workload_small_layered(n=4, order=3, side=4000.0, m0=C2_M0, seed=1, sort_by_vid=False):
+    """A c2-shaped workload at a size the oracle runs in seconds."""
+    w = workload_c2(n=n, side=side, order=order, m0=m0, sort_by_vid=sort_by_vid)
+    if seed != 1:
+        w["mesh"] = periodic_cube_mesh(n, side, jitter=0.1, seed=seed, sort_by_vid=sort_by_vid)
+        cz = w["mesh"].centroids()[:, 2]
+        w["material"] = two_layer_material(cz, z_top=side, layer_thickness=600.0 * side / 4000.0)
+    return w
