@@ -19,8 +19,9 @@ One step from t_n to t_{n+1} = t_n + dt, in the order of Appendix A:
   9. update of Eq. "time-integrated" with M = I (orthonormal basis).
 Point sources enter step 9 as strain-rate deltas; receivers sample velocity.
 
-State layout inside the oracle: Q[E, L, 10] (mode, field).  The C-ABI layout
-[E, 10, L] is produced by to_abi()/from_abi().
+State layout inside the oracle: Q[E, L, 10] (mode, field), modes of the
+Dubiner basis mapped onto each element with its vertices in increasing vertex
+id (reading R15).  The C-ABI layout [E, 10, L] is produced by to_abi()/from_abi().
 """
 from __future__ import annotations
 
@@ -68,21 +69,31 @@ def stf_integral(src, t):
 
 
 class Oracle:
-    def __init__(self, elem_xyz, elem_vid, order, material, face_bc=None, cfl=0.5):
-        self.xyz = np.asarray(elem_xyz, dtype=np.float64)
-        self.vid = np.asarray(elem_vid, dtype=np.int64)
+    def __init__(self, elem_xyz, elem_vid, order, material, face_bc=None, cfl=0.5, face_rows=None):
+        """face_rows: elements whose face tables are built (default all); step()
+        can only produce new states for those elements."""
+        xyz = np.asarray(elem_xyz, dtype=np.float64)
+        vid = np.asarray(elem_vid, dtype=np.int64)
+        # Reading R15: each element's reference map lists its vertices by
+        # increasing global vertex id, so the face nodes seen from the two
+        # elements of a face are the same physical points.
+        vorder = np.argsort(vid, axis=1, kind="stable")
+        rows = np.arange(xyz.shape[0])[:, None]
+        self.xyz = np.ascontiguousarray(xyz[rows, vorder])
+        self.vid = np.ascontiguousarray(vid[rows, vorder])
         self.E = self.xyz.shape[0]
         self.N = int(order)
         self.L = n_modes(self.N)
         self.mat = np.asarray(material, dtype=np.float64).reshape(self.E, 6)
         self.face_bc = (np.zeros((self.E, 4), dtype=np.int8) if face_bc is None
-                        else np.asarray(face_bc, dtype=np.int8))
+                        else np.asarray(face_bc, dtype=np.int8)[rows, vorder])
         if np.any(self.face_bc != 0):
             raise NotImplementedError("boundary faces are not part of this oracle")
         self.cfl = cfl
         self._reference()
         self._geometry()
         self._match_faces()
+        self.face_rows = np.arange(self.E) if face_rows is None else np.unique(np.asarray(face_rows))
         self._face_tables()
         self.sources = []
         self.receivers = None
@@ -160,21 +171,24 @@ class Oracle:
         s, t = self.qf_pts[:, 0], self.qf_pts[:, 1]
         Nf = s.size
         self.Vf_own = np.empty((4, Nf, self.L))
-        self.face_x = np.empty((self.E, 4, Nf, 3))
+        rows = self.face_rows
+        self.row_of = -np.ones(self.E, dtype=np.int64)
+        self.row_of[rows] = np.arange(rows.size)
+        X = self.xyz[rows]
+        self.face_x = np.empty((rows.size, 4, Nf, 3))
         for f in range(4):
             a, b, c = face_vertices(f)
             R = REF_VERTS
             xi = R[a] + s[:, None] * (R[b] - R[a]) + t[:, None] * (R[c] - R[a])
             self.Vf_own[f] = eval_basis(self.N, xi)
-            X = self.xyz
             self.face_x[:, f] = (X[:, a, None] + s[None, :, None] * (X[:, b] - X[:, a])[:, None]
                                  + t[None, :, None] * (X[:, c] - X[:, a])[:, None])
-        self.Vf_nbr = np.empty((self.E, 4, Nf, self.L))
+        self.Vf_nbr = np.empty((rows.size, 4, Nf, self.L))
         for f in range(4):
-            nb = self.nbr[:, f]
-            xp = self.face_x[:, f] + self.shift[:, f, None, :]            # in the neighbour's frame
+            nb = self.nbr[rows, f]
+            xp = self.face_x[:, f] + self.shift[rows, f, None, :]         # in the neighbour's frame
             xi_nb = np.einsum("ead,eqd->eqa", self.Jinv[nb], xp - self.xyz[nb, 0][:, None, :], optimize=True)
-            self.Vf_nbr[:, f] = eval_basis(self.N, xi_nb.reshape(-1, 3)).reshape(self.E, Nf, self.L)
+            self.Vf_nbr[:, f] = eval_basis(self.N, xi_nb.reshape(-1, 3)).reshape(rows.size, Nf, self.L)
 
     # ---------------- sources / receivers ----------------
     def locate(self, x, tol=1e-10):
@@ -272,7 +286,10 @@ class Oracle:
                 nb = self.nbr[rr, f]
                 n = self.normal[rr, f]
                 um = np.einsum("il,nzlp->nzip", self.Vf_own[f], U[pr], optimize=True)
-                up = np.einsum("nil,nzlp->nzip", self.Vf_nbr[rr, f], U[pos[nb]], optimize=True)
+                fr = self.row_of[rr]
+                if np.any(fr < 0):
+                    raise ValueError("face tables were not built for some requested rows")
+                up = np.einsum("nil,nzlp->nzip", self.Vf_nbr[fr, f], U[pos[nb]], optimize=True)
                 Fm = np.einsum("nzidp,nd->nzip", flux(um, mat[:, None, None, :]), n, optimize=True)
                 Fp = np.einsum("nzidp,nd->nzip", flux(up, self.mat[nb][:, None, None, :]), n, optimize=True)
                 C = np.maximum(cp[pr], cp[pos[nb]])
@@ -311,6 +328,15 @@ class Oracle:
         x = self.xyz[:, 0, None, :] + np.einsum("edk,qk->eqd", self.J, pts, optimize=True)
         vals = func(x)
         return np.einsum("q,qk,eqp->ekp", w, V, vals, optimize=True)
+
+    def to_reference(self, e, x):
+        """Reference coordinates in element e of physical points x[...,3]."""
+        return (np.asarray(x) - self.xyz[e, 0]) @ self.Jinv[e].T
+
+    def evaluate_at(self, Q, e, x):
+        """Fields [...,10] of element e at physical points x[...,3]."""
+        xi = self.to_reference(e, x).reshape(-1, 3)
+        return (eval_basis(self.N, xi) @ Q[e]).reshape(np.shape(x)[:-1] + (10,))
 
     def evaluate(self, Q, pts_ref):
         V = eval_basis(self.N, pts_ref)

@@ -99,7 +99,7 @@ def workload_c2(n=32, side=4000.0, order=4, m0=C2_M0, sort_by_vid=True):
     mat = two_layer_material(cz, z_top=side, layer_thickness=600.0 * side / 4000.0)
     src = dip_slip_source([0.5 * side, 0.5 * side, 0.75 * side], m0)
     h = side / n
-    rec = receiver_grid(8, 8, (side, side), z=0.975 * side, jitter=0.5 * h, seed=2)
+    rec = receiver_grid(8, 8, (side, side), z=0.975 * side, jitter=min(0.5 * h, side / 32.0), seed=2)
     return {"name": f"c2 jittered two-layer cube {mesh.n_elem} tets N={order}",
             "mesh": mesh, "material": mat, "order": order, "cfl": 0.5, "steps": 500,
             "sources": [src], "receivers": rec}

@@ -8,7 +8,8 @@ Legendre/Duffy rule from numpy; the Cauchy-Kovalevskaya derivatives are taken
 by exact differentiation of the polynomials in physical space; neighbours are
 found geometrically (face vertex sets equal up to a periodic box translation).
 
-Only the pointwise law (stress, damage rate, effective Lame parameters,
+Quadrature nodes follow the method's convention: each element's reference
+map lists its vertices by increasing vertex id.  Only the pointwise law (stress, damage rate, effective Lame parameters,
 B^{d,eff}), which is pinned separately, is shared.  Where the method evaluates
 a nonlinear function, it does so at quadrature nodes; those nodes (collapsed
 Gauss-Jacobi on the element in its vertex order, on each face in ascending
@@ -101,8 +102,10 @@ def duffy_rule(n):
 
 
 class BruteForce:
-    def __init__(self, xyz, N, mat, box):
-        self.xyz = np.asarray(xyz, float)
+    def __init__(self, xyz, vid, N, mat, box):
+        # node placement convention of the method (reading R15): vertices by increasing id
+        order = np.argsort(np.asarray(vid), axis=1, kind="stable")
+        self.xyz = np.asarray(xyz, float)[np.arange(len(order))[:, None], order]
         self.E = self.xyz.shape[0]
         self.N = N
         self.mat = np.asarray(mat, float)
