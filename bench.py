@@ -1,0 +1,338 @@
+"""Benchmark of the nonlinear-damage ADER-DG step on GB300.
+
+One bench step = one time step of the whole method (predictor, corrector with
+volume/source/face terms and update, point source, receivers) over the
+196,608-tet N=4 jittered two-layer periodic cube with a dip-slip point source
+and 64 receivers (synthetic, seeded).  Metric: element-updates/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N>1 (torchrun, one process per GPU) runs N independent replicas of the
+workload (the method is not sharded across GPUs here); value = all ranks'
+element updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "element-updates/s (FP32, N=4)"
+UNIT = "element-updates/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def n_modes(N):
+    return (N + 1) * (N + 2) * (N + 3) // 6
+
+
+def algorithmic_flops(N):
+    """FLOPs per element update of the method as this library formulates it
+    (FMA = 2): Taylor terms restricted to their nonzero modes (degree <= N-i),
+    volume quadrature (N+1)^3 x (N+1) time nodes, face quadrature (N+1)^2 x (N+1)
+    per face and side.  Returns (predictor, corrector)."""
+    L, NQ, NF, NT = n_modes(N), (N + 1) ** 3, (N + 1) ** 2, N + 1
+    LR = [n_modes(N - i) for i in range(N + 1)]
+    sum_hi = sum(LR[1:])
+    # predictor: CK recursion (3 reference derivatives of 9 fields), physical
+    # gradients and star products, damage rate at the volume nodes and projection
+    ck = sum(2 * 27 * LR[i] * LR[i - 1] + 2 * 81 * LR[i] + 30 * LR[i] for i in range(1, N + 1))
+    src = 2 * 6 * NQ * L + 20 * NQ + 2 * NQ * L
+    pred = ck + src
+    # corrector
+    vol_eval = 2 * NQ * (8 * L + 6 * sum_hi) + 2 * NQ * NT * (6 * N + 1)
+    point = NQ * NT * 50 + NQ * 63
+    vol_proj = 2 * L * NQ * 10
+    strain = 2 * L * (9 * L + 27) + 2 * 3 * (L + sum_hi)
+    face_tr = 4 * NF * 2 * 2 * (11 * L + 9 * sum_hi) + 4 * NF * NT * 2 * 2 * (9 * N + 1)
+    llf = 4 * NF * NT * 165
+    face_proj = 4 * 2 * L * NF * 9
+    corr = vol_eval + point + vol_proj + strain + face_tr + llf + face_proj + 2 * 10 * L
+    return pred, corr
+
+
+def algorithmic_bytes(N):
+    """Minimum HBM bytes per element update: read and write the FP32 state
+    (10 L floats each) plus 176 B of geometry, material and connectivity."""
+    return 8 * 10 * n_modes(N) + 176
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", str(self.index),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+               "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self._proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self._proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(workload, steps=1, max_seconds=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: one
+    z-layer of hexahedral cells (6 n^2 elements) advanced one step from a
+    seeded state on the full mesh.  Returns (element-updates/s, sample text, threads)."""
+    from oracle import Oracle
+    mesh, mat, N = workload["mesh"], workload["material"], workload["order"]
+    n = mesh.cells[0]
+    rows = np.arange(6 * n * n * (n // 2), 6 * n * n * (n // 2 + 1))      # one z-layer of cells
+    t_setup = time.perf_counter()
+    o = Oracle(mesh.elem_xyz, mesh.elem_vid, N, mat, face_rows=rows)
+    o.set_sources(workload["sources"])
+    setup = time.perf_counter() - t_setup
+    rng = np.random.default_rng(0)
+    Q = rng.normal(size=(mesh.n_elem, o.L, 10)) * 1e-6
+    dt = o.cfl_dt()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step(Q, dt, t=0.3, rows=rows)
+    el = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        threads = 1
+    sample = (f"{rows.size} elements (one z-layer of cells of the {mesh.n_elem}-tet mesh), "
+              f"{steps} step(s), numpy FP64; setup {setup:.1f}s excluded")
+    return rows.size * steps / el, sample, threads, el
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from synthetic import workload_c2
+    w = workload_c2(n=args.n, order=args.order)
+    vals, total = [], 0.0
+    for _ in range(args.warmup):
+        cpu_baseline(w, steps=1)
+    for _ in range(args.steps):
+        v, sample, threads, el = cpu_baseline(w, steps=1)
+        vals.append(v)
+        total += el
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * w["mesh"].n_elem / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(w, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(w, args):
+    return {"workload": w["name"], "elements": w["mesh"].n_elem, "order": w["order"],
+            "modes": n_modes(w["order"]), "fields": 10, "sources": len(w["sources"]),
+            "receivers": int(len(w["receivers"])), "l2_policy": "inputs larger than L2 "
+            "(state 2x and predictor buffers > 129 MB at N=4); no flush", "parallelism": f"replicas{args.gpus}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=32, help="cells per cube side (32 -> 196,608 tets)")
+    ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2502_09714_gb300 as dgpkg
+    from synthetic import workload_c2
+
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dgpkg.build()
+    w = workload_c2(n=args.n, order=args.order)
+    mesh, mat, N = w["mesh"], w["material"], w["order"]
+    E, L = mesh.n_elem, n_modes(N)
+    stream = torch.cuda.current_stream()
+    s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, N, cfl=w["cfl"], stream=stream)
+    s.set_material(mat)
+    s.set_sources(w["sources"])
+    s.set_receivers(w["receivers"])
+    s.set_state(np.zeros((E, 10, L), np.float32), 0.0)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    s.step(args.warmup)
+    barrier()
+    s.profile(True)
+    launches0 = s.stats()["kernel_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(args.steps)
+    ev1.record(stream)
+    barrier()
+    clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = s.profile_read()
+    s.profile(False)
+    launches = s.stats()["kernel_launches"] - launches0
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * E * args.steps / (ms_max * 1e-3)
+
+    # end to end through the public API: pinned host state in, one step, state out
+    hq = torch.zeros((E, 10, L), dtype=torch.float32).pin_memory()
+    hq_np = hq.numpy()
+    out = torch.empty_like(hq).pin_memory()
+    out_np = out.numpy()
+    s.get_state(out=out_np)
+    hq_np[...] = out_np
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s.set_state(hq_np, s.time)
+        s.step(1)
+        s.get_state(out=out_np)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * E * args.e2e_steps / float(te.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_kind = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12    # TFLOP/s
+    fp, fc = algorithmic_flops(N)
+    corr = prof["corrector"]
+    corr_ms = corr["total_ms"] / max(1, corr["launches"])
+    pred = prof["predictor"]
+    pred_ms = pred["total_ms"] / max(1, pred["launches"])
+    achieved = fc * E / (corr_ms * 1e-3) / 1e12
+    traffic = _traffic_per_launch(N, E)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(w, args),
+        "roofline": {"kernel": "k_corrector<4>", "bound": "alu", "achieved": achieved,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                     "traffic": traffic,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (max clock, {peak_kind} peaks file)",
+                     "flops_per_element": fc, "avg_ms": corr_ms},
+        "kernels": {k: {"launches": v["launches"], "avg_ms": v["total_ms"] / max(1, v["launches"])}
+                    for k, v in prof.items()},
+        "hbm": {"algorithmic_bytes_per_element": algorithmic_bytes(N),
+                "achieved_gbs": algorithmic_bytes(N) * value / world / 1e9,
+                "peak_gbs": peaks.get("hbm_gbs"),
+                "frac": algorithmic_bytes(N) * value / world / 1e9 / float(peaks.get("hbm_gbs", 6800.0))},
+        "step_flops": {"predictor": fp, "corrector": fc,
+                       "achieved_tflops": (fp + fc) * value / world / 1e12},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hq.numel() * 4),
+                "d2h_bytes_per_step": int(out.numel() * 4), "steps": args.e2e_steps},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        v, sample, threads, _ = cpu_baseline(w, steps=1)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _traffic_per_launch(N, E):
+    """DRAM bytes per corrector launch from the committed ncu summary, scaled to
+    E elements, or None when no capture of the current kernel exists."""
+    p = os.path.join(ROOT, "profiles", "corrector_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("order") != N:
+        return None
+    return d["dram_bytes_per_element"] * E
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * dg.h - C-ABI of the GB300 nonlinear-damage ADER-DG step (libdg).
+ *
+ * The library advances the 3-D wave equations of a continuum-damage (CDM,
+ * Lyakhovsky) rock on a tetrahedral mesh with the explicit ADER discontinuous
+ * Galerkin scheme of arXiv 2502.09714:
+ *   - governing equations: Sec. 2.1, Eq. "nonlinear damage models" (strain,
+ *     velocity, damage alpha) in the conservative form of Eq. "nonlinear hyper
+ *     pdes", CDM stress and damage rate of Eq. "cdb-model";
+ *   - modal Dubiner DG in space (Eq. "modal dg space"), ADER Taylor expansion in
+ *     time (Eq. "eq:taylor_expansion");
+ *   - one step = space-time predictor (Appendix A.1, Eqs. "CKIter-ref-matrix",
+ *     "CKIter-ref-source"), volume integral (Eq. "3rd term"), Rusanov face flux
+ *     from the neighbour trace (Eqs. "rusanov-flux", "2nd term"), pointwise
+ *     damage-rate source (Eq. "rhs term"), update (Eq. "time-integrated").
+ *
+ * Conventions shared by every call:
+ *   - All functions return dg_status (DG_OK = 0) and never throw.  On error the
+ *     message is available from dg_last_error(ctx) (or dg_last_error(NULL) for
+ *     failures before a context exists).
+ *   - Host pointers are borrowed for the duration of the call only; the library
+ *     copies what it keeps.  The context owns all device memory it allocates.
+ *   - Units are SI.  The 10 conservative variables are, in this order,
+ *     (eps_xx, eps_yy, eps_zz, eps_xy, eps_yz, eps_zx, v_x, v_y, v_z, alpha) with
+ *     tensor (not engineering) shear strains (Eq. "nonlinear hyper pdes").
+ *   - Modal coefficients refer to the orthonormal Dubiner basis of the unit
+ *     tetrahedron (0,0,0),(1,0,0),(0,1,0),(0,0,1), mapped affinely onto each
+ *     element with the element's vertices listed by increasing vertex id
+ *     (elem_vid), whatever their order in elem_xyz.  The same map places the
+ *     volume and face quadrature nodes, so both elements of a face evaluate
+ *     their traces at the same physical points.
+ *     Mode order: total degree ascending, then (i,j,k) lexicographic, where mode
+ *     (i,j,k) = c * u^i P_i^(0,0)((2xi-u)/u) * w^j P_j^(2i+1,0)((2eta-w)/w)
+ *               * P_k^(2i+2j+2,0)(2zeta-1),  u = 1-eta-zeta, w = 1-zeta,
+ *     c = sqrt((2i+1)(2i+2j+2)(2i+2j+2k+3)).  L = (N+1)(N+2)(N+3)/6 modes.
+ *   - State arrays use the layout q[n_elem][10][L] (element, field, mode).
+ *   - Calls are ordered on the context's CUDA stream.  One context per host
+ *     thread.  dg_step, dg_get_state* and dg_receivers_read synchronise the
+ *     stream before they return; the other calls may return before the device
+ *     work they enqueued has finished.
+ *   - Device arithmetic is FP32.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dg_ctx dg_ctx;
+
+typedef enum {
+  DG_OK = 0,
+  DG_E_ARG = 1,            /* invalid argument (NULL pointer, bad size, bad value) */
+  DG_E_MESH = 2,           /* invalid mesh: degenerate element, repeated vertex id,
+                              face not matched exactly once, bad boundary tag */
+  DG_E_ORDER = 3,          /* polynomial degree not compiled into this library */
+  DG_E_OOM = 4,            /* device or host allocation failed */
+  DG_E_CUDA = 5,           /* a CUDA runtime call failed (message has the CUDA error) */
+  DG_E_STATE = 6,          /* call out of sequence (e.g. dg_step before dg_set_material) */
+  DG_E_NONFINITE = 7,      /* a NaN/Inf appeared in the state during dg_step */
+  DG_E_NONHYPERBOLIC = 8,  /* mu_eff <= 0 or lambda_eff + 2 mu_eff <= 0 in some cell */
+  DG_E_OUTSIDE = 9,        /* a source or receiver point lies in no element */
+  DG_E_UNSUPPORTED = 10    /* feature not provided by this build (e.g. members > 1) */
+} dg_status;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc must
+ * return a device pointer aligned to at least 256 bytes, or NULL on failure.
+ * NULL in dg_mesh_desc.alloc selects cudaMalloc/cudaFree. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+  void* user;
+} dg_allocator;
+
+typedef struct {
+  int64_t n_elem;
+  const double* elem_xyz;   /* [n_elem][4][3] vertex coordinates of each element.  Periodic
+                               images are allowed: an element straddling a periodic wrap lists
+                               its unwrapped coordinates. */
+  const int64_t* elem_vid;  /* [n_elem][4] global vertex ids; periodically identified vertices
+                               share an id.  Two element faces are neighbours iff their vertex-id
+                               triples are equal.  The four ids of an element must differ. */
+  const int8_t* face_bc;    /* [n_elem][4] tag of the face opposite local vertex f: 0 = interior
+                               or periodic (must be matched exactly once); other tags are
+                               rejected with DG_E_UNSUPPORTED by this build.  NULL = all 0. */
+  int order;                /* polynomial degree N (1..5 compiled) */
+  int members;              /* ensemble members; must be 1 in this build */
+  double cfl;               /* Courant number of the default time step (see dg_dt) */
+  void* cuda_stream;        /* cudaStream_t to order all work on; NULL = legacy default stream */
+  const dg_allocator* alloc;/* optional device allocator, NULL = cudaMalloc */
+} dg_mesh_desc;
+
+/* Validate the mesh, match faces, build geometry and reference tables, and
+ * allocate device memory.  Element orientation is free (either sign of the
+ * Jacobian determinant); |det J| must be > 1e-12 * (edge scale)^3.
+ * Errors: DG_E_ARG, DG_E_MESH, DG_E_ORDER, DG_E_UNSUPPORTED, DG_E_OOM, DG_E_CUDA.
+ * On success *out owns the context (free with dg_destroy). */
+dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out);
+
+/* Per-element material [n_elem][6] = (rho, lambda0, mu0, gamma_r, xi0, C_d):
+ * density, Lame parameters of the intact rock, damage modulus gamma_r [Pa],
+ * damage onset xi0 (Eq. "cdb-model") and damage-rate coefficient C_d [1/(Pa s)].
+ * Requires rho > 0, mu0 > 0, lambda0 + 2 mu0 > 0, gamma_r >= 0, C_d >= 0 and
+ * finite values (DG_E_ARG otherwise).  member_xi0_cd must be NULL in this build.
+ * Also fixes the default time step dt = cfl * min_e 2 r_in(e) / ((2N+1) c_p(e)),
+ * r_in the inradius, c_p = sqrt((lambda0 + 2 mu0)/rho). */
+dg_status dg_set_material(dg_ctx* ctx, const double* mat, const double* member_xi0_cd);
+
+/* Moment-tensor point sources, replacing any previous set (n = 0 clears).
+ * A source acts on the strain equations as the rate
+ *     d eps/dt -= C0^{-1} : M * w(t) * delta(x - x_s),
+ * C0 the intact isotropic stiffness of the host element, M = m[6] in the field
+ * order (Mxx, Myy, Mzz, Mxy, Myz, Mzx).  w(t): stf 0 = Ricker
+ * (1 - 2 (pi f0 tau)^2) exp(-(pi f0 tau)^2), tau = t - t0 (M then is the peak
+ * moment rate); stf 1 = Gaussian rate of standard deviation f0_or_sigma and unit
+ * integral centred at t0 (M the total moment).  Each step adds the exact time
+ * integral of w over [t_n, t_n + dt].  The host element is the first element
+ * (in input order) whose closure contains x (DG_E_OUTSIDE if none).
+ * Requires dg_set_material first (DG_E_STATE). */
+typedef struct {
+  double x[3];
+  double m[6];
+  int stf;
+  double f0_or_sigma;
+  double t0;
+} dg_point_source;
+dg_status dg_set_source(dg_ctx* ctx, const dg_point_source* src, int64_t n);
+
+/* Set the modal state q[n_elem][10][L] (FP64 or FP32 host arrays, or an FP32
+ * device array in the same layout for the _device form) and the time t. */
+dg_status dg_set_state(dg_ctx* ctx, const double* q, double t);
+dg_status dg_set_state_f32(dg_ctx* ctx, const float* q, double t);
+dg_status dg_set_state_device(dg_ctx* ctx, const float* q_dev, double t);
+
+/* Read the modal state into q_out[n_elem][10][L] and the time into *t_out
+ * (t_out may be NULL). */
+dg_status dg_get_state(dg_ctx* ctx, double* q_out, double* t_out);
+dg_status dg_get_state_f32(dg_ctx* ctx, float* q_out, double* t_out);
+dg_status dg_get_state_device(dg_ctx* ctx, float* q_dev_out, double* t_out);
+
+/* Advance n_steps >= 0 steps of size dt (dt <= 0 selects dg_dt(ctx)).  Each
+ * step runs the predictor, the corrector (volume, source, faces, update), the
+ * point sources and the receiver sampling on the device.  Reads the device
+ * status word once at the end: DG_E_NONFINITE if a NaN/Inf reached the state,
+ * DG_E_NONHYPERBOLIC if an effective P or S modulus became non-positive (the
+ * state is left as computed; restore it with dg_set_state).  Requires material
+ * and state (DG_E_STATE). */
+dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt);
+
+/* Register R receivers at xyz[R][3] (replaces previous ones, resets traces).
+ * After every step the velocity (v_x, v_y, v_z) at each receiver is recorded.
+ * DG_E_OUTSIDE if a point lies in no element. */
+dg_status dg_receivers(dg_ctx* ctx, const double* xyz, int64_t R);
+
+/* Copy the recorded traces out[n_rec][R][3] (n_rec = steps since dg_receivers,
+ * at most cap records are copied) and report the number recorded in *n_rec.
+ * Traces are kept for at most 65536 steps after dg_receivers. */
+dg_status dg_receivers_read(dg_ctx* ctx, float* out, int64_t cap, int64_t* n_rec);
+
+/* Default time step (0 before dg_set_material), current time, sizes. */
+double dg_dt(const dg_ctx* ctx);
+double dg_time(const dg_ctx* ctx);
+int64_t dg_n_modes(int order);
+
+/* Counters since creation: steps taken and kernels launched by dg_step. */
+typedef struct {
+  int64_t steps;
+  int64_t kernel_launches;
+  int64_t element_updates;
+} dg_stats;
+dg_status dg_get_stats(const dg_ctx* ctx, dg_stats* out);
+
+/* Per-kernel timing: when enabled, dg_step records CUDA events around each
+ * kernel on the context's stream; dg_profile_read returns, per kernel kind,
+ * the number of launches and the summed device milliseconds since the last
+ * enable.  Kinds: 0 predictor, 1 corrector, 2 point source, 3 receivers. */
+typedef struct {
+  int64_t launches;
+  double total_ms;
+} dg_kernel_time;
+dg_status dg_profile_enable(dg_ctx* ctx, int on);
+dg_status dg_profile_read(dg_ctx* ctx, dg_kernel_time* out, int cap, int* n_kinds);
+
+/* Host-side reference data of degree `order`, for validation without a GPU.
+ * which: 0 volume nodes [Nq][4] (xi, eta, zeta, weight, weights sum to 1/6);
+ *        1 face nodes [Nf][3] (s, t, weight; weights sum to 1);
+ *        2 time nodes [Nt][2] (tau in [0,1], weight; weights sum to 1);
+ *        3 basis values at the volume nodes [Nq][L];
+ *        4 basis gradients at the volume nodes [Nq][L][3].
+ * Writes at most cap doubles; *count receives the number of doubles of the
+ * full table.  DG_E_ORDER for an unsupported degree, DG_E_ARG otherwise. */
+dg_status dg_reference_table(int order, int which, double* out, int64_t cap, int64_t* count);
+
+const char* dg_last_error(const dg_ctx* ctx);
+void dg_destroy(dg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_H */

@@ -1,0 +1,10 @@
+"""GB300-native ADER-DG step for 3-D waves in a continuum-damage (CDM) rock.
+
+The compute path is libdg (C-ABI in include/dg.h, CUDA kernels for sm_103a in
+csrc/); this package holds its in-tree build and a thin ctypes binding.
+"""
+from .build import LIB_PATH, build
+from .dg import DGError, Solver, load_library, n_modes, reference_table, torch_allocator
+
+__all__ = ["LIB_PATH", "build", "DGError", "Solver", "load_library", "n_modes", "reference_table",
+           "torch_allocator"]

@@ -1,0 +1,109 @@
+// Auxiliary kernels of libdg: state conversion between the ABI layout and the
+// internal layout, point-source injection and receiver sampling.
+#include "dg_internal.h"
+
+namespace dg {
+namespace {
+
+// internal q[e][l*10+p] <- ABI src[e][p][l]
+template <int L>
+__global__ void k_state_in(int64_t E, const void* src, int src_is_double, float* q, int qs) {
+  const int64_t e = blockIdx.x;
+  if (e >= E) return;
+  for (int w = threadIdx.x; w < qs; w += blockDim.x) {
+    float v = 0.f;
+    if (w < kFields * L) {
+      const int k = w / kFields, p = w % kFields;
+      const int64_t idx = e * kFields * L + p * L + k;
+      v = src_is_double ? static_cast<float>(static_cast<const double*>(src)[idx])
+                        : static_cast<const float*>(src)[idx];
+    }
+    q[e * qs + w] = v;
+  }
+}
+
+// ABI dst[e][p][l] <- internal q
+template <int L>
+__global__ void k_state_out(int64_t E, const float* q, int qs, void* dst, int dst_is_double) {
+  const int64_t e = blockIdx.x;
+  if (e >= E) return;
+  for (int w = threadIdx.x; w < kFields * L; w += blockDim.x) {
+    const int p = w / L, l = w % L;
+    const float v = q[e * qs + l * kFields + p];
+    const int64_t idx = e * kFields * L + w;
+    if (dst_is_double) static_cast<double*>(dst)[idx] = static_cast<double>(v);
+    else static_cast<float*>(dst)[idx] = v;
+  }
+}
+
+__global__ void k_sources(int L, int qs, int n_src, const SourceDev* src, const float* amp, int64_t step, float* q) {
+  const int s = blockIdx.x;
+  if (s >= n_src) return;
+  const float a = amp[step * n_src + s];
+  const int64_t e = src[s].elem;
+  for (int w = threadIdx.x; w < 6 * L; w += blockDim.x) {
+    const int p = w / L, l = w % L;
+    atomicAdd(&q[e * qs + l * kFields + p], -a * src[s].phi_eps[p * L + l]);
+  }
+}
+
+__global__ void k_receivers(int L, int qs, int n_rec, const ReceiverDev* rec, const float* q, float* out) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= 3 * n_rec) return;
+  const int r = w / 3, m = w % 3;
+  const int64_t e = rec[r].elem;
+  float v = 0.f;
+  for (int l = 0; l < L; ++l) v += rec[r].phi[l] * q[e * qs + l * kFields + 6 + m];
+  out[w] = v;
+}
+
+template <int N>
+cudaError_t state_in_t(int64_t E, const void* src, int dbl, float* q, cudaStream_t s) {
+  k_state_in<n_modes(N)><<<static_cast<unsigned>(E), 128, 0, s>>>(E, src, dbl, q, q_stride(N));
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t state_out_t(int64_t E, const float* q, void* dst, int dbl, cudaStream_t s) {
+  k_state_out<n_modes(N)><<<static_cast<unsigned>(E), 128, 0, s>>>(E, q, q_stride(N), dst, dbl);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_state_in(int N, int64_t E, const void* src, int dbl, float* q, cudaStream_t s) {
+  switch (N) {
+    case 1: return state_in_t<1>(E, src, dbl, q, s);
+    case 2: return state_in_t<2>(E, src, dbl, q, s);
+    case 3: return state_in_t<3>(E, src, dbl, q, s);
+    case 4: return state_in_t<4>(E, src, dbl, q, s);
+    case 5: return state_in_t<5>(E, src, dbl, q, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_state_out(int N, int64_t E, const float* q, void* dst, int dbl, cudaStream_t s) {
+  switch (N) {
+    case 1: return state_out_t<1>(E, q, dst, dbl, s);
+    case 2: return state_out_t<2>(E, q, dst, dbl, s);
+    case 3: return state_out_t<3>(E, q, dst, dbl, s);
+    case 4: return state_out_t<4>(E, q, dst, dbl, s);
+    case 5: return state_out_t<5>(E, q, dst, dbl, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_sources(int N, int n_src, const SourceDev* src, const float* amp, int64_t step,
+                           float* q, cudaStream_t s) {
+  k_sources<<<n_src, 128, 0, s>>>(n_modes(N), q_stride(N), n_src, src, amp, step, q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_receivers(int N, int n_rec, const ReceiverDev* rec, const float* q, float* out,
+                             cudaStream_t s) {
+  const int threads = 3 * n_rec;
+  k_receivers<<<(threads + 127) / 128, 128, 0, s>>>(n_modes(N), q_stride(N), n_rec, rec, q, out);
+  return cudaGetLastError();
+}
+
+}  // namespace dg

@@ -1,0 +1,778 @@
+// libdg host runtime: C-ABI entry points (include/dg.h), mesh validation and
+// face matching, element geometry, reference tables, state conversion,
+// sources/receivers, and the step loop that enqueues the CUDA kernels.
+#include "../../include/dg.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "dg_internal.h"
+#include "dg_reference.h"
+
+using namespace dg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct FaceKey {
+  int64_t a, b, c;
+  bool operator==(const FaceKey& o) const { return a == o.a && b == o.b && c == o.c; }
+};
+struct FaceKeyHash {
+  size_t operator()(const FaceKey& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int64_t v : {k.a, k.b, k.c}) {
+      h ^= static_cast<uint64_t>(v) + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+      h *= 1099511628211ull;
+    }
+    return static_cast<size_t>(h);
+  }
+};
+
+}  // namespace
+
+struct dg_ctx {
+  int N = 0, L = 0, M = 1;
+  int64_t E = 0;
+  double cfl = 0.5;
+  cudaStream_t stream = nullptr;
+  dg_allocator alloc{};
+  bool has_alloc = false;
+  std::string err;
+
+  // host copies (sorted vertex order)
+  std::vector<double> xyz_user;      // [E][4][3] as given
+  std::vector<double> xyz;           // [E][4][3] vertices by increasing vertex id
+  std::vector<double> jinv;          // [E][9] Theta^{-1} of the sorted order
+  std::vector<double> detj;          // [E] |det J|
+  std::vector<double> rin;           // [E] inradius
+  std::vector<double> mat;           // [E][6]
+  bool has_material = false, has_state = false;
+  double dt_cfl = 0.0, t = 0.0;
+
+  // device memory
+  float* q[2] = {nullptr, nullptr};
+  int cur = 0;
+  float* d = nullptr;
+  float* cp = nullptr;
+  GeomF* geom = nullptr;
+  MatF* matf = nullptr;
+  int* nbr = nullptr;
+  float* tables = nullptr;
+  unsigned* status = nullptr;
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  unsigned* status_host = nullptr;   // pinned
+
+  // sources
+  std::vector<dg_point_source> sources;
+  std::vector<SourceDev> source_host;
+  SourceDev* source_dev = nullptr;
+  float* amp_dev = nullptr;
+  int64_t amp_cap = 0;
+  float* amp_host = nullptr;         // pinned
+
+  // receivers
+  std::vector<ReceiverDev> rec_host;
+  ReceiverDev* rec_dev = nullptr;
+  float* traces = nullptr;
+  int64_t trace_cap = 0, n_rec = 0;
+
+  // stats / profiling
+  dg_stats stats{};
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  std::vector<int> event_kind;
+  dg_kernel_time prof[4]{};
+
+  std::vector<std::pair<void*, size_t>> owned;
+};
+
+namespace {
+
+dg_status fail(dg_ctx* ctx, dg_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  g_last_error = msg;
+  return s;
+}
+
+dg_status cuda_fail(dg_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, DG_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define DG_CUDA(ctx, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+void* dev_alloc(dg_ctx* ctx, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (ctx->has_alloc) {
+    p = ctx->alloc.alloc(bytes, ctx->stream, ctx->alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) ctx->owned.emplace_back(p, bytes);
+  return p;
+}
+
+void dev_free(dg_ctx* ctx, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < ctx->owned.size(); ++i) {
+    if (ctx->owned[i].first == p) {
+      if (ctx->has_alloc) ctx->alloc.free(p, ctx->owned[i].second, ctx->stream, ctx->alloc.user);
+      else cudaFree(p);
+      ctx->owned.erase(ctx->owned.begin() + i);
+      return;
+    }
+  }
+}
+
+bool supported_order(int N) { return N >= 1 && N <= kMaxOrder; }
+
+void inv3(const double* J, double* out, double* det) {
+  // J row-major 3x3; out = J^{-1}
+  const double a = J[0], b = J[1], c = J[2], d = J[3], e = J[4], f = J[5], g = J[6], h = J[7], i = J[8];
+  const double A = e * i - f * h, B = -(d * i - f * g), C = d * h - e * g;
+  const double D = det[0] = a * A + b * B + c * C;
+  out[0] = A / D; out[1] = -(b * i - c * h) / D; out[2] = (b * f - c * e) / D;
+  out[3] = B / D; out[4] = (a * i - c * g) / D;  out[5] = -(a * f - c * d) / D;
+  out[6] = C / D; out[7] = -(a * h - b * g) / D; out[8] = (a * e - b * d) / D;
+}
+
+// Reference tables of degree N (FP64), in the layout of table_layout(N).
+std::vector<double> build_tables(int N) {
+  const int L = n_modes(N), NQ = n_vol_nodes(N), NF = n_face_nodes(N), NT = N + 1;
+  const TableLayout T = table_layout(N);
+  std::vector<double> t(T.total, 0.0);
+  ref::Rule3 vr = ref::volume_rule(N + 1);
+  std::vector<double> val(L), grd(3 * L);
+  for (int q = 0; q < NQ; ++q) {
+    ref::dubiner(N, vr.xi[q], vr.eta[q], vr.zeta[q], val.data(), grd.data());
+    for (int l = 0; l < L; ++l) {
+      t[T.Vv + q * L + l] = val[l];
+      t[T.Vw + q * L + l] = vr.w[q] * val[l];
+      for (int e = 0; e < 3; ++e) t[T.Gw + (e * NQ + q) * L + l] = vr.w[q] * grd[3 * l + e];
+    }
+    // Kt[e][k][l] = int phi_k d phi_l / d xi_e (the rule is exact for degree 2N-1)
+    for (int e = 0; e < 3; ++e)
+      for (int k = 0; k < L; ++k)
+        for (int l = 0; l < L; ++l) t[T.Kt + (e * L + k) * L + l] += vr.w[q] * val[k] * grd[3 * l + e];
+  }
+  ref::Rule2 fr = ref::face_rule(N + 1);
+  const double R[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int f = 0; f < 4; ++f) {
+    int v[3], n = 0;
+    for (int j = 0; j < 4; ++j) if (j != f) v[n++] = j;
+    for (int i = 0; i < NF; ++i) {
+      double p[3];
+      for (int c = 0; c < 3; ++c)
+        p[c] = R[v[0]][c] + fr.s[i] * (R[v[1]][c] - R[v[0]][c]) + fr.t[i] * (R[v[2]][c] - R[v[0]][c]);
+      ref::dubiner(N, p[0], p[1], p[2], val.data(), nullptr);
+      for (int l = 0; l < L; ++l) {
+        t[T.Vf + (f * NF + i) * L + l] = val[l];
+        t[T.Vfw + (f * NF + i) * L + l] = fr.w[i] * val[l];
+      }
+    }
+  }
+  ref::Rule1 tr = ref::time_rule(NT);
+  for (int z = 0; z < NT; ++z) {
+    t[T.tz + z] = tr.x[z];
+    t[T.gz + z] = tr.w[z];
+  }
+  return t;
+}
+
+template <typename T>
+dg_status upload(dg_ctx* ctx, T* dst, const void* src, size_t bytes) {
+  DG_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  DG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return DG_OK;
+}
+
+// first element (input order) whose closure contains x; fills xi in the sorted order
+bool locate(const dg_ctx* ctx, const double* x, int64_t* elem, double xi_sorted[3]) {
+  const double tol = 1e-10;
+  for (int64_t e = 0; e < ctx->E; ++e) {
+    const double* X = &ctx->xyz_user[12 * e];
+    double J[9], Ji[9], det;
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) J[3 * r + c] = X[3 * (c + 1) + r] - X[r];
+    inv3(J, Ji, &det);
+    double xi[3];
+    for (int r = 0; r < 3; ++r)
+      xi[r] = Ji[3 * r] * (x[0] - X[0]) + Ji[3 * r + 1] * (x[1] - X[1]) + Ji[3 * r + 2] * (x[2] - X[2]);
+    const double b0 = 1.0 - xi[0] - xi[1] - xi[2];
+    if (b0 < -tol || xi[0] < -tol || xi[1] < -tol || xi[2] < -tol) continue;
+    *elem = e;
+    const double* Xs = &ctx->xyz[12 * e];
+    const double* Jis = &ctx->jinv[9 * e];
+    for (int r = 0; r < 3; ++r)
+      xi_sorted[r] = Jis[3 * r] * (x[0] - Xs[0]) + Jis[3 * r + 1] * (x[1] - Xs[1]) + Jis[3 * r + 2] * (x[2] - Xs[2]);
+    return true;
+  }
+  return false;
+}
+
+dg_status ensure_staging(dg_ctx* ctx, size_t bytes) {
+  if (ctx->staging_bytes >= bytes) return DG_OK;
+  dev_free(ctx, ctx->staging);
+  ctx->staging = dev_alloc(ctx, bytes);
+  ctx->staging_bytes = ctx->staging ? bytes : 0;
+  if (!ctx->staging) return fail(ctx, DG_E_OOM, "staging buffer allocation failed");
+  return DG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+int64_t dg_n_modes(int order) { return order < 0 ? 0 : n_modes(order); }
+
+const char* dg_last_error(const dg_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+dg_status dg_reference_table(int order, int which, double* out, int64_t cap, int64_t* count) {
+  if (!supported_order(order)) return fail(nullptr, DG_E_ORDER, "unsupported order");
+  const int N = order, L = n_modes(N);
+  std::vector<double> v;
+  if (which == 0) {
+    ref::Rule3 r = ref::volume_rule(N + 1);
+    for (size_t i = 0; i < r.w.size(); ++i) v.insert(v.end(), {r.xi[i], r.eta[i], r.zeta[i], r.w[i]});
+  } else if (which == 1) {
+    ref::Rule2 r = ref::face_rule(N + 1);
+    for (size_t i = 0; i < r.w.size(); ++i) v.insert(v.end(), {r.s[i], r.t[i], r.w[i]});
+  } else if (which == 2) {
+    ref::Rule1 r = ref::time_rule(N + 1);
+    for (size_t i = 0; i < r.w.size(); ++i) v.insert(v.end(), {r.x[i], r.w[i]});
+  } else if (which == 3 || which == 4) {
+    ref::Rule3 r = ref::volume_rule(N + 1);
+    std::vector<double> val(L), grd(3 * L);
+    for (size_t i = 0; i < r.w.size(); ++i) {
+      ref::dubiner(N, r.xi[i], r.eta[i], r.zeta[i], val.data(), grd.data());
+      if (which == 3) v.insert(v.end(), val.begin(), val.end());
+      else v.insert(v.end(), grd.begin(), grd.end());
+    }
+  } else {
+    return fail(nullptr, DG_E_ARG, "unknown table");
+  }
+  if (count) *count = static_cast<int64_t>(v.size());
+  if (out) std::memcpy(out, v.data(), sizeof(double) * std::min<int64_t>(cap, v.size()));
+  return DG_OK;
+}
+
+void dg_destroy(dg_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  while (!ctx->owned.empty()) dev_free(ctx, ctx->owned.back().first);
+  if (ctx->status_host) cudaFreeHost(ctx->status_host);
+  if (ctx->amp_host) cudaFreeHost(ctx->amp_host);
+  for (cudaEvent_t ev : ctx->events) cudaEventDestroy(ev);
+  delete ctx;
+}
+
+dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
+  if (!desc || !out) return fail(nullptr, DG_E_ARG, "NULL descriptor or output pointer");
+  *out = nullptr;
+  if (desc->n_elem <= 0 || !desc->elem_xyz || !desc->elem_vid)
+    return fail(nullptr, DG_E_ARG, "empty mesh or NULL mesh arrays");
+  if (desc->n_elem >= (int64_t(1) << 29)) return fail(nullptr, DG_E_ARG, "too many elements");
+  if (!supported_order(desc->order)) return fail(nullptr, DG_E_ORDER, "order must be in 1..5");
+  if (desc->members != 1) return fail(nullptr, DG_E_UNSUPPORTED, "only members == 1 is built");
+  if (!(desc->cfl > 0.0) || !std::isfinite(desc->cfl)) return fail(nullptr, DG_E_ARG, "cfl must be > 0");
+  const int64_t E = desc->n_elem;
+  if (desc->face_bc)
+    for (int64_t i = 0; i < 4 * E; ++i)
+      if (desc->face_bc[i] != 0)
+        return fail(nullptr, desc->face_bc[i] == 1 || desc->face_bc[i] == 2 ? DG_E_UNSUPPORTED : DG_E_MESH,
+                    "boundary faces are not supported by this build (only interior/periodic)");
+
+  dg_ctx* ctx = new dg_ctx();
+  ctx->N = desc->order;
+  ctx->L = n_modes(ctx->N);
+  ctx->E = E;
+  ctx->cfl = desc->cfl;
+  ctx->stream = static_cast<cudaStream_t>(desc->cuda_stream);
+  if (desc->alloc) { ctx->alloc = *desc->alloc; ctx->has_alloc = ctx->alloc.alloc && ctx->alloc.free; }
+
+  ctx->xyz_user.assign(desc->elem_xyz, desc->elem_xyz + 12 * E);
+  ctx->xyz.resize(12 * E);
+  ctx->jinv.resize(9 * E);
+  ctx->detj.resize(E);
+  ctx->rin.resize(E);
+  std::vector<int64_t> vid_sorted(4 * E);
+  std::vector<GeomF> geom(E);
+  for (int64_t e = 0; e < E; ++e) {
+    const int64_t* v = desc->elem_vid + 4 * e;
+    std::array<int, 4> ord{0, 1, 2, 3};
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return v[a] < v[b]; });
+    for (int j = 0; j < 3; ++j)
+      if (v[ord[j]] == v[ord[j + 1]]) { dg_destroy(ctx); return fail(nullptr, DG_E_MESH, "element " + std::to_string(e) + " repeats a vertex id"); }
+    for (int j = 0; j < 4; ++j) {
+      vid_sorted[4 * e + j] = v[ord[j]];
+      for (int c = 0; c < 3; ++c) ctx->xyz[12 * e + 3 * j + c] = desc->elem_xyz[12 * e + 3 * ord[j] + c];
+    }
+    const double* X = &ctx->xyz[12 * e];
+    double J[9], det;
+    double scale = 0.0;
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        J[3 * r + c] = X[3 * (c + 1) + r] - X[r];
+        scale = std::max(scale, std::fabs(J[3 * r + c]));
+      }
+    double* Ji = &ctx->jinv[9 * e];
+    inv3(J, Ji, &det);
+    if (!std::isfinite(det) || std::fabs(det) <= 1e-12 * scale * scale * scale) {
+      dg_destroy(ctx);
+      return fail(nullptr, DG_E_MESH, "element " + std::to_string(e) + " is degenerate");
+    }
+    ctx->detj[e] = std::fabs(det);
+    GeomF& g = geom[e];
+    std::memset(&g, 0, sizeof(g));
+    for (int k = 0; k < 9; ++k) g.tinv[k] = static_cast<float>(Ji[k]);
+    g.inv_detj = static_cast<float>(1.0 / ctx->detj[e]);
+    double area_sum = 0.0;
+    for (int f = 0; f < 4; ++f) {
+      int a[3], n = 0;
+      for (int j = 0; j < 4; ++j) if (j != f) a[n++] = j;
+      const double* A = X + 3 * a[0];
+      const double* B = X + 3 * a[1];
+      const double* C = X + 3 * a[2];
+      const double u[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+      const double w[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+      double nrm[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+      const double len = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+      const double* P = X + 3 * f;
+      const double side = nrm[0] * (P[0] - A[0]) + nrm[1] * (P[1] - A[1]) + nrm[2] * (P[2] - A[2]);
+      const double sgn = side > 0 ? -1.0 : 1.0;
+      for (int c = 0; c < 3; ++c) g.face[f][c] = static_cast<float>(sgn * nrm[c] / len);
+      g.face[f][3] = static_cast<float>(0.5 * len / ctx->detj[e]);
+      area_sum += 0.5 * len;
+    }
+    ctx->rin[e] = 3.0 * (ctx->detj[e] / 6.0) / area_sum;
+  }
+
+  // face matching by vertex-id triples (ascending in the sorted order)
+  std::vector<int> nbr(4 * E, -1);
+  {
+    std::unordered_map<FaceKey, int64_t, FaceKeyHash> open;
+    open.reserve(static_cast<size_t>(2 * E + 16));
+    for (int64_t e = 0; e < E; ++e)
+      for (int f = 0; f < 4; ++f) {
+        int a[3], n = 0;
+        for (int j = 0; j < 4; ++j) if (j != f) a[n++] = j;
+        FaceKey key{vid_sorted[4 * e + a[0]], vid_sorted[4 * e + a[1]], vid_sorted[4 * e + a[2]]};
+        auto it = open.find(key);
+        if (it == open.end()) {
+          open.emplace(key, 4 * e + f);
+        } else {
+          const int64_t other = it->second;
+          if (other < 0 || other / 4 == e) {
+            dg_destroy(ctx);
+            return fail(nullptr, DG_E_MESH, "face of element " + std::to_string(e) + " is shared more than twice or with itself");
+          }
+          nbr[4 * e + f] = static_cast<int>(other);                       // (elem << 2) | face
+          nbr[other] = static_cast<int>(4 * e + f);
+          it->second = -1;
+        }
+      }
+    for (const auto& kv : open)
+      if (kv.second >= 0) {
+        dg_destroy(ctx);
+        return fail(nullptr, DG_E_MESH, "unmatched interior face of element " + std::to_string(kv.second / 4));
+      }
+  }
+
+  // device allocation and upload
+  const int N = ctx->N, L = ctx->L;
+  const size_t qs = static_cast<size_t>(q_stride(N)), ds = static_cast<size_t>(d_stride(N));
+  ctx->q[0] = static_cast<float*>(dev_alloc(ctx, sizeof(float) * qs * E));
+  ctx->q[1] = static_cast<float*>(dev_alloc(ctx, sizeof(float) * qs * E));
+  ctx->d = static_cast<float*>(dev_alloc(ctx, sizeof(float) * ds * E));
+  ctx->cp = static_cast<float*>(dev_alloc(ctx, sizeof(float) * E));
+  ctx->geom = static_cast<GeomF*>(dev_alloc(ctx, sizeof(GeomF) * E));
+  ctx->matf = static_cast<MatF*>(dev_alloc(ctx, sizeof(MatF) * E));
+  ctx->nbr = static_cast<int*>(dev_alloc(ctx, sizeof(int) * 4 * E));
+  const TableLayout TL = table_layout(N);
+  ctx->tables = static_cast<float*>(dev_alloc(ctx, sizeof(float) * TL.total));
+  ctx->status = static_cast<unsigned*>(dev_alloc(ctx, sizeof(unsigned)));
+  if (!ctx->q[0] || !ctx->q[1] || !ctx->d || !ctx->cp || !ctx->geom || !ctx->matf || !ctx->nbr ||
+      !ctx->tables || !ctx->status) {
+    dg_destroy(ctx);
+    return fail(nullptr, DG_E_OOM, "device allocation failed");
+  }
+  if (cudaMallocHost(&ctx->status_host, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    dg_destroy(ctx);
+    return fail(nullptr, DG_E_OOM, "pinned allocation failed");
+  }
+  std::vector<float> tf;
+  {
+    std::vector<double> t = build_tables(N);
+    tf.assign(t.begin(), t.end());
+  }
+  dg_status st;
+  if ((st = upload(ctx, ctx->geom, geom.data(), sizeof(GeomF) * E)) != DG_OK ||
+      (st = upload(ctx, ctx->nbr, nbr.data(), sizeof(int) * 4 * E)) != DG_OK ||
+      (st = upload(ctx, ctx->tables, tf.data(), sizeof(float) * tf.size())) != DG_OK) {
+    std::string m = ctx->err;
+    dg_destroy(ctx);
+    return fail(nullptr, st, m);
+  }
+  cudaError_t ce;
+  if ((ce = cudaMemsetAsync(ctx->q[0], 0, sizeof(float) * qs * E, ctx->stream)) != cudaSuccess ||
+      (ce = cudaMemsetAsync(ctx->q[1], 0, sizeof(float) * qs * E, ctx->stream)) != cudaSuccess ||
+      (ce = cudaMemsetAsync(ctx->d, 0, sizeof(float) * ds * E, ctx->stream)) != cudaSuccess ||
+      (ce = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
+    dg_destroy(ctx);
+    return fail(nullptr, DG_E_CUDA, std::string("initialising device memory: ") + cudaGetErrorString(ce));
+  }
+  *out = ctx;
+  return DG_OK;
+}
+
+dg_status dg_set_material(dg_ctx* ctx, const double* mat, const double* member_xi0_cd) {
+  if (!ctx || !mat) return fail(ctx, DG_E_ARG, "NULL argument");
+  if (member_xi0_cd) return fail(ctx, DG_E_UNSUPPORTED, "per-member parameters need members > 1");
+  const int64_t E = ctx->E;
+  std::vector<MatF> mf(E);
+  double dt = INFINITY;
+  for (int64_t e = 0; e < E; ++e) {
+    const double* m = mat + 6 * e;
+    for (int k = 0; k < 6; ++k)
+      if (!std::isfinite(m[k])) return fail(ctx, DG_E_ARG, "non-finite material of element " + std::to_string(e));
+    const double rho = m[0], lam = m[1], mu = m[2], gr = m[3], xi0 = m[4], cd = m[5];
+    if (!(rho > 0) || !(mu > 0) || !(lam + 2 * mu > 0) || gr < 0 || cd < 0)
+      return fail(ctx, DG_E_ARG, "invalid material of element " + std::to_string(e));
+    mf[e] = MatF{float(rho), float(lam), float(mu), float(gr), float(xi0), float(cd), float(1.0 / rho), 0.f};
+    const double cp = std::sqrt((lam + 2 * mu) / rho);
+    dt = std::min(dt, ctx->cfl * 2.0 * ctx->rin[e] / ((2 * ctx->N + 1) * cp));
+  }
+  ctx->mat.assign(mat, mat + 6 * E);
+  dg_status st = upload(ctx, ctx->matf, mf.data(), sizeof(MatF) * E);
+  if (st != DG_OK) return st;
+  ctx->dt_cfl = dt;
+  ctx->has_material = true;
+  return DG_OK;
+}
+
+double dg_dt(const dg_ctx* ctx) { return ctx ? ctx->dt_cfl : 0.0; }
+double dg_time(const dg_ctx* ctx) { return ctx ? ctx->t : 0.0; }
+
+dg_status dg_get_stats(const dg_ctx* ctx, dg_stats* out) {
+  if (!ctx || !out) return fail(const_cast<dg_ctx*>(ctx), DG_E_ARG, "NULL argument");
+  *out = ctx->stats;
+  return DG_OK;
+}
+
+static dg_status set_state_impl(dg_ctx* ctx, const void* q, int is_double, bool device, double t) {
+  if (!ctx || !q) return fail(ctx, DG_E_ARG, "NULL argument");
+  if (!std::isfinite(t)) return fail(ctx, DG_E_ARG, "non-finite time");
+  const size_t n = static_cast<size_t>(ctx->E) * kFields * ctx->L;
+  const void* src = q;
+  if (!device) {
+    dg_status st = ensure_staging(ctx, n * (is_double ? 8 : 4));
+    if (st != DG_OK) return st;
+    DG_CUDA(ctx, cudaMemcpyAsync(ctx->staging, q, n * (is_double ? 8 : 4), cudaMemcpyHostToDevice, ctx->stream));
+    src = ctx->staging;
+  }
+  DG_CUDA(ctx, launch_state_in(ctx->N, ctx->E, src, is_double, ctx->q[ctx->cur], ctx->stream));
+  if (!device) DG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->t = t;
+  ctx->has_state = true;
+  return DG_OK;
+}
+
+dg_status dg_set_state(dg_ctx* ctx, const double* q, double t) { return set_state_impl(ctx, q, 1, false, t); }
+dg_status dg_set_state_f32(dg_ctx* ctx, const float* q, double t) { return set_state_impl(ctx, q, 0, false, t); }
+dg_status dg_set_state_device(dg_ctx* ctx, const float* q, double t) { return set_state_impl(ctx, q, 0, true, t); }
+
+static dg_status get_state_impl(dg_ctx* ctx, void* q, int is_double, bool device, double* t_out) {
+  if (!ctx || !q) return fail(ctx, DG_E_ARG, "NULL argument");
+  const size_t n = static_cast<size_t>(ctx->E) * kFields * ctx->L;
+  void* dst = q;
+  if (!device) {
+    dg_status st = ensure_staging(ctx, n * (is_double ? 8 : 4));
+    if (st != DG_OK) return st;
+    dst = ctx->staging;
+  }
+  DG_CUDA(ctx, launch_state_out(ctx->N, ctx->E, ctx->q[ctx->cur], dst, is_double, ctx->stream));
+  if (!device) DG_CUDA(ctx, cudaMemcpyAsync(q, ctx->staging, n * (is_double ? 8 : 4), cudaMemcpyDeviceToHost, ctx->stream));
+  DG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (t_out) *t_out = ctx->t;
+  return DG_OK;
+}
+
+dg_status dg_get_state(dg_ctx* ctx, double* q, double* t) { return get_state_impl(ctx, q, 1, false, t); }
+dg_status dg_get_state_f32(dg_ctx* ctx, float* q, double* t) { return get_state_impl(ctx, q, 0, false, t); }
+dg_status dg_get_state_device(dg_ctx* ctx, float* q, double* t) { return get_state_impl(ctx, q, 0, true, t); }
+
+dg_status dg_set_source(dg_ctx* ctx, const dg_point_source* src, int64_t n) {
+  if (!ctx || n < 0 || (n > 0 && !src)) return fail(ctx, DG_E_ARG, "invalid source list");
+  if (!ctx->has_material) return fail(ctx, DG_E_STATE, "dg_set_material must precede dg_set_source");
+  if (ctx->L > 64) return fail(ctx, DG_E_ORDER, "order too high for point sources");
+  std::vector<SourceDev> host(n);
+  std::vector<double> phi(ctx->L);
+  for (int64_t s = 0; s < n; ++s) {
+    const dg_point_source& p = src[s];
+    if (p.stf != 0 && p.stf != 1) return fail(ctx, DG_E_ARG, "unknown source time function");
+    if (!(p.f0_or_sigma > 0)) return fail(ctx, DG_E_ARG, "source f0/sigma must be > 0");
+    int64_t e;
+    double xi[3];
+    if (!locate(ctx, p.x, &e, xi)) return fail(ctx, DG_E_OUTSIDE, "source " + std::to_string(s) + " lies outside the mesh");
+    ref::dubiner(ctx->N, xi[0], xi[1], xi[2], phi.data(), nullptr);
+    const double lam = ctx->mat[6 * e + 1], mu = ctx->mat[6 * e + 2];
+    const double tr = p.m[0] + p.m[1] + p.m[2];
+    double eps[6];
+    for (int k = 0; k < 6; ++k) eps[k] = p.m[k] / (2.0 * mu);
+    for (int k = 0; k < 3; ++k) eps[k] -= lam / (2.0 * mu * (3.0 * lam + 2.0 * mu)) * tr;
+    SourceDev& d = host[s];
+    std::memset(&d, 0, sizeof(d));
+    d.elem = e;
+    for (int k = 0; k < 6; ++k)
+      for (int l = 0; l < ctx->L; ++l) d.phi_eps[k * ctx->L + l] = static_cast<float>(phi[l] * eps[k] / ctx->detj[e]);
+  }
+  dev_free(ctx, ctx->source_dev);
+  ctx->source_dev = nullptr;
+  ctx->sources.assign(src, src + n);
+  ctx->source_host = host;
+  if (n > 0) {
+    ctx->source_dev = static_cast<SourceDev*>(dev_alloc(ctx, sizeof(SourceDev) * n));
+    if (!ctx->source_dev) return fail(ctx, DG_E_OOM, "source allocation failed");
+    return upload(ctx, ctx->source_dev, host.data(), sizeof(SourceDev) * n);
+  }
+  return DG_OK;
+}
+
+dg_status dg_receivers(dg_ctx* ctx, const double* xyz, int64_t R) {
+  if (!ctx || R < 0 || (R > 0 && !xyz)) return fail(ctx, DG_E_ARG, "invalid receiver list");
+  if (ctx->L > 64) return fail(ctx, DG_E_ORDER, "order too high for receivers");
+  std::vector<ReceiverDev> host(R);
+  std::vector<double> phi(ctx->L);
+  for (int64_t r = 0; r < R; ++r) {
+    int64_t e;
+    double xi[3];
+    if (!locate(ctx, xyz + 3 * r, &e, xi)) return fail(ctx, DG_E_OUTSIDE, "receiver " + std::to_string(r) + " lies outside the mesh");
+    ref::dubiner(ctx->N, xi[0], xi[1], xi[2], phi.data(), nullptr);
+    std::memset(&host[r], 0, sizeof(ReceiverDev));
+    host[r].elem = e;
+    for (int l = 0; l < ctx->L; ++l) host[r].phi[l] = static_cast<float>(phi[l]);
+  }
+  dev_free(ctx, ctx->rec_dev);
+  dev_free(ctx, ctx->traces);
+  ctx->rec_dev = nullptr;
+  ctx->traces = nullptr;
+  ctx->trace_cap = 0;
+  ctx->n_rec = 0;
+  ctx->rec_host = host;
+  if (R > 0) {
+    ctx->rec_dev = static_cast<ReceiverDev*>(dev_alloc(ctx, sizeof(ReceiverDev) * R));
+    if (!ctx->rec_dev) return fail(ctx, DG_E_OOM, "receiver allocation failed");
+    return upload(ctx, ctx->rec_dev, host.data(), sizeof(ReceiverDev) * R);
+  }
+  return DG_OK;
+}
+
+dg_status dg_receivers_read(dg_ctx* ctx, float* out, int64_t cap, int64_t* n_rec) {
+  if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
+  const int64_t R = static_cast<int64_t>(ctx->rec_host.size());
+  if (n_rec) *n_rec = ctx->n_rec;
+  const int64_t n = std::min(cap, ctx->n_rec);
+  if (n > 0 && R > 0) {
+    if (!out) return fail(ctx, DG_E_ARG, "NULL output");
+    DG_CUDA(ctx, cudaMemcpyAsync(out, ctx->traces, sizeof(float) * 3 * R * n, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  DG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return DG_OK;
+}
+
+dg_status dg_profile_enable(dg_ctx* ctx, int on) {
+  if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
+  ctx->profiling = on != 0;
+  std::memset(ctx->prof, 0, sizeof(ctx->prof));
+  return DG_OK;
+}
+
+dg_status dg_profile_read(dg_ctx* ctx, dg_kernel_time* out, int cap, int* n_kinds) {
+  if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
+  if (n_kinds) *n_kinds = 4;
+  for (int k = 0; k < std::min(cap, 4); ++k) out[k] = ctx->prof[k];
+  return DG_OK;
+}
+
+static double stf_integral(const dg_point_source& s, double t) {
+  const double tau = t - s.t0;
+  if (s.stf == 0) {
+    const double c = (M_PI * s.f0_or_sigma) * (M_PI * s.f0_or_sigma);
+    return tau * std::exp(-c * tau * tau);
+  }
+  return 0.5 * (1.0 + std::erf(tau / (s.f0_or_sigma * std::sqrt(2.0))));
+}
+
+dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
+  if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
+  if (n_steps < 0) return fail(ctx, DG_E_ARG, "negative step count");
+  if (!ctx->has_material || !ctx->has_state) return fail(ctx, DG_E_STATE, "material and state must be set before dg_step");
+  if (dt <= 0) dt = ctx->dt_cfl;
+  if (!std::isfinite(dt)) return fail(ctx, DG_E_ARG, "non-finite dt");
+  if (n_steps == 0) return DG_OK;
+  const int nsrc = static_cast<int>(ctx->sources.size());
+  const int R = static_cast<int>(ctx->rec_host.size());
+  // per-step source amplitudes (exact time integrals of the moment-rate function)
+  if (nsrc > 0) {
+    const int64_t need = n_steps * nsrc;
+    if (ctx->amp_cap < need) {
+      dev_free(ctx, ctx->amp_dev);
+      if (ctx->amp_host) cudaFreeHost(ctx->amp_host);
+      ctx->amp_host = nullptr;
+      ctx->amp_dev = static_cast<float*>(dev_alloc(ctx, sizeof(float) * need));
+      if (!ctx->amp_dev || cudaMallocHost(&ctx->amp_host, sizeof(float) * need) != cudaSuccess) {
+        ctx->amp_cap = 0;
+        return fail(ctx, DG_E_OOM, "source amplitude buffer");
+      }
+      ctx->amp_cap = need;
+    }
+    DG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));     // amp_host may still be read by a copy
+    for (int64_t s = 0; s < n_steps; ++s) {
+      const double t0 = ctx->t + s * dt, t1 = ctx->t + (s + 1) * dt;
+      for (int k = 0; k < nsrc; ++k)
+        ctx->amp_host[s * nsrc + k] = static_cast<float>(stf_integral(ctx->sources[k], t1) - stf_integral(ctx->sources[k], t0));
+    }
+    DG_CUDA(ctx, cudaMemcpyAsync(ctx->amp_dev, ctx->amp_host, sizeof(float) * need, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  // receiver trace capacity
+  if (R > 0) {
+    const int64_t need = std::min<int64_t>(ctx->n_rec + n_steps, 65536);
+    if (need > ctx->trace_cap) {
+      int64_t cap = std::max<int64_t>(1024, ctx->trace_cap);
+      while (cap < need) cap *= 2;
+      cap = std::min<int64_t>(cap, 65536);
+      float* nt = static_cast<float*>(dev_alloc(ctx, sizeof(float) * 3 * R * cap));
+      if (!nt) return fail(ctx, DG_E_OOM, "trace buffer");
+      if (ctx->traces && ctx->n_rec > 0)
+        DG_CUDA(ctx, cudaMemcpyAsync(nt, ctx->traces, sizeof(float) * 3 * R * ctx->n_rec, cudaMemcpyDeviceToDevice, ctx->stream));
+      dev_free(ctx, ctx->traces);
+      ctx->traces = nt;
+      ctx->trace_cap = cap;
+    }
+  }
+  DG_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream));
+  // events for per-kernel timing
+  const int per_step = 2 + (nsrc > 0) + (R > 0);
+  if (ctx->profiling) {
+    const size_t need = static_cast<size_t>(n_steps * per_step + 1);
+    while (ctx->events.size() < need) {
+      cudaEvent_t ev;
+      DG_CUDA(ctx, cudaEventCreate(&ev));
+      ctx->events.push_back(ev);
+    }
+    ctx->event_kind.assign(need, -1);
+  }
+  size_t ev = 0;
+  auto mark = [&](int kind) -> cudaError_t {
+    if (!ctx->profiling) return cudaSuccess;
+    if (kind >= 0) ctx->event_kind[ev] = kind;
+    return cudaEventRecord(ctx->events[ev++], ctx->stream);
+  };
+  StepArgs a{};
+  a.E = ctx->E;
+  a.d = ctx->d;
+  a.cp = ctx->cp;
+  a.geom = ctx->geom;
+  a.mat = ctx->matf;
+  a.nbr = ctx->nbr;
+  a.tables = ctx->tables;
+  a.dt = static_cast<float>(dt);
+  a.status = ctx->status;
+  int64_t launches = 0;
+  DG_CUDA(ctx, mark(-1));
+  for (int64_t s = 0; s < n_steps; ++s) {
+    a.q_in = ctx->q[ctx->cur];
+    a.q_out = ctx->q[1 - ctx->cur];
+    DG_CUDA(ctx, launch_predictor(ctx->N, a, ctx->stream));
+    if (ctx->profiling) ctx->event_kind[ev] = 0;
+    DG_CUDA(ctx, mark(0));
+    DG_CUDA(ctx, launch_corrector(ctx->N, a, ctx->stream));
+    DG_CUDA(ctx, mark(1));
+    launches += 2;
+    ctx->cur = 1 - ctx->cur;
+    if (nsrc > 0) {
+      DG_CUDA(ctx, launch_sources(ctx->N, nsrc, ctx->source_dev, ctx->amp_dev, s, ctx->q[ctx->cur], ctx->stream));
+      DG_CUDA(ctx, mark(2));
+      ++launches;
+    }
+    if (R > 0) {
+      if (ctx->n_rec < 65536) {
+        DG_CUDA(ctx, launch_receivers(ctx->N, R, ctx->rec_dev, ctx->q[ctx->cur], ctx->traces + 3 * R * ctx->n_rec, ctx->stream));
+        ++ctx->n_rec;
+        ++launches;
+      }
+      DG_CUDA(ctx, mark(3));
+    }
+  }
+  DG_CUDA(ctx, cudaMemcpyAsync(ctx->status_host, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+  DG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->t += n_steps * dt;
+  ctx->stats.steps += n_steps;
+  ctx->stats.kernel_launches += launches;
+  ctx->stats.element_updates += n_steps * ctx->E;
+  if (ctx->profiling) {
+    for (size_t i = 1; i < ev; ++i) {
+      float ms = 0.f;
+      DG_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->events[i - 1], ctx->events[i]));
+      const int k = ctx->event_kind[i];
+      if (k >= 0 && k < 4) {
+        ctx->prof[k].launches += 1;
+        ctx->prof[k].total_ms += ms;
+      }
+    }
+  }
+  const unsigned st = *ctx->status_host;
+  if (st & kStatusNonFinite) return fail(ctx, DG_E_NONFINITE, "non-finite value in the state");
+  if (st & kStatusNonHyperbolic) return fail(ctx, DG_E_NONHYPERBOLIC, "effective moduli lost hyperbolicity");
+  if (st & kStatusIndex) return fail(ctx, DG_E_MESH, "neighbour index out of range");
+  return DG_OK;
+}
+
+}  // extern "C"
+
+namespace dg {
+
+cudaError_t launch_predictor(int N, const StepArgs& a, cudaStream_t s) {
+  switch (N) {
+    case 1: return launch_predictor_t<1>(a, s);
+    case 2: return launch_predictor_t<2>(a, s);
+    case 3: return launch_predictor_t<3>(a, s);
+    case 4: return launch_predictor_t<4>(a, s);
+    case 5: return launch_predictor_t<5>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_corrector(int N, const StepArgs& a, cudaStream_t s) {
+  switch (N) {
+    case 1: return launch_corrector_t<1>(a, s);
+    case 2: return launch_corrector_t<2>(a, s);
+    case 3: return launch_corrector_t<3>(a, s);
+    case 4: return launch_corrector_t<4>(a, s);
+    case 5: return launch_corrector_t<5>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dg

@@ -1,0 +1,131 @@
+// Internal declarations shared by the host runtime (dg_host.cpp) and the CUDA
+// kernels (dg_step_n*.cu, dg_aux.cu).  Not part of the public C-ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dg {
+
+constexpr int kFields = 10;      // eps_xx eps_yy eps_zz eps_xy eps_yz eps_zx v_x v_y v_z alpha
+constexpr int kWave = 9;         // fields that take part in the wave (flux) part
+constexpr int kMaxOrder = 5;
+
+__host__ __device__ constexpr int n_modes(int N) { return (N + 1) * (N + 2) * (N + 3) / 6; }
+__host__ __device__ constexpr int n_vol_nodes(int N) { return (N + 1) * (N + 1) * (N + 1); }
+__host__ __device__ constexpr int n_face_nodes(int N) { return (N + 1) * (N + 1); }
+__host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
+
+// Per-element state stride (floats): modal coefficients stored [L][10].
+__host__ __device__ constexpr int q_stride(int N) { return round4(kFields * n_modes(N)); }
+
+// Per-element predictor output: for i = 1..N the time derivative D^i of the 9
+// wave fields restricted to the modes of degree <= N-i ([L_{N-i}][9] each),
+// then D^1 of alpha on all L modes.
+__host__ __device__ constexpr int d_offset(int N, int i) {
+  int off = 0;
+  for (int j = 1; j < i; ++j) off += kWave * n_modes(N - j);
+  return off;
+}
+__host__ __device__ constexpr int d_alpha_offset(int N) { return d_offset(N, N + 1); }
+__host__ __device__ constexpr int d_stride(int N) { return round4(d_alpha_offset(N) + n_modes(N)); }
+
+// Reference tables of degree N (FP32, one device buffer), offsets in floats.
+struct TableLayout {
+  int Kt;     // [3][L][L]   Kt[e][k][l] = int phi_k d phi_l / d xi_e
+  int Vv;     // [NQ][L]     phi_l at volume node q
+  int Vw;     // [NQ][L]     w_q phi_l(x_q)           (volume weights sum to 1/6)
+  int Gw;     // [3][NQ][L]  w_q d phi_l / d xi_e (x_q)
+  int Vf;     // [4][NF][L]  phi_l at face node i of local face f
+  int Vfw;    // [4][NF][L]  beta_i phi_l at face node i (beta sums to 1)
+  int tz;     // [NT]        time nodes in [0,1]
+  int gz;     // [NT]        time weights (sum 1)
+  int total;
+};
+
+__host__ __device__ constexpr TableLayout table_layout(int N) {
+  TableLayout t{};
+  const int L = n_modes(N), NQ = n_vol_nodes(N), NF = n_face_nodes(N), NT = N + 1;
+  int o = 0;
+  t.Kt = o;  o += 3 * L * L;
+  t.Vv = o;  o += NQ * L;
+  t.Vw = o;  o += NQ * L;
+  t.Gw = o;  o += 3 * NQ * L;
+  t.Vf = o;  o += 4 * NF * L;
+  t.Vfw = o; o += 4 * NF * L;
+  t.tz = o;  o += NT;
+  t.gz = o;  o += NT;
+  t.total = round4(o);
+  return t;
+}
+
+// Per-element geometry (32 floats).  The element's vertices are reordered by
+// increasing global vertex id inside the library, so both sides of every face
+// parametrise it identically (face f = face opposite sorted vertex f, its
+// vertices in ascending order).
+struct GeomF {
+  float tinv[9];      // Theta^{-1}[e][d] = d xi_e / d x_d  (row-major e, d)
+  float inv_detj;     // 1 / |det J|
+  float pad0[2];
+  float face[4][4];   // outward unit normal (x, y, z) and |S_f| / |det J|
+  float pad1[4];
+};
+static_assert(sizeof(GeomF) == 32 * sizeof(float), "GeomF layout");
+
+// Per-element material (8 floats).
+struct MatF {
+  float rho, lam0, mu0, gamma_r, xi0, cd, rho_inv, pad;
+};
+
+// Status bits of the device status word.
+enum : unsigned {
+  kStatusNonFinite = 1u,
+  kStatusNonHyperbolic = 2u,
+  kStatusIndex = 4u,
+};
+
+struct StepArgs {
+  int64_t E;
+  const float* q_in;      // [E][q_stride]
+  float* q_out;           // [E][q_stride]
+  float* d;               // [E][d_stride]
+  float* cp;              // [E] effective P speed of the cell mean (for the Rusanov C)
+  const GeomF* geom;      // [E]
+  const MatF* mat;        // [E]
+  const int* nbr;         // [E][4] (neighbour element << 2) | neighbour's local face
+  const float* tables;    // table_layout(N)
+  float dt;
+  unsigned* status;
+};
+
+// Kernel launchers, one per compiled degree (dg_step_n<N>.cu), and their
+// dispatch on the runtime degree (dg_host.cpp).
+template <int N> cudaError_t launch_predictor_t(const StepArgs& a, cudaStream_t s);
+template <int N> cudaError_t launch_corrector_t(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_predictor(int N, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_corrector(int N, const StepArgs& a, cudaStream_t s);
+
+// Auxiliary kernels (dg_aux.cu).
+// State conversion between the ABI layout [E][10][L] (FP64 or FP32) and the
+// internal layout [E][q_stride] ([L][10] per element, FP32).
+cudaError_t launch_state_in(int N, int64_t E, const void* src, int src_is_double, float* q,
+                            cudaStream_t s);
+cudaError_t launch_state_out(int N, int64_t E, const float* q, void* dst, int dst_is_double,
+                             cudaStream_t s);
+
+struct SourceDev {
+  int64_t elem;
+  float phi_eps[6 * 64];   // phi_l(xi_s) * (C0^{-1}:M)_p / |J|, [6][L] (L <= 56)
+};
+// Adds -amp[step * n_src + s] * phi_eps to the strain modes of each source element.
+cudaError_t launch_sources(int N, int n_src, const SourceDev* src, const float* amp, int64_t step,
+                           float* q, cudaStream_t s);
+
+struct ReceiverDev {
+  int64_t elem;
+  float phi[64];           // phi_l(xi_r)
+};
+cudaError_t launch_receivers(int N, int n_rec, const ReceiverDev* rec, const float* q,
+                             float* traces_row, cudaStream_t s);
+
+}  // namespace dg

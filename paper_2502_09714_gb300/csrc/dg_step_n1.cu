@@ -1,0 +1,5 @@
+// Predictor/corrector kernels of degree N = 1 (one translation unit per degree
+// so that the build compiles them in parallel).
+#include "dg_step_kernels.cuh"
+
+DG_INSTANTIATE_STEP(1)

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libdg (include/dg.h): argument marshalling only.
+
+Every step of the method runs in the CUDA kernels of libdg.  If the library is
+not built this module raises on use; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB_PATH
+
+STATUS = {
+    0: "DG_OK", 1: "DG_E_ARG", 2: "DG_E_MESH", 3: "DG_E_ORDER", 4: "DG_E_OOM", 5: "DG_E_CUDA",
+    6: "DG_E_STATE", 7: "DG_E_NONFINITE", 8: "DG_E_NONHYPERBOLIC", 9: "DG_E_OUTSIDE",
+    10: "DG_E_UNSUPPORTED",
+}
+
+# every entry point declared in include/dg.h
+EXPORTS = (
+    "dg_mesh_create", "dg_set_material", "dg_set_source", "dg_set_state", "dg_set_state_f32",
+    "dg_set_state_device", "dg_get_state", "dg_get_state_f32", "dg_get_state_device", "dg_step",
+    "dg_receivers", "dg_receivers_read", "dg_dt", "dg_time", "dg_n_modes", "dg_get_stats",
+    "dg_profile_enable", "dg_profile_read", "dg_reference_table", "dg_last_error", "dg_destroy",
+)
+
+
+class DGError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{self.name}: {message}")
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("n_elem", C.c_int64), ("elem_xyz", C.POINTER(C.c_double)),
+                ("elem_vid", C.POINTER(C.c_int64)), ("face_bc", C.POINTER(C.c_int8)),
+                ("order", C.c_int), ("members", C.c_int), ("cfl", C.c_double),
+                ("cuda_stream", C.c_void_p), ("alloc", C.POINTER(Allocator))]
+
+
+class PointSource(C.Structure):
+    _fields_ = [("x", C.c_double * 3), ("m", C.c_double * 6), ("stf", C.c_int),
+                ("f0_or_sigma", C.c_double), ("t0", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("kernel_launches", C.c_int64), ("element_updates", C.c_int64)]
+
+
+class KernelTime(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
+_LIB = None
+
+
+def load_library(path: str | None = None) -> C.CDLL:
+    """Load libdg.so (built in-tree by paper_2502_09714_gb300.build.build())."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libdg is not built ({p} missing); run paper_2502_09714_gb300.build.build()")
+    lib = C.CDLL(p)
+    vp, i64, dbl = C.c_void_p, C.c_int64, C.c_double
+    sig = {
+        "dg_mesh_create": ([C.POINTER(MeshDesc), C.POINTER(vp)], C.c_int),
+        "dg_set_material": ([vp, C.POINTER(dbl), C.POINTER(dbl)], C.c_int),
+        "dg_set_source": ([vp, C.POINTER(PointSource), i64], C.c_int),
+        "dg_set_state": ([vp, C.POINTER(dbl), dbl], C.c_int),
+        "dg_set_state_f32": ([vp, C.POINTER(C.c_float), dbl], C.c_int),
+        "dg_set_state_device": ([vp, vp, dbl], C.c_int),
+        "dg_get_state": ([vp, C.POINTER(dbl), C.POINTER(dbl)], C.c_int),
+        "dg_get_state_f32": ([vp, C.POINTER(C.c_float), C.POINTER(dbl)], C.c_int),
+        "dg_get_state_device": ([vp, vp, C.POINTER(dbl)], C.c_int),
+        "dg_step": ([vp, i64, dbl], C.c_int),
+        "dg_receivers": ([vp, C.POINTER(dbl), i64], C.c_int),
+        "dg_receivers_read": ([vp, C.POINTER(C.c_float), i64, C.POINTER(i64)], C.c_int),
+        "dg_dt": ([vp], dbl),
+        "dg_time": ([vp], dbl),
+        "dg_n_modes": ([C.c_int], i64),
+        "dg_get_stats": ([vp, C.POINTER(Stats)], C.c_int),
+        "dg_profile_enable": ([vp, C.c_int], C.c_int),
+        "dg_profile_read": ([vp, C.POINTER(KernelTime), C.c_int, C.POINTER(C.c_int)], C.c_int),
+        "dg_reference_table": ([C.c_int, C.c_int, C.POINTER(dbl), i64, C.POINTER(i64)], C.c_int),
+        "dg_last_error": ([vp], C.c_char_p),
+        "dg_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def n_modes(order: int) -> int:
+    return (order + 1) * (order + 2) * (order + 3) // 6
+
+
+def reference_table(order: int, which: int) -> np.ndarray:
+    lib = load_library()
+    count = C.c_int64(0)
+    _check(lib, None, lib.dg_reference_table(order, which, None, 0, C.byref(count)))
+    out = np.empty(count.value)
+    _check(lib, None, lib.dg_reference_table(order, which, _ptr(out, C.c_double), out.size, C.byref(count)))
+    return out
+
+
+def _check(lib, ctx, status):
+    if status != 0:
+        msg = lib.dg_last_error(ctx)
+        raise DGError(status, msg.decode() if msg else "")
+
+
+def torch_allocator():
+    """An Allocator that draws device memory from torch's caching allocator."""
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      stream or torch.cuda.current_stream().cuda_stream)
+        except RuntimeError:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = Allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+    a._keep = (_alloc, _free)
+    return a
+
+
+class Solver:
+    """One libdg context: a mesh, its material, state, sources and receivers."""
+
+    def __init__(self, elem_xyz, elem_vid, order, face_bc=None, cfl=0.5, stream=None,
+                 allocator=None, members=1):
+        self.lib = load_library()
+        xyz = np.ascontiguousarray(elem_xyz, dtype=np.float64)
+        vid = np.ascontiguousarray(elem_vid, dtype=np.int64)
+        self.E = int(xyz.shape[0])
+        self.order = int(order)
+        self.L = n_modes(self.order)
+        bc = None if face_bc is None else np.ascontiguousarray(face_bc, dtype=np.int8)
+        if stream is None:
+            stream_ptr = None
+        elif isinstance(stream, int):
+            stream_ptr = stream
+        else:
+            stream_ptr = stream.cuda_stream
+        self._allocator = allocator
+        desc = MeshDesc(self.E, _ptr(xyz, C.c_double), _ptr(vid, C.c_int64),
+                        _ptr(bc, C.c_int8) if bc is not None else None, self.order, members,
+                        float(cfl), stream_ptr, C.pointer(allocator) if allocator is not None else None)
+        self.ctx = C.c_void_p()
+        _check(self.lib, None, self.lib.dg_mesh_create(C.byref(desc), C.byref(self.ctx)))
+
+    # ------------------------------------------------------------------
+    def _chk(self, status):
+        _check(self.lib, self.ctx, status)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.dg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------
+    def set_material(self, mat):
+        m = np.ascontiguousarray(mat, dtype=np.float64).reshape(self.E, 6)
+        self._chk(self.lib.dg_set_material(self.ctx, _ptr(m, C.c_double), None))
+
+    def set_sources(self, sources):
+        arr = (PointSource * max(1, len(sources)))()
+        for i, s in enumerate(sources):
+            arr[i].x[:] = [float(v) for v in s["x"]]
+            arr[i].m[:] = [float(v) for v in s["m"]]
+            arr[i].stf = int(s.get("stf", 0))
+            arr[i].f0_or_sigma = float(s.get("f0", s.get("sigma", 1.0)))
+            arr[i].t0 = float(s.get("t0", 0.0))
+        self._chk(self.lib.dg_set_source(self.ctx, arr, len(sources)))
+
+    def set_state(self, q, t=0.0):
+        """q: [E,10,L] host array (float64 or float32) or a CUDA float32 torch tensor."""
+        if hasattr(q, "is_cuda") and q.is_cuda:
+            assert q.dtype.__str__() == "torch.float32" and q.is_contiguous()
+            assert tuple(q.shape) == (self.E, 10, self.L)
+            self._chk(self.lib.dg_set_state_device(self.ctx, C.c_void_p(q.data_ptr()), float(t)))
+            return
+        if hasattr(q, "numpy"):
+            q = q.numpy()
+        if q.dtype == np.float32:
+            a = np.ascontiguousarray(q).reshape(self.E, 10, self.L)
+            self._chk(self.lib.dg_set_state_f32(self.ctx, _ptr(a, C.c_float), float(t)))
+        else:
+            a = np.ascontiguousarray(q, dtype=np.float64).reshape(self.E, 10, self.L)
+            self._chk(self.lib.dg_set_state(self.ctx, _ptr(a, C.c_double), float(t)))
+
+    def get_state(self, dtype=np.float64, out=None):
+        """Returns (q [E,10,L], t).  `out` may be a host array of matching dtype or
+        a CUDA float32 torch tensor."""
+        t = C.c_double(0.0)
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            self._chk(self.lib.dg_get_state_device(self.ctx, C.c_void_p(out.data_ptr()), C.byref(t)))
+            return out, t.value
+        if out is None:
+            out = np.empty((self.E, 10, self.L), dtype=dtype)
+        a = out.numpy() if hasattr(out, "numpy") else out
+        if a.dtype == np.float32:
+            self._chk(self.lib.dg_get_state_f32(self.ctx, _ptr(a, C.c_float), C.byref(t)))
+        else:
+            self._chk(self.lib.dg_get_state(self.ctx, _ptr(a, C.c_double), C.byref(t)))
+        return out, t.value
+
+    def step(self, n_steps=1, dt=0.0):
+        self._chk(self.lib.dg_step(self.ctx, int(n_steps), float(dt)))
+
+    def set_receivers(self, xyz):
+        x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        self.R = x.shape[0]
+        self._chk(self.lib.dg_receivers(self.ctx, _ptr(x, C.c_double), x.shape[0]))
+
+    def read_receivers(self):
+        n = C.c_int64(0)
+        self._chk(self.lib.dg_receivers_read(self.ctx, None, 0, C.byref(n)))
+        out = np.empty((n.value, self.R, 3), dtype=np.float32)
+        if n.value:
+            self._chk(self.lib.dg_receivers_read(self.ctx, _ptr(out, C.c_float), n.value, C.byref(n)))
+        return out
+
+    @property
+    def dt(self):
+        return self.lib.dg_dt(self.ctx)
+
+    @property
+    def time(self):
+        return self.lib.dg_time(self.ctx)
+
+    def stats(self):
+        s = Stats()
+        self._chk(self.lib.dg_get_stats(self.ctx, C.byref(s)))
+        return {"steps": s.steps, "kernel_launches": s.kernel_launches, "element_updates": s.element_updates}
+
+    def profile(self, on=True):
+        self._chk(self.lib.dg_profile_enable(self.ctx, int(on)))
+
+    def profile_read(self):
+        out = (KernelTime * 4)()
+        n = C.c_int(0)
+        self._chk(self.lib.dg_profile_read(self.ctx, out, 4, C.byref(n)))
+        names = ("predictor", "corrector", "source", "receivers")
+        return {names[k]: {"launches": out[k].launches, "total_ms": out[k].total_ms} for k in range(n.value)}

@@ -1,0 +1,70 @@
+"""Helpers shared by the GPU parity tests: run the same seeded workload
+through libdg (C-ABI) and through the FP64 oracle, and compare."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from oracle import Oracle, eval_basis, from_abi, tet_rule, to_abi
+
+# spec tolerances: relative L2 per field group, absolute on damage
+TOL_REL_L2 = 1e-4
+TOL_ALPHA = 1e-5
+GROUPS = {"strain": slice(0, 6), "velocity": slice(6, 9)}
+
+
+def make_solver(mesh, material, order, cfl=0.5, sources=(), receivers=None, stream=None):
+    import paper_2502_09714_gb300 as dgpkg
+    s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, order, cfl=cfl, stream=stream)
+    s.set_material(material)
+    if sources:
+        s.set_sources(list(sources))
+    if receivers is not None:
+        s.set_receivers(receivers)
+    return s
+
+
+def make_oracle(mesh, material, order, cfl=0.5, sources=(), receivers=None, face_rows=None):
+    o = Oracle(mesh.elem_xyz, mesh.elem_vid, order, material, cfl=cfl, face_rows=face_rows)
+    if sources:
+        o.set_sources(list(sources))
+    if receivers is not None:
+        o.set_receivers(receivers)
+    return o
+
+
+def rel_l2(q_gpu_abi, Q_ora, detJ, rows=None):
+    """Relative L2 (modal coefficients weighted by |J|, orthonormal basis) per
+    field group; q_gpu_abi in the ABI layout [E,10,L], Q_ora in [E,L,10]."""
+    G = from_abi(q_gpu_abi)
+    if rows is not None:
+        G, Q_ora, detJ = G[rows], Q_ora[rows] if Q_ora.shape[0] != len(rows) else Q_ora, detJ[rows]
+    w = detJ[:, None, None]
+    out = {}
+    for name, sl in GROUPS.items():
+        num = np.sum(w * (G[..., sl] - Q_ora[..., sl]) ** 2)
+        den = np.sum(w * Q_ora[..., sl] ** 2)
+        out[name] = math.sqrt(num / den) if den > 0 else math.sqrt(num)
+    return out
+
+
+def alpha_max_diff(q_gpu_abi, Q_ora, order):
+    """max over elements and volume nodes of |alpha_gpu - alpha_oracle|."""
+    pts, _ = tet_rule(order + 1)
+    V = eval_basis(order, pts)
+    G = from_abi(q_gpu_abi)
+    return float(np.max(np.abs(np.einsum("ql,el->eq", V, G[..., 9] - Q_ora[..., 9]))))
+
+
+def assert_parity(q_gpu_abi, Q_ora, detJ, order, rel=TOL_REL_L2, alpha=TOL_ALPHA):
+    errs = rel_l2(q_gpu_abi, Q_ora, detJ)
+    da = alpha_max_diff(q_gpu_abi, Q_ora, order)
+    for name, e in errs.items():
+        assert e <= rel, f"{name} rel L2 {e:.3e} > {rel:.1e}"
+    assert da <= alpha, f"alpha max diff {da:.3e} > {alpha:.1e}"
+    return errs, da
+
+
+__all__ = ["make_solver", "make_oracle", "rel_l2", "alpha_max_diff", "assert_parity", "to_abi",
+           "from_abi", "TOL_REL_L2", "TOL_ALPHA"]
