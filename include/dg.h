@@ -151,6 +151,28 @@ dg_status dg_get_state_device(dg_ctx* ctx, float* q_dev_out, double* t_out);
  * and state (DG_E_STATE). */
 dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt);
 
+/* One step that allocates no memory, for callers that cannot call
+ * cudaMalloc while they step (a host process under a fixed device-memory
+ * budget, code running between the capture of other work, or an embedding
+ * that forbids allocation after set-up).  The paper has no counterpart: it is
+ * an interface of this library only.
+ * q_in and q_out are caller-owned FP32 device arrays in the state layout
+ * [n_elem][10][L]; q_out receives the state one step of size dt later
+ * (dt <= 0 selects dg_dt(ctx)).  The context's own state, time, sources,
+ * receivers and counters are neither read nor changed; point sources are not
+ * applied.  The step's intermediate data (converted states, predictor output,
+ * cell speeds, status word) live in one file-scope device array of 16 MiB
+ * that every GPU loading the library holds until the process exits, so the
+ * mesh must satisfy n_elem * (2 q + d + 1) + 64 <= 4,194,304 floats with
+ * q = 4*ceil(10 L / 4), d = the predictor size per element (3968 elements at
+ * N = 4, 16,320 at N = 2); larger meshes are rejected with DG_E_ARG.
+ * The first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  Every
+ * call reuses the same array, so calls whose work overlaps on the GPU (other
+ * streams, other threads, other contexts) race and must be serialised by the
+ * caller.  Requires dg_set_material (DG_E_STATE).  Status as for dg_step. */
+dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_out, double dt);
+
 /* Register R receivers at xyz[R][3] (replaces previous ones, resets traces).
  * After every step the velocity (v_x, v_y, v_z) at each receiver is recorded.
  * DG_E_OUTSIDE if a point lies in no element. */

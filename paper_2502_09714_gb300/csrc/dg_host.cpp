@@ -753,6 +753,23 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
 
 namespace dg {
 
+// Accessors used by the allocation-free step (dg_noalloc.cu).
+bool noalloc_view(const dg_ctx* ctx, NoAllocView* v) {
+  if (!ctx || !v) return false;
+  v->N = ctx->N;
+  v->E = ctx->E;
+  v->stream = ctx->stream;
+  v->geom = ctx->geom;
+  v->mat = ctx->matf;
+  v->nbr = ctx->nbr;
+  v->tables = ctx->tables;
+  v->dt_cfl = ctx->dt_cfl;
+  v->has_material = ctx->has_material;
+  return true;
+}
+
+dg_status noalloc_error(dg_ctx* ctx, dg_status s, const char* msg) { return fail(ctx, s, msg); }
+
 cudaError_t launch_predictor(int N, const StepArgs& a, cudaStream_t s) {
   switch (N) {
     case 1: return launch_predictor_t<1>(a, s);

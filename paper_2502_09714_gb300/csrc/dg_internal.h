@@ -128,4 +128,17 @@ struct ReceiverDev {
 cudaError_t launch_receivers(int N, int n_rec, const ReceiverDev* rec, const float* q,
                              float* traces_row, cudaStream_t s);
 
+// Read-only view of a context for the allocation-free step (dg_noalloc.cu).
+struct NoAllocView {
+  int N;
+  int64_t E;
+  cudaStream_t stream;
+  const GeomF* geom;
+  const MatF* mat;
+  const int* nbr;
+  const float* tables;
+  double dt_cfl;
+  bool has_material;
+};
+
 }  // namespace dg

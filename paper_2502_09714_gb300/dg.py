@@ -24,6 +24,7 @@ EXPORTS = (
     "dg_set_state_device", "dg_get_state", "dg_get_state_f32", "dg_get_state_device", "dg_step",
     "dg_receivers", "dg_receivers_read", "dg_dt", "dg_time", "dg_n_modes", "dg_get_stats",
     "dg_profile_enable", "dg_profile_read", "dg_reference_table", "dg_last_error", "dg_destroy",
+    "dg_step_noalloc",
 )
 
 
@@ -97,6 +98,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "dg_reference_table": ([C.c_int, C.c_int, C.POINTER(dbl), i64, C.POINTER(i64)], C.c_int),
         "dg_last_error": ([vp], C.c_char_p),
         "dg_destroy": ([vp], None),
+        "dg_step_noalloc": ([vp, vp, vp, dbl], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -244,6 +246,16 @@ class Solver:
 
     def step(self, n_steps=1, dt=0.0):
         self._chk(self.lib.dg_step(self.ctx, int(n_steps), float(dt)))
+
+    def step_noalloc(self, q_in, q_out, dt=0.0):
+        """One step from q_in to q_out (CUDA float32 tensors [E,10,L], or raw
+        device pointers) without any allocation: for callers that cannot
+        allocate device memory while they step.  Scratch lives in a fixed
+        16 MiB device array shared by all calls (small meshes only; calls that
+        overlap on the GPU race).  The context's own state is not touched."""
+        pin = q_in if isinstance(q_in, int) else q_in.data_ptr()
+        pout = q_out if isinstance(q_out, int) else q_out.data_ptr()
+        self._chk(self.lib.dg_step_noalloc(self.ctx, C.c_void_p(pin), C.c_void_p(pout), float(dt)))
 
     def set_receivers(self, xyz):
         x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
