@@ -39,28 +39,26 @@ def n_modes(N):
 
 
 def algorithmic_flops(N):
-    """FLOPs per element update of the method as this library formulates it
-    (FMA = 2): Taylor terms restricted to their nonzero modes (degree <= N-i),
-    volume quadrature (N+1)^3 x (N+1) time nodes, face quadrature (N+1)^2 x (N+1)
-    per face and side.  Returns (predictor, corrector)."""
+    """FLOPs per element update of each kernel of the method as this library
+    formulates it (FMA = 2 flops): Taylor terms on their nonzero modes (degree
+    <= N-i), (N+1)^3 volume nodes, (N+1)^2 face nodes and N+1 time nodes, each
+    interior face's flux once (a closed mesh has 2 faces per element).
+    Returns {"predictor", "faces", "corrector"}."""
     L, NQ, NF, NT = n_modes(N), (N + 1) ** 3, (N + 1) ** 2, N + 1
     LR = [n_modes(N - i) for i in range(N + 1)]
-    sum_hi = sum(LR[1:])
-    # predictor: CK recursion (3 reference derivatives of 9 fields), physical
-    # gradients and star products, damage rate at the volume nodes and projection
-    ck = sum(2 * 27 * LR[i] * LR[i - 1] + 2 * 81 * LR[i] + 30 * LR[i] for i in range(1, N + 1))
-    src = 2 * 6 * NQ * L + 20 * NQ + 2 * NQ * L
-    pred = ck + src
-    # corrector
-    vol_eval = 2 * NQ * (8 * L + 6 * sum_hi) + 2 * NQ * NT * (6 * N + 1)
-    point = NQ * NT * 50 + NQ * 63
-    vol_proj = 2 * L * NQ * 10
-    strain = 2 * L * (9 * L + 27) + 2 * 3 * (L + sum_hi)
-    face_tr = 4 * NF * 2 * 2 * (11 * L + 9 * sum_hi) + 4 * NF * NT * 2 * 2 * (9 * N + 1)
-    llf = 4 * NF * NT * 165
-    face_proj = 4 * 2 * L * NF * 9
-    corr = vol_eval + point + vol_proj + strain + face_tr + llf + face_proj + 2 * 10 * L
-    return pred, corr
+    SH = sum(LR[1:])
+    pred = (2 * 6 * NQ * L + 20 * NQ + 2 * NQ * L                       # damage rate at t_n, projection
+            + sum(2 * 27 * LR[i] * LR[i - 1] + 192 * LR[i] for i in range(1, N + 1)))   # CK
+    per_face = (2 * NF * 2 * (11 * L + 9 * SH)                          # traces, both sides, all orders
+                + 2 * NF * NT * (18 * N + 2)                            # Taylor sums at the time nodes
+                + NF * NT * 165)                                        # two normal fluxes + Rusanov
+    faces = 2 * per_face
+    corr = (2 * NQ * (8 * L + 6 * SH) + 2 * NQ * NT * (6 * N + 1)       # strains, damage at the nodes
+            + NQ * NT * 50 + NQ * 63                                    # CDM stress/rate, stress terms
+            + 20 * L * NQ                                               # volume and source projections
+            + 18 * L * L + 63 * L + 6 * (L + SH)                        # strain rows (modal)
+            + 2 * L * 4 * NF * 9 + 10 * L)                              # face projection, update
+    return {"predictor": pred, "faces": faces, "corrector": corr}
 
 
 def algorithmic_bytes(N):
@@ -281,31 +279,31 @@ def main():
     peaks, peak_kind = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12    # TFLOP/s
-    fp, fc = algorithmic_flops(N)
-    corr = prof["corrector"]
-    corr_ms = corr["total_ms"] / max(1, corr["launches"])
-    pred = prof["predictor"]
-    pred_ms = pred["total_ms"] / max(1, pred["launches"])
-    achieved = fc * E / (corr_ms * 1e-3) / 1e12
-    traffic = _traffic_per_launch(N, E)
+    flops = algorithmic_flops(N)
+    kavg = {k: v["total_ms"] / max(1, v["launches"]) for k, v in prof.items()}
+    dom = max(("predictor", "faces", "corrector"), key=lambda k: prof[k]["total_ms"])
+    dom_ms = kavg[dom]
+    achieved = flops[dom] * E / (dom_ms * 1e-3) / 1e12
+    traffic = _traffic_per_launch(dom, N, E)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config(w, args),
-        "roofline": {"kernel": "k_corrector<4>", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": f"k_{dom}<{N}>", "bound": "alu", "achieved": achieved,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
                      "traffic": traffic,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (max clock, {peak_kind} peaks file)",
-                     "flops_per_element": fc, "avg_ms": corr_ms},
-        "kernels": {k: {"launches": v["launches"], "avg_ms": v["total_ms"] / max(1, v["launches"])}
+                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (recipe unit counts, max clock)",
+                     "flops_per_element": flops[dom], "avg_ms": dom_ms},
+        "kernels": {k: {"launches": v["launches"], "avg_ms": kavg[k],
+                        "tflops": (flops[k] * E / (kavg[k] * 1e-3) / 1e12) if k in flops and kavg[k] > 0 else None}
                     for k, v in prof.items()},
         "hbm": {"algorithmic_bytes_per_element": algorithmic_bytes(N),
                 "achieved_gbs": algorithmic_bytes(N) * value / world / 1e9,
                 "peak_gbs": peaks.get("hbm_gbs"),
                 "frac": algorithmic_bytes(N) * value / world / 1e9 / float(peaks.get("hbm_gbs", 6800.0))},
-        "step_flops": {"predictor": fp, "corrector": fc,
-                       "achieved_tflops": (fp + fc) * value / world / 1e12},
+        "step_flops": dict(flops, per_element_total=sum(flops.values()),
+                           achieved_tflops=sum(flops.values()) * value / world / 1e12),
         "gpu_launches": launches,
         "clocks": clocks.summary(),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hq.numel() * 4),
@@ -321,17 +319,26 @@ def main():
     return 0
 
 
-def _traffic_per_launch(N, E):
-    """DRAM bytes per corrector launch from the committed ncu summary, scaled to
-    E elements, or None when no capture of the current kernel exists."""
-    p = os.path.join(ROOT, "profiles", "corrector_traffic.json")
+def _kernel_source_digest():
+    import hashlib
+    p = os.path.join(ROOT, "paper_2502_09714_gb300", "csrc", "dg_step_kernels.cuh")
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic_per_launch(kernel, N, E):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
+    to E elements; None when no capture exists or the kernel source changed
+    since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("order") != N:
+    if d.get("order") != N or d.get("kernel_source_sha256_16") != _kernel_source_digest():
         return None
-    return d["dram_bytes_per_element"] * E
+    per = d.get("dram_bytes_per_element", {}).get(kernel)
+    return None if per is None else per * E
 
 
 if __name__ == "__main__":

@@ -161,11 +161,13 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt);
  * (dt <= 0 selects dg_dt(ctx)).  The context's own state, time, sources,
  * receivers and counters are neither read nor changed; point sources are not
  * applied.  The step's intermediate data (converted states, predictor output,
- * cell speeds, status word) live in one file-scope device array of 16 MiB
- * that every GPU loading the library holds until the process exits, so the
- * mesh must satisfy n_elem * (2 q + d + 1) + 64 <= 4,194,304 floats with
- * q = 4*ceil(10 L / 4), d = the predictor size per element (3968 elements at
- * N = 4, 16,320 at N = 2); larger meshes are rejected with DG_E_ARG.
+ * cell speeds, face fluxes, status word) live in one file-scope device array of
+ * 16 MiB that every GPU loading the library holds until the process exits, so
+ * the mesh must satisfy n_elem*(2q + d) + 4*ceil(n_elem/4) + n_faces*f + 64
+ * <= 4,194,304 floats with q = 4*ceil(10 L / 4), d the predictor size per
+ * element and f = 4*ceil(9 (N+1)^2 / 4) (a closed mesh has n_faces = 2 n_elem:
+ * 2,772 elements at N = 4, 9,868 at N = 2); larger meshes are rejected with
+ * DG_E_ARG.
  * The first call on a device looks up that array's device address (with the
  * device current); make that first call before any stream capture.  Every
  * call reuses the same array, so calls whose work overlaps on the GPU (other
@@ -199,7 +201,8 @@ dg_status dg_get_stats(const dg_ctx* ctx, dg_stats* out);
 /* Per-kernel timing: when enabled, dg_step records CUDA events around each
  * kernel on the context's stream; dg_profile_read returns, per kernel kind,
  * the number of launches and the summed device milliseconds since the last
- * enable.  Kinds: 0 predictor, 1 corrector, 2 point source, 3 receivers. */
+ * enable.  Kinds: 0 predictor, 1 corrector (volume terms, face projection and
+ * update), 2 point source, 3 receivers, 4 face fluxes. */
 typedef struct {
   int64_t launches;
   double total_ms;

@@ -62,6 +62,11 @@ struct dg_ctx {
   int cur = 0;
   float* d = nullptr;
   float* cp = nullptr;
+  float* ff = nullptr;               // face fluxes
+  int4* faces = nullptr;
+  int* elem_face = nullptr;
+  int64_t F = 0;
+  int grid_pred = 0, grid_face = 0, grid_corr = 0;
   GeomF* geom = nullptr;
   MatF* matf = nullptr;
   int* nbr = nullptr;
@@ -90,7 +95,7 @@ struct dg_ctx {
   bool profiling = false;
   std::vector<cudaEvent_t> events;
   std::vector<int> event_kind;
-  dg_kernel_time prof[4]{};
+  dg_kernel_time prof[5]{};
 
   std::vector<std::pair<void*, size_t>> owned;
 };
@@ -150,25 +155,47 @@ void inv3(const double* J, double* out, double* det) {
   out[6] = C / D; out[7] = -(a * h - b * g) / D; out[8] = (a * e - b * d) / D;
 }
 
+// Round an FP32 value to the nearest TF32 value (10 mantissa bits), ties away
+// from zero, as the tensor cores' conversion does.
+float tf32_round(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7F800000u) != 0x7F800000u) {
+    u += 0x1000u;
+    u &= 0xFFFFE000u;
+  }
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
 // Reference tables of degree N (FP64), in the layout of table_layout(N).
 std::vector<double> build_tables(int N) {
   const int L = n_modes(N), NQ = n_vol_nodes(N), NF = n_face_nodes(N), NT = N + 1;
+  const int LP = lp_of(N), NQP = nqp_of(N), NFP = nfp_of(N);
   const TableLayout T = table_layout(N);
   std::vector<double> t(T.total, 0.0);
   ref::Rule3 vr = ref::volume_rule(N + 1);
   std::vector<double> val(L), grd(3 * L);
+  std::vector<double> Kt(3 * L * L, 0.0);   // Kt[e][k][l] = int phi_k d phi_l / d xi_e
   for (int q = 0; q < NQ; ++q) {
     ref::dubiner(N, vr.xi[q], vr.eta[q], vr.zeta[q], val.data(), grd.data());
     for (int l = 0; l < L; ++l) {
-      t[T.Vv + q * L + l] = val[l];
-      t[T.Vw + q * L + l] = vr.w[q] * val[l];
-      for (int e = 0; e < 3; ++e) t[T.Gw + (e * NQ + q) * L + l] = vr.w[q] * grd[3 * l + e];
+      t[T.VvT + l * NQP + q] = val[l];
+      t[T.Vw + q * LP + l] = vr.w[q] * val[l];
+      for (int e = 0; e < 3; ++e) t[T.Gw + (e * NQ + q) * LP + l] = vr.w[q] * grd[3 * l + e];
     }
-    // Kt[e][k][l] = int phi_k d phi_l / d xi_e (the rule is exact for degree 2N-1)
+    // the rule is exact for the degree 2N-1 integrands of Kt
     for (int e = 0; e < 3; ++e)
       for (int k = 0; k < L; ++k)
-        for (int l = 0; l < L; ++l) t[T.Kt + (e * L + k) * L + l] += vr.w[q] * val[k] * grd[3 * l + e];
+        for (int l = 0; l < L; ++l) Kt[(e * L + k) * L + l] += vr.w[q] * val[k] * grd[3 * l + e];
   }
+  for (int e = 0; e < 3; ++e)
+    for (int k = 0; k < L; ++k)
+      for (int l = 0; l < L; ++l) {
+        t[T.KtA + (e * L + l) * LP + k] = Kt[(e * L + k) * L + l];
+        t[T.KtB + (e * L + k) * LP + l] = Kt[(e * L + k) * L + l];
+      }
   ref::Rule2 fr = ref::face_rule(N + 1);
   const double R[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
   for (int f = 0; f < 4; ++f) {
@@ -180,10 +207,20 @@ std::vector<double> build_tables(int N) {
         p[c] = R[v[0]][c] + fr.s[i] * (R[v[1]][c] - R[v[0]][c]) + fr.t[i] * (R[v[2]][c] - R[v[0]][c]);
       ref::dubiner(N, p[0], p[1], p[2], val.data(), nullptr);
       for (int l = 0; l < L; ++l) {
-        t[T.Vf + (f * NF + i) * L + l] = val[l];
-        t[T.Vfw + (f * NF + i) * L + l] = fr.w[i] * val[l];
+        t[T.VfT + (f * L + l) * NFP + i] = val[l];
+        t[T.Vfw + (f * NF + i) * LP + l] = fr.w[i] * val[l];
       }
     }
+  }
+  if (tc_volume(N)) {
+    const int KP = tc_kp(N);
+    for (int q = 0; q < NQ; ++q)
+      for (int l = 0; l < L; ++l) {
+        const float x = static_cast<float>(t[T.VvT + l * NQP + q]);
+        const float h = tf32_round(x);
+        t[T.PhiH + tc_canon(q, l, KP)] = h;
+        t[T.PhiL + tc_canon(q, l, KP)] = x - h;
+      }
   }
   ref::Rule1 tr = ref::time_rule(NT);
   for (int z = 0; z < NT; ++z) {
@@ -398,6 +435,21 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
       }
   }
 
+  // face list: each interior face once, first seen from its lower-index element
+  std::vector<int4> faces;
+  std::vector<int> elem_face(4 * E, -1);
+  faces.reserve(static_cast<size_t>(2 * E));
+  for (int64_t e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f) {
+      if (elem_face[4 * e + f] >= 0) continue;
+      const int other = nbr[4 * e + f];
+      const int64_t fid = static_cast<int64_t>(faces.size());
+      faces.push_back(make_int4(static_cast<int>(e), f, other >> 2, other & 3));
+      elem_face[4 * e + f] = static_cast<int>(fid << 1);
+      elem_face[other] = static_cast<int>((fid << 1) | 1);
+    }
+  ctx->F = static_cast<int64_t>(faces.size());
+
   // device allocation and upload
   const int N = ctx->N, L = ctx->L;
   const size_t qs = static_cast<size_t>(q_stride(N)), ds = static_cast<size_t>(d_stride(N));
@@ -405,13 +457,17 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
   ctx->q[1] = static_cast<float*>(dev_alloc(ctx, sizeof(float) * qs * E));
   ctx->d = static_cast<float*>(dev_alloc(ctx, sizeof(float) * ds * E));
   ctx->cp = static_cast<float*>(dev_alloc(ctx, sizeof(float) * E));
+  ctx->ff = static_cast<float*>(dev_alloc(ctx, sizeof(float) * ff_stride(N) * ctx->F));
+  ctx->faces = static_cast<int4*>(dev_alloc(ctx, sizeof(int4) * ctx->F));
+  ctx->elem_face = static_cast<int*>(dev_alloc(ctx, sizeof(int) * 4 * E));
   ctx->geom = static_cast<GeomF*>(dev_alloc(ctx, sizeof(GeomF) * E));
   ctx->matf = static_cast<MatF*>(dev_alloc(ctx, sizeof(MatF) * E));
   ctx->nbr = static_cast<int*>(dev_alloc(ctx, sizeof(int) * 4 * E));
   const TableLayout TL = table_layout(N);
   ctx->tables = static_cast<float*>(dev_alloc(ctx, sizeof(float) * TL.total));
   ctx->status = static_cast<unsigned*>(dev_alloc(ctx, sizeof(unsigned)));
-  if (!ctx->q[0] || !ctx->q[1] || !ctx->d || !ctx->cp || !ctx->geom || !ctx->matf || !ctx->nbr ||
+  if (!ctx->q[0] || !ctx->q[1] || !ctx->d || !ctx->cp || !ctx->ff || !ctx->faces || !ctx->elem_face ||
+      !ctx->geom || !ctx->matf || !ctx->nbr ||
       !ctx->tables || !ctx->status) {
     dg_destroy(ctx);
     return fail(nullptr, DG_E_OOM, "device allocation failed");
@@ -429,6 +485,8 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
   dg_status st;
   if ((st = upload(ctx, ctx->geom, geom.data(), sizeof(GeomF) * E)) != DG_OK ||
       (st = upload(ctx, ctx->nbr, nbr.data(), sizeof(int) * 4 * E)) != DG_OK ||
+      (st = upload(ctx, ctx->faces, faces.data(), sizeof(int4) * ctx->F)) != DG_OK ||
+      (st = upload(ctx, ctx->elem_face, elem_face.data(), sizeof(int) * 4 * E)) != DG_OK ||
       (st = upload(ctx, ctx->tables, tf.data(), sizeof(float) * tf.size())) != DG_OK) {
     std::string m = ctx->err;
     dg_destroy(ctx);
@@ -441,6 +499,14 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
       (ce = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
     dg_destroy(ctx);
     return fail(nullptr, DG_E_CUDA, std::string("initialising device memory: ") + cudaGetErrorString(ce));
+  }
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) {
+      ctx->grid_pred = ctx->grid_face = ctx->grid_corr = sms;
+    }
+    cudaGetLastError();
   }
   *out = ctx;
   return DG_OK;
@@ -610,8 +676,8 @@ dg_status dg_profile_enable(dg_ctx* ctx, int on) {
 
 dg_status dg_profile_read(dg_ctx* ctx, dg_kernel_time* out, int cap, int* n_kinds) {
   if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
-  if (n_kinds) *n_kinds = 4;
-  for (int k = 0; k < std::min(cap, 4); ++k) out[k] = ctx->prof[k];
+  if (n_kinds) *n_kinds = 5;
+  for (int k = 0; k < std::min(cap, 5); ++k) out[k] = ctx->prof[k];
   return DG_OK;
 }
 
@@ -673,7 +739,7 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
   }
   DG_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream));
   // events for per-kernel timing
-  const int per_step = 2 + (nsrc > 0) + (R > 0);
+  const int per_step = 3 + (nsrc > 0) + (R > 0);
   if (ctx->profiling) {
     const size_t need = static_cast<size_t>(n_steps * per_step + 1);
     while (ctx->events.size() < need) {
@@ -691,8 +757,15 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
   };
   StepArgs a{};
   a.E = ctx->E;
+  a.F = ctx->F;
   a.d = ctx->d;
   a.cp = ctx->cp;
+  a.ff = ctx->ff;
+  a.faces = ctx->faces;
+  a.elem_face = ctx->elem_face;
+  a.grid_pred = ctx->grid_pred;
+  a.grid_face = ctx->grid_face;
+  a.grid_corr = ctx->grid_corr;
   a.geom = ctx->geom;
   a.mat = ctx->matf;
   a.nbr = ctx->nbr;
@@ -705,11 +778,12 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
     a.q_in = ctx->q[ctx->cur];
     a.q_out = ctx->q[1 - ctx->cur];
     DG_CUDA(ctx, launch_predictor(ctx->N, a, ctx->stream));
-    if (ctx->profiling) ctx->event_kind[ev] = 0;
     DG_CUDA(ctx, mark(0));
+    DG_CUDA(ctx, launch_faces(ctx->N, a, ctx->stream));
+    DG_CUDA(ctx, mark(4));
     DG_CUDA(ctx, launch_corrector(ctx->N, a, ctx->stream));
     DG_CUDA(ctx, mark(1));
-    launches += 2;
+    launches += 3;
     ctx->cur = 1 - ctx->cur;
     if (nsrc > 0) {
       DG_CUDA(ctx, launch_sources(ctx->N, nsrc, ctx->source_dev, ctx->amp_dev, s, ctx->q[ctx->cur], ctx->stream));
@@ -736,7 +810,7 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
       float ms = 0.f;
       DG_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->events[i - 1], ctx->events[i]));
       const int k = ctx->event_kind[i];
-      if (k >= 0 && k < 4) {
+      if (k >= 0 && k < 5) {
         ctx->prof[k].launches += 1;
         ctx->prof[k].total_ms += ms;
       }
@@ -746,6 +820,7 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
   if (st & kStatusNonFinite) return fail(ctx, DG_E_NONFINITE, "non-finite value in the state");
   if (st & kStatusNonHyperbolic) return fail(ctx, DG_E_NONHYPERBOLIC, "effective moduli lost hyperbolicity");
   if (st & kStatusIndex) return fail(ctx, DG_E_MESH, "neighbour index out of range");
+  if (st & kStatusTimeout) return fail(ctx, DG_E_CUDA, "a bounded wait on the tensor cores timed out");
   return DG_OK;
 }
 
@@ -762,6 +837,9 @@ bool noalloc_view(const dg_ctx* ctx, NoAllocView* v) {
   v->geom = ctx->geom;
   v->mat = ctx->matf;
   v->nbr = ctx->nbr;
+  v->faces = ctx->faces;
+  v->elem_face = ctx->elem_face;
+  v->F = ctx->F;
   v->tables = ctx->tables;
   v->dt_cfl = ctx->dt_cfl;
   v->has_material = ctx->has_material;
@@ -777,6 +855,17 @@ cudaError_t launch_predictor(int N, const StepArgs& a, cudaStream_t s) {
     case 3: return launch_predictor_t<3>(a, s);
     case 4: return launch_predictor_t<4>(a, s);
     case 5: return launch_predictor_t<5>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_faces(int N, const StepArgs& a, cudaStream_t s) {
+  switch (N) {
+    case 1: return launch_faces_t<1>(a, s);
+    case 2: return launch_faces_t<2>(a, s);
+    case 3: return launch_faces_t<3>(a, s);
+    case 4: return launch_faces_t<4>(a, s);
+    case 5: return launch_faces_t<5>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -30,14 +30,38 @@ __host__ __device__ constexpr int d_offset(int N, int i) {
 __host__ __device__ constexpr int d_alpha_offset(int N) { return d_offset(N, N + 1); }
 __host__ __device__ constexpr int d_stride(int N) { return round4(d_alpha_offset(N) + n_modes(N)); }
 
+__host__ __device__ constexpr int round2(int x) { return (x + 1) & ~1; }
+
+// Padded sizes: LP modes (multiple of 4), NQP volume nodes and NFP face nodes
+// (multiples of 2, for two-node register tiles).
+__host__ __device__ constexpr int lp_of(int N) { return round4(n_modes(N)); }
+__host__ __device__ constexpr int nqp_of(int N) { return round2(n_vol_nodes(N)); }
+__host__ __device__ constexpr int nfp_of(int N) { return round2(n_face_nodes(N)); }
+__host__ __device__ constexpr int round8(int x) { return (x + 7) & ~7; }
+
+// Tensor-core volume evaluation (degrees 2..4, volume nodes <= 128): the basis
+// values at the volume nodes as a 128 x KP operand (KP = L rounded up to 8) in
+// the canonical K-major layout without swizzle (core matrices of 8 rows x 4
+// elements, 128 bytes; consecutive along K, then 8-row groups), split into a
+// TF32 high part and an FP32 remainder.
+__host__ __device__ constexpr bool tc_volume(int N) { return N >= 2 && N <= 4; }
+__host__ __device__ constexpr int tc_kp(int N) { return round8(n_modes(N)); }
+__host__ __device__ constexpr int tc_canon(int row, int k, int kp) {
+  return (row >> 3) * (kp / 4 * 32) + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
+}
+
 // Reference tables of degree N (FP32, one device buffer), offsets in floats.
+// Padding entries are zero; every table starts on a 16-byte boundary.
 struct TableLayout {
-  int Kt;     // [3][L][L]   Kt[e][k][l] = int phi_k d phi_l / d xi_e
-  int Vv;     // [NQ][L]     phi_l at volume node q
-  int Vw;     // [NQ][L]     w_q phi_l(x_q)           (volume weights sum to 1/6)
-  int Gw;     // [3][NQ][L]  w_q d phi_l / d xi_e (x_q)
-  int Vf;     // [4][NF][L]  phi_l at face node i of local face f
-  int Vfw;    // [4][NF][L]  beta_i phi_l at face node i (beta sums to 1)
+  int VvT;    // [L][NQP]    phi_l at volume node q
+  int Vw;     // [NQ][LP]    w_q phi_k(x_q)            (volume weights sum to 1/6)
+  int Gw;     // [3][NQ][LP] w_q d phi_k / d xi_e (x_q)
+  int KtA;    // [3][L][LP]  KtA[e][l][k] = int phi_k d phi_l / d xi_e
+  int KtB;    // [3][L][LP]  KtB[e][l][k] = int phi_l d phi_k / d xi_e
+  int VfT;    // [4][L][NFP] phi_l at face node i of local face f
+  int Vfw;    // [4][NF][LP] beta_i phi_k(x_i) at face node i of local face f (beta sums to 1)
+  int PhiH;   // [128 x KP]  canonical tensor-core operand: TF32 part of phi_l(x_q) (rows q >= NQ zero)
+  int PhiL;   // [128 x KP]  phi_l(x_q) minus its TF32 part
   int tz;     // [NT]        time nodes in [0,1]
   int gz;     // [NT]        time weights (sum 1)
   int total;
@@ -46,13 +70,17 @@ struct TableLayout {
 __host__ __device__ constexpr TableLayout table_layout(int N) {
   TableLayout t{};
   const int L = n_modes(N), NQ = n_vol_nodes(N), NF = n_face_nodes(N), NT = N + 1;
+  const int LP = lp_of(N), NQP = nqp_of(N), NFP = nfp_of(N);
   int o = 0;
-  t.Kt = o;  o += 3 * L * L;
-  t.Vv = o;  o += NQ * L;
-  t.Vw = o;  o += NQ * L;
-  t.Gw = o;  o += 3 * NQ * L;
-  t.Vf = o;  o += 4 * NF * L;
-  t.Vfw = o; o += 4 * NF * L;
+  t.VvT = o; o = round4(o + L * NQP);
+  t.Vw = o;  o = round4(o + NQ * LP);
+  t.Gw = o;  o = round4(o + 3 * NQ * LP);
+  t.KtA = o; o = round4(o + 3 * L * LP);
+  t.KtB = o; o = round4(o + 3 * L * LP);
+  t.VfT = o; o = round4(o + 4 * L * NFP);
+  t.Vfw = o; o = round4(o + 4 * NF * LP);
+  t.PhiH = o; o = round4(o + (tc_volume(N) ? 128 * tc_kp(N) : 0));
+  t.PhiL = o; o = round4(o + (tc_volume(N) ? 128 * tc_kp(N) : 0));
   t.tz = o;  o += NT;
   t.gz = o;  o += NT;
   t.total = round4(o);
@@ -82,27 +110,39 @@ enum : unsigned {
   kStatusNonFinite = 1u,
   kStatusNonHyperbolic = 2u,
   kStatusIndex = 4u,
+  kStatusTimeout = 8u,      // a bounded wait on the tensor cores ran out
 };
+
+// Time-integrated Rusanov flux of every face at its NF nodes (9 wave fields),
+// oriented with the outward normal of the face's first element.
+__host__ __device__ constexpr int ff_stride(int N) { return round4(n_face_nodes(N) * kWave); }
 
 struct StepArgs {
   int64_t E;
+  int64_t F;              // number of faces
   const float* q_in;      // [E][q_stride]
   float* q_out;           // [E][q_stride]
   float* d;               // [E][d_stride]
   float* cp;              // [E] effective P speed of the cell mean (for the Rusanov C)
+  float* ff;              // [F][ff_stride] face fluxes
   const GeomF* geom;      // [E]
   const MatF* mat;        // [E]
   const int* nbr;         // [E][4] (neighbour element << 2) | neighbour's local face
+  const int4* faces;      // [F] (element 0, its local face, element 1, its local face)
+  const int* elem_face;   // [E][4] (face id << 1) | side (side 1: flux sign reversed)
   const float* tables;    // table_layout(N)
   float dt;
   unsigned* status;
+  int grid_pred, grid_face, grid_corr;   // persistent grid sizes (0: one CTA per tile)
 };
 
 // Kernel launchers, one per compiled degree (dg_step_n<N>.cu), and their
 // dispatch on the runtime degree (dg_host.cpp).
 template <int N> cudaError_t launch_predictor_t(const StepArgs& a, cudaStream_t s);
+template <int N> cudaError_t launch_faces_t(const StepArgs& a, cudaStream_t s);
 template <int N> cudaError_t launch_corrector_t(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_predictor(int N, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_faces(int N, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_corrector(int N, const StepArgs& a, cudaStream_t s);
 
 // Auxiliary kernels (dg_aux.cu).
@@ -136,6 +176,9 @@ struct NoAllocView {
   const GeomF* geom;
   const MatF* mat;
   const int* nbr;
+  const int4* faces;
+  const int* elem_face;
+  int64_t F;
   const float* tables;
   double dt_cfl;
   bool has_material;

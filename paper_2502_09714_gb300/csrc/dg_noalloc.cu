@@ -5,7 +5,7 @@
 // set-up).  This entry point keeps every intermediate of the step in one
 // file-scope device array of fixed size instead of the context's buffers; the
 // caller passes the input and output states.  The kernels are the same
-// predictor/corrector kernels as dg_step.
+// predictor, face-flux and corrector kernels as dg_step.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -58,10 +58,12 @@ extern "C" dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_ou
   if (!v.has_material) return noalloc_error(ctx, DG_E_STATE, "dg_set_material must precede dg_step_noalloc");
   if (dt <= 0) dt = v.dt_cfl;
   if (!std::isfinite(dt)) return noalloc_error(ctx, DG_E_ARG, "non-finite dt");
-  const int64_t qs = q_stride(v.N), ds = d_stride(v.N);
-  const int64_t per_elem = 2 * qs + ds + 1;
-  const int64_t max_elem = (kScratchFloats - kStatusFloats) / per_elem;
-  if (v.E > max_elem) {
+  const int64_t qs = q_stride(v.N), ds = d_stride(v.N), ffs = ff_stride(v.N);
+  const int64_t cp_floats = (v.E + 3) / 4 * 4;
+  const int64_t need = kStatusFloats + v.E * (2 * qs + ds) + cp_floats + v.F * ffs;
+  if (need > kScratchFloats) {
+    // a closed mesh has two faces per element
+    const int64_t max_elem = (kScratchFloats - kStatusFloats - 3) / (2 * qs + ds + 1 + 2 * ffs);
     const std::string msg = "dg_step_noalloc: " + std::to_string(v.E) + " elements exceed the " +
                             std::to_string(max_elem) + "-element capacity of its 16 MiB static scratch at order " +
                             std::to_string(v.N);
@@ -72,12 +74,17 @@ extern "C" dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_ou
   if (e != cudaSuccess)
     return noalloc_error(ctx, DG_E_CUDA, (std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
   unsigned* status = reinterpret_cast<unsigned*>(base);
-  float* qa = base + kStatusFloats;          // state in, internal layout
+  float* qa = base + kStatusFloats;          // state in, internal layout (offsets keep 16-byte alignment)
   float* qb = qa + v.E * qs;                 // state out, internal layout
   float* d = qb + v.E * qs;                  // predictor output
   float* cp = d + v.E * ds;                  // effective P speed per cell
+  float* ff = cp + cp_floats;                // face fluxes (16-byte aligned)
   StepArgs a{};
   a.E = v.E;
+  a.F = v.F;
+  a.ff = ff;
+  a.faces = v.faces;
+  a.elem_face = v.elem_face;
   a.q_in = qa;
   a.q_out = qb;
   a.d = d;
@@ -92,6 +99,7 @@ extern "C" dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_ou
   if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned), v.stream)) != cudaSuccess ||
       (e = launch_state_in(v.N, v.E, q_in, 0, qa, v.stream)) != cudaSuccess ||
       (e = launch_predictor(v.N, a, v.stream)) != cudaSuccess ||
+      (e = launch_faces(v.N, a, v.stream)) != cudaSuccess ||
       (e = launch_corrector(v.N, a, v.stream)) != cudaSuccess ||
       (e = launch_state_out(v.N, v.E, qb, q_out, 0, v.stream)) != cudaSuccess)
     return noalloc_error(ctx, DG_E_CUDA, (std::string("dg_step_noalloc launch: ") + cudaGetErrorString(e)).c_str());

@@ -1,39 +1,47 @@
-// Predictor and corrector kernels of one ADER-DG step for the CDM damage
-// rheology (arXiv 2502.09714, Appendix A), FP32, templated on the degree N.
+// Kernels of one ADER-DG step for the CDM damage rheology (arXiv 2502.09714,
+// Appendix A), FP32, templated on the degree N.
 //
-// Data per element (see dg_internal.h): modal state Q[L][10]; predictor output
-// D^i (i = 1..N) of the 9 wave fields on the modes of degree <= N-i, plus
-// D^1 of alpha on all modes.  A CTA processes TE consecutive elements; their
-// data is staged in shared memory and the reference tables are read through
-// the read-only cache.
+//   k_predictor  cell-mean effective Jacobian, Cauchy-Kovalevskaya recursion
+//                (Eq. "CKIter-ref-matrix") and damage-rate source at i = 1
+//                (Eq. "CKIter-ref-source")                       -> D, cp
+//   k_faces      Rusanov flux (Eq. "rusanov-flux") at the space-time nodes of
+//                every face, once per face, time-integrated      -> FF
+//   k_corrector  volume flux and damage source (Eqs. "3rd term", "rhs term"),
+//                face term (Eq. "2nd term") from FF, update (Eq. "time-integrated")
+//
+// Each kernel is persistent: a CTA loads the reference tables it needs into
+// shared memory once, then walks over tiles of elements (or faces).  Dense
+// contractions with the shared tables are block GEMMs with 4x4 register tiles;
+// the evaluation of the Taylor coefficients at the volume nodes uses two-node
+// register tiles and feeds the pointwise CDM law directly from registers.
 #pragma once
 
+#include <cstdlib>
+
 #include "dg_internal.h"
+#include "dg_tc.cuh"
 
 namespace dg {
 
-template <int N>
-struct Dims {
-  static constexpr int L = n_modes(N);
-  static constexpr int NQ = n_vol_nodes(N);
-  static constexpr int NF = n_face_nodes(N);
-  static constexpr int NT = N + 1;
-  static constexpr int QS = q_stride(N);
-  static constexpr int DS = d_stride(N);
-  static constexpr int AOFF = d_alpha_offset(N);
-  // elements per CTA
-  static constexpr int TE = N <= 2 ? 16 : (N == 3 ? 8 : 4);
-  // corrector scratch per element: volume-node data or neighbour copies + face fluxes
-  static constexpr int XS_VOL = NQ * 10;
-  static constexpr int XS_FACE = QS + DS + NF * 9;
-  static constexpr int XS = round4(XS_VOL > XS_FACE ? XS_VOL : XS_FACE);
-  static constexpr int IS = round4(L * 3);
-  static constexpr int AS = round4(L * 10);
-  static constexpr int PRED_SMEM = TE * (QS + 2 * round4(L * 9) + round4(NQ) + 16);
-  static constexpr int CORR_SMEM = TE * (QS + DS + AS + IS + XS);
-};
+__host__ __device__ constexpr int sum_hi(int N) {
+  int s = 0;
+  for (int o = 1; o <= N; ++o) s += n_modes(N - o);
+  return s;
+}
+// first row of Taylor order o >= 1 in the stacked higher-order arrays
+__host__ __device__ constexpr int row_hi(int N, int o) {
+  int s = 0;
+  for (int j = 1; j < o; ++j) s += n_modes(N - j);
+  return s;
+}
 
-__host__ __device__ constexpr int lr(int N, int i) { return n_modes(N - i); }
+template <int N>
+struct Dim {
+  static constexpr int L = n_modes(N), NQ = n_vol_nodes(N), NF = n_face_nodes(N), NT = N + 1;
+  static constexpr int LP = lp_of(N), NQP = nqp_of(N), NFP = nfp_of(N);
+  static constexpr int QS = q_stride(N), DS = d_stride(N), AOFF = d_alpha_offset(N), FFS = ff_stride(N);
+  static constexpr int SH = sum_hi(N);
+};
 
 // CDM stress (Eq. "cdb-model") and damage rate, with xi = 0 below I2 = 1e-30
 // and the rate written as C_d gamma_r max(0, I1 sqrt(I2) - xi0 I2).
@@ -85,355 +93,397 @@ __device__ __forceinline__ void normal_flux(const float u[10], const MatF& m, co
   F[8] = -m.rho_inv * (sig[5] * n[0] + sig[4] * n[1] + sig[2] * n[2]);
 }
 
-// ---------------------------------------------------------------------------
-// Predictor: cell-mean effective Jacobian, Cauchy-Kovalevskaya recursion
-// (Eq. "CKIter-ref-matrix") and the damage-rate source at i = 1
-// (Eq. "CKIter-ref-source").
-// ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(128) k_predictor(StepArgs a) {
-  using Dm = Dims<N>;
-  constexpr int L = Dm::L, NQ = Dm::NQ, QS = Dm::QS, DS = Dm::DS, TE = Dm::TE;
-  constexpr int L9 = round4(L * 9);
-  constexpr TableLayout T = table_layout(N);
-  extern __shared__ float4 smem4[];
-  float* sQ = reinterpret_cast<float*>(smem4);   // [TE][QS]
-  float* sP = sQ + TE * QS;                      // [TE][L9] D^i for odd i
-  float* sN = sP + TE * L9;                      // [TE][L9] D^i for even i
-  float* sR = sN + TE * L9;                      // [TE][NQ] damage rate at the nodes
-  float* sC = sR + TE * round4(NQ);              // [TE][16] per-element coefficients
-  const float* tb = a.tables;
-  const int64_t e0 = static_cast<int64_t>(blockIdx.x) * TE;
-  const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
+__device__ __forceinline__ void copy_to_smem(float* dst, const float* src, int n) {
+  for (int w = threadIdx.x; w < n; w += blockDim.x) dst[w] = __ldg(src + w);
+}
 
-  {
-    const float4* src = reinterpret_cast<const float4*>(a.q_in + e0 * QS);
-    float4* dst = reinterpret_cast<float4*>(sQ);
-    for (int w = threadIdx.x; w < ne * QS / 4; w += blockDim.x) dst[w] = __ldg(src + w);
-  }
-  __syncthreads();
-
-  if (threadIdx.x < ne) {
-    const int e = threadIdx.x;
-    const int64_t ge = e0 + e;
-    const MatF m = a.mat[ge];
-    const float r6 = 2.449489742783178f;   // phi_0 = sqrt(6): cell mean = Q_0 sqrt(6)
-    float u[6];
-    for (int p = 0; p < 6; ++p) u[p] = sQ[e * QS + p] * r6;
-    const float alpha = sQ[e * QS + 9] * r6;
-    const float I1 = u[0] + u[1] + u[2];
-    const float I2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + 2.f * (u[3] * u[3] + u[4] * u[4] + u[5] * u[5]);
-    const float xi = I2 > 1e-30f ? I1 * rsqrtf(I2) : 0.f;
-    // effective Lame parameters at the cell mean (Eq. "effective-cdb", mu sign from Eq. "cdb-model")
-    const float lam = m.lam0 - alpha * m.gamma_r * xi * (1.f / 3.f);
-    const float mu = m.mu0 + alpha * m.xi0 * m.gamma_r - 0.5f * alpha * m.gamma_r * xi;
-    if (!(mu > 0.f) || !(lam + 2.f * mu > 0.f)) atomicOr(a.status, kStatusNonHyperbolic);
-    a.cp[ge] = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * m.rho_inv);
-    float* c = sC + e * 16;
-    c[0] = lam * m.rho_inv;
-    c[1] = mu * m.rho_inv;
-    const GeomF* g = a.geom + ge;
-    for (int k = 0; k < 9; ++k) c[2 + k] = g->tinv[k];
-  }
-
-  // damage rate at the volume nodes from the state at t_n
-  for (int w = threadIdx.x; w < ne * NQ; w += blockDim.x) {
-    const int e = w / NQ, q = w - e * NQ;
-    const float* vv = tb + T.Vv + q * L;
-    const float* qe = sQ + e * QS;
-    float eps[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int l = 0; l < L; ++l) {
-      const float phi = __ldg(vv + l);
+// Block GEMM: C[m][n] = sum_k A[k*lda + m] B[k*ldb + n], m < M, n < Nc (both
+// multiples of 4, rows 16-byte aligned).  Work items are (m-quad, n-quad,
+// k-split); out(m, n, value) receives each entry once.  With KS > 1 the split
+// sums go through `partial` (KS*M*Nc floats) and the call contains two
+// __syncthreads, so every thread of the block must make it.
+template <int KS, class Out>
+__device__ __forceinline__ void block_gemm(const float* __restrict__ A, int lda,
+                                           const float* __restrict__ B, int ldb, int M, int Nc,
+                                           int K, float* partial, Out out) {
+  const int mq = M >> 2, nq = Nc >> 2, tiles = mq * nq;
+  const int kchunk = (K + KS - 1) / KS;
+  for (int w = threadIdx.x; w < tiles * KS; w += blockDim.x) {
+    const int ks = w / tiles, r = w - ks * tiles;
+    const int mi = r % mq, ni = r / mq;
+    float acc[4][4];
 #pragma unroll
-      for (int p = 0; p < 6; ++p) eps[p] = fmaf(phi, qe[l * 10 + p], eps[p]);
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    const int k0 = ks * kchunk;
+    const int k1 = min(K, k0 + kchunk);
+    const float* ap = A + 4 * mi;
+    const float* bp = B + 4 * ni;
+#pragma unroll 4
+    for (int k = k0; k < k1; ++k) {
+      const float4 a = *reinterpret_cast<const float4*>(ap + k * lda);
+      const float4 b = *reinterpret_cast<const float4*>(bp + k * ldb);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
-    sR[e * round4(NQ) + q] = cdm_rate(eps, a.mat[e0 + e]);
+    if (KS == 1) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out(4 * mi + i, 4 * ni + j, acc[i][j]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4*>(partial + (ks * M + 4 * mi + i) * Nc + 4 * ni) =
+            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    }
   }
-  __syncthreads();
-  // D^1 of alpha = projection of the rate (mass matrix = identity)
-  for (int w = threadIdx.x; w < ne * L; w += blockDim.x) {
-    const int e = w / L, k = w - e * L;
-    const float* r = sR + e * round4(NQ);
-    float acc = 0.f;
-    for (int q = 0; q < NQ; ++q) acc = fmaf(__ldg(tb + T.Vw + q * L + k), r[q], acc);
-    a.d[(e0 + e) * DS + Dm::AOFF + k] = acc;
-  }
-
-  // Cauchy-Kovalevskaya: D^i_kp = -sum_e Kt^e_kl D^{i-1}_lq (Theta^{-1}_ed B^d_pq)
-#pragma unroll 1
-  for (int i = 1; i <= N; ++i) {
-    const int Lin = n_modes(N - i + 1), Lout = n_modes(N - i);
-    const float* prev = (i == 1) ? sQ : ((i & 1) ? sN : sP);
-    const int pstride = (i == 1) ? QS : L9;
-    const int pld = (i == 1) ? 10 : 9;
-    float* cur = (i & 1) ? sP : sN;
-    const int doff = d_offset(N, i);
-    for (int w = threadIdx.x; w < ne * Lout; w += blockDim.x) {
-      const int e = w / Lout, k = w - e * Lout;
-      float g[3][9];
+  if (KS > 1) {
+    __syncthreads();
+    for (int w = threadIdx.x; w < M * Nc; w += blockDim.x) {
+      float v = 0.f;
 #pragma unroll
-      for (int f = 0; f < 9; ++f) g[0][f] = g[1][f] = g[2][f] = 0.f;
-      const float* kt = tb + T.Kt + k * L;
-      const float* pe = prev + e * pstride;
-      for (int l = 0; l < Lin; ++l) {
-        const float k0 = __ldg(kt + l), k1 = __ldg(kt + L * L + l), k2 = __ldg(kt + 2 * L * L + l);
-        const float* pr = pe + l * pld;
-#pragma unroll
-        for (int f = 0; f < 9; ++f) {
-          const float v = pr[f];
-          g[0][f] = fmaf(k0, v, g[0][f]);
-          g[1][f] = fmaf(k1, v, g[1][f]);
-          g[2][f] = fmaf(k2, v, g[2][f]);
-        }
-      }
-      const float* c = sC + e * 16;
-      float gd[3][9];   // d/dx_d of field f, projected
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int f = 0; f < 9; ++f) gd[d][f] = c[2 + d] * g[0][f] + c[5 + d] * g[1][f] + c[8 + d] * g[2][f];
-      const float lr_ = c[0], mr = c[1];
-      float Di[9];
-      Di[0] = gd[0][6];
-      Di[1] = gd[1][7];
-      Di[2] = gd[2][8];
-      Di[3] = 0.5f * (gd[1][6] + gd[0][7]);
-      Di[4] = 0.5f * (gd[2][7] + gd[1][8]);
-      Di[5] = 0.5f * (gd[0][8] + gd[2][6]);
-      Di[6] = lr_ * (gd[0][0] + gd[0][1] + gd[0][2]) + 2.f * mr * (gd[0][0] + gd[1][3] + gd[2][5]);
-      Di[7] = lr_ * (gd[1][0] + gd[1][1] + gd[1][2]) + 2.f * mr * (gd[0][3] + gd[1][1] + gd[2][4]);
-      Di[8] = lr_ * (gd[2][0] + gd[2][1] + gd[2][2]) + 2.f * mr * (gd[0][5] + gd[1][4] + gd[2][2]);
-      float* out = cur + e * L9 + k * 9;
-      float* gout = a.d + (e0 + e) * DS + doff + k * 9;
-#pragma unroll
-      for (int f = 0; f < 9; ++f) {
-        out[f] = Di[f];
-        gout[f] = Di[f];
-      }
+      for (int ks = 0; ks < KS; ++ks) v += partial[ks * M * Nc + w];
+      out(w / Nc, w % Nc, v);
     }
     __syncthreads();
   }
 }
 
-// ---------------------------------------------------------------------------
-// Corrector: volume flux and damage source by space-time quadrature
-// (Eqs. "3rd term", "rhs term"), Rusanov face flux with the neighbour trace
-// (Eqs. "rusanov-flux", "2nd term"), update (Eq. "time-integrated").
-// ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(128) k_corrector(StepArgs a) {
-  using Dm = Dims<N>;
-  constexpr int L = Dm::L, NQ = Dm::NQ, NF = Dm::NF, NT = Dm::NT, QS = Dm::QS, DS = Dm::DS;
-  constexpr int TE = Dm::TE, XS = Dm::XS, IS = Dm::IS, AS = Dm::AS, AOFF = Dm::AOFF;
+// ===========================================================================
+// Predictor
+// ===========================================================================
+template <int N, bool TSM>
+struct PredCfg : Dim<N> {
+  using D = Dim<N>;
+  static constexpr int TE = N >= 4 ? 8 : 16;
+  static constexpr int THREADS = 256;
+  static constexpr int CW = 12 * TE;                       // CK column width: (element, 9 fields + 3 pad)
+  static constexpr int KS_SRC = N >= 4 ? 8 : 4;
+  // shared memory carve-up (floats); tables only when TSM
+  static constexpr int oVvT = 0;
+  static constexpr int oVw = TSM ? round4(oVvT + D::L * D::NQP) : 0;
+  static constexpr int oKtA = TSM ? round4(oVw + D::NQ * D::LP) : 0;
+  static constexpr int oQ = TSM ? round4(oKtA + 3 * D::L * D::LP) : 0;
+  static constexpr int oC0 = oQ + TE * D::QS;              // [L][8 TE] strains at t_n
+  static constexpr int oR = oC0 + D::L * 8 * TE;           // [NQ][TE] damage rate at the nodes
+  static constexpr int oP0 = round4(oR + D::NQ * TE);      // [L][CW] CK input
+  static constexpr int oP1 = oP0 + D::L * CW;              // [L][CW] CK output
+  static constexpr int oPart = oP1 + D::L * CW;            // split-K partial sums
+  static constexpr int PART = KS_SRC * D::LP * TE;
+  static constexpr int oCoef = oPart + PART;               // [TE][16]
+  static constexpr int SMEM = oCoef + 16 * TE;
+  static constexpr bool FITS = SMEM * 4 <= 227 * 1024;
+  static_assert(FITS || TSM, "predictor shared memory");
+};
+
+template <int N, bool TSM>
+__global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
+  using C = PredCfg<N, TSM>;
+  constexpr int L = C::L, NQ = C::NQ, NQP = C::NQP, LP = C::LP, QS = C::QS, DS = C::DS, TE = C::TE;
+  constexpr int CW = C::CW;
   constexpr TableLayout T = table_layout(N);
   extern __shared__ float4 smem4[];
-  float* sQ = reinterpret_cast<float*>(smem4);   // [TE][QS]  own state
-  float* sD = sQ + TE * QS;                      // [TE][DS]  own predictor
-  float* sA = sD + TE * DS;                      // [TE][AS]  update accumulator
-  float* sI = sA + TE * AS;                      // [TE][IS]  time-integrated velocity
-  float* sX = sI + TE * IS;                      // [TE][XS]  scratch
-  const float* tb = a.tables;
-  const float dt = a.dt;
-  const int64_t e0 = static_cast<int64_t>(blockIdx.x) * TE;
-  const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
-
-  {
-    const float4* srcq = reinterpret_cast<const float4*>(a.q_in + e0 * QS);
-    const float4* srcd = reinterpret_cast<const float4*>(a.d + e0 * DS);
-    for (int w = threadIdx.x; w < ne * QS / 4; w += blockDim.x) reinterpret_cast<float4*>(sQ)[w] = __ldg(srcq + w);
-    for (int w = threadIdx.x; w < ne * DS / 4; w += blockDim.x) reinterpret_cast<float4*>(sD)[w] = __ldg(srcd + w);
-    for (int w = threadIdx.x; w < TE * AS; w += blockDim.x) sA[w] = 0.f;
-  }
-  __syncthreads();
-
-  // time integral of the velocity Taylor series over [0, dt]
-  for (int w = threadIdx.x; w < ne * L; w += blockDim.x) {
-    const int e = w / L, l = w - e * L;
-    float iv[3];
-    for (int m = 0; m < 3; ++m) iv[m] = dt * sQ[e * QS + l * 10 + 6 + m];
-    float c = dt;
-#pragma unroll
-    for (int o = 1; o <= N; ++o) {
-      c *= dt / static_cast<float>(o + 1);
-      if (l < n_modes(N - o))
-        for (int m = 0; m < 3; ++m) iv[m] = fmaf(c, sD[e * DS + d_offset(N, o) + l * 9 + 6 + m], iv[m]);
-    }
-    for (int m = 0; m < 3; ++m) sI[e * IS + l * 3 + m] = iv[m];
+  float* sm = reinterpret_cast<float*>(smem4);
+  const float* sVvT = TSM ? sm + C::oVvT : a.tables + T.VvT;
+  const float* sVw = TSM ? sm + C::oVw : a.tables + T.Vw;
+  const float* sKtA = TSM ? sm + C::oKtA : a.tables + T.KtA;
+  float* sQ = sm + C::oQ;
+  float* sC0 = sm + C::oC0;
+  float* sR = sm + C::oR;
+  float* sP0 = sm + C::oP0;
+  float* sP1 = sm + C::oP1;
+  float* sPart = sm + C::oPart;
+  float* sCoef = sm + C::oCoef;
+  if (TSM) {
+    copy_to_smem(sm + C::oVvT, a.tables + T.VvT, L * NQP);
+    copy_to_smem(sm + C::oVw, a.tables + T.Vw, NQ * LP);
+    copy_to_smem(sm + C::oKtA, a.tables + T.KtA, 3 * L * LP);
   }
 
-  // volume nodes: strain and damage in time, CDM stress and rate, time integral
-  for (int w = threadIdx.x; w < ne * NQ; w += blockDim.x) {
-    const int e = w / NQ, q = w - e * NQ;
-    const int64_t ge = e0 + e;
-    const MatF m = a.mat[ge];
-    const float* vv = tb + T.Vv + q * L;
-    const float* qe = sQ + e * QS;
-    const float* de = sD + e * DS;
-    float t0[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float ta1 = 0.f;
-    for (int l = 0; l < L; ++l) {
-      const float phi = __ldg(vv + l);
-#pragma unroll
-      for (int p = 0; p < 6; ++p) t0[p] = fmaf(phi, qe[l * 10 + p], t0[p]);
-      t0[6] = fmaf(phi, qe[l * 10 + 9], t0[6]);
-      ta1 = fmaf(phi, de[AOFF + l], ta1);
-    }
-    float th[N][6];
-#pragma unroll
-    for (int o = 1; o <= N; ++o) {
-#pragma unroll
-      for (int p = 0; p < 6; ++p) th[o - 1][p] = 0.f;
-      const float* dd = de + d_offset(N, o);
-      for (int l = 0; l < n_modes(N - o); ++l) {
-        const float phi = __ldg(vv + l);
-#pragma unroll
-        for (int p = 0; p < 6; ++p) th[o - 1][p] = fmaf(phi, dd[l * 9 + p], th[o - 1][p]);
-      }
-    }
-    float sb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, rb = 0.f;
-#pragma unroll
-    for (int z = 0; z < NT; ++z) {
-      const float tau = __ldg(tb + T.tz + z) * dt, gam = __ldg(tb + T.gz + z) * dt;
-      float eps[6];
-#pragma unroll
-      for (int p = 0; p < 6; ++p) eps[p] = t0[p];
-      float c = 1.f;
-#pragma unroll
-      for (int o = 1; o <= N; ++o) {
-        c *= tau / static_cast<float>(o);
-#pragma unroll
-        for (int p = 0; p < 6; ++p) eps[p] = fmaf(c, th[o - 1][p], eps[p]);
-      }
-      const float alpha = fmaf(tau, ta1, t0[6]);
-      float sig[6], r;
-      cdm_point(eps, alpha, m, sig, &r);
-#pragma unroll
-      for (int p = 0; p < 6; ++p) sb[p] = fmaf(gam, sig[p], sb[p]);
-      rb = fmaf(gam, r, rb);
-    }
-    // T[e'][m] = -(1/rho) sum_d Theta^{-1}_{e'd} sigma_md, so that the velocity rows of
-    // the volume term are sum_q sum_e' (w_q d phi_k / d xi_e')(x_q) T[e'][m](x_q)
-    const float S[3][3] = {{sb[0], sb[3], sb[5]}, {sb[3], sb[1], sb[4]}, {sb[5], sb[4], sb[2]}};
-    const float* ti = a.geom[ge].tinv;
-    float* x = sX + e * XS + q * 10;
-#pragma unroll
-    for (int ep = 0; ep < 3; ++ep)
-#pragma unroll
-      for (int mc = 0; mc < 3; ++mc)
-        x[ep * 3 + mc] = -m.rho_inv * (ti[ep * 3 + 0] * S[mc][0] + ti[ep * 3 + 1] * S[mc][1] + ti[ep * 3 + 2] * S[mc][2]);
-    x[9] = rb;
-  }
-  __syncthreads();
-
-  // projections of the volume terms onto the modes
-  for (int w = threadIdx.x; w < ne * L; w += blockDim.x) {
-    const int e = w / L, k = w - e * L;
-    const float* xe = sX + e * XS;
-    float acc[3] = {0.f, 0.f, 0.f}, src = 0.f;
-    for (int q = 0; q < NQ; ++q) {
-      const float* x = xe + q * 10;
-      const float g0 = __ldg(tb + T.Gw + (0 * NQ + q) * L + k);
-      const float g1 = __ldg(tb + T.Gw + (1 * NQ + q) * L + k);
-      const float g2 = __ldg(tb + T.Gw + (2 * NQ + q) * L + k);
-#pragma unroll
-      for (int mc = 0; mc < 3; ++mc) acc[mc] += g0 * x[mc] + g1 * x[3 + mc] + g2 * x[6 + mc];
-      src = fmaf(__ldg(tb + T.Vw + q * L + k), x[9], src);
-    }
-    // strain rows (linear in v): -(1/2) int (v_i d_j phi_k + v_j d_i phi_k), taken modally
-    float H[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    const float* iv = sI + e * IS;
-    for (int l = 0; l < L; ++l) {
-      const float k0 = __ldg(tb + T.Kt + (0 * L + l) * L + k);
-      const float k1 = __ldg(tb + T.Kt + (1 * L + l) * L + k);
-      const float k2 = __ldg(tb + T.Kt + (2 * L + l) * L + k);
-#pragma unroll
-      for (int mc = 0; mc < 3; ++mc) {
-        const float v = iv[l * 3 + mc];
-        H[0][mc] = fmaf(k0, v, H[0][mc]);
-        H[1][mc] = fmaf(k1, v, H[1][mc]);
-        H[2][mc] = fmaf(k2, v, H[2][mc]);
-      }
-    }
-    const float* ti = a.geom[e0 + e].tinv;
-    float hd[3][3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-#pragma unroll
-      for (int mc = 0; mc < 3; ++mc) hd[d][mc] = ti[0 * 3 + d] * H[0][mc] + ti[1 * 3 + d] * H[1][mc] + ti[2 * 3 + d] * H[2][mc];
-    float* acc_out = sA + e * AS + k * 10;
-    acc_out[0] -= hd[0][0];
-    acc_out[1] -= hd[1][1];
-    acc_out[2] -= hd[2][2];
-    acc_out[3] -= 0.5f * (hd[1][0] + hd[0][1]);
-    acc_out[4] -= 0.5f * (hd[2][1] + hd[1][2]);
-    acc_out[5] -= 0.5f * (hd[0][2] + hd[2][0]);
-    acc_out[6] += acc[0];
-    acc_out[7] += acc[1];
-    acc_out[8] += acc[2];
-    acc_out[9] += src;
-  }
-  __syncthreads();
-
-  // faces
-#pragma unroll 1
-  for (int f = 0; f < 4; ++f) {
-    // stage the neighbours' state and predictor
-    constexpr int CH = (QS + DS) / 4;
-    for (int w = threadIdx.x; w < ne * CH; w += blockDim.x) {
-      const int e = w / CH, c = w - e * CH;
-      const int nbv = a.nbr[(e0 + e) * 4 + f];
-      const int64_t nbe = nbv >> 2;
-      float4 v;
-      if (c < QS / 4) v = __ldg(reinterpret_cast<const float4*>(a.q_in + nbe * QS) + c);
-      else v = __ldg(reinterpret_cast<const float4*>(a.d + nbe * DS) + (c - QS / 4));
-      reinterpret_cast<float4*>(sX + e * XS)[c] = v;
+  const int64_t ntiles = (a.E + TE - 1) / TE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * TE;
+    const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
+    __syncthreads();
+    {
+      const float4* src = reinterpret_cast<const float4*>(a.q_in + e0 * QS);
+      float4* dst = reinterpret_cast<float4*>(sQ);
+      for (int w = threadIdx.x; w < TE * QS / 4; w += blockDim.x)
+        dst[w] = w < ne * QS / 4 ? __ldg(src + w) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    for (int w = threadIdx.x; w < ne * NF; w += blockDim.x) {
-      const int e = w / NF, i = w - e * NF;
+    // per element: effective moduli at the cell mean (Eq. "effective-cdb", mu sign from Eq. "cdb-model")
+    if (threadIdx.x < ne) {
+      const int e = threadIdx.x;
       const int64_t ge = e0 + e;
-      const int nbv = a.nbr[ge * 4 + f];
-      const int64_t nbe = nbv >> 2;
-      const int fn = nbv & 3;
-      const float* vo = tb + T.Vf + (f * NF + i) * L;
-      const float* vn = tb + T.Vf + (fn * NF + i) * L;
-      const float* qo = sQ + e * QS;
-      const float* dO = sD + e * DS;
-      const float* qn = sX + e * XS;
-      const float* dn = qn + QS;
-      float o0[10], n0[10], oa1 = 0.f, na1 = 0.f;
+      const MatF m = a.mat[ge];
+      const float r6 = 2.449489742783178f;   // phi_0 = sqrt(6): cell mean = Q_0 sqrt(6)
+      float u[6];
+      for (int p = 0; p < 6; ++p) u[p] = sQ[e * QS + p] * r6;
+      const float alpha = sQ[e * QS + 9] * r6;
+      const float I1 = u[0] + u[1] + u[2];
+      const float I2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + 2.f * (u[3] * u[3] + u[4] * u[4] + u[5] * u[5]);
+      const float xi = I2 > 1e-30f ? I1 * rsqrtf(I2) : 0.f;
+      const float lam = m.lam0 - alpha * m.gamma_r * xi * (1.f / 3.f);
+      const float mu = m.mu0 + alpha * m.xi0 * m.gamma_r - 0.5f * alpha * m.gamma_r * xi;
+      if (!(mu > 0.f) || !(lam + 2.f * mu > 0.f)) atomicOr(a.status, kStatusNonHyperbolic);
+      a.cp[ge] = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * m.rho_inv);
+      float* c = sCoef + e * 16;
+      c[0] = lam * m.rho_inv;
+      c[1] = mu * m.rho_inv;
+      const GeomF* g = a.geom + ge;
+      for (int k = 0; k < 9; ++k) c[2 + k] = g->tinv[k];
+    }
+    // coefficient arrays: strains at t_n [l][e*8 + c] and the CK input [l][e*12 + p]
+    for (int w = threadIdx.x; w < L * TE; w += blockDim.x) {
+      const int l = w / TE, e = w - l * TE;
+      const float* q = sQ + e * QS + l * 10;
+      float* c0 = sC0 + l * 8 * TE + e * 8;
+      float* p0 = sP0 + l * CW + e * 12;
 #pragma unroll
-      for (int p = 0; p < 10; ++p) o0[p] = n0[p] = 0.f;
+      for (int p = 0; p < 6; ++p) c0[p] = q[p];
+      c0[6] = c0[7] = 0.f;
+#pragma unroll
+      for (int p = 0; p < 9; ++p) p0[p] = q[p];
+      p0[9] = p0[10] = p0[11] = 0.f;
+    }
+    __syncthreads();
+
+    // damage rate at the volume nodes from the state at t_n (two nodes per item)
+    constexpr int NPAIR = NQP / 2;
+    for (int w = threadIdx.x; w < TE * NPAIR; w += blockDim.x) {
+      const int e = w / NPAIR, j = w - e * NPAIR;
+      float acc[2][6];
+#pragma unroll
+      for (int n = 0; n < 2; ++n)
+#pragma unroll
+        for (int p = 0; p < 6; ++p) acc[n][p] = 0.f;
+#pragma unroll 5
       for (int l = 0; l < L; ++l) {
-        const float po = __ldg(vo + l), pn = __ldg(vn + l);
+        const float2 ph = *reinterpret_cast<const float2*>(sVvT + l * NQP + 2 * j);
+        const float4 c0 = *reinterpret_cast<const float4*>(sC0 + l * 8 * TE + e * 8);
+        const float2 c1 = *reinterpret_cast<const float2*>(sC0 + l * 8 * TE + e * 8 + 4);
+        const float cv[6] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y};
 #pragma unroll
-        for (int p = 0; p < 10; ++p) {
-          o0[p] = fmaf(po, qo[l * 10 + p], o0[p]);
-          n0[p] = fmaf(pn, qn[l * 10 + p], n0[p]);
+        for (int p = 0; p < 6; ++p) {
+          acc[0][p] = fmaf(ph.x, cv[p], acc[0][p]);
+          acc[1][p] = fmaf(ph.y, cv[p], acc[1][p]);
         }
-        oa1 = fmaf(po, dO[AOFF + l], oa1);
-        na1 = fmaf(pn, dn[AOFF + l], na1);
       }
-      float oh[N][9], nh[N][9];
+      const MatF m = a.mat[e0 + (e < ne ? e : 0)];
 #pragma unroll
-      for (int o = 1; o <= N; ++o) {
+      for (int n = 0; n < 2; ++n) {
+        const int q = 2 * j + n;
+        if (q < NQ) sR[q * TE + e] = e < ne ? cdm_rate(acc[n], m) : 0.f;
+      }
+    }
+    __syncthreads();
+    // D^1 of alpha = projection of the rate (mass matrix = identity)
+    block_gemm<C::KS_SRC>(sVw, LP, sR, TE, LP, TE, NQ, sPart, [&](int k, int e, float v) {
+      if (k < L && e < ne) a.d[(e0 + e) * DS + C::AOFF + k] = v;
+    });
+
+    // Cauchy-Kovalevskaya: D^i_kp = -sum_e Kt^e_kl D^{i-1}_lq (Theta^{-1}_ed B^d_pq)
+#pragma unroll 1
+    for (int i = 1; i <= N; ++i) {
+      const int Lin = n_modes(N - i + 1), Lout = n_modes(N - i);
+      const float* pin = (i & 1) ? sP0 : sP1;
+      float* pout = (i & 1) ? sP1 : sP0;
+      const int doff = d_offset(N, i);
+      for (int w = threadIdx.x; w < TE * Lout; w += blockDim.x) {
+        const int k = w / TE, e = w - k * TE;
+        float g[3][9];
 #pragma unroll
-        for (int p = 0; p < 9; ++p) oh[o - 1][p] = nh[o - 1][p] = 0.f;
-        const int off = d_offset(N, o);
-        for (int l = 0; l < n_modes(N - o); ++l) {
-          const float po = __ldg(vo + l), pn = __ldg(vn + l);
+        for (int f = 0; f < 9; ++f) g[0][f] = g[1][f] = g[2][f] = 0.f;
+        for (int l = 0; l < Lin; ++l) {
+          const float k0 = sKtA[(0 * L + l) * LP + k], k1 = sKtA[(1 * L + l) * LP + k], k2 = sKtA[(2 * L + l) * LP + k];
+          const float4 p0 = *reinterpret_cast<const float4*>(pin + l * CW + e * 12);
+          const float4 p1 = *reinterpret_cast<const float4*>(pin + l * CW + e * 12 + 4);
+          const float p8 = pin[l * CW + e * 12 + 8];
+          const float pv[9] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p8};
 #pragma unroll
-          for (int p = 0; p < 9; ++p) {
-            oh[o - 1][p] = fmaf(po, dO[off + l * 9 + p], oh[o - 1][p]);
-            nh[o - 1][p] = fmaf(pn, dn[off + l * 9 + p], nh[o - 1][p]);
+          for (int f = 0; f < 9; ++f) {
+            g[0][f] = fmaf(k0, pv[f], g[0][f]);
+            g[1][f] = fmaf(k1, pv[f], g[1][f]);
+            g[2][f] = fmaf(k2, pv[f], g[2][f]);
           }
         }
+        const float* c = sCoef + e * 16;
+        float gd[3][9];   // d/dx_d of field f, projected
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int f = 0; f < 9; ++f) gd[d][f] = c[2 + d] * g[0][f] + c[5 + d] * g[1][f] + c[8 + d] * g[2][f];
+        const float lr_ = c[0], mr = c[1];
+        float Di[9];
+        Di[0] = gd[0][6];
+        Di[1] = gd[1][7];
+        Di[2] = gd[2][8];
+        Di[3] = 0.5f * (gd[1][6] + gd[0][7]);
+        Di[4] = 0.5f * (gd[2][7] + gd[1][8]);
+        Di[5] = 0.5f * (gd[0][8] + gd[2][6]);
+        Di[6] = lr_ * (gd[0][0] + gd[0][1] + gd[0][2]) + 2.f * mr * (gd[0][0] + gd[1][3] + gd[2][5]);
+        Di[7] = lr_ * (gd[1][0] + gd[1][1] + gd[1][2]) + 2.f * mr * (gd[0][3] + gd[1][1] + gd[2][4]);
+        Di[8] = lr_ * (gd[2][0] + gd[2][1] + gd[2][2]) + 2.f * mr * (gd[0][5] + gd[1][4] + gd[2][2]);
+        float* po = pout + k * CW + e * 12;
+        *reinterpret_cast<float4*>(po) = make_float4(Di[0], Di[1], Di[2], Di[3]);
+        *reinterpret_cast<float4*>(po + 4) = make_float4(Di[4], Di[5], Di[6], Di[7]);
+        *reinterpret_cast<float4*>(po + 8) = make_float4(Di[8], 0.f, 0.f, 0.f);
+        if (e < ne) {
+          float* gout = a.d + (e0 + e) * DS + doff + k * 9;
+#pragma unroll
+          for (int f = 0; f < 9; ++f) gout[f] = Di[f];
+        }
       }
-      const GeomF* g = a.geom + ge;
-      const float n[3] = {g->face[f][0], g->face[f][1], g->face[f][2]};
-      const float scale = g->face[f][3];
-      const MatF mo = a.mat[ge], mn = a.mat[nbe];
-      const float C = fmaxf(a.cp[ge], a.cp[nbe]);
+      __syncthreads();
+    }
+  }
+}
+
+// ===========================================================================
+// Faces: Rusanov flux at the space-time nodes of each face, once per face
+// ===========================================================================
+template <int N, bool TSM>
+struct FaceCfg : Dim<N> {
+  using D = Dim<N>;
+  static constexpr int TF = N >= 4 ? 4 : (N == 3 ? 8 : 16);
+  static constexpr int THREADS = 128;
+  static constexpr int CROWS = D::L + D::SH;               // coefficient rows per side
+  static constexpr int oVfT = 0;
+  static constexpr int oC = TSM ? round4(oVfT + 4 * D::L * D::NFP) : 0;   // [TF][2][CROWS][12]
+  static constexpr int oTr = oC + TF * 2 * CROWS * 12;          // [TF][2][N+1][NFP][12]
+  static constexpr int SMEM = oTr + TF * 2 * (N + 1) * D::NFP * 12;
+  static constexpr bool FITS = SMEM * 4 <= 227 * 1024;
+  static_assert(FITS || TSM, "face kernel shared memory");
+};
+
+template <int N, bool TSM>
+__global__ void __launch_bounds__(128) k_faces(StepArgs a) {
+  using C = FaceCfg<N, TSM>;
+  constexpr int L = C::L, NF = C::NF, NFP = C::NFP, NT = C::NT, QS = C::QS, DS = C::DS, TF = C::TF;
+  constexpr int CROWS = C::CROWS, FFS = C::FFS;
+  constexpr TableLayout T = table_layout(N);
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  const float* sVfT = TSM ? sm + C::oVfT : a.tables + T.VfT;
+  float* sC = sm + C::oC;
+  float* sTr = sm + C::oTr;
+  const float* tb = a.tables;
+  const float dt = a.dt;
+  if (TSM) copy_to_smem(sm + C::oVfT, tb + T.VfT, 4 * L * NFP);
+
+  const int64_t ntiles = (a.F + TF - 1) / TF;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t f0 = tile * TF;
+    const int nf = static_cast<int>(min(static_cast<int64_t>(TF), a.F - f0));
+    __syncthreads();
+    // stage both sides: rows l < L: (Q[l][0..9], D1alpha[l], 0); rows of order o >= 1: (D^o[l][0..8], 0, 0, 0)
+    for (int w = threadIdx.x; w < TF * 2 * CROWS; w += blockDim.x) {
+      const int fc = w / (2 * CROWS), r2 = w - fc * 2 * CROWS;
+      const int side = r2 / CROWS, r = r2 - side * CROWS;
+      float v[12];
+#pragma unroll
+      for (int p = 0; p < 12; ++p) v[p] = 0.f;
+      if (fc < nf) {
+        const int4 fa = a.faces[f0 + fc];
+        const int64_t e = side ? fa.z : fa.x;
+        if (r < L) {
+          const float* q = a.q_in + e * QS + r * 10;
+#pragma unroll
+          for (int p = 0; p < 10; ++p) v[p] = __ldg(q + p);
+          v[10] = __ldg(a.d + e * DS + C::AOFF + r);
+        } else {
+          // locate the order of row r
+          int o = 1, rr = r - L;
+          while (rr >= n_modes(N - o)) { rr -= n_modes(N - o); ++o; }
+          const float* dd = a.d + e * DS + d_offset(N, o) + rr * 9;
+#pragma unroll
+          for (int p = 0; p < 9; ++p) v[p] = __ldg(dd + p);
+        }
+      }
+      float4* dst = reinterpret_cast<float4*>(sC + ((fc * 2 + side) * CROWS + r) * 12);
+      dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+      dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+      dst[2] = make_float4(v[8], v[9], v[10], v[11]);
+    }
+    __syncthreads();
+    // traces of each Taylor order at the face nodes (two nodes x 12 columns per item)
+    constexpr int NPAIR = NFP / 2;
+    for (int w = threadIdx.x; w < TF * 2 * (N + 1) * NPAIR; w += blockDim.x) {
+      const int j = w % NPAIR;
+      const int r1 = w / NPAIR;
+      const int o = r1 % (N + 1);
+      const int fs = r1 / (N + 1);            // face * 2 + side
+      const int fc = fs >> 1, side = fs & 1;
+      int lf = 0;
+      if (fc < nf) {
+        const int4 fa = a.faces[f0 + fc];
+        lf = side ? fa.w : fa.y;
+      }
+      const int K = o == 0 ? L : n_modes(N - o);
+      const int row0 = o == 0 ? 0 : L + row_hi(N, o);
+      const float* cb = sC + (fs * CROWS + row0) * 12;
+      const float* tab = sVfT + lf * L * NFP + 2 * j;
+      float acc[2][12];
+#pragma unroll
+      for (int n = 0; n < 2; ++n)
+#pragma unroll
+        for (int p = 0; p < 12; ++p) acc[n][p] = 0.f;
+      for (int l = 0; l < K; ++l) {
+        const float2 ph = *reinterpret_cast<const float2*>(tab + l * NFP);
+        const float4 c0 = *reinterpret_cast<const float4*>(cb + l * 12);
+        const float4 c1 = *reinterpret_cast<const float4*>(cb + l * 12 + 4);
+        const float4 c2 = *reinterpret_cast<const float4*>(cb + l * 12 + 8);
+        const float cv[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
+#pragma unroll
+        for (int p = 0; p < 12; ++p) {
+          acc[0][p] = fmaf(ph.x, cv[p], acc[0][p]);
+          acc[1][p] = fmaf(ph.y, cv[p], acc[1][p]);
+        }
+      }
+#pragma unroll
+      for (int n = 0; n < 2; ++n) {
+        float4* dst = reinterpret_cast<float4*>(sTr + ((fs * (N + 1) + o) * NFP + 2 * j + n) * 12);
+        dst[0] = make_float4(acc[n][0], acc[n][1], acc[n][2], acc[n][3]);
+        dst[1] = make_float4(acc[n][4], acc[n][5], acc[n][6], acc[n][7]);
+        dst[2] = make_float4(acc[n][8], acc[n][9], acc[n][10], acc[n][11]);
+      }
+    }
+    __syncthreads();
+    // Rusanov flux at the space-time nodes, integrated in time
+    for (int w = threadIdx.x; w < TF * NF; w += blockDim.x) {
+      const int fc = w / NF, i = w - fc * NF;
+      if (fc >= nf) continue;
+      const int4 fa = a.faces[f0 + fc];
+      const int64_t em = fa.x, ep = fa.z;
+      const GeomF* g = a.geom + em;
+      const float n[3] = {g->face[fa.y][0], g->face[fa.y][1], g->face[fa.y][2]};
+      const MatF mm = a.mat[em], mp = a.mat[ep];
+      const float Cs = fmaxf(a.cp[em], a.cp[ep]);
+      float tm[N + 1][9], tp[N + 1][9];
+      float am0, am1, ap0, ap1;
+#pragma unroll
+      for (int o = 0; o <= N; ++o) {
+        const float* xm = sTr + (((fc * 2 + 0) * (N + 1) + o) * NFP + i) * 12;
+        const float* xp = sTr + (((fc * 2 + 1) * (N + 1) + o) * NFP + i) * 12;
+#pragma unroll
+        for (int p = 0; p < 9; ++p) {
+          tm[o][p] = xm[p];
+          tp[o][p] = xp[p];
+        }
+        if (o == 0) {
+          am0 = xm[9];
+          am1 = xm[10];
+          ap0 = xp[9];
+          ap1 = xp[10];
+        }
+      }
       float Fb[9];
 #pragma unroll
       for (int p = 0; p < 9; ++p) Fb[p] = 0.f;
@@ -442,87 +492,674 @@ __global__ void __launch_bounds__(128) k_corrector(StepArgs a) {
         const float tau = __ldg(tb + T.tz + z) * dt, gam = __ldg(tb + T.gz + z) * dt;
         float um[10], up[10];
 #pragma unroll
-        for (int p = 0; p < 10; ++p) { um[p] = o0[p]; up[p] = n0[p]; }
-        um[9] = fmaf(tau, oa1, um[9]);
-        up[9] = fmaf(tau, na1, up[9]);
+        for (int p = 0; p < 9; ++p) {
+          um[p] = tm[0][p];
+          up[p] = tp[0][p];
+        }
         float c = 1.f;
 #pragma unroll
         for (int o = 1; o <= N; ++o) {
           c *= tau / static_cast<float>(o);
 #pragma unroll
           for (int p = 0; p < 9; ++p) {
-            um[p] = fmaf(c, oh[o - 1][p], um[p]);
-            up[p] = fmaf(c, nh[o - 1][p], up[p]);
+            um[p] = fmaf(c, tm[o][p], um[p]);
+            up[p] = fmaf(c, tp[o][p], up[p]);
           }
         }
+        um[9] = fmaf(tau, am1, am0);
+        up[9] = fmaf(tau, ap1, ap0);
         float Fm[9], Fp[9];
-        normal_flux(um, mo, n, Fm);
-        normal_flux(up, mn, n, Fp);
+        normal_flux(um, mm, n, Fm);
+        normal_flux(up, mp, n, Fp);
 #pragma unroll
-        for (int p = 0; p < 9; ++p) Fb[p] = fmaf(gam, 0.5f * (Fm[p] + Fp[p]) + 0.5f * C * (um[p] - up[p]), Fb[p]);
+        for (int p = 0; p < 9; ++p) Fb[p] = fmaf(gam, 0.5f * (Fm[p] + Fp[p]) + 0.5f * Cs * (um[p] - up[p]), Fb[p]);
       }
-      float* fo = sX + e * XS + QS + DS + i * 9;
+      float* out = a.ff + (f0 + fc) * FFS + i * 9;
 #pragma unroll
-      for (int p = 0; p < 9; ++p) fo[p] = Fb[p] * scale;
+      for (int p = 0; p < 9; ++p) out[p] = Fb[p];
+    }
+  }
+}
+
+// ===========================================================================
+// Corrector: volume terms, face terms from the face fluxes, update
+// ===========================================================================
+// The velocity rows of the volume term, sum_q w_q d phi_k/d xi_e' (x_q) T_e'm(x_q),
+// are taken as sum_l (int phi_l d phi_k/d xi_e') That_e'm,l with That the
+// projection of T by the volume rule: d phi_k/d xi_e' has degree N-1, so the two
+// agree up to rounding, and the same derivative table serves the strain rows.
+template <int N, bool TSM>
+struct CorrCfg : Dim<N> {
+  using D = Dim<N>;
+  static constexpr int TE = N >= 4 ? 4 : (N == 3 ? 8 : 16);
+  static constexpr int THREADS = 256;
+  static constexpr int NV = 3 * TE;                        // (element, component) columns
+  static constexpr int NB = 10 * TE;                       // nodal columns (element, 9 stress terms + rate)
+  static constexpr int NM = 2 * NV;                        // modal columns: time-integrated v | That_e'
+  static constexpr int NFC = 9 * TE;                       // face columns (element, field)
+  static constexpr int KS_PRJ = N >= 4 ? 2 : 1, KS_MOD = 1, KS_FACE = N >= 4 ? 2 : 1;
+  // tables (only when TSM)
+  static constexpr int oVvT = 0;
+  static constexpr int oVw = TSM ? round4(oVvT + D::L * D::NQP) : 0;   // [NQ][LP]
+  static constexpr int oKtB = TSM ? round4(oVw + D::NQ * D::LP) : 0;   // [3][L][LP]
+  static constexpr int oVfw = TSM ? round4(oKtB + 3 * D::L * D::LP) : 0;   // [4 NF][LP]
+  // element tile
+  static constexpr int oQ = TSM ? round4(oVfw + 4 * D::NF * D::LP) : 0;   // [TE][QS]
+  static constexpr int oC0 = oQ + TE * D::QS;              // [L][8 TE]  eps(6), alpha0, alpha1
+  static constexpr int oCh = oC0 + D::L * 8 * TE;          // [SH][8 TE] higher-order strain rows
+  static constexpr int BN = D::NQ * NB, BF = 4 * D::NF * NFC;
+  static constexpr int oB = oCh + round4(D::SH) * 8 * TE;  // [NQ][NB] nodal terms | [4 NF][NFC] face fluxes
+  static constexpr int oM = oB + round4(BN > BF ? BN : BF);     // [3][L][NM] modal GEMM inputs
+  static constexpr int oA = oM + 3 * D::L * NM;            // [TE][L][10] update accumulator
+  static constexpr int oH = oA + TE * D::L * 10;           // [3][LP][NM] modal GEMM outputs
+  static constexpr int P1 = KS_PRJ * D::LP * NB, P2 = KS_FACE * D::LP * NFC;
+  static constexpr int oPart = oH + 3 * D::LP * NM;
+  static constexpr int SMEM = oPart + (P1 > P2 ? P1 : P2);
+  static constexpr bool FITS = SMEM * 4 <= 227 * 1024;
+  static_assert(FITS || TSM, "corrector shared memory");
+};
+
+// Second half of the corrector, shared by the SIMT and tensor-core variants:
+// projection of the nodal terms (sB: [NQ][10 TE], columns (element, 9 stress
+// terms T_e'm, integrated rate)) by the volume rule, modal derivative of the
+// velocity and strain rows, face term from the face fluxes, update.  sM holds
+// the time-integrated velocity in columns [0, 3 TE) of each [L][6 TE] block.
+template <int N, int TE, int KS_PRJ, int KS_FACE>
+__device__ __forceinline__ void corrector_tail(const StepArgs& a, int64_t e0, int ne, const float* sVw,
+                                               const float* sKtB, const float* sVfw, const float* sQ, float* sM,
+                                               float* sB, float* sA, float* sH, float* sPart,
+                                               const float* sFraw = nullptr) {
+  using D = Dim<N>;
+  constexpr int L = D::L, NQ = D::NQ, NF = D::NF, LP = D::LP, QS = D::QS, FFS = D::FFS;
+  constexpr int NV = 3 * TE, NB = 10 * TE, NM = 2 * NV, NFC = 9 * TE;
+    // projection by the volume rule: That_e'm (into the modal inputs) and the damage source
+    block_gemm<KS_PRJ>(sVw, LP, sB, NB, LP, NB, NQ, sPart, [&](int l, int col, float v) {
+      if (l < L) {
+        const int e = col / 10, c = col - 10 * e;
+        if (c < 9) sM[((c / 3) * L + l) * NM + NV + e * 3 + c % 3] = v;
+        else sA[(e * L + l) * 10 + 9] += v;
+      }
+    });
+    if (KS_PRJ == 1) __syncthreads();
+    // modal derivative: H_e'[k][col] = sum_l int phi_l d phi_k/d xi_e' M_e'[l][col], e' = 0..2 in one pass
+    {
+      constexpr int MQ = LP / 4, NQQ = NM / 4, TILES = MQ * NQQ;
+      for (int w = threadIdx.x; w < 3 * TILES; w += blockDim.x) {
+        const int ep = w / TILES, r = w - ep * TILES;
+        const int mi = r % MQ, ni = r / MQ;
+        const float* A = sKtB + ep * L * LP + 4 * mi;
+        const float* B = sM + ep * L * NM + 4 * ni;
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 5
+        for (int l = 0; l < L; ++l) {
+          const float4 av = *reinterpret_cast<const float4*>(A + l * LP);
+          const float4 bv = *reinterpret_cast<const float4*>(B + l * NM);
+          const float x[4] = {av.x, av.y, av.z, av.w}, y[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(x[i], y[j], acc[i][j]);
+        }
+        float* h = sH + ep * LP * NM;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          *reinterpret_cast<float4*>(h + (4 * mi + i) * NM + 4 * ni) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      }
+    }
+    // face fluxes of the tile's elements, signed and scaled by |S_f| / |J| (sB is free again)
+    for (int w = threadIdx.x; w < TE * 4 * NF * 9; w += blockDim.x) {
+      const int e = w / (4 * NF * 9), r = w - e * 4 * NF * 9;
+      const int f = r / (NF * 9), r2 = r - f * NF * 9;
+      const int i = r2 / 9, p = r2 - 9 * i;
+      float v = 0.f;
+      if (e < ne) {
+        const int64_t ge = e0 + e;
+        const int ef = a.elem_face[ge * 4 + f];
+        const float sc = a.geom[ge].face[f][3] * ((ef & 1) ? -1.f : 1.f);
+        v = sc * (sFraw ? sFraw[(e * 4 + f) * FFS + i * 9 + p]
+                        : __ldg(a.ff + static_cast<int64_t>(ef >> 1) * FFS + i * 9 + p));
+      }
+      sB[(f * NF + i) * NFC + e * 9 + p] = v;
     }
     __syncthreads();
-    for (int w = threadIdx.x; w < ne * L; w += blockDim.x) {
+    // strain rows -(v_i d_j phi + v_j d_i phi)/2 and velocity rows from the modal derivatives
+    for (int w = threadIdx.x; w < TE * L; w += blockDim.x) {
       const int e = w / L, k = w - e * L;
-      const float* fe = sX + e * XS + QS + DS;
-      float acc[9];
+      const float* ti = a.geom[e0 + (e < ne ? e : 0)].tinv;
+      float hd[3][3];
 #pragma unroll
-      for (int p = 0; p < 9; ++p) acc[p] = 0.f;
-      for (int i = 0; i < NF; ++i) {
-        const float v = __ldg(tb + T.Vfw + (f * NF + i) * L + k);
+      for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int p = 0; p < 9; ++p) acc[p] = fmaf(v, fe[i * 9 + p], acc[p]);
-      }
-      float* ao = sA + e * AS + k * 10;
+        for (int mc = 0; mc < 3; ++mc)
+          hd[d][mc] = ti[0 * 3 + d] * sH[(0 * LP + k) * NM + e * 3 + mc] + ti[1 * 3 + d] * sH[(1 * LP + k) * NM + e * 3 + mc] +
+                      ti[2 * 3 + d] * sH[(2 * LP + k) * NM + e * 3 + mc];
+      float* ao = sA + (e * L + k) * 10;
+      ao[0] -= hd[0][0];
+      ao[1] -= hd[1][1];
+      ao[2] -= hd[2][2];
+      ao[3] -= 0.5f * (hd[1][0] + hd[0][1]);
+      ao[4] -= 0.5f * (hd[2][1] + hd[1][2]);
+      ao[5] -= 0.5f * (hd[0][2] + hd[2][0]);
 #pragma unroll
-      for (int p = 0; p < 9; ++p) ao[p] -= acc[p];
+      for (int mc = 0; mc < 3; ++mc)
+        ao[6 + mc] += sH[(0 * LP + k) * NM + NV + e * 3 + mc] + sH[(1 * LP + k) * NM + NV + e * 3 + mc] +
+                      sH[(2 * LP + k) * NM + NV + e * 3 + mc];
     }
     __syncthreads();
+    block_gemm<KS_FACE>(sVfw, LP, sB, NFC, LP, NFC, 4 * NF, sPart, [&](int k, int col, float v) {
+      if (k < L) {
+        const int e = col / 9, p = col - 9 * e;
+        sA[(e * L + k) * 10 + p] -= v;
+      }
+    });
+    if (KS_FACE == 1) __syncthreads();
+    // update
+    bool bad = false;
+    for (int w = threadIdx.x; w < ne * L * 10; w += blockDim.x) {
+      const int e = w / (L * 10), r = w - e * (L * 10);
+      const float v = sQ[e * QS + r] + sA[e * L * 10 + r];
+      bad |= !isfinite(v);
+      a.q_out[(e0 + e) * QS + r] = v;
+    }
+    if (bad) atomicOr(a.status, kStatusNonFinite);
+}
+
+template <int N, bool TSM>
+__global__ void __launch_bounds__(256) k_corrector(StepArgs a) {
+  using C = CorrCfg<N, TSM>;
+  constexpr int L = C::L, NQ = C::NQ, NQP = C::NQP, NF = C::NF, NT = C::NT, LP = C::LP;
+  constexpr int QS = C::QS, DS = C::DS, AOFF = C::AOFF, FFS = C::FFS, TE = C::TE;
+  constexpr int NV = C::NV, NB = C::NB, NM = C::NM, NFC = C::NFC;
+  constexpr TableLayout T = table_layout(N);
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  const float* sVvT = TSM ? sm + C::oVvT : a.tables + T.VvT;
+  const float* sVw = TSM ? sm + C::oVw : a.tables + T.Vw;
+  const float* sKtB = TSM ? sm + C::oKtB : a.tables + T.KtB;
+  const float* sVfw = TSM ? sm + C::oVfw : a.tables + T.Vfw;
+  float* sQ = sm + C::oQ;
+  float* sC0 = sm + C::oC0;
+  float* sCh = sm + C::oCh;
+  float* sB = sm + C::oB;
+  float* sM = sm + C::oM;
+  float* sA = sm + C::oA;
+  float* sH = sm + C::oH;
+  float* sPart = sm + C::oPart;
+  const float* tb = a.tables;
+  const float dt = a.dt;
+  if (TSM) {
+    copy_to_smem(sm + C::oVvT, tb + T.VvT, L * NQP);
+    copy_to_smem(sm + C::oVw, tb + T.Vw, NQ * LP);
+    copy_to_smem(sm + C::oKtB, tb + T.KtB, 3 * L * LP);
+    copy_to_smem(sm + C::oVfw, tb + T.Vfw, 4 * NF * LP);
+  }
+  float tz[NT], gz[NT];
+#pragma unroll
+  for (int z = 0; z < NT; ++z) {
+    tz[z] = __ldg(tb + T.tz + z) * dt;
+    gz[z] = __ldg(tb + T.gz + z) * dt;
   }
 
-  // update
-  bool bad = false;
-  for (int w = threadIdx.x; w < ne * L * 10; w += blockDim.x) {
-    const int e = w / (L * 10), r = w - e * (L * 10);
-    const float v = sQ[e * QS + r] + sA[e * AS + r];
-    bad |= !isfinite(v);
-    a.q_out[(e0 + e) * QS + r] = v;
+  const int64_t ntiles = (a.E + TE - 1) / TE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * TE;
+    const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
+    __syncthreads();
+    {
+      const float4* src = reinterpret_cast<const float4*>(a.q_in + e0 * QS);
+      float4* dst = reinterpret_cast<float4*>(sQ);
+      for (int w = threadIdx.x; w < TE * QS / 4; w += blockDim.x)
+        dst[w] = w < ne * QS / 4 ? __ldg(src + w) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int w = threadIdx.x; w < TE * L * 10; w += blockDim.x) sA[w] = 0.f;
+    }
+    __syncthreads();
+    // coefficient arrays of the volume evaluation and the time-integrated velocity
+    for (int w = threadIdx.x; w < L * TE; w += blockDim.x) {
+      const int l = w / TE, e = w - l * TE;
+      const float* q = sQ + e * QS + l * 10;
+      const bool live = e < ne;
+      const float* de = a.d + (e0 + (live ? e : 0)) * DS;
+      float* c0 = sC0 + l * 8 * TE + e * 8;
+#pragma unroll
+      for (int p = 0; p < 6; ++p) c0[p] = q[p];
+      c0[6] = q[9];
+      c0[7] = live ? __ldg(de + AOFF + l) : 0.f;
+      float iv[3] = {dt * q[6], dt * q[7], dt * q[8]};
+      float c = dt;
+#pragma unroll
+      for (int o = 1; o <= N; ++o) {
+        c *= dt / static_cast<float>(o + 1);
+        if (l < n_modes(N - o)) {
+          const float* dd = de + d_offset(N, o) + l * 9;
+          float* ch = sCh + (row_hi(N, o) + l) * 8 * TE + e * 8;
+#pragma unroll
+          for (int p = 0; p < 6; ++p) ch[p] = live ? __ldg(dd + p) : 0.f;
+          ch[6] = ch[7] = 0.f;
+#pragma unroll
+          for (int m = 0; m < 3; ++m) iv[m] = fmaf(c, live ? __ldg(dd + 6 + m) : 0.f, iv[m]);
+        }
+      }
+#pragma unroll
+      for (int ep = 0; ep < 3; ++ep)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) sM[(ep * L + l) * NM + e * 3 + m] = iv[m];
+    }
+    __syncthreads();
+
+    // volume nodes: strains and damage in time, CDM stress and rate, time integral
+    constexpr int NPAIR = NQP / 2;
+    for (int w = threadIdx.x; w < TE * NPAIR; w += blockDim.x) {
+      const int e = w / NPAIR, j = w - e * NPAIR;
+      float a0[2][8];
+      float ah[N][2][6];
+#pragma unroll
+      for (int n = 0; n < 2; ++n) {
+#pragma unroll
+        for (int p = 0; p < 8; ++p) a0[n][p] = 0.f;
+#pragma unroll
+        for (int o = 0; o < N; ++o)
+#pragma unroll
+          for (int p = 0; p < 6; ++p) ah[o][n][p] = 0.f;
+      }
+#pragma unroll 5
+      for (int l = 0; l < L; ++l) {
+        const float2 ph = *reinterpret_cast<const float2*>(sVvT + l * NQP + 2 * j);
+        const float4 c0 = *reinterpret_cast<const float4*>(sC0 + l * 8 * TE + e * 8);
+        const float4 c1 = *reinterpret_cast<const float4*>(sC0 + l * 8 * TE + e * 8 + 4);
+        const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          a0[0][p] = fmaf(ph.x, cv[p], a0[0][p]);
+          a0[1][p] = fmaf(ph.y, cv[p], a0[1][p]);
+        }
+      }
+#pragma unroll
+      for (int o = 1; o <= N; ++o) {
+        const int rb = row_hi(N, o);
+#pragma unroll 4
+        for (int l = 0; l < n_modes(N - o); ++l) {
+          const float2 ph = *reinterpret_cast<const float2*>(sVvT + l * NQP + 2 * j);
+          const float4 c0 = *reinterpret_cast<const float4*>(sCh + (rb + l) * 8 * TE + e * 8);
+          const float2 c1 = *reinterpret_cast<const float2*>(sCh + (rb + l) * 8 * TE + e * 8 + 4);
+          const float cv[6] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y};
+#pragma unroll
+          for (int p = 0; p < 6; ++p) {
+            ah[o - 1][0][p] = fmaf(ph.x, cv[p], ah[o - 1][0][p]);
+            ah[o - 1][1][p] = fmaf(ph.y, cv[p], ah[o - 1][1][p]);
+          }
+        }
+      }
+      const bool live = e < ne;
+      const int64_t ge = e0 + (live ? e : 0);
+      const MatF m = a.mat[ge];
+      const float* ti = a.geom[ge].tinv;
+#pragma unroll
+      for (int n = 0; n < 2; ++n) {
+        const int q = 2 * j + n;
+        if (q >= NQ) continue;
+        float sb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, rb = 0.f;
+#pragma unroll
+        for (int z = 0; z < NT; ++z) {
+          float eps[6];
+#pragma unroll
+          for (int p = 0; p < 6; ++p) eps[p] = a0[n][p];
+          float c = 1.f;
+#pragma unroll
+          for (int o = 1; o <= N; ++o) {
+            c *= tz[z] / static_cast<float>(o);
+#pragma unroll
+            for (int p = 0; p < 6; ++p) eps[p] = fmaf(c, ah[o - 1][n][p], eps[p]);
+          }
+          const float alpha = fmaf(tz[z], a0[n][7], a0[n][6]);
+          float sig[6], r;
+          cdm_point(eps, alpha, m, sig, &r);
+#pragma unroll
+          for (int p = 0; p < 6; ++p) sb[p] = fmaf(gz[z], sig[p], sb[p]);
+          rb = fmaf(gz[z], r, rb);
+        }
+        // T_e'm = -(1/rho) sum_d Theta^{-1}_{e'd} sigma_md (time integrated) and the integrated rate
+        const float S[3][3] = {{sb[0], sb[3], sb[5]}, {sb[3], sb[1], sb[4]}, {sb[5], sb[4], sb[2]}};
+        float* bq = sB + q * NB + e * 10;
+#pragma unroll
+        for (int ep = 0; ep < 3; ++ep)
+#pragma unroll
+          for (int mc = 0; mc < 3; ++mc)
+            bq[ep * 3 + mc] =
+                live ? -m.rho_inv * (ti[ep * 3 + 0] * S[mc][0] + ti[ep * 3 + 1] * S[mc][1] + ti[ep * 3 + 2] * S[mc][2])
+                     : 0.f;
+        bq[9] = live ? rb : 0.f;
+      }
+    }
+    __syncthreads();
+    corrector_tail<N, TE, C::KS_PRJ, C::KS_FACE>(a, e0, ne, sVw, sKtB, sVfw, sQ, sM, sB, sA, sH, sPart);
   }
-  if (bad) atomicOr(a.status, kStatusNonFinite);
+}
+
+// ===========================================================================
+// Corrector with the volume evaluation on the tensor cores (degrees 2..4)
+// ===========================================================================
+// The Taylor expansion at the N+1 time nodes, U(t_z) = sum_i t_z^i/i! D^i, is
+// formed modally per element (columns (element, time node, eps_xx..eps_zx,
+// alpha, 0)); one tcgen05 GEMM with the basis table as the 128 x KP operand
+// gives every column at every volume node in TMEM, in 3xTF32 (TF32 high parts
+// and FP32 remainders of both operands: FP32-level accuracy).  Thread q of
+// warps w and w+4 owns TMEM lane (volume node) q and reads its columns.
+template <int N>
+struct CorrTcCfg : Dim<N> {
+  using D = Dim<N>;
+  static constexpr int TE = 4;
+  static constexpr int THREADS = 256;
+  static constexpr int KP = tc_kp(N);
+  static constexpr int NCOL = D::NT * 8;                   // columns per element
+  static constexpr int NBC = TE * NCOL;                    // MMA N
+  static constexpr int TMEM_COLS = NBC <= 32 ? 32 : (NBC <= 64 ? 64 : (NBC <= 128 ? 128 : 256));
+  static constexpr int NV = 3 * TE, NB = 10 * TE, NM = 2 * NV, NFC = 9 * TE;
+  static constexpr int KS_PRJ = N >= 4 ? 2 : 1, KS_FACE = N >= 4 ? 2 : 1;
+  static constexpr int oPhiH = 0;
+  static constexpr int oPhiL = oPhiH + 128 * KP;
+  static constexpr int oVw = oPhiL + 128 * KP;
+  static constexpr int oKtB = round4(oVw + D::NQ * D::LP);
+  static constexpr int oVfw = round4(oKtB + 3 * D::L * D::LP);
+  static constexpr int oBeH = round4(oVfw + 4 * D::NF * D::LP);   // [NBC x KP] canonical
+  static constexpr int oBeL = oBeH + NBC * KP;
+  static constexpr int oQ = oBeL + NBC * KP;
+  static constexpr int oM = oQ + TE * D::QS;
+  static constexpr int BN = D::NQ * NB, BF = 4 * D::NF * NFC;
+  static constexpr int oB = oM + 3 * D::L * NM;
+  static constexpr int oA = oB + round4(BN > BF ? BN : BF);
+  static constexpr int oH = oA + TE * D::L * 10;
+  static constexpr int P1 = KS_PRJ * D::LP * NB, P2 = KS_FACE * D::LP * NFC;
+  static constexpr int oPart = oH + 3 * D::LP * NM;
+  static constexpr int oDraw = oPart + (P1 > P2 ? P1 : P2);     // [TE][DS] predictor output
+  static constexpr int oFraw = oDraw + TE * D::DS;               // [TE][4][FFS] face fluxes
+  static constexpr int SMEM = oFraw + TE * 4 * D::FFS;
+  static_assert(D::NQ <= 128 && NBC % 16 == 0 && NBC <= 256, "tensor-core tile shape");
+  static_assert(SMEM * 4 <= 227 * 1024, "tensor-core corrector shared memory");
+};
+
+template <int N>
+__global__ void __launch_bounds__(256, 1) k_corrector_tc(StepArgs a) {
+  using C = CorrTcCfg<N>;
+  constexpr int L = C::L, NQ = C::NQ, NF = C::NF, NT = C::NT, LP = C::LP, QS = C::QS, DS = C::DS;
+  constexpr int AOFF = C::AOFF, TE = C::TE, KP = C::KP, NCOL = C::NCOL, NBC = C::NBC, NB = C::NB, NM = C::NM;
+  constexpr TableLayout T = table_layout(N);
+  constexpr int kWaitLimit = 1 << 24;
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  float* sPhiH = sm + C::oPhiH;
+  float* sPhiL = sm + C::oPhiL;
+  const float* sVw = sm + C::oVw;
+  const float* sKtB = sm + C::oKtB;
+  const float* sVfw = sm + C::oVfw;
+  float* sBeH = sm + C::oBeH;
+  float* sBeL = sm + C::oBeL;
+  float* sQ = sm + C::oQ;
+  float* sM = sm + C::oM;
+  float* sB = sm + C::oB;
+  float* sA = sm + C::oA;
+  float* sH = sm + C::oH;
+  float* sPart = sm + C::oPart;
+  float* sDraw = sm + C::oDraw;
+  float* sFraw = sm + C::oFraw;
+  constexpr int FFS = C::FFS;
+  const float* tb = a.tables;
+  const float dt = a.dt;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  copy_to_smem(sPhiH, tb + T.PhiH, 128 * KP);
+  copy_to_smem(sPhiL, tb + T.PhiL, 128 * KP);
+  copy_to_smem(sm + C::oVw, tb + T.Vw, NQ * LP);
+  copy_to_smem(sm + C::oKtB, tb + T.KtB, 3 * L * LP);
+  copy_to_smem(sm + C::oVfw, tb + T.Vfw, 4 * NF * LP);
+  float tz[NT], gz[NT];
+#pragma unroll
+  for (int z = 0; z < NT; ++z) {
+    tz[z] = __ldg(tb + T.tz + z) * dt;
+    gz[z] = __ldg(tb + T.gz + z) * dt;
+  }
+  if (warp == 0) tc::alloc(&tmem_base, C::TMEM_COLS);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base;
+  uint32_t phase = 0;
+  bool failed = false;
+
+  const int64_t ntiles = (a.E + TE - 1) / TE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * TE;
+    const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
+    __syncthreads();
+    // one batch of asynchronous copies: state, predictor output and face fluxes of the tile
+    for (int w = tid; w < ne * QS / 4; w += blockDim.x) tc::cp_async16(sQ + 4 * w, a.q_in + e0 * QS + 4 * w);
+    for (int w = tid; w < ne * DS / 4; w += blockDim.x) tc::cp_async16(sDraw + 4 * w, a.d + e0 * DS + 4 * w);
+    for (int w = tid; w < ne * FFS; w += blockDim.x) {     // ne * 4 faces * FFS/4 chunks
+      const int e = w / FFS, r = w - e * FFS;
+      const int f = r / (FFS / 4), c = r - f * (FFS / 4);
+      const int64_t fid = a.elem_face[(e0 + e) * 4 + f] >> 1;
+      tc::cp_async16(sFraw + (e * 4 + f) * FFS + 4 * c, a.ff + fid * FFS + 4 * c);
+    }
+    for (int w = ne * QS + tid; w < TE * QS; w += blockDim.x) sQ[w] = 0.f;
+    for (int w = tid; w < TE * L * 10; w += blockDim.x) sA[w] = 0.f;
+    tc::cp_async_wait_all();
+    __syncthreads();
+    // Taylor expansion at the time nodes (GEMM operand) and time-integrated velocity
+    for (int w = tid; w < KP * TE; w += blockDim.x) {
+      const int l = w / TE, e = w - l * TE;
+      float u[NT][7];
+#pragma unroll
+      for (int z = 0; z < NT; ++z)
+#pragma unroll
+        for (int p = 0; p < 7; ++p) u[z][p] = 0.f;
+      float iv[3] = {0.f, 0.f, 0.f};
+      if (l < L && e < ne) {
+        const float* q = sQ + e * QS + l * 10;
+        const float* de = sDraw + e * DS;
+        const float a1 = de[AOFF + l];
+#pragma unroll
+        for (int z = 0; z < NT; ++z) {
+#pragma unroll
+          for (int p = 0; p < 6; ++p) u[z][p] = q[p];
+          u[z][6] = fmaf(tz[z], a1, q[9]);
+        }
+        iv[0] = dt * q[6];
+        iv[1] = dt * q[7];
+        iv[2] = dt * q[8];
+        float ci = dt;
+#pragma unroll
+        for (int o = 1; o <= N; ++o) {
+          ci *= dt / static_cast<float>(o + 1);
+          if (l < n_modes(N - o)) {
+            const float* dd = de + d_offset(N, o) + l * 9;
+            float dv[9];
+#pragma unroll
+            for (int p = 0; p < 9; ++p) dv[p] = dd[p];
+#pragma unroll
+            for (int z = 0; z < NT; ++z) {
+              float c = 1.f;
+#pragma unroll
+              for (int j = 1; j <= o; ++j) c *= tz[z] / static_cast<float>(j);
+#pragma unroll
+              for (int p = 0; p < 6; ++p) u[z][p] = fmaf(c, dv[p], u[z][p]);
+            }
+#pragma unroll
+            for (int m = 0; m < 3; ++m) iv[m] = fmaf(ci, dv[6 + m], iv[m]);
+          }
+        }
+      }
+#pragma unroll
+      for (int z = 0; z < NT; ++z)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float x = c < 7 ? u[z][c] : 0.f;
+          const float h = tc::tf32_hi(x);
+          const int idx = tc_canon(e * NCOL + z * 8 + c, l, KP);
+          sBeH[idx] = h;
+          sBeL[idx] = x - h;
+        }
+      if (l < L) {
+#pragma unroll
+        for (int ep = 0; ep < 3; ++ep)
+#pragma unroll
+          for (int m = 0; m < 3; ++m) sM[(ep * L + l) * NM + e * 3 + m] = iv[m];
+      }
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      constexpr uint32_t idesc = tc::idesc_tf32(128, NBC);
+      const uint32_t aH = tc::smem_u32(sPhiH), aL = tc::smem_u32(sPhiL);
+      const uint32_t bH = tc::smem_u32(sBeH), bL = tc::smem_u32(sBeL);
+#pragma unroll
+      for (int ks = 0; ks < KP / 8; ++ks) {
+        const uint32_t off = ks * 256;   // 8 K-elements = 2 core matrices
+        tc::mma_tf32(tmem, tc::desc_kmajor(aH + off, KP), tc::desc_kmajor(bH + off, KP), idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32(tmem, tc::desc_kmajor(aH + off, KP), tc::desc_kmajor(bL + off, KP), idesc, 1u);
+        tc::mma_tf32(tmem, tc::desc_kmajor(aL + off, KP), tc::desc_kmajor(bH + off, KP), idesc, 1u);
+      }
+      tc::commit(&mbar);
+    }
+    const bool ok = tc::wait_parity(&mbar, phase, kWaitLimit);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after();
+    // volume nodes: CDM stress and rate at the time nodes, time integral
+    {
+      const int q = 32 * (warp & 3) + lane;
+      const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
+#pragma unroll 1
+      for (int ei = 0; ei < TE / 2; ++ei) {
+        const int e = (warp >> 2) * (TE / 2) + ei;
+        float v[NCOL];
+        tc::ld_cols<NCOL>(tmem + lane_base + e * NCOL, v);
+        tc::wait_ld();
+        if (q < NQ) {
+          const bool live = e < ne;
+          const int64_t ge = e0 + (live ? e : 0);
+          const MatF m = a.mat[ge];
+          const float* ti = a.geom[ge].tinv;
+          float sb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, rb = 0.f;
+#pragma unroll
+          for (int z = 0; z < NT; ++z) {
+            float sig[6], r;
+            cdm_point(v + z * 8, v[z * 8 + 6], m, sig, &r);
+#pragma unroll
+            for (int p = 0; p < 6; ++p) sb[p] = fmaf(gz[z], sig[p], sb[p]);
+            rb = fmaf(gz[z], r, rb);
+          }
+          const float S[3][3] = {{sb[0], sb[3], sb[5]}, {sb[3], sb[1], sb[4]}, {sb[5], sb[4], sb[2]}};
+          float* bq = sB + q * NB + e * 10;
+#pragma unroll
+          for (int ep = 0; ep < 3; ++ep)
+#pragma unroll
+            for (int mc = 0; mc < 3; ++mc)
+              bq[ep * 3 + mc] =
+                  live ? -m.rho_inv * (ti[ep * 3 + 0] * S[mc][0] + ti[ep * 3 + 1] * S[mc][1] + ti[ep * 3 + 2] * S[mc][2])
+                       : 0.f;
+          bq[9] = live ? rb : 0.f;
+        }
+      }
+    }
+    tc::fence_before();
+    __syncthreads();
+    corrector_tail<N, TE, C::KS_PRJ, C::KS_FACE>(a, e0, ne, sVw, sKtB, sVfw, sQ, sM, sB, sA, sH, sPart, sFraw);
+  }
+  if (failed) {
+    if (tid == 0) atomicOr(a.status, kStatusTimeout);
+    tc::wait_parity(&mbar, phase ^ 1u, kWaitLimit);   // let the MMAs in flight finish before freeing TMEM
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::dealloc(tmem, C::TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
+template <class Cfg, class Kern>
+cudaError_t launch_persistent(Kern kern, int64_t tiles, int grid_hint, const StepArgs& a, cudaStream_t s,
+                              bool* configured, int* max_blocks) {
+  const size_t smem = sizeof(float) * Cfg::SMEM;
+  if (!*configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, smem);
+    if (e != cudaSuccess) return e;
+    *max_blocks = per_sm > 0 ? per_sm : 1;
+    *configured = true;
+  }
+  int64_t grid = grid_hint > 0 ? static_cast<int64_t>(grid_hint) * *max_blocks : tiles;
+  if (grid > tiles) grid = tiles;
+  if (grid < 1) grid = 1;
+  kern<<<static_cast<unsigned>(grid), Cfg::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Kernel variants (bit 0: predictor with shared-memory tables on a persistent
+// grid; bit 1: face kernel likewise; bit 2: SIMT corrector likewise; bit 3:
+// SIMT corrector instead of the tensor-core one).  Clear bits read the tables
+// through the L1 cache with one CTA per tile.  The default is the fastest
+// measured combination on GB300; DG_KERNEL_VARIANT overrides it for tuning.
+inline int table_residency_mask() {
+  static int mask = -1;
+  if (mask < 0) {
+    const char* s = getenv("DG_KERNEL_VARIANT");
+    mask = s ? atoi(s) : 1;
+  }
+  return mask;
 }
 
 template <int N>
 cudaError_t launch_predictor_impl(const StepArgs& a, cudaStream_t s) {
-  using Dm = Dims<N>;
-  const size_t smem = sizeof(float) * Dm::PRED_SMEM;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_predictor<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
+  static bool cfg[2] = {false, false};
+  static int blocks[2] = {1, 1};
+  const int64_t tiles = (a.E + PredCfg<N, true>::TE - 1) / PredCfg<N, true>::TE;
+  if constexpr (PredCfg<N, true>::FITS) {
+    if (table_residency_mask() & 1)
+      return launch_persistent<PredCfg<N, true>>(k_predictor<N, true>, tiles, a.grid_pred, a, s, &cfg[1], &blocks[1]);
   }
-  const int64_t blocks = (a.E + Dm::TE - 1) / Dm::TE;
-  k_predictor<N><<<static_cast<unsigned>(blocks), 128, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_persistent<PredCfg<N, false>>(k_predictor<N, false>, tiles, 0, a, s, &cfg[0], &blocks[0]);
+}
+
+template <int N>
+cudaError_t launch_faces_impl(const StepArgs& a, cudaStream_t s) {
+  static bool cfg[2] = {false, false};
+  static int blocks[2] = {1, 1};
+  const int64_t tiles = (a.F + FaceCfg<N, true>::TF - 1) / FaceCfg<N, true>::TF;
+  if constexpr (FaceCfg<N, true>::FITS) {
+    if (table_residency_mask() & 2)
+      return launch_persistent<FaceCfg<N, true>>(k_faces<N, true>, tiles, a.grid_face, a, s, &cfg[1], &blocks[1]);
+  }
+  return launch_persistent<FaceCfg<N, false>>(k_faces<N, false>, tiles, 0, a, s, &cfg[0], &blocks[0]);
 }
 
 template <int N>
 cudaError_t launch_corrector_impl(const StepArgs& a, cudaStream_t s) {
-  using Dm = Dims<N>;
-  const size_t smem = sizeof(float) * Dm::CORR_SMEM;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_corrector<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
+  static bool cfg[3] = {false, false, false};
+  static int blocks[3] = {1, 1, 1};
+  if constexpr (tc_volume(N)) {
+    if (!(table_residency_mask() & 8)) {
+      const int64_t tiles = (a.E + CorrTcCfg<N>::TE - 1) / CorrTcCfg<N>::TE;
+      return launch_persistent<CorrTcCfg<N>>(k_corrector_tc<N>, tiles, a.grid_corr > 0 ? a.grid_corr : 148, a, s,
+                                             &cfg[2], &blocks[2]);
+    }
   }
-  const int64_t blocks = (a.E + Dm::TE - 1) / Dm::TE;
-  k_corrector<N><<<static_cast<unsigned>(blocks), 128, smem, s>>>(a);
-  return cudaGetLastError();
+  const int64_t tiles = (a.E + CorrCfg<N, true>::TE - 1) / CorrCfg<N, true>::TE;
+  if constexpr (CorrCfg<N, true>::FITS) {
+    if (table_residency_mask() & 4)
+      return launch_persistent<CorrCfg<N, true>>(k_corrector<N, true>, tiles, a.grid_corr, a, s, &cfg[1], &blocks[1]);
+  }
+  return launch_persistent<CorrCfg<N, false>>(k_corrector<N, false>, tiles, 0, a, s, &cfg[0], &blocks[0]);
 }
 
 }  // namespace dg
@@ -531,6 +1168,9 @@ cudaError_t launch_corrector_impl(const StepArgs& a, cudaStream_t s) {
   namespace dg {                                                                                \
   template <> cudaError_t launch_predictor_t<N>(const StepArgs& a, cudaStream_t s) {           \
     return launch_predictor_impl<N>(a, s);                                                      \
+  }                                                                                             \
+  template <> cudaError_t launch_faces_t<N>(const StepArgs& a, cudaStream_t s) {               \
+    return launch_faces_impl<N>(a, s);                                                          \
   }                                                                                             \
   template <> cudaError_t launch_corrector_t<N>(const StepArgs& a, cudaStream_t s) {           \
     return launch_corrector_impl<N>(a, s);                                                      \

@@ -287,8 +287,8 @@ class Solver:
         self._chk(self.lib.dg_profile_enable(self.ctx, int(on)))
 
     def profile_read(self):
-        out = (KernelTime * 4)()
+        out = (KernelTime * 5)()
         n = C.c_int(0)
-        self._chk(self.lib.dg_profile_read(self.ctx, out, 4, C.byref(n)))
-        names = ("predictor", "corrector", "source", "receivers")
+        self._chk(self.lib.dg_profile_read(self.ctx, out, 5, C.byref(n)))
+        names = ("predictor", "corrector", "source", "receivers", "faces")
         return {names[k]: {"launches": out[k].launches, "total_ms": out[k].total_ms} for k in range(n.value)}

@@ -176,7 +176,8 @@ def test_zero_state_and_empty_calls():
     assert np.all(q == 0.0)
     assert t == pytest.approx(5 * s.dt)
     st = s.stats()
-    assert st["steps"] == 5 and st["kernel_launches"] == 10 and st["element_updates"] == 5 * mesh.n_elem
+    # predictor, face fluxes and corrector per step
+    assert st["steps"] == 5 and st["kernel_launches"] == 15 and st["element_updates"] == 5 * mesh.n_elem
 
 
 def test_status_nonfinite_and_nonhyperbolic():
@@ -219,6 +220,7 @@ def test_profile_counts_kernels():
     s.step(7)
     p = s.profile_read()
     assert p["predictor"]["launches"] == 7 and p["corrector"]["launches"] == 7
+    assert p["faces"]["launches"] == 7
     assert p["source"]["launches"] == 7 and p["receivers"]["launches"] == 7
-    assert p["corrector"]["total_ms"] > 0
-    assert s.stats()["kernel_launches"] == 28
+    assert p["corrector"]["total_ms"] > 0 and p["faces"]["total_ms"] > 0
+    assert s.stats()["kernel_launches"] == 35
