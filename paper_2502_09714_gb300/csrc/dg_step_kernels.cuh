@@ -568,7 +568,7 @@ template <int N, int TE, int KS_PRJ, int KS_FACE>
 __device__ __forceinline__ void corrector_tail(const StepArgs& a, int64_t e0, int ne, const float* sVw,
                                                const float* sKtB, const float* sVfw, const float* sQ, float* sM,
                                                float* sB, float* sA, float* sH, float* sPart,
-                                               const float* sFraw = nullptr) {
+                                               const float* sFraw = nullptr, const float* sGeo = nullptr) {
   using D = Dim<N>;
   constexpr int L = D::L, NQ = D::NQ, NF = D::NF, LP = D::LP, QS = D::QS, FFS = D::FFS;
   constexpr int NV = 3 * TE, NB = 10 * TE, NM = 2 * NV, NFC = 9 * TE;
@@ -617,11 +617,14 @@ __device__ __forceinline__ void corrector_tail(const StepArgs& a, int64_t e0, in
       const int i = r2 / 9, p = r2 - 9 * i;
       float v = 0.f;
       if (e < ne) {
-        const int64_t ge = e0 + e;
-        const int ef = a.elem_face[ge * 4 + f];
-        const float sc = a.geom[ge].face[f][3] * ((ef & 1) ? -1.f : 1.f);
-        v = sc * (sFraw ? sFraw[(e * 4 + f) * FFS + i * 9 + p]
-                        : __ldg(a.ff + static_cast<int64_t>(ef >> 1) * FFS + i * 9 + p));
+        if (sFraw) {
+          v = sGeo[e * 32 + 17 + f] * sFraw[(e * 4 + f) * FFS + i * 9 + p];
+        } else {
+          const int64_t ge = e0 + e;
+          const int ef = a.elem_face[ge * 4 + f];
+          const float sc = a.geom[ge].face[f][3] * ((ef & 1) ? -1.f : 1.f);
+          v = sc * __ldg(a.ff + static_cast<int64_t>(ef >> 1) * FFS + i * 9 + p);
+        }
       }
       sB[(f * NF + i) * NFC + e * 9 + p] = v;
     }
@@ -629,7 +632,7 @@ __device__ __forceinline__ void corrector_tail(const StepArgs& a, int64_t e0, in
     // strain rows -(v_i d_j phi + v_j d_i phi)/2 and velocity rows from the modal derivatives
     for (int w = threadIdx.x; w < TE * L; w += blockDim.x) {
       const int e = w / L, k = w - e * L;
-      const float* ti = a.geom[e0 + (e < ne ? e : 0)].tinv;
+      const float* ti = sGeo ? sGeo + e * 32 : a.geom[e0 + (e < ne ? e : 0)].tinv;
       float hd[3][3];
 #pragma unroll
       for (int d = 0; d < 3; ++d)
@@ -852,7 +855,8 @@ template <int N>
 struct CorrTcCfg : Dim<N> {
   using D = Dim<N>;
   static constexpr int TE = 4;
-  static constexpr int THREADS = 256;
+  static constexpr int THREADS = 512;
+  static constexpr int GROUPS = THREADS / 128;             // warp groups reading TMEM (4 warps each)
   static constexpr int KP = tc_kp(N);
   static constexpr int NCOL = D::NT * 8;                   // columns per element
   static constexpr int NBC = TE * NCOL;                    // MMA N
@@ -876,13 +880,14 @@ struct CorrTcCfg : Dim<N> {
   static constexpr int oPart = oH + 3 * D::LP * NM;
   static constexpr int oDraw = oPart + (P1 > P2 ? P1 : P2);     // [TE][DS] predictor output
   static constexpr int oFraw = oDraw + TE * D::DS;               // [TE][4][FFS] face fluxes
-  static constexpr int SMEM = oFraw + TE * 4 * D::FFS;
+  static constexpr int oGeo = oFraw + TE * 4 * D::FFS;           // [TE][32]: Theta^{-1}, material, face scales
+  static constexpr int SMEM = oGeo + TE * 32;
   static_assert(D::NQ <= 128 && NBC % 16 == 0 && NBC <= 256, "tensor-core tile shape");
   static_assert(SMEM * 4 <= 227 * 1024, "tensor-core corrector shared memory");
 };
 
 template <int N>
-__global__ void __launch_bounds__(256, 1) k_corrector_tc(StepArgs a) {
+__global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepArgs a) {
   using C = CorrTcCfg<N>;
   constexpr int L = C::L, NQ = C::NQ, NF = C::NF, NT = C::NT, LP = C::LP, QS = C::QS, DS = C::DS;
   constexpr int AOFF = C::AOFF, TE = C::TE, KP = C::KP, NCOL = C::NCOL, NBC = C::NBC, NB = C::NB, NM = C::NM;
@@ -907,6 +912,7 @@ __global__ void __launch_bounds__(256, 1) k_corrector_tc(StepArgs a) {
   float* sPart = sm + C::oPart;
   float* sDraw = sm + C::oDraw;
   float* sFraw = sm + C::oFraw;
+  float* sGeo = sm + C::oGeo;
   constexpr int FFS = C::FFS;
   const float* tb = a.tables;
   const float dt = a.dt;
@@ -947,6 +953,23 @@ __global__ void __launch_bounds__(256, 1) k_corrector_tc(StepArgs a) {
     }
     for (int w = ne * QS + tid; w < TE * QS; w += blockDim.x) sQ[w] = 0.f;
     for (int w = tid; w < TE * L * 10; w += blockDim.x) sA[w] = 0.f;
+    // per element: Theta^{-1} [0,9), material [9,17), signed |S_f|/|J| [17,21)
+    for (int w = tid; w < TE * 21; w += blockDim.x) {
+      const int e = w / 21, c = w - 21 * e;
+      float v = 0.f;
+      if (e < ne) {
+        const int64_t ge = e0 + e;
+        if (c < 9) {
+          v = a.geom[ge].tinv[c];
+        } else if (c < 17) {
+          v = reinterpret_cast<const float*>(a.mat + ge)[c - 9];
+        } else {
+          const int f = c - 17;
+          v = a.geom[ge].face[f][3] * ((a.elem_face[ge * 4 + f] & 1) ? -1.f : 1.f);
+        }
+      }
+      sGeo[e * 32 + c] = v;
+    }
     tc::cp_async_wait_all();
     __syncthreads();
     // Taylor expansion at the time nodes (GEMM operand) and time-integrated velocity
@@ -1039,16 +1062,18 @@ __global__ void __launch_bounds__(256, 1) k_corrector_tc(StepArgs a) {
       const int q = 32 * (warp & 3) + lane;
       const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
 #pragma unroll 1
-      for (int ei = 0; ei < TE / 2; ++ei) {
-        const int e = (warp >> 2) * (TE / 2) + ei;
+      for (int ei = 0; ei < TE / C::GROUPS; ++ei) {
+        const int e = (warp >> 2) * (TE / C::GROUPS) + ei;
         float v[NCOL];
         tc::ld_cols<NCOL>(tmem + lane_base + e * NCOL, v);
         tc::wait_ld();
         if (q < NQ) {
           const bool live = e < ne;
-          const int64_t ge = e0 + (live ? e : 0);
-          const MatF m = a.mat[ge];
-          const float* ti = a.geom[ge].tinv;
+          const float* gm = sGeo + e * 32;
+          MatF m;
+          m.rho = gm[9]; m.lam0 = gm[10]; m.mu0 = gm[11]; m.gamma_r = gm[12];
+          m.xi0 = gm[13]; m.cd = gm[14]; m.rho_inv = gm[15]; m.pad = 0.f;
+          const float* ti = gm;
           float sb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, rb = 0.f;
 #pragma unroll
           for (int z = 0; z < NT; ++z) {
@@ -1073,7 +1098,7 @@ __global__ void __launch_bounds__(256, 1) k_corrector_tc(StepArgs a) {
     }
     tc::fence_before();
     __syncthreads();
-    corrector_tail<N, TE, C::KS_PRJ, C::KS_FACE>(a, e0, ne, sVw, sKtB, sVfw, sQ, sM, sB, sA, sH, sPart, sFraw);
+    corrector_tail<N, TE, C::KS_PRJ, C::KS_FACE>(a, e0, ne, sVw, sKtB, sVfw, sQ, sM, sB, sA, sH, sPart, sFraw, sGeo);
   }
   if (failed) {
     if (tid == 0) atomicOr(a.status, kStatusTimeout);
