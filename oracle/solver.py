@@ -15,7 +15,9 @@ One step from t_n to t_{n+1} = t_n + dt, in the order of Appendix A:
   8. Rusanov flux (Eq. "rusanov-flux") at the face space-time nodes
      (Eq. "2nd term"), neighbour trace taken at the same physical point by
      inverting the neighbour's affine map, C = max of the two cells'
-     effective P speeds (reading R3), no flux on alpha (reading R6);
+     effective P speeds (reading R3), no flux on alpha (reading R6); on
+     boundary faces the absorbing or free-surface flux of Appendix A
+     ("Free surface and absorbing boundary conditions", oracle/boundary.py);
   9. update of Eq. "time-integrated" with M = I (orthonormal basis).
 Point sources enter step 9 as strain-rate deltas; receivers sample velocity.
 
@@ -30,6 +32,7 @@ import math
 import numpy as np
 
 from .basis import eval_basis, mode_list, n_modes
+from .boundary import boundary_matrix
 from .quadrature import gauss_legendre_01, tet_rule, tri_rule
 from .rheology import (cdm_damage_rate, cdm_energy, effective_lame, flux,
                        invariants, jacobian_eff)
@@ -87,8 +90,8 @@ class Oracle:
         self.mat = np.asarray(material, dtype=np.float64).reshape(self.E, 6)
         self.face_bc = (np.zeros((self.E, 4), dtype=np.int8) if face_bc is None
                         else np.asarray(face_bc, dtype=np.int8)[rows, vorder])
-        if np.any(self.face_bc != 0):
-            raise NotImplementedError("boundary faces are not part of this oracle")
+        if np.any((self.face_bc < 0) | (self.face_bc > 2)):
+            raise MeshError("face tags must be 0 (interior), 1 (free surface) or 2 (absorbing)")
         self.cfl = cfl
         self._reference()
         self._geometry()
@@ -143,6 +146,9 @@ class Oracle:
         return float(np.min(self.cfl * 2.0 * self.r_in / ((2 * self.N + 1) * cp)))
 
     def _match_faces(self):
+        """Interior faces pair up by their vertex-id triple; a face tagged as a
+        boundary (free surface or absorbing) must belong to one element only
+        and keeps nbr = -1."""
         keys = {}
         for e in range(self.E):
             if len(set(self.vid[e].tolist())) != 4:
@@ -154,6 +160,11 @@ class Oracle:
         self.nbr_face = -np.ones((self.E, 4), dtype=np.int64)
         self.shift = np.zeros((self.E, 4, 3))
         for key, lst in keys.items():
+            tagged = [self.face_bc[e, f] != 0 for e, f in lst]
+            if any(tagged):
+                if len(lst) != 1:
+                    raise MeshError(f"boundary face {key} is shared by {len(lst)} element faces")
+                continue
             if len(lst) != 2 or lst[0][0] == lst[1][0]:
                 raise MeshError(f"face {key} is shared by {len(lst)} element faces")
             (e0, f0), (e1, f1) = lst
@@ -183,12 +194,14 @@ class Oracle:
             self.Vf_own[f] = eval_basis(self.N, xi)
             self.face_x[:, f] = (X[:, a, None] + s[None, :, None] * (X[:, b] - X[:, a])[:, None]
                                  + t[None, :, None] * (X[:, c] - X[:, a])[:, None])
-        self.Vf_nbr = np.empty((rows.size, 4, Nf, self.L))
+        self.Vf_nbr = np.zeros((rows.size, 4, Nf, self.L))
         for f in range(4):
             nb = self.nbr[rows, f]
-            xp = self.face_x[:, f] + self.shift[rows, f, None, :]         # in the neighbour's frame
-            xi_nb = np.einsum("ead,eqd->eqa", self.Jinv[nb], xp - self.xyz[nb, 0][:, None, :], optimize=True)
-            self.Vf_nbr[:, f] = eval_basis(self.N, xi_nb.reshape(-1, 3)).reshape(rows.size, Nf, self.L)
+            inner = nb >= 0                                               # boundary faces have no neighbour
+            nbi = nb[inner]
+            xp = self.face_x[inner, f] + self.shift[rows[inner], f, None, :]   # in the neighbour's frame
+            xi_nb = np.einsum("ead,eqd->eqa", self.Jinv[nbi], xp - self.xyz[nbi, 0][:, None, :], optimize=True)
+            self.Vf_nbr[inner, f] = eval_basis(self.N, xi_nb.reshape(-1, 3)).reshape(nbi.size, Nf, self.L)
 
     # ---------------- sources / receivers ----------------
     def locate(self, x, tol=1e-10):
@@ -230,7 +243,8 @@ class Oracle:
     # ---------------- the step ----------------
     def predictor(self, Q, rows):
         """Steps 1-5 for the elements in `rows`: Taylor coefficients D[i] of shape
-        [len(rows), L, 10], i = 0..N, and the effective P speed of each cell."""
+        [len(rows), L, 10], i = 0..N, the effective P speed of each cell and its
+        effective Lame parameters (lambda_eff, mu_eff)."""
         mat = self.mat[rows]
         Qr = Q[rows]
         ubar = Qr[:, 0, :] * PHI0                                         # 1. cell mean
@@ -249,17 +263,18 @@ class Oracle:
                 r = cdm_damage_rate(uq, mat[:, None, :])
                 Di[:, :, 9] += np.einsum("q,qk,nq->nk", self.qv_w, self.Vv, r, optimize=True)
             D.append(Di)
-        return np.stack(D, axis=0), cp
+        return np.stack(D, axis=0), cp, (lam, mu)
 
     def step(self, Q, dt, t=0.0, rows=None):
         """Advance Q[E,L,10] by dt; returns the new state (all elements, or only
         `rows` when given, as an array [len(rows),L,10])."""
         self.flag_nonhyperbolic = False
         out_rows = np.arange(self.E) if rows is None else np.asarray(rows, dtype=np.int64)
-        need = np.unique(np.concatenate([out_rows, self.nbr[out_rows].ravel()]))
+        nbrs = self.nbr[out_rows].ravel()
+        need = np.unique(np.concatenate([out_rows, nbrs[nbrs >= 0]]))
         pos = -np.ones(self.E, dtype=np.int64)
         pos[need] = np.arange(need.size)
-        D, cp = self.predictor(Q, need)
+        D, cp, (lam_eff, mu_eff) = self.predictor(Q, need)
         tz = self.qt_x * dt
         gz = self.qt_w * dt
         N = self.N
@@ -284,16 +299,24 @@ class Oracle:
             face = np.zeros((rr.size, self.L, 10))
             for f in range(4):
                 nb = self.nbr[rr, f]
+                inner = nb >= 0
+                nbs = np.where(inner, nb, rr)          # boundary rows: placeholder, replaced below
                 n = self.normal[rr, f]
                 um = np.einsum("il,nzlp->nzip", self.Vf_own[f], U[pr], optimize=True)
                 fr = self.row_of[rr]
                 if np.any(fr < 0):
                     raise ValueError("face tables were not built for some requested rows")
-                up = np.einsum("nil,nzlp->nzip", self.Vf_nbr[fr, f], U[pos[nb]], optimize=True)
+                up = np.einsum("nil,nzlp->nzip", self.Vf_nbr[fr, f], U[pos[nbs]], optimize=True)
                 Fm = np.einsum("nzidp,nd->nzip", flux(um, mat[:, None, None, :]), n, optimize=True)
-                Fp = np.einsum("nzidp,nd->nzip", flux(up, self.mat[nb][:, None, None, :]), n, optimize=True)
-                C = np.maximum(cp[pr], cp[pos[nb]])
+                Fp = np.einsum("nzidp,nd->nzip", flux(up, self.mat[nbs][:, None, None, :]), n, optimize=True)
+                C = np.maximum(cp[pr], cp[pos[nbs]])
                 Fs = 0.5 * (Fp + Fm) + 0.5 * C[:, None, None, None] * (um - up)
+                # boundary faces (Appendix A): flux matrix of the face applied to the own trace
+                for k in np.nonzero(~inner)[0]:
+                    e = rr[k]
+                    Mb = boundary_matrix(int(self.face_bc[e, f]), self.normal[e, f], lam_eff[pr[k]],
+                                         mu_eff[pr[k]], self.mat[e, 0])
+                    Fs[k] = np.einsum("pq,ziq->zip", Mb, um[k])
                 Fs[..., 9] = 0.0
                 face += self.area[rr, f][:, None, None] * np.einsum(
                     "z,i,ik,nzip->nkp", gz, self.qf_w, self.Vf_own[f], Fs, optimize=True)

@@ -6,7 +6,10 @@ neighbour search: every element carries a polynomial in the scaled monomials
 ((x - c)/h)^a, |a| <= N; mass matrices and exact integrals use a high-order
 Legendre/Duffy rule from numpy; the Cauchy-Kovalevskaya derivatives are taken
 by exact differentiation of the polynomials in physical space; neighbours are
-found geometrically (face vertex sets equal up to a periodic box translation).
+found geometrically (face vertex sets equal up to a periodic box translation);
+boundary faces use a closed-form characteristic flux in global coordinates
+(boundary_flux_closed_form) rather than the face rotation and eigenvector
+matrices the oracle builds.
 
 Quadrature nodes follow the method's convention: each element's reference
 map lists its vertices by increasing vertex id.  Only the pointwise law (stress, damage rate, effective Lame parameters,
@@ -101,12 +104,61 @@ def duffy_rule(n):
     return np.array(P), np.array(W)
 
 
+def boundary_flux_closed_form(bc, u, n, lam, mu, rho):
+    """Normal flux on a boundary face in global coordinates, derived here from
+    the characteristic decomposition of the effective isotropic Jacobian
+    instead of the face rotation and eigenvector matrices.
+
+    With tau = sigma n the traction (sigma from the effective Hooke law),
+    a = -v.n + c_p sigma_nn / (lambda + 2 mu) and the tangential vector
+    b = -v_tan / 2 + c_s (eps n)_tan:
+      free surface: the boundary state has zero traction and the incoming
+        characteristic amplitudes that achieve it, so the flux is the strain
+        part a n n^T + n b^T + b n^T and zero velocity flux;
+      absorbing: half of that strain part, and the velocity flux
+        (-sigma_nn / rho + c_p v.n) n / 2 + (-tau_tan / rho + c_s v_tan) / 2
+        (only the outgoing characteristics).
+    alpha has no flux.  u: [..., 10]; returns [..., 10]."""
+    u = np.asarray(u, float)
+    n = np.asarray(n, float)
+    cp, cs = math.sqrt((lam + 2 * mu) / rho), math.sqrt(mu / rho)
+    Em = u[..., SYM_IDX]                                   # [...,3,3]
+    v = u[..., 6:9]
+    I1 = Em[..., 0, 0] + Em[..., 1, 1] + Em[..., 2, 2]
+    En = Em @ n
+    enn = En @ n
+    snn = lam * I1 + 2 * mu * enn
+    vn = v @ n
+    vt = v - vn[..., None] * n
+    et = En - enn[..., None] * n
+    a = -vn + cp * snn / (lam + 2 * mu)
+    b = -0.5 * vt + cs * et
+    Fe = (a[..., None, None] * np.outer(n, n) + n[:, None] * b[..., None, :]
+          + b[..., :, None] * n[None, :])
+    F = np.zeros_like(u)
+    for p, (i, j) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (2, 0))):
+        F[..., p] = Fe[..., i, j]
+    if bc == 1:
+        return F
+    if bc != 2:
+        raise ValueError(bc)
+    F[..., 0:6] *= 0.5
+    F[..., 6:9] = (0.5 * (-snn / rho + cp * vn))[..., None] * n + 0.5 * (-2 * mu * et / rho + cs * vt)
+    return F
+
+
+SYM_IDX = np.array([[0, 3, 5], [3, 1, 4], [5, 4, 2]])
+
+
 class BruteForce:
-    def __init__(self, xyz, vid, N, mat, box):
+    def __init__(self, xyz, vid, N, mat, box, face_bc=None):
         # node placement convention of the method (reading R15): vertices by increasing id
         order = np.argsort(np.asarray(vid), axis=1, kind="stable")
-        self.xyz = np.asarray(xyz, float)[np.arange(len(order))[:, None], order]
+        rows = np.arange(len(order))[:, None]
+        self.xyz = np.asarray(xyz, float)[rows, order]
         self.E = self.xyz.shape[0]
+        self.face_bc = (np.zeros((self.E, 4), dtype=np.int8) if face_bc is None
+                        else np.asarray(face_bc)[rows, order])
         self.N = N
         self.mat = np.asarray(mat, float)
         self.box = np.asarray(box, float)
@@ -137,6 +189,8 @@ class BruteForce:
         keyed = {}
         for e in range(self.E):
             for f in range(4):
+                if self.face_bc[e, f] != 0:
+                    continue
                 vs = self.xyz[e, [v for v in range(4) if v != f]]
                 wrapped = np.mod(vs + 1e-6 * self.box, self.box)
                 key = tuple(sorted(tuple(np.round(w / self.box * 1e6).astype(int)) for w in wrapped))
@@ -164,11 +218,13 @@ class BruteForce:
         N, E = self.N, self.E
         taylor = []
         cp = np.empty(E)
+        lame = np.empty((E, 2))
         for e in range(E):
             p, mat = self.polys[e], self.mat[e]
             xq, W = self.hq[e]
             ubar = (W @ (p.values(xq) @ C[e])) / W.sum()
             lam, mu = effective_lame(ubar, mat)
+            lame[e] = lam, mu
             cp[e] = math.sqrt((lam + 2 * mu) / mat[0])
             B = jacobian_eff(np.array(lam), np.array(mu), np.array(mat[0]))
             Dm = [p.diff_matrix(d) for d in range(3)]
@@ -220,6 +276,10 @@ class BruteForce:
                 Vf = p.values(xf)
                 for tz, gz in zip(self.tx * dt, self.tw * dt):
                     um = u_at(e, xf, tz)
+                    if nb < 0:
+                        Fs = boundary_flux_closed_form(int(self.face_bc[e, f]), um, n, lame[e, 0], lame[e, 1], mat[0])
+                        rhs -= gz * Vf.T @ (Wf[:, None] * Fs)
+                        continue
                     up = u_at(nb, xf + self.shift[e, f], tz)
                     Fm = np.einsum("qdp,d->qp", flux(um, mat), n)
                     Fp = np.einsum("qdp,d->qp", flux(up, self.mat[nb]), n)
