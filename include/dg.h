@@ -85,8 +85,12 @@ typedef struct {
                                share an id.  Two element faces are neighbours iff their vertex-id
                                triples are equal.  The four ids of an element must differ. */
   const int8_t* face_bc;    /* [n_elem][4] tag of the face opposite local vertex f: 0 = interior
-                               or periodic (must be matched exactly once); other tags are
-                               rejected with DG_E_UNSUPPORTED by this build.  NULL = all 0. */
+                               or periodic (must be matched exactly once), 1 = free surface,
+                               2 = absorbing (Appendix A, "Free surface and absorbing boundary
+                               conditions"; must belong to this element only).  Boundary fluxes
+                               use the effective Lame parameters of the element's cell mean.
+                               Any other tag, a tagged face that is shared or an untagged face
+                               that is not matched is DG_E_MESH.  NULL = all 0. */
   int order;                /* polynomial degree N (1..5 compiled) */
   int members;              /* ensemble members; must be 1 in this build */
   double cfl;               /* Courant number of the default time step (see dg_dt) */
@@ -165,9 +169,9 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt);
  * 16 MiB that every GPU loading the library holds until the process exits, so
  * the mesh must satisfy n_elem*(2q + d) + 4*ceil(n_elem/4) + n_faces*f + 64
  * <= 4,194,304 floats with q = 4*ceil(10 L / 4), d the predictor size per
- * element and f = 4*ceil(9 (N+1)^2 / 4) (a closed mesh has n_faces = 2 n_elem:
- * 2,772 elements at N = 4, 9,868 at N = 2); larger meshes are rejected with
- * DG_E_ARG.
+ * element and f = 4*ceil(9 (N+1)^2 / 4), n_faces = interior faces + boundary
+ * faces (a mesh without boundary faces has n_faces = 2 n_elem: 2,772 elements
+ * at N = 4, 9,868 at N = 2); larger meshes are rejected with DG_E_ARG.
  * The first call on a device looks up that array's device address (with the
  * device current); make that first call before any stream capture.  Every
  * call reuses the same array, so calls whose work overlaps on the GPU (other

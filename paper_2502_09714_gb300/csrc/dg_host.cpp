@@ -65,7 +65,8 @@ struct dg_ctx {
   float* ff = nullptr;               // face fluxes
   int4* faces = nullptr;
   int* elem_face = nullptr;
-  int64_t F = 0;
+  int64_t F = 0;            // faces in the flux list: interior first, then boundary
+  int64_t F_interior = 0;
   int grid_pred = 0, grid_face = 0, grid_corr = 0;
   GeomF* geom = nullptr;
   MatF* matf = nullptr;
@@ -335,9 +336,8 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
   const int64_t E = desc->n_elem;
   if (desc->face_bc)
     for (int64_t i = 0; i < 4 * E; ++i)
-      if (desc->face_bc[i] != 0)
-        return fail(nullptr, desc->face_bc[i] == 1 || desc->face_bc[i] == 2 ? DG_E_UNSUPPORTED : DG_E_MESH,
-                    "boundary faces are not supported by this build (only interior/periodic)");
+      if (desc->face_bc[i] < 0 || desc->face_bc[i] > 2)
+        return fail(nullptr, DG_E_MESH, "face tags must be 0 (interior), 1 (free surface) or 2 (absorbing)");
 
   dg_ctx* ctx = new dg_ctx();
   ctx->N = desc->order;
@@ -353,6 +353,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
   ctx->detj.resize(E);
   ctx->rin.resize(E);
   std::vector<int64_t> vid_sorted(4 * E);
+  std::vector<int8_t> bc_sorted(4 * E, 0);
   std::vector<GeomF> geom(E);
   for (int64_t e = 0; e < E; ++e) {
     const int64_t* v = desc->elem_vid + 4 * e;
@@ -362,6 +363,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
       if (v[ord[j]] == v[ord[j + 1]]) { dg_destroy(ctx); return fail(nullptr, DG_E_MESH, "element " + std::to_string(e) + " repeats a vertex id"); }
     for (int j = 0; j < 4; ++j) {
       vid_sorted[4 * e + j] = v[ord[j]];
+      if (desc->face_bc) bc_sorted[4 * e + j] = desc->face_bc[4 * e + ord[j]];   // face j is opposite vertex j
       for (int c = 0; c < 3; ++c) ctx->xyz[12 * e + 3 * j + c] = desc->elem_xyz[12 * e + 3 * ord[j] + c];
     }
     const double* X = &ctx->xyz[12 * e];
@@ -404,9 +406,11 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
     ctx->rin[e] = 3.0 * (ctx->detj[e] / 6.0) / area_sum;
   }
 
-  // face matching by vertex-id triples (ascending in the sorted order)
+  // face matching by vertex-id triples (ascending in the sorted order); a tagged
+  // boundary face must belong to one element only (map value kBoundary)
   std::vector<int> nbr(4 * E, -1);
   {
+    constexpr int64_t kMatched = -1, kBoundary = -2;
     std::unordered_map<FaceKey, int64_t, FaceKeyHash> open;
     open.reserve(static_cast<size_t>(2 * E + 16));
     for (int64_t e = 0; e < E; ++e)
@@ -414,18 +418,23 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
         int a[3], n = 0;
         for (int j = 0; j < 4; ++j) if (j != f) a[n++] = j;
         FaceKey key{vid_sorted[4 * e + a[0]], vid_sorted[4 * e + a[1]], vid_sorted[4 * e + a[2]]};
+        const bool tagged = bc_sorted[4 * e + f] != 0;
         auto it = open.find(key);
         if (it == open.end()) {
-          open.emplace(key, 4 * e + f);
+          open.emplace(key, tagged ? kBoundary : 4 * e + f);
         } else {
           const int64_t other = it->second;
-          if (other < 0 || other / 4 == e) {
+          if (tagged || other == kBoundary) {
+            dg_destroy(ctx);
+            return fail(nullptr, DG_E_MESH, "boundary face of element " + std::to_string(e) + " is shared with another element");
+          }
+          if (other == kMatched || other / 4 == e) {
             dg_destroy(ctx);
             return fail(nullptr, DG_E_MESH, "face of element " + std::to_string(e) + " is shared more than twice or with itself");
           }
           nbr[4 * e + f] = static_cast<int>(other);                       // (elem << 2) | face
           nbr[other] = static_cast<int>(4 * e + f);
-          it->second = -1;
+          it->second = kMatched;
         }
       }
     for (const auto& kv : open)
@@ -435,19 +444,27 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
       }
   }
 
-  // face list: each interior face once, first seen from its lower-index element
+  // face list: each interior face once, first seen from its lower-index element;
+  // then the boundary faces as (element, face, -1, tag)
   std::vector<int4> faces;
   std::vector<int> elem_face(4 * E, -1);
   faces.reserve(static_cast<size_t>(2 * E));
   for (int64_t e = 0; e < E; ++e)
     for (int f = 0; f < 4; ++f) {
-      if (elem_face[4 * e + f] >= 0) continue;
+      if (elem_face[4 * e + f] >= 0 || bc_sorted[4 * e + f] != 0) continue;
       const int other = nbr[4 * e + f];
       const int64_t fid = static_cast<int64_t>(faces.size());
       faces.push_back(make_int4(static_cast<int>(e), f, other >> 2, other & 3));
       elem_face[4 * e + f] = static_cast<int>(fid << 1);
       elem_face[other] = static_cast<int>((fid << 1) | 1);
     }
+  ctx->F_interior = static_cast<int64_t>(faces.size());
+  for (int64_t e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f)
+      if (bc_sorted[4 * e + f] != 0) {
+        elem_face[4 * e + f] = static_cast<int>(static_cast<int64_t>(faces.size()) << 1);
+        faces.push_back(make_int4(static_cast<int>(e), f, -1, bc_sorted[4 * e + f]));
+      }
   ctx->F = static_cast<int64_t>(faces.size());
 
   // device allocation and upload

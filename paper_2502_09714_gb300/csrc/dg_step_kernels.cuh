@@ -5,7 +5,8 @@
 //                (Eq. "CKIter-ref-matrix") and damage-rate source at i = 1
 //                (Eq. "CKIter-ref-source")                       -> D, cp
 //   k_faces      Rusanov flux (Eq. "rusanov-flux") at the space-time nodes of
-//                every face, once per face, time-integrated      -> FF
+//                every interior face, once per face, time-integrated; absorbing
+//                and free-surface fluxes (Appendix A) on boundary faces -> FF
 //   k_corrector  volume flux and damage source (Eqs. "3rd term", "rhs term"),
 //                face term (Eq. "2nd term") from FF, update (Eq. "time-integrated")
 //
@@ -91,6 +92,65 @@ __device__ __forceinline__ void normal_flux(const float u[10], const MatF& m, co
   F[6] = -m.rho_inv * (sig[0] * n[0] + sig[3] * n[1] + sig[5] * n[2]);
   F[7] = -m.rho_inv * (sig[3] * n[0] + sig[1] * n[1] + sig[4] * n[2]);
   F[8] = -m.rho_inv * (sig[5] * n[0] + sig[4] * n[1] + sig[2] * n[2]);
+}
+
+// Effective Lame parameters at a cell mean (Eq. "effective-cdb" with the sign of
+// the xi0 term taken from Eq. "cdb-model"); q0 holds the ten mode-0 coefficients.
+__device__ __forceinline__ void effective_lame(const float* q0, const MatF& m, float* lam, float* mu) {
+  const float r6 = 2.449489742783178f;   // phi_0 = sqrt(6): cell mean = Q_0 sqrt(6)
+  float u[6];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) u[p] = q0[p] * r6;
+  const float alpha = q0[9] * r6;
+  const float I1 = u[0] + u[1] + u[2];
+  const float I2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + 2.f * (u[3] * u[3] + u[4] * u[4] + u[5] * u[5]);
+  const float xi = I2 > 1e-30f ? I1 * rsqrtf(I2) : 0.f;
+  *lam = m.lam0 - alpha * m.gamma_r * xi * (1.f / 3.f);
+  *mu = m.mu0 + alpha * m.xi0 * m.gamma_r - 0.5f * alpha * m.gamma_r * xi;
+}
+
+// Normal flux on a boundary face (Appendix A, Eqs. "absorbing-flux" and
+// "freeSurface-flux") written in global coordinates.  Characteristic analysis
+// of the effective isotropic Jacobian along n gives, with the traction
+// component sigma_nn = lambda I1 + 2 mu eps_nn, the tangential parts
+// v_tan = v - (v.n) n and e_tan = eps n - eps_nn n,
+//   a = -v.n + c_p sigma_nn / (lambda + 2 mu),   b = -v_tan / 2 + c_s e_tan:
+// free surface (bc 1): strain flux a n n^T + n b^T + b n^T, velocity flux 0
+//   (the boundary state is traction free);
+// absorbing (bc 2): half that strain flux and the velocity flux
+//   ((-sigma_nn / rho + c_p v.n) n + (-2 mu e_tan / rho + c_s v_tan)) / 2
+//   (only the outgoing characteristics).
+// k_p = c_p / (lambda + 2 mu).  The rotation into the face frame drops out, so
+// no tangent vectors are needed.
+__device__ __forceinline__ void boundary_flux(int bc, const float u[9], const float n[3], float lam, float mu,
+                                              float rho_inv, float cp, float cs, float k_p, float F[9]) {
+  const float En[3] = {u[0] * n[0] + u[3] * n[1] + u[5] * n[2], u[3] * n[0] + u[1] * n[1] + u[4] * n[2],
+                       u[5] * n[0] + u[4] * n[1] + u[2] * n[2]};
+  const float enn = En[0] * n[0] + En[1] * n[1] + En[2] * n[2];
+  const float snn = lam * (u[0] + u[1] + u[2]) + 2.f * mu * enn;
+  const float vn = u[6] * n[0] + u[7] * n[1] + u[8] * n[2];
+  const float a = -vn + k_p * snn;
+  float b[3], et[3], vt[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    vt[i] = u[6 + i] - vn * n[i];
+    et[i] = En[i] - enn * n[i];
+    b[i] = -0.5f * vt[i] + cs * et[i];
+  }
+  const float h = bc == 2 ? 0.5f : 1.f;
+  F[0] = h * (a * n[0] * n[0] + 2.f * n[0] * b[0]);
+  F[1] = h * (a * n[1] * n[1] + 2.f * n[1] * b[1]);
+  F[2] = h * (a * n[2] * n[2] + 2.f * n[2] * b[2]);
+  F[3] = h * (a * n[0] * n[1] + n[0] * b[1] + b[0] * n[1]);
+  F[4] = h * (a * n[1] * n[2] + n[1] * b[2] + b[1] * n[2]);
+  F[5] = h * (a * n[2] * n[0] + n[2] * b[0] + b[2] * n[0]);
+  if (bc == 2) {
+    const float pn = 0.5f * (-snn * rho_inv + cp * vn);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[6 + i] = pn * n[i] + 0.5f * (-2.f * mu * et[i] * rho_inv + cs * vt[i]);
+  } else {
+    F[6] = F[7] = F[8] = 0.f;
+  }
 }
 
 __device__ __forceinline__ void copy_to_smem(float* dst, const float* src, int n) {
@@ -223,15 +283,8 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
       const int e = threadIdx.x;
       const int64_t ge = e0 + e;
       const MatF m = a.mat[ge];
-      const float r6 = 2.449489742783178f;   // phi_0 = sqrt(6): cell mean = Q_0 sqrt(6)
-      float u[6];
-      for (int p = 0; p < 6; ++p) u[p] = sQ[e * QS + p] * r6;
-      const float alpha = sQ[e * QS + 9] * r6;
-      const float I1 = u[0] + u[1] + u[2];
-      const float I2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + 2.f * (u[3] * u[3] + u[4] * u[4] + u[5] * u[5]);
-      const float xi = I2 > 1e-30f ? I1 * rsqrtf(I2) : 0.f;
-      const float lam = m.lam0 - alpha * m.gamma_r * xi * (1.f / 3.f);
-      const float mu = m.mu0 + alpha * m.xi0 * m.gamma_r - 0.5f * alpha * m.gamma_r * xi;
+      float lam, mu;
+      effective_lame(sQ + e * QS, m, &lam, &mu);
       if (!(mu > 0.f) || !(lam + 2.f * mu > 0.f)) atomicOr(a.status, kStatusNonHyperbolic);
       a.cp[ge] = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * m.rho_inv);
       float* c = sCoef + e * 16;
@@ -347,7 +400,9 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
 }
 
 // ===========================================================================
-// Faces: Rusanov flux at the space-time nodes of each face, once per face
+// Faces: Rusanov flux at the space-time nodes of each interior face, once per
+// face; boundary faces (side 1 absent, tag in the fourth entry) take the
+// absorbing or free-surface flux
 // ===========================================================================
 template <int N, bool TSM>
 struct FaceCfg : Dim<N> {
@@ -390,8 +445,8 @@ __global__ void __launch_bounds__(128) k_faces(StepArgs a) {
       float v[12];
 #pragma unroll
       for (int p = 0; p < 12; ++p) v[p] = 0.f;
-      if (fc < nf) {
-        const int4 fa = a.faces[f0 + fc];
+      const int4 fa = fc < nf ? a.faces[f0 + fc] : make_int4(0, 0, -1, 0);
+      if (fc < nf && !(side && fa.z < 0)) {        // a boundary face has no side 1
         const int64_t e = side ? fa.z : fa.x;
         if (r < L) {
           const float* q = a.q_in + e * QS + r * 10;
@@ -424,7 +479,7 @@ __global__ void __launch_bounds__(128) k_faces(StepArgs a) {
       int lf = 0;
       if (fc < nf) {
         const int4 fa = a.faces[f0 + fc];
-        lf = side ? fa.w : fa.y;
+        lf = side ? (fa.z < 0 ? 0 : fa.w) : fa.y;
       }
       const int K = o == 0 ? L : n_modes(N - o);
       const int row0 = o == 0 ? 0 : L + row_hi(N, o);
@@ -464,7 +519,37 @@ __global__ void __launch_bounds__(128) k_faces(StepArgs a) {
       const int64_t em = fa.x, ep = fa.z;
       const GeomF* g = a.geom + em;
       const float n[3] = {g->face[fa.y][0], g->face[fa.y][1], g->face[fa.y][2]};
-      const MatF mm = a.mat[em], mp = a.mat[ep];
+      const MatF mm = a.mat[em];
+      if (ep < 0) {
+        // boundary face: the flux is linear in the own trace for the cell-mean moduli, so
+        // the trace is integrated in time first
+        float lam, mu;
+        effective_lame(sC + (fc * 2 * CROWS) * 12, mm, &lam, &mu);
+        const float cp = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * mm.rho_inv), cs = sqrtf(fmaxf(mu, 0.f) * mm.rho_inv);
+        const float k_p = lam + 2.f * mu > 0.f ? cp / (lam + 2.f * mu) : 0.f;
+        float ui[9];
+#pragma unroll
+        for (int p = 0; p < 9; ++p) ui[p] = 0.f;
+#pragma unroll
+        for (int z = 0; z < NT; ++z) {
+          const float tau = __ldg(tb + T.tz + z) * dt, gam = __ldg(tb + T.gz + z) * dt;
+          float c = gam;
+#pragma unroll
+          for (int o = 0; o <= N; ++o) {
+            if (o > 0) c *= tau / static_cast<float>(o);
+            const float* xm = sTr + (((fc * 2 + 0) * (N + 1) + o) * NFP + i) * 12;
+#pragma unroll
+            for (int p = 0; p < 9; ++p) ui[p] = fmaf(c, xm[p], ui[p]);
+          }
+        }
+        float Fb[9];
+        boundary_flux(fa.w, ui, n, lam, mu, mm.rho_inv, cp, cs, k_p, Fb);
+        float* out = a.ff + (f0 + fc) * FFS + i * 9;
+#pragma unroll
+        for (int p = 0; p < 9; ++p) out[p] = Fb[p];
+        continue;
+      }
+      const MatF mp = a.mat[ep];
       const float Cs = fmaxf(a.cp[em], a.cp[ep]);
       float tm[N + 1][9], tp[N + 1][9];
       float am0, am1, ap0, ap1;

@@ -14,9 +14,14 @@ TOL_ALPHA = 1e-5
 GROUPS = {"strain": slice(0, 6), "velocity": slice(6, 9)}
 
 
+def _tags(mesh):
+    bc = getattr(mesh, "face_bc", None)
+    return bc if bc is not None and np.any(bc != 0) else None
+
+
 def make_solver(mesh, material, order, cfl=0.5, sources=(), receivers=None, stream=None):
     import paper_2502_09714_gb300 as dgpkg
-    s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, order, cfl=cfl, stream=stream)
+    s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, order, face_bc=_tags(mesh), cfl=cfl, stream=stream)
     s.set_material(material)
     if sources:
         s.set_sources(list(sources))
@@ -26,7 +31,8 @@ def make_solver(mesh, material, order, cfl=0.5, sources=(), receivers=None, stre
 
 
 def make_oracle(mesh, material, order, cfl=0.5, sources=(), receivers=None, face_rows=None):
-    o = Oracle(mesh.elem_xyz, mesh.elem_vid, order, material, cfl=cfl, face_rows=face_rows)
+    o = Oracle(mesh.elem_xyz, mesh.elem_vid, order, material, face_bc=_tags(mesh), cfl=cfl,
+               face_rows=face_rows)
     if sources:
         o.set_sources(list(sources))
     if receivers is not None:

@@ -14,6 +14,7 @@ import paper_2502_09714_gb300 as dgpkg
 from paper_2502_09714_gb300.dg import EXPORTS, DGError
 from oracle import eval_basis, n_modes
 from synthetic import periodic_cube_mesh
+from synthetic.mesh import kuhn_box_mesh
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -107,11 +108,27 @@ def test_mesh_validation_errors_before_device_work(lib):
     with pytest.raises(DGError) as ei:
         dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, 2, members=4)
     assert ei.value.name == "DG_E_UNSUPPORTED"
+    # a tag on a shared face, and an unknown tag, are mesh errors
     bc = np.zeros((mesh.n_elem, 4), np.int8)
     bc[0, 0] = 2
     with pytest.raises(DGError) as ei:
         dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, 2, face_bc=bc)
-    assert ei.value.name == "DG_E_UNSUPPORTED"
+    assert ei.value.name == "DG_E_MESH"
+    bc[0, 0] = 3
+    with pytest.raises(DGError) as ei:
+        dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, 2, face_bc=bc)
+    assert ei.value.name == "DG_E_MESH"
+    # a closed box with tagged outer faces passes validation (on a machine
+    # without a GPU the first device allocation is what fails)
+    g = np.linspace(0.0, 4000.0, 3)
+    box = kuhn_box_mesh(g, g, g, periodic=(False, False, True), jitter=0.1)
+    try:
+        dgpkg.Solver(box.elem_xyz, box.elem_vid, 2, face_bc=box.face_bc)
+    except DGError as err:
+        assert err.name != "DG_E_MESH", str(err)
+    with pytest.raises(DGError) as ei:
+        dgpkg.Solver(box.elem_xyz, box.elem_vid, 2)       # outer faces untagged
+    assert ei.value.name == "DG_E_MESH"
     with pytest.raises(DGError) as ei:
         dgpkg.Solver(mesh.elem_xyz[:0], mesh.elem_vid[:0], 2)
     assert ei.value.name == "DG_E_ARG"
