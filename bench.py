@@ -23,6 +23,11 @@ import sys
 import threading
 import time
 
+# The CPU baseline (the FP64 oracle) runs on one host thread: BLAS thread pools
+# are pinned before numpy loads so that the reported core count is exact.
+for _var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_var, "1")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -150,10 +155,10 @@ def cpu_baseline(workload, steps=1, max_seconds=None):
     try:
         from threadpoolctl import threadpool_info
         threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:
-        threads = 1
+    except Exception:          # threadpoolctl absent: the pinned BLAS thread count
+        threads = int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
     sample = (f"{rows.size} elements (one z-layer of cells of the {mesh.n_elem}-tet mesh), "
-              f"{steps} step(s), numpy FP64; setup {setup:.1f}s excluded")
+              f"{steps} step(s), numpy FP64 with {threads} BLAS thread(s); setup {setup:.1f}s excluded")
     return rows.size * steps / el, sample, threads, el
 
 
@@ -290,7 +295,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config(w, args),
-        "roofline": {"kernel": f"k_{dom}<{N}>", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": _kernel_name(dom, N), "bound": "alu", "achieved": achieved,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
                      "traffic": traffic,
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (recipe unit counts, max clock)",
@@ -317,6 +322,16 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _kernel_name(kind, N):
+    """Name of the CUDA kernel that runs `kind` at degree N (the corrector's
+    volume evaluation runs on the tensor cores for 2 <= N <= 4 unless bit 3 of
+    DG_KERNEL_VARIANT selects the all-SIMT corrector)."""
+    variant = int(os.environ.get("DG_KERNEL_VARIANT", "1"))
+    if kind == "corrector" and 2 <= N <= 4 and not (variant & 8):
+        return f"k_corrector_tc<{N}>"
+    return f"k_{kind}<{N}>"
 
 
 def _kernel_source_digest():

@@ -607,6 +607,266 @@ __global__ void __launch_bounds__(128) k_faces(StepArgs a) {
 }
 
 // ===========================================================================
+// Faces, second form: persistent CTAs of 256 threads, two per SM.  Per tile of
+// TF faces: both sides' state and predictor output staged in shared memory by
+// one batch of asynchronous copies, with the per-face normal, speeds and
+// materials; the traces as register-tiled products with the face basis table
+// (G face nodes x 4 or 3 columns per thread, loops fully unrolled, warps 0-3
+// on order 0 and warps 4-7 on orders >= 1, whose mode counts add up to about
+// the same work); the flux at the face nodes with two threads per node, each
+// over half of the time nodes.
+// ===========================================================================
+template <int N>
+struct FluxCfg : Dim<N> {
+  using D = Dim<N>;
+  static constexpr int THREADS = 256;
+  static constexpr int G = N == 4 ? 5 : 4;                  // face nodes per trace tile
+  static constexpr int NG = (D::NF + G - 1) / G;            // node groups
+  static constexpr int NGG = NG * G;                        // padded face nodes
+  static constexpr int GP = G == 5 ? 8 : 4;                 // stride of a node group in the table
+  static constexpr int TF = 64 / (3 * NG);                  // faces per tile: 2 TF NG 3 <= 128 units per kind
+  static constexpr int UPK = 2 * TF * NG * 3;               // trace units per kind
+  static constexpr int RAW = D::QS + D::DS;                 // staged floats per side: state, predictor output
+  static constexpr int META = 28;                           // per face: n, |S|/|J|, cp-, cp+, tag, local faces, materials
+  static constexpr int oV = 0;                              // [4][L][NG][GP] phi_l at the face nodes
+  static constexpr int oRaw = round4(oV + 4 * D::L * NG * GP);   // [TF][2][RAW]
+  static constexpr int oMeta = oRaw + TF * 2 * RAW;         // [TF][META]
+  static constexpr int oTr = round4(oMeta + TF * META);     // [TF][2][N+1][NGG][12] traces per order
+  static constexpr int SMEM = oTr + TF * 2 * (N + 1) * NGG * 12;
+  static_assert(TF >= 1 && UPK <= 128, "trace units per kind");
+  static_assert(SMEM * 4 * 2 <= 227 * 1024, "two face CTAs per SM");
+};
+
+template <int N>
+__device__ __forceinline__ void load_group(const float* v, float* out) {
+  using C = FluxCfg<N>;
+  const float4 a = *reinterpret_cast<const float4*>(v);
+  out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+  if constexpr (C::G == 5) out[4] = v[4];
+}
+
+template <int N>
+__global__ void __launch_bounds__(256, 2) k_face_flux(StepArgs a) {
+  using C = FluxCfg<N>;
+  constexpr int L = C::L, NF = C::NF, NFP = C::NFP, NT = C::NT, QS = C::QS, DS = C::DS, AOFF = C::AOFF;
+  constexpr int FFS = C::FFS, TF = C::TF, G = C::G, NG = C::NG, NGG = C::NGG, GP = C::GP, RAW = C::RAW;
+  constexpr int META = C::META, UPK = C::UPK;
+  constexpr TableLayout T = table_layout(N);
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  float* sV = sm + C::oV;
+  float* sRaw = sm + C::oRaw;
+  float* sMeta = sm + C::oMeta;
+  float* sTr = sm + C::oTr;
+  const float* tb = a.tables;
+  const float dt = a.dt;
+  const int tid = threadIdx.x;
+  // face basis table regrouped by node groups (zero beyond the NF face nodes)
+  for (int w = tid; w < 4 * L * NG * GP; w += C::THREADS) {
+    const int n = w % GP, r = w / GP;
+    const int g = r % NG, r2 = r / NG;
+    const int l = r2 % L, lf = r2 / L;
+    const int node = g * G + n;
+    sV[w] = (n < G && node < NF) ? __ldg(tb + T.VfT + (lf * L + l) * NFP + node) : 0.f;
+  }
+
+  const int64_t ntiles = (a.F + TF - 1) / TF;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t f0 = tile * TF;
+    const int nf = static_cast<int>(min(static_cast<int64_t>(TF), a.F - f0));
+    __syncthreads();
+    // one batch of asynchronous copies: per face the normal, both cells' P speeds and
+    // materials; per side the state and the predictor output as stored
+    constexpr int CH = RAW / 4;                  // 16-byte chunks per side
+    for (int w = tid; w < TF * (2 * CH + 8); w += C::THREADS) {
+      const int fc = w / (2 * CH + 8), r = w - fc * (2 * CH + 8);
+      if (fc >= nf) continue;
+      const int4 fa = a.faces[f0 + fc];
+      const bool bnd = fa.z < 0;
+      if (r < 2 * CH) {
+        const int side = r / CH, ch = r - side * CH;
+        if (side && bnd) continue;
+        const int64_t e = side ? fa.z : fa.x;
+        float* dst = sRaw + (2 * fc + side) * RAW + 4 * ch;
+        if (ch < QS / 4) tc::cp_async16(dst, a.q_in + e * QS + 4 * ch);
+        else tc::cp_async16(dst, a.d + e * DS + 4 * (ch - QS / 4));
+      } else {
+        float* mt = sMeta + fc * META;
+        const int k = r - 2 * CH;
+        const int64_t ep = bnd ? fa.x : fa.z;
+        if (k == 0) tc::cp_async16(mt, &a.geom[fa.x].face[fa.y][0]);
+        else if (k == 1) tc::cp_async4(mt + 4, a.cp + fa.x);
+        else if (k == 2) tc::cp_async4(mt + 5, a.cp + ep);
+        else if (k == 3) {
+          mt[6] = bnd ? static_cast<float>(fa.w) : 0.f;   // boundary tag
+          mt[7] = static_cast<float>(fa.y);               // local face of side 0
+          mt[24] = bnd ? 0.f : static_cast<float>(fa.w);  // local face of side 1
+        } else {
+          const int half = (k - 4) & 1, which = (k - 4) >> 1;
+          tc::cp_async16(mt + 8 + 8 * which + 4 * half,
+                         reinterpret_cast<const float*>(a.mat + (which ? ep : fa.x)) + 4 * half);
+        }
+      }
+    }
+    tc::cp_async_wait_all();
+    __syncthreads();
+
+    // traces: warps 0-3 order 0 (G nodes x 4 columns), warps 4-7 orders 1..N (G nodes x 3 fields)
+    {
+      const int kind = tid >> 7, lu = tid & 127;
+      if (lu < UPK) {
+        const int s2 = lu / (NG * 3), r = lu - s2 * (NG * 3);
+        const int g = r / 3, c = r - 3 * g;
+        const int fc = s2 >> 1, side = s2 & 1;
+        const float* mt = sMeta + fc * META;
+        if (fc < nf && !(side && mt[6] != 0.f)) {
+          const int lf = static_cast<int>(side ? mt[24] : mt[7]);
+          const float* V = sV + (lf * L * NG + g) * GP;
+          const float* R = sRaw + s2 * RAW;
+          float* out = sTr + (s2 * (N + 1)) * NGG * 12 + (g * G) * 12;
+          if (kind == 0) {
+            // columns 4c..4c+3 of (the ten fields, D^1 alpha, 0); the state is [L][10]
+            const bool c2 = c == 2;
+            const float* pB = c2 ? R + QS + AOFF : R + 4 * c + 2;
+            const int sB = c2 ? 1 : 10, o3 = c2 ? 0 : 4 * c + 3;
+            float acc[G][4];
+#pragma unroll
+            for (int n = 0; n < G; ++n)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) acc[n][j] = 0.f;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+              float v[G];
+              load_group<N>(V + l * NG * GP, v);
+              const float2 x01 = *reinterpret_cast<const float2*>(R + l * 10 + 4 * c);
+              const float x2 = pB[l * sB], x3r = R[l * 10 + o3];
+              const float x[4] = {x01.x, x01.y, x2, c2 ? 0.f : x3r};
+#pragma unroll
+              for (int n = 0; n < G; ++n)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[n][j] = fmaf(v[n], x[j], acc[n][j]);
+            }
+#pragma unroll
+            for (int n = 0; n < G; ++n)
+              *reinterpret_cast<float4*>(out + n * 12 + 4 * c) = make_float4(acc[n][0], acc[n][1], acc[n][2], acc[n][3]);
+          } else {
+            const float* Dh = R + QS + 3 * c;
+#pragma unroll
+            for (int o = 1; o <= N; ++o) {
+              float acc[G][3];
+#pragma unroll
+              for (int n = 0; n < G; ++n)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) acc[n][j] = 0.f;
+#pragma unroll
+              for (int l = 0; l < n_modes(N - o); ++l) {
+                float v[G];
+                load_group<N>(V + l * NG * GP, v);
+                const float* xr = Dh + d_offset(N, o) + l * 9;
+                const float x[3] = {xr[0], xr[1], xr[2]};
+#pragma unroll
+                for (int n = 0; n < G; ++n)
+#pragma unroll
+                  for (int j = 0; j < 3; ++j) acc[n][j] = fmaf(v[n], x[j], acc[n][j]);
+              }
+              float* oo = out + o * NGG * 12 + 3 * c;
+#pragma unroll
+              for (int n = 0; n < G; ++n)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) oo[n * 12 + j] = acc[n][j];
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // flux at the face nodes, time-integrated: two threads per (face, node), each
+    // over half of the time nodes, combined by a shuffle
+    for (int w0 = 0; w0 < 2 * TF * NF; w0 += C::THREADS) {
+      const int w = w0 + tid;
+      const int pair = w >> 1, half = w & 1;
+      const int fc = pair / NF, i = pair - fc * NF;
+      float Fb[9];
+#pragma unroll
+      for (int p = 0; p < 9; ++p) Fb[p] = 0.f;
+      if (fc < nf) {
+        const float* mt = sMeta + fc * META;
+        const float n[3] = {mt[0], mt[1], mt[2]};
+        const int bc = static_cast<int>(mt[6]);
+        MatF mm, mp;
+        {
+          const float* m0 = mt + 8;
+          mm.rho = m0[0]; mm.lam0 = m0[1]; mm.mu0 = m0[2]; mm.gamma_r = m0[3];
+          mm.xi0 = m0[4]; mm.cd = m0[5]; mm.rho_inv = m0[6]; mm.pad = 0.f;
+          const float* m1 = mt + 16;
+          mp.rho = m1[0]; mp.lam0 = m1[1]; mp.mu0 = m1[2]; mp.gamma_r = m1[3];
+          mp.xi0 = m1[4]; mp.cd = m1[5]; mp.rho_inv = m1[6]; mp.pad = 0.f;
+        }
+        float lam = 0.f, mu = 0.f, cpb = 0.f, csb = 0.f, k_p = 0.f;
+        if (bc != 0) {
+          effective_lame(sRaw + (2 * fc) * RAW, mm, &lam, &mu);   // row 0 of the state: the cell-mean modes
+          cpb = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * mm.rho_inv);
+          csb = sqrtf(fmaxf(mu, 0.f) * mm.rho_inv);
+          k_p = lam + 2.f * mu > 0.f ? cpb / (lam + 2.f * mu) : 0.f;
+        }
+        const float Cs = fmaxf(mt[4], mt[5]);
+        const float* Tm = sTr + (2 * fc) * (N + 1) * NGG * 12 + i * 12;
+        const float* Tp = Tm + (N + 1) * NGG * 12;
+        constexpr int ZH = (NT + 1) / 2;
+        for (int z = half * ZH; z < (half ? NT : ZH); ++z) {
+          const float tau = __ldg(tb + T.tz + z) * dt, gam = __ldg(tb + T.gz + z) * dt;
+          float um[10], up[10];
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            const float* t0 = sd ? Tp : Tm;
+            float* u = sd ? up : um;
+            const float4 a0 = *reinterpret_cast<const float4*>(t0);
+            const float4 a1 = *reinterpret_cast<const float4*>(t0 + 4);
+            const float4 a2 = *reinterpret_cast<const float4*>(t0 + 8);
+            u[0] = a0.x; u[1] = a0.y; u[2] = a0.z; u[3] = a0.w;
+            u[4] = a1.x; u[5] = a1.y; u[6] = a1.z; u[7] = a1.w;
+            u[8] = a2.x; u[9] = fmaf(tau, a2.z, a2.y);
+            float c = 1.f;
+#pragma unroll
+            for (int o = 1; o <= N; ++o) {
+              c *= tau / static_cast<float>(o);
+              const float* to = t0 + o * NGG * 12;
+              const float4 b0 = *reinterpret_cast<const float4*>(to);
+              const float4 b1 = *reinterpret_cast<const float4*>(to + 4);
+              const float b2 = to[8];
+              u[0] = fmaf(c, b0.x, u[0]); u[1] = fmaf(c, b0.y, u[1]); u[2] = fmaf(c, b0.z, u[2]);
+              u[3] = fmaf(c, b0.w, u[3]); u[4] = fmaf(c, b1.x, u[4]); u[5] = fmaf(c, b1.y, u[5]);
+              u[6] = fmaf(c, b1.z, u[6]); u[7] = fmaf(c, b1.w, u[7]); u[8] = fmaf(c, b2, u[8]);
+            }
+            if (bc != 0) break;                 // a boundary face has no side 1
+          }
+          float F[9];
+          if (bc != 0) {
+            boundary_flux(bc, um, n, lam, mu, mm.rho_inv, cpb, csb, k_p, F);
+          } else {
+            float Fm[9], Fp[9];
+            normal_flux(um, mm, n, Fm);
+            normal_flux(up, mp, n, Fp);
+#pragma unroll
+            for (int p = 0; p < 9; ++p) F[p] = 0.5f * (Fm[p] + Fp[p]) + 0.5f * Cs * (um[p] - up[p]);
+          }
+#pragma unroll
+          for (int p = 0; p < 9; ++p) Fb[p] = fmaf(gam, F[p], Fb[p]);
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < 9; ++p) Fb[p] += __shfl_down_sync(0xffffffffu, Fb[p], 1);
+      if (fc < nf && half == 0) {
+        float* out = a.ff + (f0 + fc) * FFS + i * 9;
+#pragma unroll
+        for (int p = 0; p < 9; ++p) out[p] = Fb[p];
+      }
+    }
+  }
+}
+
+// ===========================================================================
 // Corrector: volume terms, face terms from the face fluxes, update
 // ===========================================================================
 // The velocity rows of the volume term, sum_q w_q d phi_k/d xi_e' (x_q) T_e'm(x_q),
@@ -1216,8 +1476,9 @@ cudaError_t launch_persistent(Kern kern, int64_t tiles, int grid_hint, const Ste
 }
 
 // Kernel variants (bit 0: predictor with shared-memory tables on a persistent
-// grid; bit 1: face kernel likewise; bit 2: SIMT corrector likewise; bit 3:
-// SIMT corrector instead of the tensor-core one).  Clear bits read the tables
+// grid; bit 1: first-form face kernel likewise; bit 2: SIMT corrector likewise;
+// bit 3: SIMT corrector instead of the tensor-core one; bit 4: first-form face
+// kernel instead of k_face_flux).  Clear bits read the tables
 // through the L1 cache with one CTA per tile.  The default is the fastest
 // measured combination on GB300; DG_KERNEL_VARIANT overrides it for tuning.
 inline int table_residency_mask() {
@@ -1243,8 +1504,13 @@ cudaError_t launch_predictor_impl(const StepArgs& a, cudaStream_t s) {
 
 template <int N>
 cudaError_t launch_faces_impl(const StepArgs& a, cudaStream_t s) {
-  static bool cfg[2] = {false, false};
-  static int blocks[2] = {1, 1};
+  static bool cfg[3] = {false, false, false};
+  static int blocks[3] = {1, 1, 1};
+  if (!(table_residency_mask() & 16)) {
+    const int64_t tiles = (a.F + FluxCfg<N>::TF - 1) / FluxCfg<N>::TF;
+    return launch_persistent<FluxCfg<N>>(k_face_flux<N>, tiles, a.grid_face > 0 ? a.grid_face : 148, a, s,
+                                         &cfg[2], &blocks[2]);
+  }
   const int64_t tiles = (a.F + FaceCfg<N, true>::TF - 1) / FaceCfg<N, true>::TF;
   if constexpr (FaceCfg<N, true>::FITS) {
     if (table_residency_mask() & 2)
