@@ -8,7 +8,7 @@ import numpy as np
 
 from oracle import Oracle, eval_basis, from_abi, tet_rule, to_abi
 
-# spec tolerances: relative L2 per field group, absolute on damage
+# parity tolerances: relative L2 per field group, absolute on damage
 TOL_REL_L2 = 1e-4
 TOL_ALPHA = 1e-5
 GROUPS = {"strain": slice(0, 6), "velocity": slice(6, 9)}

@@ -1,5 +1,5 @@
 """GPU parity: libdg (FP32 CUDA, through the C-ABI) against the FP64 oracle on
-the same seeded inputs.  Bar (the benchmark spec): relative L2 <= 1e-4 per field group
+the same seeded inputs.  Bar: relative L2 <= 1e-4 per field group
 (strains, velocities) and |alpha_gpu - alpha_oracle| <= 1e-5 at the volume
 nodes, after the run."""
 import math
