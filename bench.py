@@ -205,6 +205,8 @@ def main():
     ap.add_argument("--order", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ensemble-members", type=int, default=0,
+                    help="also time the ensemble workload (N=3, this many members) against one member")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -314,6 +316,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hq.numel() * 4),
                 "d2h_bytes_per_step": int(out.numel() * 4), "steps": args.e2e_steps},
     }
+    if args.ensemble_members > 1:
+        line["ensemble"] = run_ensemble(args, dgpkg, torch, stream)
     if not args.no_cpu_baseline and world == 1:
         v, sample, threads, _ = cpu_baseline(w, steps=1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
@@ -322,6 +326,42 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_ensemble(args, dgpkg, torch, stream, steps=10, warmup=3):
+    """Per-member throughput of the ensemble form (all members advance in one
+    set of launches per step) against the same mesh run with one member."""
+    from synthetic import workload_c4
+    w = workload_c4(n=args.n, members=args.ensemble_members)
+    mesh, mat, N, M = w["mesh"], w["material"], w["order"], w["members"]
+    E, L = mesh.n_elem, n_modes(N)
+    rate = {}
+    for members in (1, M):
+        s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, N, cfl=w["cfl"], stream=stream, members=members)
+        if members == 1:
+            m1 = mat.copy()
+            m1[:, 4:6] = w["member_xi0_cd"][0]
+            s.set_material(m1)
+        else:
+            s.set_material(mat, w["member_xi0_cd"])
+        s.set_sources(w["sources"])
+        s.set_receivers(w["receivers"])
+        shape = (E, 10, L) if members == 1 else (members, E, 10, L)
+        q = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        s.set_state(q, 0.0)
+        s.step(warmup)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        rate[members] = E * members * steps / (ev0.elapsed_time(ev1) * 1e-3)
+        s.close()
+        del q
+    return {"workload": w["name"], "members": M, "order": N, "elements": E, "steps": steps,
+            "member_updates_per_s": rate[M], "single_member_updates_per_s": rate[1],
+            "per_member_ratio": rate[M] / rate[1]}
 
 
 def _kernel_name(kind, N):

@@ -33,7 +33,8 @@
  *     (i,j,k) = c * u^i P_i^(0,0)((2xi-u)/u) * w^j P_j^(2i+1,0)((2eta-w)/w)
  *               * P_k^(2i+2j+2,0)(2zeta-1),  u = 1-eta-zeta, w = 1-zeta,
  *     c = sqrt((2i+1)(2i+2j+2)(2i+2j+2k+3)).  L = (N+1)(N+2)(N+3)/6 modes.
- *   - State arrays use the layout q[n_elem][10][L] (element, field, mode).
+ *   - State arrays use the layout q[members][n_elem][10][L] (member, element,
+ *     field, mode); with one member this is q[n_elem][10][L].
  *   - Calls are ordered on the context's CUDA stream.  One context per host
  *     thread.  dg_step, dg_get_state* and dg_receivers_read synchronise the
  *     stream before they return; the other calls may return before the device
@@ -92,7 +93,11 @@ typedef struct {
                                Any other tag, a tagged face that is shared or an untagged face
                                that is not matched is DG_E_MESH.  NULL = all 0. */
   int order;                /* polynomial degree N (1..5 compiled) */
-  int members;              /* ensemble members; must be 1 in this build */
+  int members;              /* ensemble members M >= 1: M copies of the state advance together
+                               on the same mesh, each with its own damage parameters (xi0, C_d;
+                               see dg_set_material) and its own copy of the sources and
+                               receivers; every kernel of a step runs once over all members.
+                               n_elem * members < 2^29. */
   double cfl;               /* Courant number of the default time step (see dg_dt) */
   void* cuda_stream;        /* cudaStream_t to order all work on; NULL = legacy default stream */
   const dg_allocator* alloc;/* optional device allocator, NULL = cudaMalloc */
@@ -109,7 +114,10 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out);
  * density, Lame parameters of the intact rock, damage modulus gamma_r [Pa],
  * damage onset xi0 (Eq. "cdb-model") and damage-rate coefficient C_d [1/(Pa s)].
  * Requires rho > 0, mu0 > 0, lambda0 + 2 mu0 > 0, gamma_r >= 0, C_d >= 0 and
- * finite values (DG_E_ARG otherwise).  member_xi0_cd must be NULL in this build.
+ * finite values (DG_E_ARG otherwise).  member_xi0_cd: NULL (every member takes
+ * xi0 and C_d from mat) or [members][n_elem][2] per-member (xi0, C_d), C_d >= 0;
+ * non-NULL with one member is DG_E_ARG.  rho, lambda0, mu0 and gamma_r are
+ * shared by the members.
  * Also fixes the default time step dt = cfl * min_e 2 r_in(e) / ((2N+1) c_p(e)),
  * r_in the inradius, c_p = sqrt((lambda0 + 2 mu0)/rho). */
 dg_status dg_set_material(dg_ctx* ctx, const double* mat, const double* member_xi0_cd);
@@ -134,14 +142,14 @@ typedef struct {
 } dg_point_source;
 dg_status dg_set_source(dg_ctx* ctx, const dg_point_source* src, int64_t n);
 
-/* Set the modal state q[n_elem][10][L] (FP64 or FP32 host arrays, or an FP32
- * device array in the same layout for the _device form) and the time t. */
+/* Set the modal state q[members][n_elem][10][L] (FP64 or FP32 host arrays, or
+ * an FP32 device array in the same layout for the _device form) and the time t. */
 dg_status dg_set_state(dg_ctx* ctx, const double* q, double t);
 dg_status dg_set_state_f32(dg_ctx* ctx, const float* q, double t);
 dg_status dg_set_state_device(dg_ctx* ctx, const float* q_dev, double t);
 
-/* Read the modal state into q_out[n_elem][10][L] and the time into *t_out
- * (t_out may be NULL). */
+/* Read the modal state into q_out[members][n_elem][10][L] and the time into
+ * *t_out (t_out may be NULL). */
 dg_status dg_get_state(dg_ctx* ctx, double* q_out, double* t_out);
 dg_status dg_get_state_f32(dg_ctx* ctx, float* q_out, double* t_out);
 dg_status dg_get_state_device(dg_ctx* ctx, float* q_dev_out, double* t_out);
@@ -176,7 +184,8 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt);
  * device current); make that first call before any stream capture.  Every
  * call reuses the same array, so calls whose work overlaps on the GPU (other
  * streams, other threads, other contexts) race and must be serialised by the
- * caller.  Requires dg_set_material (DG_E_STATE).  Status as for dg_step. */
+ * caller.  Requires dg_set_material (DG_E_STATE) and one member
+ * (DG_E_UNSUPPORTED otherwise).  Status as for dg_step. */
 dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_out, double dt);
 
 /* Register R receivers at xyz[R][3] (replaces previous ones, resets traces).
@@ -184,8 +193,9 @@ dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_out, double d
  * DG_E_OUTSIDE if a point lies in no element. */
 dg_status dg_receivers(dg_ctx* ctx, const double* xyz, int64_t R);
 
-/* Copy the recorded traces out[n_rec][R][3] (n_rec = steps since dg_receivers,
- * at most cap records are copied) and report the number recorded in *n_rec.
+/* Copy the recorded traces out[n_rec][members][R][3] (n_rec = steps since
+ * dg_receivers, at most cap records are copied) and report the number recorded
+ * in *n_rec.
  * Traces are kept for at most 65536 steps after dg_receivers. */
 dg_status dg_receivers_read(dg_ctx* ctx, float* out, int64_t cap, int64_t* n_rec);
 

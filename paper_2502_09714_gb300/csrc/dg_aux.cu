@@ -5,32 +5,36 @@
 namespace dg {
 namespace {
 
-// internal q[e][l*10+p] <- ABI src[e][p][l]
+// internal q[v][l*10+p] <- ABI src[m][e][p][l], v = e*M + m
 template <int L>
-__global__ void k_state_in(int64_t E, const void* src, int src_is_double, float* q, int qs) {
-  const int64_t e = blockIdx.x;
-  if (e >= E) return;
+__global__ void k_state_in(int64_t E, int M, const void* src, int src_is_double, float* q, int qs) {
+  const int64_t v = blockIdx.x;
+  if (v >= E * M) return;
+  const int64_t e = v / M, m = v - e * M;
+  const int64_t base = (m * E + e) * kFields * L;
   for (int w = threadIdx.x; w < qs; w += blockDim.x) {
-    float v = 0.f;
+    float val = 0.f;
     if (w < kFields * L) {
       const int k = w / kFields, p = w % kFields;
-      const int64_t idx = e * kFields * L + p * L + k;
-      v = src_is_double ? static_cast<float>(static_cast<const double*>(src)[idx])
-                        : static_cast<const float*>(src)[idx];
+      const int64_t idx = base + p * L + k;
+      val = src_is_double ? static_cast<float>(static_cast<const double*>(src)[idx])
+                          : static_cast<const float*>(src)[idx];
     }
-    q[e * qs + w] = v;
+    q[v * qs + w] = val;
   }
 }
 
-// ABI dst[e][p][l] <- internal q
+// ABI dst[m][e][p][l] <- internal q[v], v = e*M + m
 template <int L>
-__global__ void k_state_out(int64_t E, const float* q, int qs, void* dst, int dst_is_double) {
-  const int64_t e = blockIdx.x;
-  if (e >= E) return;
+__global__ void k_state_out(int64_t E, int M, const float* q, int qs, void* dst, int dst_is_double) {
+  const int64_t vi = blockIdx.x;
+  if (vi >= E * M) return;
+  const int64_t e = vi / M, m = vi - e * M;
+  const int64_t base = (m * E + e) * kFields * L;
   for (int w = threadIdx.x; w < kFields * L; w += blockDim.x) {
     const int p = w / L, l = w % L;
-    const float v = q[e * qs + l * kFields + p];
-    const int64_t idx = e * kFields * L + w;
+    const float v = q[vi * qs + l * kFields + p];
+    const int64_t idx = base + w;
     if (dst_is_double) static_cast<double*>(dst)[idx] = static_cast<double>(v);
     else static_cast<float*>(dst)[idx] = v;
   }
@@ -58,37 +62,37 @@ __global__ void k_receivers(int L, int qs, int n_rec, const ReceiverDev* rec, co
 }
 
 template <int N>
-cudaError_t state_in_t(int64_t E, const void* src, int dbl, float* q, cudaStream_t s) {
-  k_state_in<n_modes(N)><<<static_cast<unsigned>(E), 128, 0, s>>>(E, src, dbl, q, q_stride(N));
+cudaError_t state_in_t(int64_t E, int M, const void* src, int dbl, float* q, cudaStream_t s) {
+  k_state_in<n_modes(N)><<<static_cast<unsigned>(E * M), 128, 0, s>>>(E, M, src, dbl, q, q_stride(N));
   return cudaGetLastError();
 }
 
 template <int N>
-cudaError_t state_out_t(int64_t E, const float* q, void* dst, int dbl, cudaStream_t s) {
-  k_state_out<n_modes(N)><<<static_cast<unsigned>(E), 128, 0, s>>>(E, q, q_stride(N), dst, dbl);
+cudaError_t state_out_t(int64_t E, int M, const float* q, void* dst, int dbl, cudaStream_t s) {
+  k_state_out<n_modes(N)><<<static_cast<unsigned>(E * M), 128, 0, s>>>(E, M, q, q_stride(N), dst, dbl);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_state_in(int N, int64_t E, const void* src, int dbl, float* q, cudaStream_t s) {
+cudaError_t launch_state_in(int N, int64_t E, int M, const void* src, int dbl, float* q, cudaStream_t s) {
   switch (N) {
-    case 1: return state_in_t<1>(E, src, dbl, q, s);
-    case 2: return state_in_t<2>(E, src, dbl, q, s);
-    case 3: return state_in_t<3>(E, src, dbl, q, s);
-    case 4: return state_in_t<4>(E, src, dbl, q, s);
-    case 5: return state_in_t<5>(E, src, dbl, q, s);
+    case 1: return state_in_t<1>(E, M, src, dbl, q, s);
+    case 2: return state_in_t<2>(E, M, src, dbl, q, s);
+    case 3: return state_in_t<3>(E, M, src, dbl, q, s);
+    case 4: return state_in_t<4>(E, M, src, dbl, q, s);
+    case 5: return state_in_t<5>(E, M, src, dbl, q, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_state_out(int N, int64_t E, const float* q, void* dst, int dbl, cudaStream_t s) {
+cudaError_t launch_state_out(int N, int64_t E, int M, const float* q, void* dst, int dbl, cudaStream_t s) {
   switch (N) {
-    case 1: return state_out_t<1>(E, q, dst, dbl, s);
-    case 2: return state_out_t<2>(E, q, dst, dbl, s);
-    case 3: return state_out_t<3>(E, q, dst, dbl, s);
-    case 4: return state_out_t<4>(E, q, dst, dbl, s);
-    case 5: return state_out_t<5>(E, q, dst, dbl, s);
+    case 1: return state_out_t<1>(E, M, q, dst, dbl, s);
+    case 2: return state_out_t<2>(E, M, q, dst, dbl, s);
+    case 3: return state_out_t<3>(E, M, q, dst, dbl, s);
+    case 4: return state_out_t<4>(E, M, q, dst, dbl, s);
+    case 5: return state_out_t<5>(E, M, q, dst, dbl, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -40,7 +40,8 @@ struct FaceKeyHash {
 
 struct dg_ctx {
   int N = 0, L = 0, M = 1;
-  int64_t E = 0;
+  int64_t E = 0;                     // mesh elements
+  int64_t EV = 0;                    // element copies on the device: E x members, member fastest
   double cfl = 0.5;
   cudaStream_t stream = nullptr;
   dg_allocator alloc{};
@@ -53,7 +54,7 @@ struct dg_ctx {
   std::vector<double> jinv;          // [E][9] Theta^{-1} of the sorted order
   std::vector<double> detj;          // [E] |det J|
   std::vector<double> rin;           // [E] inradius
-  std::vector<double> mat;           // [E][6]
+  std::vector<double> mat;           // [E][6] (member 0's xi0 and C_d when members > 1)
   bool has_material = false, has_state = false;
   double dt_cfl = 0.0, t = 0.0;
 
@@ -79,14 +80,14 @@ struct dg_ctx {
 
   // sources
   std::vector<dg_point_source> sources;
-  std::vector<SourceDev> source_host;
+  std::vector<SourceDev> source_host;   // sources x members (member fastest)
   SourceDev* source_dev = nullptr;
   float* amp_dev = nullptr;
   int64_t amp_cap = 0;
   float* amp_host = nullptr;         // pinned
 
   // receivers
-  std::vector<ReceiverDev> rec_host;
+  std::vector<ReceiverDev> rec_host;    // members x receivers (receiver fastest)
   ReceiverDev* rec_dev = nullptr;
   float* traces = nullptr;
   int64_t trace_cap = 0, n_rec = 0;
@@ -331,9 +332,11 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
     return fail(nullptr, DG_E_ARG, "empty mesh or NULL mesh arrays");
   if (desc->n_elem >= (int64_t(1) << 29)) return fail(nullptr, DG_E_ARG, "too many elements");
   if (!supported_order(desc->order)) return fail(nullptr, DG_E_ORDER, "order must be in 1..5");
-  if (desc->members != 1) return fail(nullptr, DG_E_UNSUPPORTED, "only members == 1 is built");
+  if (desc->members < 1) return fail(nullptr, DG_E_ARG, "members must be >= 1");
   if (!(desc->cfl > 0.0) || !std::isfinite(desc->cfl)) return fail(nullptr, DG_E_ARG, "cfl must be > 0");
   const int64_t E = desc->n_elem;
+  const int64_t M = desc->members;
+  if (E * M >= (int64_t(1) << 29)) return fail(nullptr, DG_E_ARG, "too many element copies (n_elem x members)");
   if (desc->face_bc)
     for (int64_t i = 0; i < 4 * E; ++i)
       if (desc->face_bc[i] < 0 || desc->face_bc[i] > 2)
@@ -343,6 +346,8 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
   ctx->N = desc->order;
   ctx->L = n_modes(ctx->N);
   ctx->E = E;
+  ctx->M = static_cast<int>(M);
+  ctx->EV = E * M;
   ctx->cfl = desc->cfl;
   ctx->stream = static_cast<cudaStream_t>(desc->cuda_stream);
   if (desc->alloc) { ctx->alloc = *desc->alloc; ctx->has_alloc = ctx->alloc.alloc && ctx->alloc.free; }
@@ -466,20 +471,57 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
         faces.push_back(make_int4(static_cast<int>(e), f, -1, bc_sorted[4 * e + f]));
       }
   ctx->F = static_cast<int64_t>(faces.size());
+  if (ctx->F * M >= (int64_t(1) << 30)) {
+    dg_destroy(ctx);
+    return fail(nullptr, DG_E_ARG, "too many faces x members");
+  }
+
+  // ensemble: copy v = e * M + m of element e for member m, and copy fid * M + m of face fid;
+  // member m's copies only see each other
+  if (M > 1) {
+    const int64_t EV = E * M;
+    std::vector<GeomF> geom_v(EV);
+    std::vector<int> nbr_v(4 * EV, -1), elem_face_v(4 * EV, -1);
+    std::vector<int4> faces_v(ctx->F * M);
+    for (int64_t e = 0; e < E; ++e)
+      for (int64_t m = 0; m < M; ++m) {
+        const int64_t v = e * M + m;
+        geom_v[v] = geom[e];
+        for (int f = 0; f < 4; ++f) {
+          const int nb = nbr[4 * e + f];
+          if (nb >= 0) nbr_v[4 * v + f] = static_cast<int>((((nb >> 2) * M + m) << 2) | (nb & 3));
+          const int ef = elem_face[4 * e + f];
+          elem_face_v[4 * v + f] = static_cast<int>((((ef >> 1) * M + m) << 1) | (ef & 1));
+        }
+      }
+    for (int64_t fid = 0; fid < ctx->F; ++fid)
+      for (int64_t m = 0; m < M; ++m) {
+        const int4 fa = faces[fid];
+        faces_v[fid * M + m] = make_int4(static_cast<int>(fa.x * M + m), fa.y,
+                                         fa.z < 0 ? fa.z : static_cast<int>(fa.z * M + m), fa.w);
+      }
+    geom.swap(geom_v);
+    nbr.swap(nbr_v);
+    elem_face.swap(elem_face_v);
+    faces.swap(faces_v);
+    ctx->F *= M;
+    ctx->F_interior *= M;
+  }
 
   // device allocation and upload
   const int N = ctx->N, L = ctx->L;
   const size_t qs = static_cast<size_t>(q_stride(N)), ds = static_cast<size_t>(d_stride(N));
-  ctx->q[0] = static_cast<float*>(dev_alloc(ctx, sizeof(float) * qs * E));
-  ctx->q[1] = static_cast<float*>(dev_alloc(ctx, sizeof(float) * qs * E));
-  ctx->d = static_cast<float*>(dev_alloc(ctx, sizeof(float) * ds * E));
-  ctx->cp = static_cast<float*>(dev_alloc(ctx, sizeof(float) * E));
+  const int64_t EV = ctx->EV;
+  ctx->q[0] = static_cast<float*>(dev_alloc(ctx, sizeof(float) * qs * EV));
+  ctx->q[1] = static_cast<float*>(dev_alloc(ctx, sizeof(float) * qs * EV));
+  ctx->d = static_cast<float*>(dev_alloc(ctx, sizeof(float) * ds * EV));
+  ctx->cp = static_cast<float*>(dev_alloc(ctx, sizeof(float) * EV));
   ctx->ff = static_cast<float*>(dev_alloc(ctx, sizeof(float) * ff_stride(N) * ctx->F));
   ctx->faces = static_cast<int4*>(dev_alloc(ctx, sizeof(int4) * ctx->F));
-  ctx->elem_face = static_cast<int*>(dev_alloc(ctx, sizeof(int) * 4 * E));
-  ctx->geom = static_cast<GeomF*>(dev_alloc(ctx, sizeof(GeomF) * E));
-  ctx->matf = static_cast<MatF*>(dev_alloc(ctx, sizeof(MatF) * E));
-  ctx->nbr = static_cast<int*>(dev_alloc(ctx, sizeof(int) * 4 * E));
+  ctx->elem_face = static_cast<int*>(dev_alloc(ctx, sizeof(int) * 4 * EV));
+  ctx->geom = static_cast<GeomF*>(dev_alloc(ctx, sizeof(GeomF) * EV));
+  ctx->matf = static_cast<MatF*>(dev_alloc(ctx, sizeof(MatF) * EV));
+  ctx->nbr = static_cast<int*>(dev_alloc(ctx, sizeof(int) * 4 * EV));
   const TableLayout TL = table_layout(N);
   ctx->tables = static_cast<float*>(dev_alloc(ctx, sizeof(float) * TL.total));
   ctx->status = static_cast<unsigned*>(dev_alloc(ctx, sizeof(unsigned)));
@@ -500,19 +542,19 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
     tf.assign(t.begin(), t.end());
   }
   dg_status st;
-  if ((st = upload(ctx, ctx->geom, geom.data(), sizeof(GeomF) * E)) != DG_OK ||
-      (st = upload(ctx, ctx->nbr, nbr.data(), sizeof(int) * 4 * E)) != DG_OK ||
+  if ((st = upload(ctx, ctx->geom, geom.data(), sizeof(GeomF) * EV)) != DG_OK ||
+      (st = upload(ctx, ctx->nbr, nbr.data(), sizeof(int) * 4 * EV)) != DG_OK ||
       (st = upload(ctx, ctx->faces, faces.data(), sizeof(int4) * ctx->F)) != DG_OK ||
-      (st = upload(ctx, ctx->elem_face, elem_face.data(), sizeof(int) * 4 * E)) != DG_OK ||
+      (st = upload(ctx, ctx->elem_face, elem_face.data(), sizeof(int) * 4 * EV)) != DG_OK ||
       (st = upload(ctx, ctx->tables, tf.data(), sizeof(float) * tf.size())) != DG_OK) {
     std::string m = ctx->err;
     dg_destroy(ctx);
     return fail(nullptr, st, m);
   }
   cudaError_t ce;
-  if ((ce = cudaMemsetAsync(ctx->q[0], 0, sizeof(float) * qs * E, ctx->stream)) != cudaSuccess ||
-      (ce = cudaMemsetAsync(ctx->q[1], 0, sizeof(float) * qs * E, ctx->stream)) != cudaSuccess ||
-      (ce = cudaMemsetAsync(ctx->d, 0, sizeof(float) * ds * E, ctx->stream)) != cudaSuccess ||
+  if ((ce = cudaMemsetAsync(ctx->q[0], 0, sizeof(float) * qs * EV, ctx->stream)) != cudaSuccess ||
+      (ce = cudaMemsetAsync(ctx->q[1], 0, sizeof(float) * qs * EV, ctx->stream)) != cudaSuccess ||
+      (ce = cudaMemsetAsync(ctx->d, 0, sizeof(float) * ds * EV, ctx->stream)) != cudaSuccess ||
       (ce = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) {
     dg_destroy(ctx);
     return fail(nullptr, DG_E_CUDA, std::string("initialising device memory: ") + cudaGetErrorString(ce));
@@ -531,23 +573,32 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
 
 dg_status dg_set_material(dg_ctx* ctx, const double* mat, const double* member_xi0_cd) {
   if (!ctx || !mat) return fail(ctx, DG_E_ARG, "NULL argument");
-  if (member_xi0_cd) return fail(ctx, DG_E_UNSUPPORTED, "per-member parameters need members > 1");
-  const int64_t E = ctx->E;
-  std::vector<MatF> mf(E);
+  if (member_xi0_cd && ctx->M == 1) return fail(ctx, DG_E_ARG, "per-member parameters need members > 1");
+  const int64_t E = ctx->E, M = ctx->M;
+  std::vector<MatF> mf(ctx->EV);
   double dt = INFINITY;
   for (int64_t e = 0; e < E; ++e) {
     const double* m = mat + 6 * e;
     for (int k = 0; k < 6; ++k)
       if (!std::isfinite(m[k])) return fail(ctx, DG_E_ARG, "non-finite material of element " + std::to_string(e));
-    const double rho = m[0], lam = m[1], mu = m[2], gr = m[3], xi0 = m[4], cd = m[5];
-    if (!(rho > 0) || !(mu > 0) || !(lam + 2 * mu > 0) || gr < 0 || cd < 0)
+    const double rho = m[0], lam = m[1], mu = m[2], gr = m[3];
+    if (!(rho > 0) || !(mu > 0) || !(lam + 2 * mu > 0) || gr < 0 || m[5] < 0)
       return fail(ctx, DG_E_ARG, "invalid material of element " + std::to_string(e));
-    mf[e] = MatF{float(rho), float(lam), float(mu), float(gr), float(xi0), float(cd), float(1.0 / rho), 0.f};
+    for (int64_t k = 0; k < M; ++k) {
+      double xi0 = m[4], cd = m[5];
+      if (member_xi0_cd) {
+        xi0 = member_xi0_cd[2 * (k * E + e)];
+        cd = member_xi0_cd[2 * (k * E + e) + 1];
+        if (!std::isfinite(xi0) || !std::isfinite(cd) || cd < 0)
+          return fail(ctx, DG_E_ARG, "invalid member parameters of element " + std::to_string(e));
+      }
+      mf[e * M + k] = MatF{float(rho), float(lam), float(mu), float(gr), float(xi0), float(cd), float(1.0 / rho), 0.f};
+    }
     const double cp = std::sqrt((lam + 2 * mu) / rho);
     dt = std::min(dt, ctx->cfl * 2.0 * ctx->rin[e] / ((2 * ctx->N + 1) * cp));
   }
   ctx->mat.assign(mat, mat + 6 * E);
-  dg_status st = upload(ctx, ctx->matf, mf.data(), sizeof(MatF) * E);
+  dg_status st = upload(ctx, ctx->matf, mf.data(), sizeof(MatF) * ctx->EV);
   if (st != DG_OK) return st;
   ctx->dt_cfl = dt;
   ctx->has_material = true;
@@ -566,7 +617,7 @@ dg_status dg_get_stats(const dg_ctx* ctx, dg_stats* out) {
 static dg_status set_state_impl(dg_ctx* ctx, const void* q, int is_double, bool device, double t) {
   if (!ctx || !q) return fail(ctx, DG_E_ARG, "NULL argument");
   if (!std::isfinite(t)) return fail(ctx, DG_E_ARG, "non-finite time");
-  const size_t n = static_cast<size_t>(ctx->E) * kFields * ctx->L;
+  const size_t n = static_cast<size_t>(ctx->EV) * kFields * ctx->L;
   const void* src = q;
   if (!device) {
     dg_status st = ensure_staging(ctx, n * (is_double ? 8 : 4));
@@ -574,7 +625,7 @@ static dg_status set_state_impl(dg_ctx* ctx, const void* q, int is_double, bool 
     DG_CUDA(ctx, cudaMemcpyAsync(ctx->staging, q, n * (is_double ? 8 : 4), cudaMemcpyHostToDevice, ctx->stream));
     src = ctx->staging;
   }
-  DG_CUDA(ctx, launch_state_in(ctx->N, ctx->E, src, is_double, ctx->q[ctx->cur], ctx->stream));
+  DG_CUDA(ctx, launch_state_in(ctx->N, ctx->E, ctx->M, src, is_double, ctx->q[ctx->cur], ctx->stream));
   if (!device) DG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->t = t;
   ctx->has_state = true;
@@ -587,14 +638,14 @@ dg_status dg_set_state_device(dg_ctx* ctx, const float* q, double t) { return se
 
 static dg_status get_state_impl(dg_ctx* ctx, void* q, int is_double, bool device, double* t_out) {
   if (!ctx || !q) return fail(ctx, DG_E_ARG, "NULL argument");
-  const size_t n = static_cast<size_t>(ctx->E) * kFields * ctx->L;
+  const size_t n = static_cast<size_t>(ctx->EV) * kFields * ctx->L;
   void* dst = q;
   if (!device) {
     dg_status st = ensure_staging(ctx, n * (is_double ? 8 : 4));
     if (st != DG_OK) return st;
     dst = ctx->staging;
   }
-  DG_CUDA(ctx, launch_state_out(ctx->N, ctx->E, ctx->q[ctx->cur], dst, is_double, ctx->stream));
+  DG_CUDA(ctx, launch_state_out(ctx->N, ctx->E, ctx->M, ctx->q[ctx->cur], dst, is_double, ctx->stream));
   if (!device) DG_CUDA(ctx, cudaMemcpyAsync(q, ctx->staging, n * (is_double ? 8 : 4), cudaMemcpyDeviceToHost, ctx->stream));
   DG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (t_out) *t_out = ctx->t;
@@ -609,7 +660,8 @@ dg_status dg_set_source(dg_ctx* ctx, const dg_point_source* src, int64_t n) {
   if (!ctx || n < 0 || (n > 0 && !src)) return fail(ctx, DG_E_ARG, "invalid source list");
   if (!ctx->has_material) return fail(ctx, DG_E_STATE, "dg_set_material must precede dg_set_source");
   if (ctx->L > 64) return fail(ctx, DG_E_ORDER, "order too high for point sources");
-  std::vector<SourceDev> host(n);
+  const int64_t M = ctx->M;
+  std::vector<SourceDev> host(n * M);
   std::vector<double> phi(ctx->L);
   for (int64_t s = 0; s < n; ++s) {
     const dg_point_source& p = src[s];
@@ -624,20 +676,24 @@ dg_status dg_set_source(dg_ctx* ctx, const dg_point_source* src, int64_t n) {
     double eps[6];
     for (int k = 0; k < 6; ++k) eps[k] = p.m[k] / (2.0 * mu);
     for (int k = 0; k < 3; ++k) eps[k] -= lam / (2.0 * mu * (3.0 * lam + 2.0 * mu)) * tr;
-    SourceDev& d = host[s];
+    SourceDev& d = host[s * M];
     std::memset(&d, 0, sizeof(d));
-    d.elem = e;
+    d.elem = e * M;
     for (int k = 0; k < 6; ++k)
       for (int l = 0; l < ctx->L; ++l) d.phi_eps[k * ctx->L + l] = static_cast<float>(phi[l] * eps[k] / ctx->detj[e]);
+    for (int64_t m = 1; m < M; ++m) {            // the same source in every member
+      host[s * M + m] = d;
+      host[s * M + m].elem = e * M + m;
+    }
   }
   dev_free(ctx, ctx->source_dev);
   ctx->source_dev = nullptr;
   ctx->sources.assign(src, src + n);
   ctx->source_host = host;
   if (n > 0) {
-    ctx->source_dev = static_cast<SourceDev*>(dev_alloc(ctx, sizeof(SourceDev) * n));
+    ctx->source_dev = static_cast<SourceDev*>(dev_alloc(ctx, sizeof(SourceDev) * n * M));
     if (!ctx->source_dev) return fail(ctx, DG_E_OOM, "source allocation failed");
-    return upload(ctx, ctx->source_dev, host.data(), sizeof(SourceDev) * n);
+    return upload(ctx, ctx->source_dev, host.data(), sizeof(SourceDev) * n * M);
   }
   return DG_OK;
 }
@@ -645,16 +701,20 @@ dg_status dg_set_source(dg_ctx* ctx, const dg_point_source* src, int64_t n) {
 dg_status dg_receivers(dg_ctx* ctx, const double* xyz, int64_t R) {
   if (!ctx || R < 0 || (R > 0 && !xyz)) return fail(ctx, DG_E_ARG, "invalid receiver list");
   if (ctx->L > 64) return fail(ctx, DG_E_ORDER, "order too high for receivers");
-  std::vector<ReceiverDev> host(R);
+  const int64_t M = ctx->M;
+  std::vector<ReceiverDev> host(R * M);
   std::vector<double> phi(ctx->L);
   for (int64_t r = 0; r < R; ++r) {
     int64_t e;
     double xi[3];
     if (!locate(ctx, xyz + 3 * r, &e, xi)) return fail(ctx, DG_E_OUTSIDE, "receiver " + std::to_string(r) + " lies outside the mesh");
     ref::dubiner(ctx->N, xi[0], xi[1], xi[2], phi.data(), nullptr);
-    std::memset(&host[r], 0, sizeof(ReceiverDev));
-    host[r].elem = e;
-    for (int l = 0; l < ctx->L; ++l) host[r].phi[l] = static_cast<float>(phi[l]);
+    for (int64_t m = 0; m < M; ++m) {           // member m's copy of receiver r at m * R + r
+      ReceiverDev& h = host[m * R + r];
+      std::memset(&h, 0, sizeof(ReceiverDev));
+      h.elem = e * M + m;
+      for (int l = 0; l < ctx->L; ++l) h.phi[l] = static_cast<float>(phi[l]);
+    }
   }
   dev_free(ctx, ctx->rec_dev);
   dev_free(ctx, ctx->traces);
@@ -664,9 +724,9 @@ dg_status dg_receivers(dg_ctx* ctx, const double* xyz, int64_t R) {
   ctx->n_rec = 0;
   ctx->rec_host = host;
   if (R > 0) {
-    ctx->rec_dev = static_cast<ReceiverDev*>(dev_alloc(ctx, sizeof(ReceiverDev) * R));
+    ctx->rec_dev = static_cast<ReceiverDev*>(dev_alloc(ctx, sizeof(ReceiverDev) * R * M));
     if (!ctx->rec_dev) return fail(ctx, DG_E_OOM, "receiver allocation failed");
-    return upload(ctx, ctx->rec_dev, host.data(), sizeof(ReceiverDev) * R);
+    return upload(ctx, ctx->rec_dev, host.data(), sizeof(ReceiverDev) * R * M);
   }
   return DG_OK;
 }
@@ -714,8 +774,9 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
   if (dt <= 0) dt = ctx->dt_cfl;
   if (!std::isfinite(dt)) return fail(ctx, DG_E_ARG, "non-finite dt");
   if (n_steps == 0) return DG_OK;
-  const int nsrc = static_cast<int>(ctx->sources.size());
-  const int R = static_cast<int>(ctx->rec_host.size());
+  const int nsrc = static_cast<int>(ctx->source_host.size());     // sources x members
+  const int R = static_cast<int>(ctx->rec_host.size());           // receivers x members
+  const int M = ctx->M;
   // per-step source amplitudes (exact time integrals of the moment-rate function)
   if (nsrc > 0) {
     const int64_t need = n_steps * nsrc;
@@ -734,7 +795,8 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
     for (int64_t s = 0; s < n_steps; ++s) {
       const double t0 = ctx->t + s * dt, t1 = ctx->t + (s + 1) * dt;
       for (int k = 0; k < nsrc; ++k)
-        ctx->amp_host[s * nsrc + k] = static_cast<float>(stf_integral(ctx->sources[k], t1) - stf_integral(ctx->sources[k], t0));
+        ctx->amp_host[s * nsrc + k] =
+            static_cast<float>(stf_integral(ctx->sources[k / M], t1) - stf_integral(ctx->sources[k / M], t0));
     }
     DG_CUDA(ctx, cudaMemcpyAsync(ctx->amp_dev, ctx->amp_host, sizeof(float) * need, cudaMemcpyHostToDevice, ctx->stream));
   }
@@ -773,7 +835,7 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
     return cudaEventRecord(ctx->events[ev++], ctx->stream);
   };
   StepArgs a{};
-  a.E = ctx->E;
+  a.E = ctx->EV;
   a.F = ctx->F;
   a.d = ctx->d;
   a.cp = ctx->cp;
@@ -821,7 +883,7 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
   ctx->t += n_steps * dt;
   ctx->stats.steps += n_steps;
   ctx->stats.kernel_launches += launches;
-  ctx->stats.element_updates += n_steps * ctx->E;
+  ctx->stats.element_updates += n_steps * ctx->EV;
   if (ctx->profiling) {
     for (size_t i = 1; i < ev; ++i) {
       float ms = 0.f;
@@ -849,7 +911,8 @@ namespace dg {
 bool noalloc_view(const dg_ctx* ctx, NoAllocView* v) {
   if (!ctx || !v) return false;
   v->N = ctx->N;
-  v->E = ctx->E;
+  v->E = ctx->EV;
+  v->M = ctx->M;
   v->stream = ctx->stream;
   v->geom = ctx->geom;
   v->mat = ctx->matf;

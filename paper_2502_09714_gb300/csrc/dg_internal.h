@@ -146,11 +146,12 @@ cudaError_t launch_faces(int N, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_corrector(int N, const StepArgs& a, cudaStream_t s);
 
 // Auxiliary kernels (dg_aux.cu).
-// State conversion between the ABI layout [E][10][L] (FP64 or FP32) and the
-// internal layout [E][q_stride] ([L][10] per element, FP32).
-cudaError_t launch_state_in(int N, int64_t E, const void* src, int src_is_double, float* q,
+// State conversion between the ABI layout [M][E][10][L] (FP64 or FP32) and the
+// internal layout [E*M][q_stride] (copy e*M + m of element e for member m,
+// [L][10] per copy, FP32).
+cudaError_t launch_state_in(int N, int64_t E, int M, const void* src, int src_is_double, float* q,
                             cudaStream_t s);
-cudaError_t launch_state_out(int N, int64_t E, const float* q, void* dst, int dst_is_double,
+cudaError_t launch_state_out(int N, int64_t E, int M, const float* q, void* dst, int dst_is_double,
                              cudaStream_t s);
 
 struct SourceDev {
@@ -171,7 +172,8 @@ cudaError_t launch_receivers(int N, int n_rec, const ReceiverDev* rec, const flo
 // Read-only view of a context for the allocation-free step (dg_noalloc.cu).
 struct NoAllocView {
   int N;
-  int64_t E;
+  int64_t E;              // element copies (mesh elements x members)
+  int M;
   cudaStream_t stream;
   const GeomF* geom;
   const MatF* mat;

@@ -56,6 +56,7 @@ extern "C" dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_ou
   if (!ctx || !noalloc_view(ctx, &v)) return noalloc_error(ctx, DG_E_ARG, "NULL context");
   if (!q_in || !q_out) return noalloc_error(ctx, DG_E_ARG, "NULL state pointer");
   if (!v.has_material) return noalloc_error(ctx, DG_E_STATE, "dg_set_material must precede dg_step_noalloc");
+  if (v.M != 1) return noalloc_error(ctx, DG_E_UNSUPPORTED, "dg_step_noalloc takes one member only");
   if (dt <= 0) dt = v.dt_cfl;
   if (!std::isfinite(dt)) return noalloc_error(ctx, DG_E_ARG, "non-finite dt");
   const int64_t qs = q_stride(v.N), ds = d_stride(v.N), ffs = ff_stride(v.N);
@@ -97,11 +98,11 @@ extern "C" dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_ou
   a.status = status;
   // the array keeps the previous call's contents: the status word must start at zero
   if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned), v.stream)) != cudaSuccess ||
-      (e = launch_state_in(v.N, v.E, q_in, 0, qa, v.stream)) != cudaSuccess ||
+      (e = launch_state_in(v.N, v.E, 1, q_in, 0, qa, v.stream)) != cudaSuccess ||
       (e = launch_predictor(v.N, a, v.stream)) != cudaSuccess ||
       (e = launch_faces(v.N, a, v.stream)) != cudaSuccess ||
       (e = launch_corrector(v.N, a, v.stream)) != cudaSuccess ||
-      (e = launch_state_out(v.N, v.E, qb, q_out, 0, v.stream)) != cudaSuccess)
+      (e = launch_state_out(v.N, v.E, 1, qb, q_out, 0, v.stream)) != cudaSuccess)
     return noalloc_error(ctx, DG_E_CUDA, (std::string("dg_step_noalloc launch: ") + cudaGetErrorString(e)).c_str());
   unsigned st = 0;
   if ((e = cudaMemcpyAsync(&st, status, sizeof(unsigned), cudaMemcpyDeviceToHost, v.stream)) != cudaSuccess ||
@@ -109,5 +110,6 @@ extern "C" dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_ou
     return noalloc_error(ctx, DG_E_CUDA, (std::string("dg_step_noalloc: ") + cudaGetErrorString(e)).c_str());
   if (st & kStatusNonFinite) return noalloc_error(ctx, DG_E_NONFINITE, "non-finite value in the state");
   if (st & kStatusNonHyperbolic) return noalloc_error(ctx, DG_E_NONHYPERBOLIC, "effective moduli lost hyperbolicity");
+  if (st & kStatusTimeout) return noalloc_error(ctx, DG_E_CUDA, "a bounded wait on the tensor cores timed out");
   return DG_OK;
 }

@@ -160,6 +160,7 @@ class Solver:
         xyz = np.ascontiguousarray(elem_xyz, dtype=np.float64)
         vid = np.ascontiguousarray(elem_vid, dtype=np.int64)
         self.E = int(xyz.shape[0])
+        self.M = int(members)
         self.order = int(order)
         self.L = n_modes(self.order)
         bc = None if face_bc is None else np.ascontiguousarray(face_bc, dtype=np.int8)
@@ -198,9 +199,15 @@ class Solver:
         self.close()
 
     # ------------------------------------------------------------------
-    def set_material(self, mat):
+    def set_material(self, mat, member_xi0_cd=None):
+        """mat [E,6] = (rho, lambda0, mu0, gamma_r, xi0, C_d); member_xi0_cd
+        [M,E,2] per-member (xi0, C_d) or None."""
         m = np.ascontiguousarray(mat, dtype=np.float64).reshape(self.E, 6)
-        self._chk(self.lib.dg_set_material(self.ctx, _ptr(m, C.c_double), None))
+        mp = None
+        if member_xi0_cd is not None:
+            mp = np.ascontiguousarray(member_xi0_cd, dtype=np.float64).reshape(self.M, self.E, 2)
+        self._chk(self.lib.dg_set_material(self.ctx, _ptr(m, C.c_double),
+                                           _ptr(mp, C.c_double) if mp is not None else None))
 
     def set_sources(self, sources):
         arr = (PointSource * max(1, len(sources)))()
@@ -212,31 +219,35 @@ class Solver:
             arr[i].t0 = float(s.get("t0", 0.0))
         self._chk(self.lib.dg_set_source(self.ctx, arr, len(sources)))
 
+    def _shape(self):
+        return (self.E, 10, self.L) if self.M == 1 else (self.M, self.E, 10, self.L)
+
     def set_state(self, q, t=0.0):
-        """q: [E,10,L] host array (float64 or float32) or a CUDA float32 torch tensor."""
+        """q: [E,10,L] ([M,E,10,L] with several members) host array (float64 or
+        float32) or a CUDA float32 torch tensor."""
         if hasattr(q, "is_cuda") and q.is_cuda:
             assert q.dtype.__str__() == "torch.float32" and q.is_contiguous()
-            assert tuple(q.shape) == (self.E, 10, self.L)
+            assert tuple(q.shape) == self._shape()
             self._chk(self.lib.dg_set_state_device(self.ctx, C.c_void_p(q.data_ptr()), float(t)))
             return
         if hasattr(q, "numpy"):
             q = q.numpy()
         if q.dtype == np.float32:
-            a = np.ascontiguousarray(q).reshape(self.E, 10, self.L)
+            a = np.ascontiguousarray(q).reshape(self._shape())
             self._chk(self.lib.dg_set_state_f32(self.ctx, _ptr(a, C.c_float), float(t)))
         else:
-            a = np.ascontiguousarray(q, dtype=np.float64).reshape(self.E, 10, self.L)
+            a = np.ascontiguousarray(q, dtype=np.float64).reshape(self._shape())
             self._chk(self.lib.dg_set_state(self.ctx, _ptr(a, C.c_double), float(t)))
 
     def get_state(self, dtype=np.float64, out=None):
-        """Returns (q [E,10,L], t).  `out` may be a host array of matching dtype or
-        a CUDA float32 torch tensor."""
+        """Returns (q [E,10,L] or [M,E,10,L], t).  `out` may be a host array of
+        matching dtype or a CUDA float32 torch tensor."""
         t = C.c_double(0.0)
         if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
             self._chk(self.lib.dg_get_state_device(self.ctx, C.c_void_p(out.data_ptr()), C.byref(t)))
             return out, t.value
         if out is None:
-            out = np.empty((self.E, 10, self.L), dtype=dtype)
+            out = np.empty(self._shape(), dtype=dtype)
         a = out.numpy() if hasattr(out, "numpy") else out
         if a.dtype == np.float32:
             self._chk(self.lib.dg_get_state_f32(self.ctx, _ptr(a, C.c_float), C.byref(t)))
@@ -265,7 +276,7 @@ class Solver:
     def read_receivers(self):
         n = C.c_int64(0)
         self._chk(self.lib.dg_receivers_read(self.ctx, None, 0, C.byref(n)))
-        out = np.empty((n.value, self.R, 3), dtype=np.float32)
+        out = np.empty((n.value, self.R, 3) if self.M == 1 else (n.value, self.M, self.R, 3), dtype=np.float32)
         if n.value:
             self._chk(self.lib.dg_receivers_read(self.ctx, _ptr(out, C.c_float), n.value, C.byref(n)))
         return out

@@ -8,11 +8,11 @@ CUDA library (through its C-ABI) and the FP64 oracle consume these arrays.
 from .mesh import Mesh, kuhn_box_mesh, periodic_cube_mesh
 from .workloads import (
     FIELD_NAMES, rock_material, two_layer_material, uniform_material,
-    dip_slip_source, receiver_grid, workload_c1, workload_c2, workload_small_layered,
+    dip_slip_source, receiver_grid, workload_c1, workload_c2, workload_c4, workload_small_layered,
 )
 
 __all__ = [
     "Mesh", "kuhn_box_mesh", "periodic_cube_mesh", "FIELD_NAMES", "rock_material",
     "two_layer_material", "uniform_material", "dip_slip_source", "receiver_grid",
-    "workload_c1", "workload_c2", "workload_small_layered",
+    "workload_c1", "workload_c2", "workload_c4", "workload_small_layered",
 ]

@@ -105,6 +105,24 @@ def workload_c2(n=32, side=4000.0, order=4, m0=C2_M0, sort_by_vid=True):
             "sources": [src], "receivers": rec}
 
 
+def workload_c4(n=32, side=4000.0, order=3, members=32, seed=3, sort_by_vid=True):
+    """The ensemble workload: c2's mesh, layers, source and receivers at degree
+    3, with `members` parameter sets drawn per member (seeded):
+    xi0 ~ U[-1.0, -0.6] and log C_d ~ U[log 1e-5, log 1e-3], C_d in 1/(Pa s).
+    member_xi0_cd has the C-ABI layout [members][n_elem][2]."""
+    w = workload_c2(n=n, side=side, order=order, sort_by_vid=sort_by_vid)
+    rng = np.random.default_rng(seed)
+    xi0 = rng.uniform(-1.0, -0.6, size=members)
+    cd = np.exp(rng.uniform(np.log(1e-5), np.log(1e-3), size=members))
+    E = w["mesh"].n_elem
+    par = np.empty((members, E, 2))
+    par[:, :, 0] = xi0[:, None]
+    par[:, :, 1] = cd[:, None]
+    w.update(name=f"c4 ensemble of {members} on the {E}-tet two-layer cube N={order}",
+             members=members, member_xi0_cd=par)
+    return w
+
+
 def workload_small_layered(n=4, order=3, side=4000.0, m0=C2_M0, seed=1, sort_by_vid=False):
     """A c2-shaped workload at a size the oracle runs in seconds."""
     w = workload_c2(n=n, side=side, order=order, m0=m0, sort_by_vid=sort_by_vid)

@@ -106,8 +106,8 @@ def test_mesh_validation_errors_before_device_work(lib):
         dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, 9)
     assert ei.value.name == "DG_E_ORDER"
     with pytest.raises(DGError) as ei:
-        dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, 2, members=4)
-    assert ei.value.name == "DG_E_UNSUPPORTED"
+        dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, 2, members=0)
+    assert ei.value.name == "DG_E_ARG"
     # a tag on a shared face, and an unknown tag, are mesh errors
     bc = np.zeros((mesh.n_elem, 4), np.int8)
     bc[0, 0] = 2
