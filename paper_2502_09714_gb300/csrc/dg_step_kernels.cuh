@@ -1213,20 +1213,29 @@ struct CorrTcCfg : Dim<N> {
   static constexpr int oVw = oPhiL + 128 * KP;
   static constexpr int oKtB = round4(oVw + D::NQ * D::LP);
   static constexpr int oVfw = round4(oKtB + 3 * D::L * D::LP);
+  // GEMM operand (TF32 high parts and remainders); once the MMA has completed the
+  // region holds the nodal terms, then the split-K partial sums and the modal outputs
   static constexpr int oBeH = round4(oVfw + 4 * D::NF * D::LP);   // [NBC x KP] canonical
   static constexpr int oBeL = oBeH + NBC * KP;
-  static constexpr int oQ = oBeL + NBC * KP;
-  static constexpr int oM = oQ + TE * D::QS;
+  static constexpr int BE_END = oBeL + NBC * KP;
   static constexpr int BN = D::NQ * NB, BF = 4 * D::NF * NFC;
-  static constexpr int oB = oM + 3 * D::L * NM;
-  static constexpr int oA = oB + round4(BN > BF ? BN : BF);
-  static constexpr int oH = oA + TE * D::L * 10;
-  static constexpr int P1 = KS_PRJ * D::LP * NB, P2 = KS_FACE * D::LP * NFC;
-  static constexpr int oPart = oH + 3 * D::LP * NM;
-  static constexpr int oDraw = oPart + (P1 > P2 ? P1 : P2);     // [TE][DS] predictor output
-  static constexpr int oFraw = oDraw + TE * D::DS;               // [TE][4][FFS] face fluxes
-  static constexpr int oGeo = oFraw + TE * 4 * D::FFS;           // [TE][32]: Theta^{-1}, material, face scales
+  static constexpr int B_SIZE = round4(BN > BF ? BN : BF);
+  static constexpr int P1 = KS_PRJ * D::LP * NB, P2 = KS_FACE * D::LP * NFC, P3 = 3 * D::LP * NM;
+  static constexpr int PART = round4(P1 > P2 ? (P1 > P3 ? P1 : P3) : (P2 > P3 ? P2 : P3));
+  static constexpr int oB = oBeH;
+  static constexpr int oPart = oB + B_SIZE;                // also the modal outputs H ([3][LP][NM])
+  static constexpr int oH = oPart;
+  static constexpr int oM = BE_END;                        // [3][L][NM] modal GEMM inputs
+  static constexpr int oA = oM + 3 * D::L * NM;            // [TE][L][10] update accumulator
+  // two tile buffers filled by asynchronous copies (the next tile's while this one computes):
+  // state, predictor output, face fluxes, raw geometry (GeomF, MatF, face ids)
+  static constexpr int GRAW = 48;
+  static constexpr int bQ = 0, bD = TE * D::QS, bF = bD + TE * D::DS, bG = bF + TE * 4 * D::FFS;
+  static constexpr int BUF = bG + TE * GRAW;
+  static constexpr int oBuf = round4(oA + TE * D::L * 10);
+  static constexpr int oGeo = oBuf + 2 * BUF;              // [TE][32]: Theta^{-1}, material, face scales
   static constexpr int SMEM = oGeo + TE * 32;
+  static_assert(oBeH + B_SIZE + PART <= BE_END, "nodal terms and partial sums fit the operand region");
   static_assert(D::NQ <= 128 && NBC % 16 == 0 && NBC <= 256, "tensor-core tile shape");
   static_assert(SMEM * 4 <= 227 * 1024, "tensor-core corrector shared memory");
 };
@@ -1249,16 +1258,13 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
   const float* sVfw = sm + C::oVfw;
   float* sBeH = sm + C::oBeH;
   float* sBeL = sm + C::oBeL;
-  float* sQ = sm + C::oQ;
   float* sM = sm + C::oM;
   float* sB = sm + C::oB;
   float* sA = sm + C::oA;
   float* sH = sm + C::oH;
   float* sPart = sm + C::oPart;
-  float* sDraw = sm + C::oDraw;
-  float* sFraw = sm + C::oFraw;
   float* sGeo = sm + C::oGeo;
-  constexpr int FFS = C::FFS;
+  constexpr int FFS = C::FFS, GRAW = C::GRAW;
   const float* tb = a.tables;
   const float dt = a.dt;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1282,60 +1288,69 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
   uint32_t phase = 0;
   bool failed = false;
 
-  const int64_t ntiles = (a.E + TE - 1) / TE;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t e0 = tile * TE;
+  // one batch of asynchronous copies of a tile: state, predictor output, face fluxes,
+  // geometry, material and face ids
+  auto issue = [&](int64_t tl, float* buf) {
+    const int64_t e0 = tl * TE;
     const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
-    __syncthreads();
-    // one batch of asynchronous copies: state, predictor output and face fluxes of the tile
-    for (int w = tid; w < ne * QS / 4; w += blockDim.x) tc::cp_async16(sQ + 4 * w, a.q_in + e0 * QS + 4 * w);
-    for (int w = tid; w < ne * DS / 4; w += blockDim.x) tc::cp_async16(sDraw + 4 * w, a.d + e0 * DS + 4 * w);
+    for (int w = tid; w < ne * QS / 4; w += blockDim.x) tc::cp_async16(buf + C::bQ + 4 * w, a.q_in + e0 * QS + 4 * w);
+    for (int w = tid; w < ne * DS / 4; w += blockDim.x) tc::cp_async16(buf + C::bD + 4 * w, a.d + e0 * DS + 4 * w);
     for (int w = tid; w < ne * FFS; w += blockDim.x) {     // ne * 4 faces * FFS/4 chunks
       const int e = w / FFS, r = w - e * FFS;
       const int f = r / (FFS / 4), c = r - f * (FFS / 4);
       const int64_t fid = a.elem_face[(e0 + e) * 4 + f] >> 1;
-      tc::cp_async16(sFraw + (e * 4 + f) * FFS + 4 * c, a.ff + fid * FFS + 4 * c);
+      tc::cp_async16(buf + C::bF + (e * 4 + f) * FFS + 4 * c, a.ff + fid * FFS + 4 * c);
     }
+    for (int w = tid; w < ne * 11; w += blockDim.x) {
+      const int e = w / 11, k = w - 11 * e;
+      float* g = buf + C::bG + e * GRAW;
+      if (k < 8) tc::cp_async16(g + 4 * k, reinterpret_cast<const float*>(a.geom + e0 + e) + 4 * k);
+      else if (k < 10) tc::cp_async16(g + 32 + 4 * (k - 8), reinterpret_cast<const float*>(a.mat + e0 + e) + 4 * (k - 8));
+      else tc::cp_async16(g + 40, a.elem_face + (e0 + e) * 4);
+    }
+  };
+
+  const int64_t ntiles = (a.E + TE - 1) / TE;
+  if (static_cast<int64_t>(blockIdx.x) < ntiles) issue(blockIdx.x, sm + C::oBuf);
+  tc::cp_async_commit();
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int64_t e0 = tile * TE;
+    const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
+    float* buf = sm + C::oBuf + (it & 1) * C::BUF;
+    float* sQ = buf + C::bQ;
+    const float* sDraw = buf + C::bD;
+    const float* sFraw = buf + C::bF;
+    const float* sGraw = buf + C::bG;
+    __syncthreads();                         // the previous tile is done with every buffer
+    tc::cp_async_wait<0>();                  // this tile's copies have landed
     for (int w = ne * QS + tid; w < TE * QS; w += blockDim.x) sQ[w] = 0.f;
     for (int w = tid; w < TE * L * 10; w += blockDim.x) sA[w] = 0.f;
+    __syncthreads();
     // per element: Theta^{-1} [0,9), material [9,17), signed |S_f|/|J| [17,21)
     for (int w = tid; w < TE * 21; w += blockDim.x) {
       const int e = w / 21, c = w - 21 * e;
+      const float* g = sGraw + e * GRAW;
       float v = 0.f;
       if (e < ne) {
-        const int64_t ge = e0 + e;
         if (c < 9) {
-          v = a.geom[ge].tinv[c];
+          v = g[c];
         } else if (c < 17) {
-          v = reinterpret_cast<const float*>(a.mat + ge)[c - 9];
+          v = g[32 + c - 9];
         } else {
           const int f = c - 17;
-          v = a.geom[ge].face[f][3] * ((a.elem_face[ge * 4 + f] & 1) ? -1.f : 1.f);
+          v = g[12 + 4 * f + 3] * ((__float_as_int(g[40 + f]) & 1) ? -1.f : 1.f);
         }
       }
       sGeo[e * 32 + c] = v;
     }
-    tc::cp_async_wait_all();
-    __syncthreads();
-    // Taylor expansion at the time nodes (GEMM operand) and time-integrated velocity
-    for (int w = tid; w < KP * TE; w += blockDim.x) {
+    // time-integrated velocity (modal), the first 3 TE columns of each [L][NM] block of sM
+    for (int w = tid; w < L * TE; w += blockDim.x) {
       const int l = w / TE, e = w - l * TE;
-      float u[NT][7];
-#pragma unroll
-      for (int z = 0; z < NT; ++z)
-#pragma unroll
-        for (int p = 0; p < 7; ++p) u[z][p] = 0.f;
       float iv[3] = {0.f, 0.f, 0.f};
-      if (l < L && e < ne) {
+      if (e < ne) {
         const float* q = sQ + e * QS + l * 10;
         const float* de = sDraw + e * DS;
-        const float a1 = de[AOFF + l];
-#pragma unroll
-        for (int z = 0; z < NT; ++z) {
-#pragma unroll
-          for (int p = 0; p < 6; ++p) u[z][p] = q[p];
-          u[z][6] = fmaf(tz[z], a1, q[9]);
-        }
         iv[0] = dt * q[6];
         iv[1] = dt * q[7];
         iv[2] = dt * q[8];
@@ -1344,38 +1359,54 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
         for (int o = 1; o <= N; ++o) {
           ci *= dt / static_cast<float>(o + 1);
           if (l < n_modes(N - o)) {
-            const float* dd = de + d_offset(N, o) + l * 9;
-            float dv[9];
+            const float* dd = de + d_offset(N, o) + l * 9 + 6;
 #pragma unroll
-            for (int p = 0; p < 9; ++p) dv[p] = dd[p];
-#pragma unroll
-            for (int z = 0; z < NT; ++z) {
-              float c = 1.f;
-#pragma unroll
-              for (int j = 1; j <= o; ++j) c *= tz[z] / static_cast<float>(j);
-#pragma unroll
-              for (int p = 0; p < 6; ++p) u[z][p] = fmaf(c, dv[p], u[z][p]);
-            }
-#pragma unroll
-            for (int m = 0; m < 3; ++m) iv[m] = fmaf(ci, dv[6 + m], iv[m]);
+            for (int m = 0; m < 3; ++m) iv[m] = fmaf(ci, dd[m], iv[m]);
           }
         }
       }
 #pragma unroll
-      for (int z = 0; z < NT; ++z)
+      for (int ep = 0; ep < 3; ++ep)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const float x = c < 7 ? u[z][c] : 0.f;
+        for (int m = 0; m < 3; ++m) sM[(ep * L + l) * NM + e * 3 + m] = iv[m];
+    }
+    // GEMM operand: U(t_z) = sum_o t_z^o / o! D^o at mode l for channels c = eps_xx..eps_zx,
+    // alpha, 0.  Lane (c, l mod 4) of a warp holds one channel of one mode for all time
+    // nodes, so each store of a warp fills one core matrix without bank conflicts.
+    {
+      const int c = lane & 7, l4 = lane >> 3;
+      for (int pi = warp; pi < TE * (KP / 4); pi += C::THREADS / 32) {
+        const int e = pi / (KP / 4), lq = pi - e * (KP / 4);
+        const int l = lq * 4 + l4;
+        float base = 0.f, dd[N + 1];
+#pragma unroll
+        for (int o = 0; o <= N; ++o) dd[o] = 0.f;
+        if (l < L && e < ne && c < 7) {
+          const float* q = sQ + e * QS + l * 10;
+          const float* de = sDraw + e * DS;
+          base = q[c < 6 ? c : 9];
+#pragma unroll
+          for (int o = 1; o <= N; ++o) {
+            if (c < 6) {
+              if (l < n_modes(N - o)) dd[o] = de[d_offset(N, o) + l * 9 + c];
+            } else if (o == 1) {
+              dd[1] = de[AOFF + l];
+            }
+          }
+        }
+#pragma unroll
+        for (int z = 0; z < NT; ++z) {
+          float x = base, cc = 1.f;
+#pragma unroll
+          for (int o = 1; o <= N; ++o) {
+            cc *= tz[z] / static_cast<float>(o);
+            x = fmaf(cc, dd[o], x);
+          }
           const float h = tc::tf32_hi(x);
           const int idx = tc_canon(e * NCOL + z * 8 + c, l, KP);
           sBeH[idx] = h;
           sBeL[idx] = x - h;
         }
-      if (l < L) {
-#pragma unroll
-        for (int ep = 0; ep < 3; ++ep)
-#pragma unroll
-          for (int m = 0; m < 3; ++m) sM[(ep * L + l) * NM + e * 3 + m] = iv[m];
       }
     }
     tc::fence_smem_to_async();
@@ -1395,6 +1426,9 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
       }
       tc::commit(&mbar);
     }
+    // while the tensor cores run: the next tile's copies into the other buffer
+    if (tile + gridDim.x < ntiles) issue(tile + gridDim.x, sm + C::oBuf + ((it + 1) & 1) * C::BUF);
+    tc::cp_async_commit();
     const bool ok = tc::wait_parity(&mbar, phase, kWaitLimit);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
@@ -1445,6 +1479,7 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
     __syncthreads();
     corrector_tail<N, TE, C::KS_PRJ, C::KS_FACE>(a, e0, ne, sVw, sKtB, sVfw, sQ, sM, sB, sA, sH, sPart, sFraw, sGeo);
   }
+  tc::cp_async_wait<0>();                    // no copy may still be in flight at exit
   if (failed) {
     if (tid == 0) atomicOr(a.status, kStatusTimeout);
     tc::wait_parity(&mbar, phase ^ 1u, kWaitLimit);   // let the MMAs in flight finish before freeing TMEM
