@@ -224,3 +224,42 @@ def test_profile_counts_kernels():
     assert p["source"]["launches"] == 7 and p["receivers"]["launches"] == 7
     assert p["corrector"]["total_ms"] > 0 and p["faces"]["total_ms"] > 0
     assert s.stats()["kernel_launches"] == 35
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_anisotropic_prestrain_plane_wave(N):
+    """Sec. 3.3's setting on the GPU: uniform pre-strain 1e-3 rotated by 30 degrees,
+    alpha = 0.5, gamma_r = 37 GPa, C_d = 0, a small P-like plane perturbation along
+    x; 12 steps against the oracle (the change over the run is compared)."""
+    import test_oracle_anisotropy as ani
+    from synthetic.mesh import kuhn_box_mesh
+    t = ani._table()
+    mat1 = np.array([t["rho"], t["lambda0"], t["mu0"], t["gamma_r"], t["xi0"], t["Cd"]])
+    u0 = ani._pre_state(t, math.radians(30.0))
+    w, V = np.linalg.eigh(ani._acoustic_tensor(u0, mat1))
+    c, a = math.sqrt(w[2]), V[:, 2]
+    Lx, n = 1.0 / t["k"], 4
+    grids = [np.linspace(0.0, Lx, n + 1)] + [np.linspace(0.0, 3 * Lx / n, 4)] * 2
+    mesh = kuhn_box_mesh(*grids, periodic=(True, True, True), jitter=0.1, seed=5)
+    mat = np.tile(mat1, (mesh.n_elem, 1))
+    o = make_oracle(mesh, mat, N)
+    E = 0.5 * (np.outer([1.0, 0.0, 0.0], a) + np.outer(a, [1.0, 0.0, 0.0]))
+
+    def init(x):
+        g = t["A0"] * np.sin(2 * np.pi * t["k"] * x[..., 0])
+        u = np.broadcast_to(u0, x.shape[:-1] + (10,)).copy()
+        for p, (i, j) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (2, 0))):
+            u[..., p] += E[i, j] * g
+        u[..., 6:9] += -c * a * g[..., None]
+        return u
+    Q0 = o.project(init)
+    dt = o.cfl_dt()
+    s = make_solver(mesh, mat, N)
+    s.set_state(to_abi(Q0))
+    s.step(12, dt)
+    q, _ = s.get_state()
+    Q = o.run(Q0, dt, 12)
+    errs = rel_l2(to_abi(from_abi(q) - Q0), Q - Q0, o.detJ)
+    for name, e in errs.items():
+        assert e <= TOL_REL_L2, (name, e)
+    assert alpha_max_diff(q, Q, N) <= TOL_ALPHA
