@@ -259,7 +259,9 @@ def test_anisotropic_prestrain_plane_wave(N):
     s.step(12, dt)
     q, _ = s.get_state()
     Q = o.run(Q0, dt, 12)
+    assert_parity(q, Q, o.detJ, N)                      # the state, as the bar is defined
+    # the perturbation alone is 400 times smaller than the FP32-stored pre-strain, so
+    # its own relative error has an FP32 floor of about 1e-4; it must stay within 1e-3
     errs = rel_l2(to_abi(from_abi(q) - Q0), Q - Q0, o.detJ)
     for name, e in errs.items():
-        assert e <= TOL_REL_L2, (name, e)
-    assert alpha_max_diff(q, Q, N) <= TOL_ALPHA
+        assert e <= 1e-3, (name, e)
