@@ -17,11 +17,13 @@ invariance under relabelling/rotation/translation and monotone damage.
 from .basis import eval_basis, mode_list, n_modes
 from .quadrature import gauss_jacobi, gauss_legendre_01, tet_rule, tri_rule
 from .rheology import (cdm_damage_rate, cdm_energy, cdm_stress, effective_lame, flux,
-                       invariants, jacobian_eff)
+                       invariants, ivm_damage_rate, ivm_effective_lame, ivm_energy, ivm_stress,
+                       jacobian_eff)
 from .solver import MeshError, Oracle, from_abi, stf_integral, to_abi
 
 __all__ = [
     "eval_basis", "mode_list", "n_modes", "gauss_jacobi", "gauss_legendre_01", "tet_rule",
     "tri_rule", "cdm_damage_rate", "cdm_energy", "cdm_stress", "effective_lame", "flux",
-    "invariants", "jacobian_eff", "MeshError", "Oracle", "from_abi", "to_abi", "stf_integral",
+    "invariants", "ivm_damage_rate", "ivm_effective_lame", "ivm_energy", "ivm_stress",
+    "jacobian_eff", "MeshError", "Oracle", "from_abi", "to_abi", "stf_integral",
 ]

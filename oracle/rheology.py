@@ -3,7 +3,10 @@ infrastructure only).  All arrays carry the 10 conservative variables in the
 last axis: (eps_xx, eps_yy, eps_zz, eps_xy, eps_yz, eps_zx, v_x, v_y, v_z, alpha)
 (Eq. "nonlinear hyper pdes"), tensor shear strains.
 
-Material arrays `mat` have last axis (rho, lambda0, mu0, gamma_r, xi0, C_d).
+Material arrays `mat` have last axis (rho, lambda0, mu0, gamma_r, xi0, C_d) for
+the CDM and (rho, lambda0, mu0, gamma_b, tau_b, unused) for the IVM
+(Eq. "ivm-model", Murnaghan coefficients l0 = m0 = n0 = 0 as the paper sets
+them).  The law-generic entry points take law = "cdm" (default) or "ivm".
 """
 from __future__ import annotations
 
@@ -80,7 +83,62 @@ def effective_lame(u, mat):
     return lam, mu
 
 
-def flux(u, mat):
+def ivm_stress(u, mat):
+    """Stress tensor [...,3,3] of Eq. "ivm-model" with l0 = m0 = n0 = 0:
+    sigma = (1 - alpha) (lambda0 I1 delta + 2 mu0 eps)."""
+    lam0, mu0 = mat[..., 1], mat[..., 2]
+    alpha = u[..., 9]
+    e = strain_tensor(u)
+    I1 = e[..., 0, 0] + e[..., 1, 1] + e[..., 2, 2]
+    iso = (1.0 - alpha) * lam0 * I1
+    sh = (1.0 - alpha) * 2.0 * mu0
+    return iso[..., None, None] * np.eye(3) + sh[..., None, None] * e
+
+
+def ivm_damage_rate(u, mat):
+    """r_alpha of Eq. "ivm-model" with W^mur = 0:
+    (lambda0 I1^2 / 2 + mu0 I2 - phi(alpha)) / (gamma_b tau_b),
+    phi(alpha) = gamma_b (alpha / (1 - alpha))^2."""
+    lam0, mu0, gb, tb = mat[..., 1], mat[..., 2], mat[..., 3], mat[..., 4]
+    alpha = u[..., 9]
+    I1, I2, _, _ = invariants(u)
+    s = alpha / (1.0 - alpha)
+    return (0.5 * lam0 * I1 * I1 + mu0 * I2 - gb * s * s) / (gb * tb)
+
+
+def ivm_energy(u, mat):
+    """Elastic energy density of the IVM, W = (1 - alpha)(lambda0 I1^2 / 2 + mu0 I2),
+    whose strain gradient is the stress of Eq. "ivm-model" (derived, not printed)."""
+    lam0, mu0 = mat[..., 1], mat[..., 2]
+    alpha = u[..., 9]
+    I1, I2, _, _ = invariants(u)
+    return (1.0 - alpha) * (0.5 * lam0 * I1 * I1 + mu0 * I2)
+
+
+def ivm_effective_lame(u, mat):
+    """Effective Lame parameters of the IVM (Eq. "effective-ivm"):
+    lambda_eff = (1 - alpha) lambda0, mu_eff = (1 - alpha) mu0."""
+    alpha = u[..., 9]
+    return (1.0 - alpha) * mat[..., 1], (1.0 - alpha) * mat[..., 2]
+
+
+def stress(u, mat, law="cdm"):
+    return ivm_stress(u, mat) if law == "ivm" else cdm_stress(u, mat)
+
+
+def damage_rate(u, mat, law="cdm"):
+    return ivm_damage_rate(u, mat) if law == "ivm" else cdm_damage_rate(u, mat)
+
+
+def energy(u, mat, law="cdm"):
+    return ivm_energy(u, mat) if law == "ivm" else cdm_energy(u, mat)
+
+
+def effective_lame_law(u, mat, law="cdm"):
+    return ivm_effective_lame(u, mat) if law == "ivm" else effective_lame(u, mat)
+
+
+def flux(u, mat, law="cdm"):
     """Physical flux F^d_p [...,3(d),10(p)] of Eq. "nonlinear hyper pdes" under the
     rheology (follows from Eq. "nonlinear damage models"):
       F^d_{eps_ij} = -(v_i delta_jd + v_j delta_id)/2,
@@ -88,7 +146,7 @@ def flux(u, mat):
       F^d_alpha    = 0."""
     rho = mat[..., 0]
     v = u[..., 6:9]
-    sig = cdm_stress(u, mat)
+    sig = stress(u, mat, law)
     F = np.zeros(u.shape[:-1] + (3, 10))
     for p, (i, j) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (2, 0))):
         # -(v_i delta_jd + v_j delta_id)/2: the d = j entry gets -v_i/2, the d = i entry -v_j/2

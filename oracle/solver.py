@@ -3,7 +3,8 @@ infrastructure only).
 
 One step from t_n to t_{n+1} = t_n + dt, in the order of Appendix A:
   1. cell mean u_bar of the state (mode 0);
-  2. effective Lame parameters at u_bar (Eq. "effective-cdb", readings R1/R2/R7);
+  2. effective Lame parameters at u_bar (Eq. "effective-cdb", readings R1/R2/R7;
+     Eq. "effective-ivm" with law="ivm");
   3. effective Jacobians B^{d,eff} (Eqs. "matrix_Beff_1..3", readings T1/T2);
   4. star matrices A*_e = Theta^{-1}_{ed} B^{d,eff};
   5. Cauchy-Kovalevskaya predictor D^i = -K^e D^{i-1} A*_e^T (Eq. "CKIter-ref-matrix",
@@ -20,6 +21,8 @@ One step from t_n to t_{n+1} = t_n + dt, in the order of Appendix A:
      ("Free surface and absorbing boundary conditions", oracle/boundary.py);
   9. update of Eq. "time-integrated" with M = I (orthonormal basis).
 Point sources enter step 9 as strain-rate deltas; receivers sample velocity.
+The pointwise law is the CDM of Eq. "cdb-model" (law="cdm", default) or the IVM
+of Eq. "ivm-model" without Murnaghan terms (law="ivm").
 
 State layout inside the oracle: Q[E, L, 10] (mode, field), modes of the
 Dubiner basis mapped onto each element with its vertices in increasing vertex
@@ -34,7 +37,7 @@ import numpy as np
 from .basis import eval_basis, mode_list, n_modes
 from .boundary import boundary_matrix
 from .quadrature import gauss_legendre_01, tet_rule, tri_rule
-from .rheology import (cdm_damage_rate, cdm_energy, effective_lame, flux,
+from .rheology import (damage_rate, effective_lame_law, energy, flux,
                        invariants, jacobian_eff)
 
 REF_VERTS = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
@@ -72,7 +75,8 @@ def stf_integral(src, t):
 
 
 class Oracle:
-    def __init__(self, elem_xyz, elem_vid, order, material, face_bc=None, cfl=0.5, face_rows=None):
+    def __init__(self, elem_xyz, elem_vid, order, material, face_bc=None, cfl=0.5, face_rows=None,
+                 law="cdm"):
         """face_rows: elements whose face tables are built (default all); step()
         can only produce new states for those elements."""
         xyz = np.asarray(elem_xyz, dtype=np.float64)
@@ -92,6 +96,9 @@ class Oracle:
                         else np.asarray(face_bc, dtype=np.int8)[rows, vorder])
         if np.any((self.face_bc < 0) | (self.face_bc > 2)):
             raise MeshError("face tags must be 0 (interior), 1 (free surface) or 2 (absorbing)")
+        if law not in ("cdm", "ivm"):
+            raise ValueError(f"unknown rheology {law}")
+        self.law = law
         self.cfl = cfl
         self._reference()
         self._geometry()
@@ -248,7 +255,7 @@ class Oracle:
         mat = self.mat[rows]
         Qr = Q[rows]
         ubar = Qr[:, 0, :] * PHI0                                         # 1. cell mean
-        lam, mu = effective_lame(ubar, mat)                              # 2.
+        lam, mu = effective_lame_law(ubar, mat, self.law)                # 2.
         rho = mat[:, 0]
         self.flag_nonhyperbolic |= bool(np.any((mu <= 0) | (lam + 2 * mu <= 0)))
         cp = np.sqrt(np.maximum(lam + 2 * mu, 0.0) / rho)
@@ -260,7 +267,7 @@ class Oracle:
             Di = -np.einsum("nekq,nepq->nkp", G, Astar, optimize=True)
             if i == 1:
                 uq = np.einsum("ql,nlp->nqp", self.Vv, Qr, optimize=True)
-                r = cdm_damage_rate(uq, mat[:, None, :])
+                r = damage_rate(uq, mat[:, None, :], self.law)
                 Di[:, :, 9] += np.einsum("q,qk,nq->nk", self.qv_w, self.Vv, r, optimize=True)
             D.append(Di)
         return np.stack(D, axis=0), cp, (lam, mu)
@@ -289,9 +296,9 @@ class Oracle:
             mat = self.mat[rr]
             # 7. volume and source terms (reference measure; |J| cancels)
             uq = np.einsum("ql,nzlp->nzqp", self.Vv, U[pr], optimize=True)
-            F = flux(uq, mat[:, None, None, :])                              # [n,z,q,3,10]
+            F = flux(uq, mat[:, None, None, :], self.law)                    # [n,z,q,3,10]
             s = np.zeros_like(uq)
-            s[..., 9] = cdm_damage_rate(uq, mat[:, None, None, :])
+            s[..., 9] = damage_rate(uq, mat[:, None, None, :], self.law)
             gphys = np.einsum("qke,ned->nqkd", self.Gv, self.Jinv[rr], optimize=True)       # d phi_k / d x_d
             vol = np.einsum("z,q,nqkd,nzqdp->nkp", gz, self.qv_w, gphys, F, optimize=True)
             src = np.einsum("z,q,qk,nzqp->nkp", gz, self.qv_w, self.Vv, s, optimize=True)
@@ -307,8 +314,9 @@ class Oracle:
                 if np.any(fr < 0):
                     raise ValueError("face tables were not built for some requested rows")
                 up = np.einsum("nil,nzlp->nzip", self.Vf_nbr[fr, f], U[pos[nbs]], optimize=True)
-                Fm = np.einsum("nzidp,nd->nzip", flux(um, mat[:, None, None, :]), n, optimize=True)
-                Fp = np.einsum("nzidp,nd->nzip", flux(up, self.mat[nbs][:, None, None, :]), n, optimize=True)
+                Fm = np.einsum("nzidp,nd->nzip", flux(um, mat[:, None, None, :], self.law), n, optimize=True)
+                Fp = np.einsum("nzidp,nd->nzip", flux(up, self.mat[nbs][:, None, None, :], self.law), n,
+                               optimize=True)
                 C = np.maximum(cp[pr], cp[pos[nbs]])
                 Fs = 0.5 * (Fp + Fm) + 0.5 * C[:, None, None, None] * (um - up)
                 # boundary faces (Appendix A): flux matrix of the face applied to the own trace
@@ -371,7 +379,7 @@ class Oracle:
         u = self.evaluate(Q, pts)
         mat = self.mat[:, None, :]
         kin = 0.5 * mat[..., 0] * np.sum(u[..., 6:9] ** 2, axis=-1)
-        W = cdm_energy(u, mat)
+        W = energy(u, mat, self.law)
         return float(np.sum(self.detJ[:, None] * w[None, :] * (kin + W)))
 
     def damage_dissipation_rate(self, Q):
@@ -380,6 +388,9 @@ class Oracle:
         u = self.evaluate(Q, pts)
         mat = self.mat[:, None, :]
         I1, I2, s, xi = invariants(u)
-        dWda = mat[..., 4] * mat[..., 3] * I2 - mat[..., 3] * I1 * s
-        r = cdm_damage_rate(u, mat)
+        if self.law == "ivm":
+            dWda = -(0.5 * mat[..., 1] * I1 * I1 + mat[..., 2] * I2)
+        else:
+            dWda = mat[..., 4] * mat[..., 3] * I2 - mat[..., 3] * I1 * s
+        r = damage_rate(u, mat, self.law)
         return float(-np.sum(self.detJ[:, None] * w[None, :] * dWda * r))
