@@ -110,6 +110,13 @@ typedef struct {
  * On success *out owns the context (free with dg_destroy). */
 dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out);
 
+/* Pointwise law of the step: DG_LAW_CDM (default; Eq. "cdb-model") or DG_LAW_IVM
+ * (Eq. "ivm-model" with the Murnaghan coefficients l0 = m0 = n0 = 0, effective Lame
+ * parameters of Eq. "effective-ivm").  Changing the law invalidates the material:
+ * call dg_set_material again before dg_step.  DG_E_ARG for another value. */
+enum { DG_LAW_CDM = 0, DG_LAW_IVM = 1 };
+dg_status dg_set_rheology(dg_ctx* ctx, int law);
+
 /* Per-element material [n_elem][6] = (rho, lambda0, mu0, gamma_r, xi0, C_d):
  * density, Lame parameters of the intact rock, damage modulus gamma_r [Pa],
  * damage onset xi0 (Eq. "cdb-model") and damage-rate coefficient C_d [1/(Pa s)].
@@ -117,7 +124,10 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out);
  * finite values (DG_E_ARG otherwise).  member_xi0_cd: NULL (every member takes
  * xi0 and C_d from mat) or [members][n_elem][2] per-member (xi0, C_d), C_d >= 0;
  * non-NULL with one member is DG_E_ARG.  rho, lambda0, mu0 and gamma_r are
- * shared by the members.
+ * shared by the members.  Under DG_LAW_IVM the rows are
+ * (rho, lambda0, mu0, gamma_b, tau_b, unused) with gamma_b > 0 [Pa] the scale of
+ * the storage energy and tau_b > 0 [s] the damage time scale, and
+ * member_xi0_cd must be NULL.
  * Also fixes the default time step dt = cfl * min_e 2 r_in(e) / ((2N+1) c_p(e)),
  * r_in the inradius, c_p = sqrt((lambda0 + 2 mu0)/rho). */
 dg_status dg_set_material(dg_ctx* ctx, const double* mat, const double* member_xi0_cd);

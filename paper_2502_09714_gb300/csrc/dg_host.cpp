@@ -40,6 +40,7 @@ struct FaceKeyHash {
 
 struct dg_ctx {
   int N = 0, L = 0, M = 1;
+  int law = 0;                       // 0 = CDM, 1 = IVM
   int64_t E = 0;                     // mesh elements
   int64_t EV = 0;                    // element copies on the device: E x members, member fastest
   double cfl = 0.5;
@@ -571,9 +572,18 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
   return DG_OK;
 }
 
+dg_status dg_set_rheology(dg_ctx* ctx, int law) {
+  if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
+  if (law != DG_LAW_CDM && law != DG_LAW_IVM) return fail(ctx, DG_E_ARG, "unknown rheology");
+  if (law != ctx->law) ctx->has_material = false;   // the material slots change meaning
+  ctx->law = law;
+  return DG_OK;
+}
+
 dg_status dg_set_material(dg_ctx* ctx, const double* mat, const double* member_xi0_cd) {
   if (!ctx || !mat) return fail(ctx, DG_E_ARG, "NULL argument");
   if (member_xi0_cd && ctx->M == 1) return fail(ctx, DG_E_ARG, "per-member parameters need members > 1");
+  if (member_xi0_cd && ctx->law != DG_LAW_CDM) return fail(ctx, DG_E_ARG, "per-member parameters are CDM (xi0, C_d)");
   const int64_t E = ctx->E, M = ctx->M;
   std::vector<MatF> mf(ctx->EV);
   double dt = INFINITY;
@@ -582,8 +592,19 @@ dg_status dg_set_material(dg_ctx* ctx, const double* mat, const double* member_x
     for (int k = 0; k < 6; ++k)
       if (!std::isfinite(m[k])) return fail(ctx, DG_E_ARG, "non-finite material of element " + std::to_string(e));
     const double rho = m[0], lam = m[1], mu = m[2], gr = m[3];
-    if (!(rho > 0) || !(mu > 0) || !(lam + 2 * mu > 0) || gr < 0 || m[5] < 0)
+    if (!(rho > 0) || !(mu > 0) || !(lam + 2 * mu > 0))
       return fail(ctx, DG_E_ARG, "invalid material of element " + std::to_string(e));
+    if (ctx->law == DG_LAW_IVM) {
+      // (rho, lambda0, mu0, gamma_b, tau_b, -): gamma_b in gamma_r, 1/(gamma_b tau_b) in C_d
+      if (!(m[3] > 0) || !(m[4] > 0)) return fail(ctx, DG_E_ARG, "IVM needs gamma_b > 0 and tau_b > 0, element " + std::to_string(e));
+      const MatF f{float(rho), float(lam), float(mu), float(m[3]), float(m[4]), float(1.0 / (m[3] * m[4])),
+                   float(1.0 / rho), 0.f};
+      for (int64_t k = 0; k < M; ++k) mf[e * M + k] = f;
+      const double cp = std::sqrt((lam + 2 * mu) / rho);
+      dt = std::min(dt, ctx->cfl * 2.0 * ctx->rin[e] / ((2 * ctx->N + 1) * cp));
+      continue;
+    }
+    if (gr < 0 || m[5] < 0) return fail(ctx, DG_E_ARG, "invalid material of element " + std::to_string(e));
     for (int64_t k = 0; k < M; ++k) {
       double xi0 = m[4], cd = m[5];
       if (member_xi0_cd) {
@@ -845,6 +866,7 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
   a.grid_pred = ctx->grid_pred;
   a.grid_face = ctx->grid_face;
   a.grid_corr = ctx->grid_corr;
+  a.law = ctx->law;
   a.geom = ctx->geom;
   a.mat = ctx->matf;
   a.nbr = ctx->nbr;
@@ -923,6 +945,7 @@ bool noalloc_view(const dg_ctx* ctx, NoAllocView* v) {
   v->tables = ctx->tables;
   v->dt_cfl = ctx->dt_cfl;
   v->has_material = ctx->has_material;
+  v->law = ctx->law;
   return true;
 }
 

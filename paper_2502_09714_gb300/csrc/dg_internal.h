@@ -134,6 +134,7 @@ struct StepArgs {
   float dt;
   unsigned* status;
   int grid_pred, grid_face, grid_corr;   // persistent grid sizes (0: one CTA per tile)
+  int law;                // pointwise law: 0 = CDM (Eq. "cdb-model"), 1 = IVM (Eq. "ivm-model")
 };
 
 // Kernel launchers, one per compiled degree (dg_step_n<N>.cu), and their
@@ -184,6 +185,7 @@ struct NoAllocView {
   const float* tables;
   double dt_cfl;
   bool has_material;
+  int law;
 };
 
 }  // namespace dg

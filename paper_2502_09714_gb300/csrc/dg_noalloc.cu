@@ -96,6 +96,7 @@ extern "C" dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_ou
   a.tables = v.tables;
   a.dt = static_cast<float>(dt);
   a.status = status;
+  a.law = v.law;
   // the array keeps the previous call's contents: the status word must start at zero
   if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned), v.stream)) != cudaSuccess ||
       (e = launch_state_in(v.N, v.E, 1, q_in, 0, qa, v.stream)) != cudaSuccess ||

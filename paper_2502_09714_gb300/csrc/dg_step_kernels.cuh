@@ -77,11 +77,45 @@ __device__ __forceinline__ float cdm_rate(const float e[6], const MatF& m) {
   return m.cd * m.gamma_r * fmaxf(0.f, I1 * s - m.xi0 * I2);
 }
 
+// IVM (Eq. "ivm-model" with l0 = m0 = n0 = 0): sigma = (1 - alpha)(lambda0 I1 delta
+// + 2 mu0 eps) and r = (lambda0 I1^2/2 + mu0 I2 - gamma_b (alpha/(1-alpha))^2) /
+// (gamma_b tau_b); the material holds gamma_b in gamma_r and 1/(gamma_b tau_b) in cd.
+__device__ __forceinline__ void ivm_point(const float e[6], float alpha, const MatF& m, float sig[6],
+                                          float* rate) {
+  const float I1 = e[0] + e[1] + e[2];
+  const float I2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + 2.f * (e[3] * e[3] + e[4] * e[4] + e[5] * e[5]);
+  const float f = 1.f - alpha;
+  const float iso = f * m.lam0 * I1, sh = 2.f * f * m.mu0;
+  sig[0] = iso + sh * e[0];
+  sig[1] = iso + sh * e[1];
+  sig[2] = iso + sh * e[2];
+  sig[3] = sh * e[3];
+  sig[4] = sh * e[4];
+  sig[5] = sh * e[5];
+  const float s = alpha / f;
+  *rate = m.cd * (0.5f * m.lam0 * I1 * I1 + m.mu0 * I2 - m.gamma_r * s * s);
+}
+
+// The pointwise law selected for the step: 0 = CDM, 1 = IVM.
+__device__ __forceinline__ void law_point(int law, const float e[6], float alpha, const MatF& m, float sig[6],
+                                          float* rate) {
+  if (law == 1) ivm_point(e, alpha, m, sig, rate);
+  else cdm_point(e, alpha, m, sig, rate);
+}
+__device__ __forceinline__ float law_rate(int law, const float e[6], float alpha, const MatF& m) {
+  if (law == 1) {
+    float sig[6], r;
+    ivm_point(e, alpha, m, sig, &r);
+    return r;
+  }
+  return cdm_rate(e, m);
+}
+
 // Normal flux F^d(u) n_d of the 9 wave fields (Eq. "nonlinear hyper pdes"):
 // strain rows -(v_i n_j + v_j n_i)/2, velocity rows -sigma_ij n_j / rho.
-__device__ __forceinline__ void normal_flux(const float u[10], const MatF& m, const float n[3], float F[9]) {
+__device__ __forceinline__ void normal_flux(int law, const float u[10], const MatF& m, const float n[3], float F[9]) {
   float sig[6], r;
-  cdm_point(u, u[9], m, sig, &r);
+  law_point(law, u, u[9], m, sig, &r);
   const float vx = u[6], vy = u[7], vz = u[8];
   F[0] = -vx * n[0];
   F[1] = -vy * n[1];
@@ -94,10 +128,17 @@ __device__ __forceinline__ void normal_flux(const float u[10], const MatF& m, co
   F[8] = -m.rho_inv * (sig[5] * n[0] + sig[4] * n[1] + sig[2] * n[2]);
 }
 
-// Effective Lame parameters at a cell mean (Eq. "effective-cdb" with the sign of
-// the xi0 term taken from Eq. "cdb-model"); q0 holds the ten mode-0 coefficients.
-__device__ __forceinline__ void effective_lame(const float* q0, const MatF& m, float* lam, float* mu) {
+// Effective Lame parameters at a cell mean (CDM: Eq. "effective-cdb" with the sign
+// of the xi0 term taken from Eq. "cdb-model"; IVM: Eq. "effective-ivm"); q0 holds the
+// ten mode-0 coefficients.
+__device__ __forceinline__ void effective_lame(int law, const float* q0, const MatF& m, float* lam, float* mu) {
   const float r6 = 2.449489742783178f;   // phi_0 = sqrt(6): cell mean = Q_0 sqrt(6)
+  if (law == 1) {
+    const float f = 1.f - q0[9] * r6;
+    *lam = f * m.lam0;
+    *mu = f * m.mu0;
+    return;
+  }
   float u[6];
 #pragma unroll
   for (int p = 0; p < 6; ++p) u[p] = q0[p] * r6;
@@ -284,7 +325,7 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
       const int64_t ge = e0 + e;
       const MatF m = a.mat[ge];
       float lam, mu;
-      effective_lame(sQ + e * QS, m, &lam, &mu);
+      effective_lame(a.law, sQ + e * QS, m, &lam, &mu);
       if (!(mu > 0.f) || !(lam + 2.f * mu > 0.f)) atomicOr(a.status, kStatusNonHyperbolic);
       a.cp[ge] = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * m.rho_inv);
       float* c = sCoef + e * 16;
@@ -301,7 +342,8 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
       float* p0 = sP0 + l * CW + e * 12;
 #pragma unroll
       for (int p = 0; p < 6; ++p) c0[p] = q[p];
-      c0[6] = c0[7] = 0.f;
+      c0[6] = q[9];
+      c0[7] = 0.f;
 #pragma unroll
       for (int p = 0; p < 9; ++p) p0[p] = q[p];
       p0[9] = p0[10] = p0[11] = 0.f;
@@ -312,19 +354,20 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
     constexpr int NPAIR = NQP / 2;
     for (int w = threadIdx.x; w < TE * NPAIR; w += blockDim.x) {
       const int e = w / NPAIR, j = w - e * NPAIR;
-      float acc[2][6];
+      constexpr int NC = 7;                  // six strains and alpha at the node
+      float acc[2][NC];
 #pragma unroll
       for (int n = 0; n < 2; ++n)
 #pragma unroll
-        for (int p = 0; p < 6; ++p) acc[n][p] = 0.f;
+        for (int p = 0; p < NC; ++p) acc[n][p] = 0.f;
 #pragma unroll 5
       for (int l = 0; l < L; ++l) {
         const float2 ph = *reinterpret_cast<const float2*>(sVvT + l * NQP + 2 * j);
         const float4 c0 = *reinterpret_cast<const float4*>(sC0 + l * 8 * TE + e * 8);
-        const float2 c1 = *reinterpret_cast<const float2*>(sC0 + l * 8 * TE + e * 8 + 4);
-        const float cv[6] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y};
+        const float4 c1 = *reinterpret_cast<const float4*>(sC0 + l * 8 * TE + e * 8 + 4);
+        const float cv[NC] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z};
 #pragma unroll
-        for (int p = 0; p < 6; ++p) {
+        for (int p = 0; p < NC; ++p) {
           acc[0][p] = fmaf(ph.x, cv[p], acc[0][p]);
           acc[1][p] = fmaf(ph.y, cv[p], acc[1][p]);
         }
@@ -333,7 +376,7 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
 #pragma unroll
       for (int n = 0; n < 2; ++n) {
         const int q = 2 * j + n;
-        if (q < NQ) sR[q * TE + e] = e < ne ? cdm_rate(acc[n], m) : 0.f;
+        if (q < NQ) sR[q * TE + e] = e < ne ? law_rate(a.law, acc[n], acc[n][6], m) : 0.f;
       }
     }
     __syncthreads();
@@ -524,7 +567,7 @@ __global__ void __launch_bounds__(128) k_faces(StepArgs a) {
         // boundary face: the flux is linear in the own trace for the cell-mean moduli, so
         // the trace is integrated in time first
         float lam, mu;
-        effective_lame(sC + (fc * 2 * CROWS) * 12, mm, &lam, &mu);
+        effective_lame(a.law, sC + (fc * 2 * CROWS) * 12, mm, &lam, &mu);
         const float cp = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * mm.rho_inv), cs = sqrtf(fmaxf(mu, 0.f) * mm.rho_inv);
         const float k_p = lam + 2.f * mu > 0.f ? cp / (lam + 2.f * mu) : 0.f;
         float ui[9];
@@ -594,8 +637,8 @@ __global__ void __launch_bounds__(128) k_faces(StepArgs a) {
         um[9] = fmaf(tau, am1, am0);
         up[9] = fmaf(tau, ap1, ap0);
         float Fm[9], Fp[9];
-        normal_flux(um, mm, n, Fm);
-        normal_flux(up, mp, n, Fp);
+        normal_flux(a.law, um, mm, n, Fm);
+        normal_flux(a.law, up, mp, n, Fp);
 #pragma unroll
         for (int p = 0; p < 9; ++p) Fb[p] = fmaf(gam, 0.5f * (Fm[p] + Fp[p]) + 0.5f * Cs * (um[p] - up[p]), Fb[p]);
       }
@@ -805,7 +848,7 @@ __global__ void __launch_bounds__(256, 2) k_face_flux(StepArgs a) {
         }
         float lam = 0.f, mu = 0.f, cpb = 0.f, csb = 0.f, k_p = 0.f;
         if (bc != 0) {
-          effective_lame(sRaw + (2 * fc) * RAW, mm, &lam, &mu);   // row 0 of the state: the cell-mean modes
+          effective_lame(a.law, sRaw + (2 * fc) * RAW, mm, &lam, &mu);   // row 0 of the state: the cell-mean modes
           cpb = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * mm.rho_inv);
           csb = sqrtf(fmaxf(mu, 0.f) * mm.rho_inv);
           k_p = lam + 2.f * mu > 0.f ? cpb / (lam + 2.f * mu) : 0.f;
@@ -846,8 +889,8 @@ __global__ void __launch_bounds__(256, 2) k_face_flux(StepArgs a) {
             boundary_flux(bc, um, n, lam, mu, mm.rho_inv, cpb, csb, k_p, F);
           } else {
             float Fm[9], Fp[9];
-            normal_flux(um, mm, n, Fm);
-            normal_flux(up, mp, n, Fp);
+            normal_flux(a.law, um, mm, n, Fm);
+            normal_flux(a.law, up, mp, n, Fp);
 #pragma unroll
             for (int p = 0; p < 9; ++p) F[p] = 0.5f * (Fm[p] + Fp[p]) + 0.5f * Cs * (um[p] - up[p]);
           }
@@ -1164,7 +1207,7 @@ __global__ void __launch_bounds__(256) k_corrector(StepArgs a) {
           }
           const float alpha = fmaf(tz[z], a0[n][7], a0[n][6]);
           float sig[6], r;
-          cdm_point(eps, alpha, m, sig, &r);
+          law_point(a.law, eps, alpha, m, sig, &r);
 #pragma unroll
           for (int p = 0; p < 6; ++p) sb[p] = fmaf(gz[z], sig[p], sb[p]);
           rb = fmaf(gz[z], r, rb);
@@ -1457,7 +1500,7 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
 #pragma unroll
           for (int z = 0; z < NT; ++z) {
             float sig[6], r;
-            cdm_point(v + z * 8, v[z * 8 + 6], m, sig, &r);
+            law_point(a.law, v + z * 8, v[z * 8 + 6], m, sig, &r);
 #pragma unroll
             for (int p = 0; p < 6; ++p) sb[p] = fmaf(gz[z], sig[p], sb[p]);
             rb = fmaf(gz[z], r, rb);

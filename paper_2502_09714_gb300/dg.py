@@ -24,7 +24,7 @@ EXPORTS = (
     "dg_set_state_device", "dg_get_state", "dg_get_state_f32", "dg_get_state_device", "dg_step",
     "dg_receivers", "dg_receivers_read", "dg_dt", "dg_time", "dg_n_modes", "dg_get_stats",
     "dg_profile_enable", "dg_profile_read", "dg_reference_table", "dg_last_error", "dg_destroy",
-    "dg_step_noalloc",
+    "dg_step_noalloc", "dg_set_rheology",
 )
 
 
@@ -79,6 +79,7 @@ def load_library(path: str | None = None) -> C.CDLL:
     sig = {
         "dg_mesh_create": ([C.POINTER(MeshDesc), C.POINTER(vp)], C.c_int),
         "dg_set_material": ([vp, C.POINTER(dbl), C.POINTER(dbl)], C.c_int),
+        "dg_set_rheology": ([vp, C.c_int], C.c_int),
         "dg_set_source": ([vp, C.POINTER(PointSource), i64], C.c_int),
         "dg_set_state": ([vp, C.POINTER(dbl), dbl], C.c_int),
         "dg_set_state_f32": ([vp, C.POINTER(C.c_float), dbl], C.c_int),
@@ -155,7 +156,7 @@ class Solver:
     """One libdg context: a mesh, its material, state, sources and receivers."""
 
     def __init__(self, elem_xyz, elem_vid, order, face_bc=None, cfl=0.5, stream=None,
-                 allocator=None, members=1):
+                 allocator=None, members=1, law="cdm"):
         self.lib = load_library()
         xyz = np.ascontiguousarray(elem_xyz, dtype=np.float64)
         vid = np.ascontiguousarray(elem_vid, dtype=np.int64)
@@ -176,6 +177,12 @@ class Solver:
                         float(cfl), stream_ptr, C.pointer(allocator) if allocator is not None else None)
         self.ctx = C.c_void_p()
         _check(self.lib, None, self.lib.dg_mesh_create(C.byref(desc), C.byref(self.ctx)))
+        if law != "cdm":
+            self.set_rheology(law)
+
+    def set_rheology(self, law):
+        """law: "cdm" (Eq. "cdb-model") or "ivm" (Eq. "ivm-model"); set the material after."""
+        self._chk(self.lib.dg_set_rheology(self.ctx, {"cdm": 0, "ivm": 1}[law]))
 
     # ------------------------------------------------------------------
     def _chk(self, status):
