@@ -205,6 +205,8 @@ def main():
     ap.add_argument("--order", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="c2: 196,608-tet two-layer cube (the benchmark); c3: ~4.35 M-tet regional-shaped box")
     ap.add_argument("--ensemble-members", type=int, default=0,
                     help="also time the ensemble workload (N=3, this many members) against one member")
     args = ap.parse_args()
@@ -221,11 +223,16 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dgpkg.build()
-    w = workload_c2(n=args.n, order=args.order)
+    if args.workload == "c3":
+        from synthetic.regional import workload_c3
+        w = workload_c3(order=args.order)
+    else:
+        w = workload_c2(n=args.n, order=args.order)
     mesh, mat, N = w["mesh"], w["material"], w["order"]
     E, L = mesh.n_elem, n_modes(N)
     stream = torch.cuda.current_stream()
-    s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, N, cfl=w["cfl"], stream=stream)
+    bc = mesh.face_bc if np.any(mesh.face_bc != 0) else None
+    s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, N, face_bc=bc, cfl=w["cfl"], stream=stream)
     s.set_material(mat)
     s.set_sources(w["sources"])
     s.set_receivers(w["receivers"])

@@ -65,12 +65,13 @@ def stf_integral(src, t):
     """Antiderivative of the moment-rate time function, zero at -infinity.
     stf 0: Ricker w(t) = (1 - 2 c tau^2) exp(-c tau^2), c = (pi f0)^2, tau = t - t0,
            antiderivative tau exp(-c tau^2);
-    stf 1: Gaussian rate of width sigma (f0 field), unit integral."""
+    stf 1: Gaussian rate of standard deviation sigma (the "sigma" field, or "f0"
+           as in the C-ABI's f0_or_sigma), unit integral."""
     tau = t - src["t0"]
     if src["stf"] == 0:
         c = (math.pi * src["f0"]) ** 2
         return tau * math.exp(-c * tau * tau)
-    sig = src["f0"]
+    sig = src["sigma"] if "sigma" in src else src["f0"]
     return 0.5 * (1.0 + math.erf(tau / (sig * math.sqrt(2.0))))
 
 

@@ -101,6 +101,11 @@ struct dg_ctx {
   dg_kernel_time prof[5]{};
 
   std::vector<std::pair<void*, size_t>> owned;
+
+  // point location: uniform buckets over the element bounding boxes (built on first use)
+  double bb_lo[3] = {0, 0, 0}, bb_cell[3] = {1, 1, 1};
+  int bb_n[3] = {0, 0, 0};
+  std::vector<int64_t> bucket_start, bucket_elems;
 };
 
 namespace {
@@ -241,9 +246,77 @@ dg_status upload(dg_ctx* ctx, T* dst, const void* src, size_t bytes) {
 }
 
 // first element (input order) whose closure contains x; fills xi in the sorted order
-bool locate(const dg_ctx* ctx, const double* x, int64_t* elem, double xi_sorted[3]) {
+void build_buckets(dg_ctx* ctx) {
+  const int64_t E = ctx->E;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = 0; i < 4 * E; ++i)
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = std::min(lo[c], ctx->xyz_user[3 * i + c]);
+      hi[c] = std::max(hi[c], ctx->xyz_user[3 * i + c]);
+    }
+  // about one bucket per element, shaped like the mesh's bounding box
+  double ext[3], vol = 1.0;
+  for (int c = 0; c < 3; ++c) {
+    ext[c] = std::max(hi[c] - lo[c], 1e-300);
+    vol *= ext[c];
+  }
+  const double cell = std::cbrt(vol / static_cast<double>(std::max<int64_t>(E, 1)));
+  int64_t total = 1;
+  for (int c = 0; c < 3; ++c) {
+    ctx->bb_n[c] = static_cast<int>(std::min<double>(std::max(1.0, std::ceil(ext[c] / cell)), 2048.0));
+    ctx->bb_lo[c] = lo[c];
+    ctx->bb_cell[c] = ext[c] / ctx->bb_n[c];
+    total *= ctx->bb_n[c];
+  }
+  auto range = [&](int64_t e, int lo_i[3], int hi_i[3]) {
+    for (int c = 0; c < 3; ++c) {
+      double a = INFINITY, b = -INFINITY;
+      for (int v = 0; v < 4; ++v) {
+        a = std::min(a, ctx->xyz_user[12 * e + 3 * v + c]);
+        b = std::max(b, ctx->xyz_user[12 * e + 3 * v + c]);
+      }
+      const double pad = 1e-9 * (b - a) + 1e-300;
+      lo_i[c] = std::max(0, static_cast<int>(std::floor((a - pad - ctx->bb_lo[c]) / ctx->bb_cell[c])));
+      hi_i[c] = std::min(ctx->bb_n[c] - 1, static_cast<int>(std::floor((b + pad - ctx->bb_lo[c]) / ctx->bb_cell[c])));
+    }
+  };
+  std::vector<int64_t> count(total + 1, 0);
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      for (int64_t i = 0; i < total; ++i) count[i + 1] += count[i];
+      ctx->bucket_start = count;
+      ctx->bucket_elems.assign(count[total], 0);
+    }
+    std::vector<int64_t> fill;
+    if (pass == 1) fill.assign(ctx->bucket_start.begin(), ctx->bucket_start.end() - 1);
+    for (int64_t e = 0; e < E; ++e) {           // ascending element order within each bucket
+      int a[3], b[3];
+      range(e, a, b);
+      for (int i = a[0]; i <= b[0]; ++i)
+        for (int j = a[1]; j <= b[1]; ++j)
+          for (int k = a[2]; k <= b[2]; ++k) {
+            const int64_t id = (static_cast<int64_t>(k) * ctx->bb_n[1] + j) * ctx->bb_n[0] + i;
+            if (pass == 0) ++count[id + 1];
+            else ctx->bucket_elems[fill[id]++] = e;
+          }
+    }
+  }
+}
+
+// The first element (input order) whose closure contains x, and x in that
+// element's reference coordinates of the sorted vertex order.
+bool locate(dg_ctx* ctx, const double* x, int64_t* elem, double xi_sorted[3]) {
   const double tol = 1e-10;
-  for (int64_t e = 0; e < ctx->E; ++e) {
+  if (ctx->bucket_start.empty()) build_buckets(ctx);
+  int idx[3];
+  for (int c = 0; c < 3; ++c) {
+    const double t = (x[c] - ctx->bb_lo[c]) / ctx->bb_cell[c];
+    if (!(t >= -1e-9 * ctx->bb_n[c]) || !(t <= ctx->bb_n[c] * (1 + 1e-9))) return false;
+    idx[c] = std::min(ctx->bb_n[c] - 1, std::max(0, static_cast<int>(std::floor(t))));
+  }
+  const int64_t id = (static_cast<int64_t>(idx[2]) * ctx->bb_n[1] + idx[1]) * ctx->bb_n[0] + idx[0];
+  for (int64_t k = ctx->bucket_start[id]; k < ctx->bucket_start[id + 1]; ++k) {
+    const int64_t e = ctx->bucket_elems[k];
     const double* X = &ctx->xyz_user[12 * e];
     double J[9], Ji[9], det;
     for (int r = 0; r < 3; ++r)

@@ -74,3 +74,54 @@ def assert_parity(q_gpu_abi, Q_ora, detJ, order, rel=TOL_REL_L2, alpha=TOL_ALPHA
 
 __all__ = ["make_solver", "make_oracle", "rel_l2", "alpha_max_diff", "assert_parity", "to_abi",
            "from_abi", "TOL_REL_L2", "TOL_ALPHA"]
+
+
+def face_neighbours(mesh):
+    """[E, 4] element across each face (the face opposite local vertex f), -1 on
+    boundary faces: vertex-id triples matched with one sort (no oracle code)."""
+    vid = np.asarray(mesh.elem_vid)
+    E = vid.shape[0]
+    keys = np.empty((4 * E, 3), dtype=np.int64)
+    for f in range(4):
+        keys[f::4] = np.sort(np.delete(vid, f, axis=1), axis=1)
+    order = np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))
+    ks = keys[order]
+    same = np.all(ks[1:] == ks[:-1], axis=1)
+    nbr = -np.ones(4 * E, dtype=np.int64)
+    i = np.nonzero(same)[0]
+    a, b = order[i], order[i + 1]
+    nbr[a] = b // 4
+    nbr[b] = a // 4
+    return nbr.reshape(E, 4)
+
+
+def submesh_oracle(mesh, material, order, rows, sources=(), law="cdm", cfl=0.5):
+    """An oracle over `rows` and their face neighbours only, for stepping `rows`
+    of a mesh too large for the oracle: faces of the neighbours that leave the
+    sub-mesh are tagged absorbing (they only enter the neighbours' own updates,
+    which are not compared).  Returns (oracle, element ids of the sub-mesh in
+    global order, positions of `rows` in it).  Sources outside the sub-mesh are
+    dropped."""
+    from oracle import MeshError, Oracle
+    nbr = face_neighbours(mesh)
+    rows = np.unique(np.asarray(rows))
+    nb = nbr[rows].ravel()
+    elems = np.unique(np.concatenate([rows, nb[nb >= 0]]))
+    pos = -np.ones(mesh.n_elem, dtype=np.int64)
+    pos[elems] = np.arange(elems.size)
+    bc = np.array(mesh.face_bc[elems], dtype=np.int8)
+    inner = nbr[elems]
+    leaving = (inner >= 0) & (pos[np.maximum(inner, 0)] < 0)
+    bc[leaving] = 2
+    o = Oracle(mesh.elem_xyz[elems], mesh.elem_vid[elems], order, material[elems], face_bc=bc, cfl=cfl,
+               face_rows=pos[rows], law=law)
+    kept = []
+    for s in sources:
+        try:
+            o.locate(s["x"])
+            kept.append(s)
+        except MeshError:
+            pass
+    if kept:
+        o.set_sources(kept)
+    return o, elems, pos[rows]
