@@ -44,6 +44,10 @@ struct Dim {
   static constexpr int SH = sum_hi(N);
 };
 
+// Row stride of the nodal terms [NQ][10 TE]: padded so that consecutive volume
+// nodes (one per lane) do not fall on the same banks.
+__host__ __device__ constexpr int nb_stride(int te) { return 10 * te % 8 == 0 ? 10 * te + 4 : 10 * te; }
+
 // CDM stress (Eq. "cdb-model") and damage rate, with xi = 0 below I2 = 1e-30
 // and the rate written as C_d gamma_r max(0, I1 sqrt(I2) - xi0 I2).
 __device__ __forceinline__ void cdm_point(const float e[6], float alpha, const MatF& m,
@@ -669,10 +673,15 @@ struct FluxCfg : Dim<N> {
   static constexpr int GP = G == 5 ? 8 : 4;                 // stride of a node group in the table
   static constexpr int TF = 64 / (3 * NG);                  // faces per tile: 2 TF NG 3 <= 128 units per kind
   static constexpr int UPK = 2 * TF * NG * 3;               // trace units per kind
-  static constexpr int RAW = D::QS + D::DS;                 // staged floats per side: state, predictor output
+  static constexpr int RAW_USED = D::QS + D::DS;            // staged floats per side: state, predictor output
+  static constexpr int RAW = RAW_USED % 32 == 0 ? RAW_USED + 4 : RAW_USED;   // side stride off the bank period
+  // node group g of a table row starts at g GP + 4 (g / (32 / GP)): groups that would
+  // fall on the same banks are shifted by 16 bytes
+  static constexpr int goff(int g) { return g * GP + 4 * (g / (32 / GP)); }
+  static constexpr int VROW = round4(goff(NG - 1) + GP);
   static constexpr int META = 28;                           // per face: n, |S|/|J|, cp-, cp+, tag, local faces, materials
-  static constexpr int oV = 0;                              // [4][L][NG][GP] phi_l at the face nodes
-  static constexpr int oRaw = round4(oV + 4 * D::L * NG * GP);   // [TF][2][RAW]
+  static constexpr int oV = 0;                              // [4][L][VROW] phi_l at the face nodes
+  static constexpr int oRaw = round4(oV + 4 * D::L * VROW);  // [TF][2][RAW]
   static constexpr int oMeta = oRaw + TF * 2 * RAW;         // [TF][META]
   static constexpr int oTr = round4(oMeta + TF * META);     // [TF][2][N+1][NGG][12] traces per order
   static constexpr int SMEM = oTr + TF * 2 * (N + 1) * NGG * 12;
@@ -710,7 +719,7 @@ __global__ void __launch_bounds__(256, 2) k_face_flux(StepArgs a) {
     const int g = r % NG, r2 = r / NG;
     const int l = r2 % L, lf = r2 / L;
     const int node = g * G + n;
-    sV[w] = (n < G && node < NF) ? __ldg(tb + T.VfT + (lf * L + l) * NFP + node) : 0.f;
+    sV[(lf * L + l) * C::VROW + C::goff(g) + n] = (n < G && node < NF) ? __ldg(tb + T.VfT + (lf * L + l) * NFP + node) : 0.f;
   }
 
   const int64_t ntiles = (a.F + TF - 1) / TF;
@@ -720,7 +729,7 @@ __global__ void __launch_bounds__(256, 2) k_face_flux(StepArgs a) {
     __syncthreads();
     // one batch of asynchronous copies: per face the normal, both cells' P speeds and
     // materials; per side the state and the predictor output as stored
-    constexpr int CH = RAW / 4;                  // 16-byte chunks per side
+    constexpr int CH = C::RAW_USED / 4;          // 16-byte chunks per side
     for (int w = tid; w < TF * (2 * CH + 8); w += C::THREADS) {
       const int fc = w / (2 * CH + 8), r = w - fc * (2 * CH + 8);
       if (fc >= nf) continue;
@@ -764,7 +773,7 @@ __global__ void __launch_bounds__(256, 2) k_face_flux(StepArgs a) {
         const float* mt = sMeta + fc * META;
         if (fc < nf && !(side && mt[6] != 0.f)) {
           const int lf = static_cast<int>(side ? mt[24] : mt[7]);
-          const float* V = sV + (lf * L * NG + g) * GP;
+          const float* V = sV + lf * L * C::VROW + C::goff(g);
           const float* R = sRaw + s2 * RAW;
           float* out = sTr + (s2 * (N + 1)) * NGG * 12 + (g * G) * 12;
           if (kind == 0) {
@@ -780,7 +789,7 @@ __global__ void __launch_bounds__(256, 2) k_face_flux(StepArgs a) {
 #pragma unroll
             for (int l = 0; l < L; ++l) {
               float v[G];
-              load_group<N>(V + l * NG * GP, v);
+              load_group<N>(V + l * C::VROW, v);
               const float2 x01 = *reinterpret_cast<const float2*>(R + l * 10 + 4 * c);
               const float x2 = pB[l * sB], x3r = R[l * 10 + o3];
               const float x[4] = {x01.x, x01.y, x2, c2 ? 0.f : x3r};
@@ -804,7 +813,7 @@ __global__ void __launch_bounds__(256, 2) k_face_flux(StepArgs a) {
 #pragma unroll
               for (int l = 0; l < n_modes(N - o); ++l) {
                 float v[G];
-                load_group<N>(V + l * NG * GP, v);
+                load_group<N>(V + l * C::VROW, v);
                 const float* xr = Dh + d_offset(N, o) + l * 9;
                 const float x[3] = {xr[0], xr[1], xr[2]};
 #pragma unroll
@@ -935,7 +944,7 @@ struct CorrCfg : Dim<N> {
   static constexpr int oQ = TSM ? round4(oVfw + 4 * D::NF * D::LP) : 0;   // [TE][QS]
   static constexpr int oC0 = oQ + TE * D::QS;              // [L][8 TE]  eps(6), alpha0, alpha1
   static constexpr int oCh = oC0 + D::L * 8 * TE;          // [SH][8 TE] higher-order strain rows
-  static constexpr int BN = D::NQ * NB, BF = 4 * D::NF * NFC;
+  static constexpr int BN = D::NQ * nb_stride(TE), BF = 4 * D::NF * NFC;
   static constexpr int oB = oCh + round4(D::SH) * 8 * TE;  // [NQ][NB] nodal terms | [4 NF][NFC] face fluxes
   static constexpr int oM = oB + round4(BN > BF ? BN : BF);     // [3][L][NM] modal GEMM inputs
   static constexpr int oA = oM + 3 * D::L * NM;            // [TE][L][10] update accumulator
@@ -961,7 +970,7 @@ __device__ __forceinline__ void corrector_tail(const StepArgs& a, int64_t e0, in
   constexpr int L = D::L, NQ = D::NQ, NF = D::NF, LP = D::LP, QS = D::QS, FFS = D::FFS;
   constexpr int NV = 3 * TE, NB = 10 * TE, NM = 2 * NV, NFC = 9 * TE;
     // projection by the volume rule: That_e'm (into the modal inputs) and the damage source
-    block_gemm<KS_PRJ>(sVw, LP, sB, NB, LP, NB, NQ, sPart, [&](int l, int col, float v) {
+    block_gemm<KS_PRJ>(sVw, LP, sB, nb_stride(TE), LP, NB, NQ, sPart, [&](int l, int col, float v) {
       if (l < L) {
         const int e = col / 10, c = col - 10 * e;
         if (c < 9) sM[((c / 3) * L + l) * NM + NV + e * 3 + c % 3] = v;
@@ -1019,7 +1028,7 @@ __device__ __forceinline__ void corrector_tail(const StepArgs& a, int64_t e0, in
     __syncthreads();
     // strain rows -(v_i d_j phi + v_j d_i phi)/2 and velocity rows from the modal derivatives
     for (int w = threadIdx.x; w < TE * L; w += blockDim.x) {
-      const int e = w / L, k = w - e * L;
+      const int k = w / TE, e = w - k * TE;     // element fastest: lanes spread over the banks of sH
       const float* ti = sGeo ? sGeo + e * 32 : a.geom[e0 + (e < ne ? e : 0)].tinv;
       float hd[3][3];
 #pragma unroll
@@ -1214,7 +1223,7 @@ __global__ void __launch_bounds__(256) k_corrector(StepArgs a) {
         }
         // T_e'm = -(1/rho) sum_d Theta^{-1}_{e'd} sigma_md (time integrated) and the integrated rate
         const float S[3][3] = {{sb[0], sb[3], sb[5]}, {sb[3], sb[1], sb[4]}, {sb[5], sb[4], sb[2]}};
-        float* bq = sB + q * NB + e * 10;
+        float* bq = sB + q * nb_stride(TE) + e * 10;
 #pragma unroll
         for (int ep = 0; ep < 3; ++ep)
 #pragma unroll
@@ -1261,7 +1270,7 @@ struct CorrTcCfg : Dim<N> {
   static constexpr int oBeH = round4(oVfw + 4 * D::NF * D::LP);   // [NBC x KP] canonical
   static constexpr int oBeL = oBeH + NBC * KP;
   static constexpr int BE_END = oBeL + NBC * KP;
-  static constexpr int BN = D::NQ * NB, BF = 4 * D::NF * NFC;
+  static constexpr int BN = D::NQ * nb_stride(TE), BF = 4 * D::NF * NFC;
   static constexpr int B_SIZE = round4(BN > BF ? BN : BF);
   static constexpr int P1 = KS_PRJ * D::LP * NB, P2 = KS_FACE * D::LP * NFC, P3 = 3 * D::LP * NM;
   static constexpr int PART = round4(P1 > P2 ? (P1 > P3 ? P1 : P3) : (P2 > P3 ? P2 : P3));
@@ -1506,7 +1515,7 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
             rb = fmaf(gz[z], r, rb);
           }
           const float S[3][3] = {{sb[0], sb[3], sb[5]}, {sb[3], sb[1], sb[4]}, {sb[5], sb[4], sb[2]}};
-          float* bq = sB + q * NB + e * 10;
+          float* bq = sB + q * nb_stride(TE) + e * 10;
 #pragma unroll
           for (int ep = 0; ep < 3; ++ep)
 #pragma unroll
