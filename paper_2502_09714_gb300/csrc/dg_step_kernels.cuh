@@ -215,7 +215,7 @@ __device__ __forceinline__ void block_gemm(const float* __restrict__ A, int lda,
   const int kchunk = (K + KS - 1) / KS;
   for (int w = threadIdx.x; w < tiles * KS; w += blockDim.x) {
     const int ks = w / tiles, r = w - ks * tiles;
-    const int mi = r % mq, ni = r / mq;
+    const int mi = r / nq, ni = r - mi * nq;   // column quad fastest: the partial stores of a warp are contiguous
     float acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -983,7 +983,7 @@ __device__ __forceinline__ void corrector_tail(const StepArgs& a, int64_t e0, in
       constexpr int MQ = LP / 4, NQQ = NM / 4, TILES = MQ * NQQ;
       for (int w = threadIdx.x; w < 3 * TILES; w += blockDim.x) {
         const int ep = w / TILES, r = w - ep * TILES;
-        const int mi = r % MQ, ni = r / MQ;
+        const int ni = r % NQQ, mi = r / NQQ;   // column quad fastest: contiguous stores
         const float* A = sKtB + ep * L * LP + 4 * mi;
         const float* B = sM + ep * L * NM + 4 * ni;
         float acc[4][4];
