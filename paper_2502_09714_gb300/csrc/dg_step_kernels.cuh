@@ -667,11 +667,12 @@ template <int N>
 struct FluxCfg : Dim<N> {
   using D = Dim<N>;
   static constexpr int THREADS = 256;
+  static constexpr int KT = THREADS / 2;                    // threads per trace kind
   static constexpr int G = N == 4 ? 5 : 4;                  // face nodes per trace tile
   static constexpr int NG = (D::NF + G - 1) / G;            // node groups
   static constexpr int NGG = NG * G;                        // padded face nodes
   static constexpr int GP = G == 5 ? 8 : 4;                 // stride of a node group in the table
-  static constexpr int TF = 64 / (3 * NG);                  // faces per tile: 2 TF NG 3 <= 128 units per kind
+  static constexpr int TF = KT / (6 * NG);                  // faces per tile: 2 TF NG 3 <= KT units per kind
   static constexpr int UPK = 2 * TF * NG * 3;               // trace units per kind
   static constexpr int RAW_USED = D::QS + D::DS;            // staged floats per side: state, predictor output
   static constexpr int RAW = RAW_USED % 32 == 0 ? RAW_USED + 4 : RAW_USED;   // side stride off the bank period
@@ -685,8 +686,8 @@ struct FluxCfg : Dim<N> {
   static constexpr int oMeta = oRaw + TF * 2 * RAW;         // [TF][META]
   static constexpr int oTr = round4(oMeta + TF * META);     // [TF][2][N+1][NGG][12] traces per order
   static constexpr int SMEM = oTr + TF * 2 * (N + 1) * NGG * 12;
-  static_assert(TF >= 1 && UPK <= 128, "trace units per kind");
-  static_assert(SMEM * 4 * 2 <= 227 * 1024, "two face CTAs per SM");
+  static_assert(TF >= 1 && UPK <= KT, "trace units per kind");
+  static_assert(THREADS > 256 || SMEM * 4 * 2 <= 227 * 1024, "two face CTAs per SM");
 };
 
 template <int N>
@@ -698,7 +699,7 @@ __device__ __forceinline__ void load_group(const float* v, float* out) {
 }
 
 template <int N>
-__global__ void __launch_bounds__(256, 2) k_face_flux(StepArgs a) {
+__global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS) k_face_flux(StepArgs a) {
   using C = FluxCfg<N>;
   constexpr int L = C::L, NF = C::NF, NFP = C::NFP, NT = C::NT, QS = C::QS, DS = C::DS, AOFF = C::AOFF;
   constexpr int FFS = C::FFS, TF = C::TF, G = C::G, NG = C::NG, NGG = C::NGG, GP = C::GP, RAW = C::RAW;
@@ -765,7 +766,7 @@ __global__ void __launch_bounds__(256, 2) k_face_flux(StepArgs a) {
 
     // traces: warps 0-3 order 0 (G nodes x 4 columns), warps 4-7 orders 1..N (G nodes x 3 fields)
     {
-      const int kind = tid >> 7, lu = tid & 127;
+      const int kind = tid / C::KT, lu = tid - kind * C::KT;
       if (lu < UPK) {
         const int s2 = lu / (NG * 3), r = lu - s2 * (NG * 3);
         const int g = r / 3, c = r - 3 * g;
