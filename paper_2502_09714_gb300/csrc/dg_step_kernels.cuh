@@ -1,20 +1,23 @@
-// Kernels of one ADER-DG step for the CDM damage rheology (arXiv 2502.09714,
-// Appendix A), FP32, templated on the degree N.
+// Kernels of one ADER-DG step for the damage rheologies of arXiv 2502.09714
+// (CDM of Eq. "cdb-model", IVM of Eq. "ivm-model"; Appendix A), FP32, templated
+// on the degree N.
 //
 //   k_predictor  cell-mean effective Jacobian, Cauchy-Kovalevskaya recursion
 //                (Eq. "CKIter-ref-matrix") and damage-rate source at i = 1
 //                (Eq. "CKIter-ref-source")                       -> D, cp
-//   k_faces      Rusanov flux (Eq. "rusanov-flux") at the space-time nodes of
+//   k_face_flux  Rusanov flux (Eq. "rusanov-flux") at the space-time nodes of
 //                every interior face, once per face, time-integrated; absorbing
 //                and free-surface fluxes (Appendix A) on boundary faces -> FF
-//   k_corrector  volume flux and damage source (Eqs. "3rd term", "rhs term"),
-//                face term (Eq. "2nd term") from FF, update (Eq. "time-integrated")
+//   k_corrector_tc (degrees 2..4) / k_corrector (1, 5): volume flux and damage
+//                source (Eqs. "3rd term", "rhs term"), face term (Eq. "2nd
+//                term") from FF, update (Eq. "time-integrated")
 //
 // Each kernel is persistent: a CTA loads the reference tables it needs into
-// shared memory once, then walks over tiles of elements (or faces).  Dense
-// contractions with the shared tables are block GEMMs with 4x4 register tiles;
-// the evaluation of the Taylor coefficients at the volume nodes uses two-node
-// register tiles and feeds the pointwise CDM law directly from registers.
+// shared memory once, then walks over tiles of elements (or faces).  The
+// evaluation of the Taylor expansion at the volume nodes runs on the tensor
+// cores (tcgen05, 3xTF32) for degrees 2..4 and feeds the pointwise law from
+// tensor memory; the other contractions with the shared tables are block GEMMs
+// with 4x4 register tiles.
 #pragma once
 
 #include <cstdlib>
@@ -449,212 +452,7 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
 // ===========================================================================
 // Faces: Rusanov flux at the space-time nodes of each interior face, once per
 // face; boundary faces (side 1 absent, tag in the fourth entry) take the
-// absorbing or free-surface flux
-// ===========================================================================
-template <int N, bool TSM>
-struct FaceCfg : Dim<N> {
-  using D = Dim<N>;
-  static constexpr int TF = N >= 4 ? 4 : (N == 3 ? 8 : 16);
-  static constexpr int THREADS = 128;
-  static constexpr int CROWS = D::L + D::SH;               // coefficient rows per side
-  static constexpr int oVfT = 0;
-  static constexpr int oC = TSM ? round4(oVfT + 4 * D::L * D::NFP) : 0;   // [TF][2][CROWS][12]
-  static constexpr int oTr = oC + TF * 2 * CROWS * 12;          // [TF][2][N+1][NFP][12]
-  static constexpr int SMEM = oTr + TF * 2 * (N + 1) * D::NFP * 12;
-  static constexpr bool FITS = SMEM * 4 <= 227 * 1024;
-  static_assert(FITS || TSM, "face kernel shared memory");
-};
-
-template <int N, bool TSM>
-__global__ void __launch_bounds__(128) k_faces(StepArgs a) {
-  using C = FaceCfg<N, TSM>;
-  constexpr int L = C::L, NF = C::NF, NFP = C::NFP, NT = C::NT, QS = C::QS, DS = C::DS, TF = C::TF;
-  constexpr int CROWS = C::CROWS, FFS = C::FFS;
-  constexpr TableLayout T = table_layout(N);
-  extern __shared__ float4 smem4[];
-  float* sm = reinterpret_cast<float*>(smem4);
-  const float* sVfT = TSM ? sm + C::oVfT : a.tables + T.VfT;
-  float* sC = sm + C::oC;
-  float* sTr = sm + C::oTr;
-  const float* tb = a.tables;
-  const float dt = a.dt;
-  if (TSM) copy_to_smem(sm + C::oVfT, tb + T.VfT, 4 * L * NFP);
-
-  const int64_t ntiles = (a.F + TF - 1) / TF;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t f0 = tile * TF;
-    const int nf = static_cast<int>(min(static_cast<int64_t>(TF), a.F - f0));
-    __syncthreads();
-    // stage both sides: rows l < L: (Q[l][0..9], D1alpha[l], 0); rows of order o >= 1: (D^o[l][0..8], 0, 0, 0)
-    for (int w = threadIdx.x; w < TF * 2 * CROWS; w += blockDim.x) {
-      const int fc = w / (2 * CROWS), r2 = w - fc * 2 * CROWS;
-      const int side = r2 / CROWS, r = r2 - side * CROWS;
-      float v[12];
-#pragma unroll
-      for (int p = 0; p < 12; ++p) v[p] = 0.f;
-      const int4 fa = fc < nf ? a.faces[f0 + fc] : make_int4(0, 0, -1, 0);
-      if (fc < nf && !(side && fa.z < 0)) {        // a boundary face has no side 1
-        const int64_t e = side ? fa.z : fa.x;
-        if (r < L) {
-          const float* q = a.q_in + e * QS + r * 10;
-#pragma unroll
-          for (int p = 0; p < 10; ++p) v[p] = __ldg(q + p);
-          v[10] = __ldg(a.d + e * DS + C::AOFF + r);
-        } else {
-          // locate the order of row r
-          int o = 1, rr = r - L;
-          while (rr >= n_modes(N - o)) { rr -= n_modes(N - o); ++o; }
-          const float* dd = a.d + e * DS + d_offset(N, o) + rr * 9;
-#pragma unroll
-          for (int p = 0; p < 9; ++p) v[p] = __ldg(dd + p);
-        }
-      }
-      float4* dst = reinterpret_cast<float4*>(sC + ((fc * 2 + side) * CROWS + r) * 12);
-      dst[0] = make_float4(v[0], v[1], v[2], v[3]);
-      dst[1] = make_float4(v[4], v[5], v[6], v[7]);
-      dst[2] = make_float4(v[8], v[9], v[10], v[11]);
-    }
-    __syncthreads();
-    // traces of each Taylor order at the face nodes (two nodes x 12 columns per item)
-    constexpr int NPAIR = NFP / 2;
-    for (int w = threadIdx.x; w < TF * 2 * (N + 1) * NPAIR; w += blockDim.x) {
-      const int j = w % NPAIR;
-      const int r1 = w / NPAIR;
-      const int o = r1 % (N + 1);
-      const int fs = r1 / (N + 1);            // face * 2 + side
-      const int fc = fs >> 1, side = fs & 1;
-      int lf = 0;
-      if (fc < nf) {
-        const int4 fa = a.faces[f0 + fc];
-        lf = side ? (fa.z < 0 ? 0 : fa.w) : fa.y;
-      }
-      const int K = o == 0 ? L : n_modes(N - o);
-      const int row0 = o == 0 ? 0 : L + row_hi(N, o);
-      const float* cb = sC + (fs * CROWS + row0) * 12;
-      const float* tab = sVfT + lf * L * NFP + 2 * j;
-      float acc[2][12];
-#pragma unroll
-      for (int n = 0; n < 2; ++n)
-#pragma unroll
-        for (int p = 0; p < 12; ++p) acc[n][p] = 0.f;
-      for (int l = 0; l < K; ++l) {
-        const float2 ph = *reinterpret_cast<const float2*>(tab + l * NFP);
-        const float4 c0 = *reinterpret_cast<const float4*>(cb + l * 12);
-        const float4 c1 = *reinterpret_cast<const float4*>(cb + l * 12 + 4);
-        const float4 c2 = *reinterpret_cast<const float4*>(cb + l * 12 + 8);
-        const float cv[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
-#pragma unroll
-        for (int p = 0; p < 12; ++p) {
-          acc[0][p] = fmaf(ph.x, cv[p], acc[0][p]);
-          acc[1][p] = fmaf(ph.y, cv[p], acc[1][p]);
-        }
-      }
-#pragma unroll
-      for (int n = 0; n < 2; ++n) {
-        float4* dst = reinterpret_cast<float4*>(sTr + ((fs * (N + 1) + o) * NFP + 2 * j + n) * 12);
-        dst[0] = make_float4(acc[n][0], acc[n][1], acc[n][2], acc[n][3]);
-        dst[1] = make_float4(acc[n][4], acc[n][5], acc[n][6], acc[n][7]);
-        dst[2] = make_float4(acc[n][8], acc[n][9], acc[n][10], acc[n][11]);
-      }
-    }
-    __syncthreads();
-    // Rusanov flux at the space-time nodes, integrated in time
-    for (int w = threadIdx.x; w < TF * NF; w += blockDim.x) {
-      const int fc = w / NF, i = w - fc * NF;
-      if (fc >= nf) continue;
-      const int4 fa = a.faces[f0 + fc];
-      const int64_t em = fa.x, ep = fa.z;
-      const GeomF* g = a.geom + em;
-      const float n[3] = {g->face[fa.y][0], g->face[fa.y][1], g->face[fa.y][2]};
-      const MatF mm = a.mat[em];
-      if (ep < 0) {
-        // boundary face: the flux is linear in the own trace for the cell-mean moduli, so
-        // the trace is integrated in time first
-        float lam, mu;
-        effective_lame(a.law, sC + (fc * 2 * CROWS) * 12, mm, &lam, &mu);
-        const float cp = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * mm.rho_inv), cs = sqrtf(fmaxf(mu, 0.f) * mm.rho_inv);
-        const float k_p = lam + 2.f * mu > 0.f ? cp / (lam + 2.f * mu) : 0.f;
-        float ui[9];
-#pragma unroll
-        for (int p = 0; p < 9; ++p) ui[p] = 0.f;
-#pragma unroll
-        for (int z = 0; z < NT; ++z) {
-          const float tau = __ldg(tb + T.tz + z) * dt, gam = __ldg(tb + T.gz + z) * dt;
-          float c = gam;
-#pragma unroll
-          for (int o = 0; o <= N; ++o) {
-            if (o > 0) c *= tau / static_cast<float>(o);
-            const float* xm = sTr + (((fc * 2 + 0) * (N + 1) + o) * NFP + i) * 12;
-#pragma unroll
-            for (int p = 0; p < 9; ++p) ui[p] = fmaf(c, xm[p], ui[p]);
-          }
-        }
-        float Fb[9];
-        boundary_flux(fa.w, ui, n, lam, mu, mm.rho_inv, cp, cs, k_p, Fb);
-        float* out = a.ff + (f0 + fc) * FFS + i * 9;
-#pragma unroll
-        for (int p = 0; p < 9; ++p) out[p] = Fb[p];
-        continue;
-      }
-      const MatF mp = a.mat[ep];
-      const float Cs = fmaxf(a.cp[em], a.cp[ep]);
-      float tm[N + 1][9], tp[N + 1][9];
-      float am0, am1, ap0, ap1;
-#pragma unroll
-      for (int o = 0; o <= N; ++o) {
-        const float* xm = sTr + (((fc * 2 + 0) * (N + 1) + o) * NFP + i) * 12;
-        const float* xp = sTr + (((fc * 2 + 1) * (N + 1) + o) * NFP + i) * 12;
-#pragma unroll
-        for (int p = 0; p < 9; ++p) {
-          tm[o][p] = xm[p];
-          tp[o][p] = xp[p];
-        }
-        if (o == 0) {
-          am0 = xm[9];
-          am1 = xm[10];
-          ap0 = xp[9];
-          ap1 = xp[10];
-        }
-      }
-      float Fb[9];
-#pragma unroll
-      for (int p = 0; p < 9; ++p) Fb[p] = 0.f;
-#pragma unroll
-      for (int z = 0; z < NT; ++z) {
-        const float tau = __ldg(tb + T.tz + z) * dt, gam = __ldg(tb + T.gz + z) * dt;
-        float um[10], up[10];
-#pragma unroll
-        for (int p = 0; p < 9; ++p) {
-          um[p] = tm[0][p];
-          up[p] = tp[0][p];
-        }
-        float c = 1.f;
-#pragma unroll
-        for (int o = 1; o <= N; ++o) {
-          c *= tau / static_cast<float>(o);
-#pragma unroll
-          for (int p = 0; p < 9; ++p) {
-            um[p] = fmaf(c, tm[o][p], um[p]);
-            up[p] = fmaf(c, tp[o][p], up[p]);
-          }
-        }
-        um[9] = fmaf(tau, am1, am0);
-        up[9] = fmaf(tau, ap1, ap0);
-        float Fm[9], Fp[9];
-        normal_flux(a.law, um, mm, n, Fm);
-        normal_flux(a.law, up, mp, n, Fp);
-#pragma unroll
-        for (int p = 0; p < 9; ++p) Fb[p] = fmaf(gam, 0.5f * (Fm[p] + Fp[p]) + 0.5f * Cs * (um[p] - up[p]), Fb[p]);
-      }
-      float* out = a.ff + (f0 + fc) * FFS + i * 9;
-#pragma unroll
-      for (int p = 0; p < 9; ++p) out[p] = Fb[p];
-    }
-  }
-}
-
-// ===========================================================================
-// Faces, second form: persistent CTAs of 256 threads, two per SM.  Per tile of
+// absorbing or free-surface flux.  Persistent CTAs of 256 threads, two per SM.  Per tile of
 // TF faces: both sides' state and predictor output staged in shared memory by
 // one batch of asynchronous copies, with the per-face normal, speeds and
 // materials; the traces as register-tiled products with the face basis table
@@ -1564,9 +1362,8 @@ cudaError_t launch_persistent(Kern kern, int64_t tiles, int grid_hint, const Ste
 }
 
 // Kernel variants (bit 0: predictor with shared-memory tables on a persistent
-// grid; bit 1: first-form face kernel likewise; bit 2: SIMT corrector likewise;
-// bit 3: SIMT corrector instead of the tensor-core one; bit 4: first-form face
-// kernel instead of k_face_flux).  Clear bits read the tables
+// grid; bit 2: SIMT corrector likewise; bit 3: SIMT corrector instead of the
+// tensor-core one).  Clear bits read the tables
 // through the L1 cache with one CTA per tile.  The default is the fastest
 // measured combination on GB300; DG_KERNEL_VARIANT overrides it for tuning.
 inline int table_residency_mask() {
@@ -1592,19 +1389,11 @@ cudaError_t launch_predictor_impl(const StepArgs& a, cudaStream_t s) {
 
 template <int N>
 cudaError_t launch_faces_impl(const StepArgs& a, cudaStream_t s) {
-  static bool cfg[3] = {false, false, false};
-  static int blocks[3] = {1, 1, 1};
-  if (!(table_residency_mask() & 16)) {
-    const int64_t tiles = (a.F + FluxCfg<N>::TF - 1) / FluxCfg<N>::TF;
-    return launch_persistent<FluxCfg<N>>(k_face_flux<N>, tiles, a.grid_face > 0 ? a.grid_face : 148, a, s,
-                                         &cfg[2], &blocks[2]);
-  }
-  const int64_t tiles = (a.F + FaceCfg<N, true>::TF - 1) / FaceCfg<N, true>::TF;
-  if constexpr (FaceCfg<N, true>::FITS) {
-    if (table_residency_mask() & 2)
-      return launch_persistent<FaceCfg<N, true>>(k_faces<N, true>, tiles, a.grid_face, a, s, &cfg[1], &blocks[1]);
-  }
-  return launch_persistent<FaceCfg<N, false>>(k_faces<N, false>, tiles, 0, a, s, &cfg[0], &blocks[0]);
+  static bool cfg = false;
+  static int blocks = 1;
+  const int64_t tiles = (a.F + FluxCfg<N>::TF - 1) / FluxCfg<N>::TF;
+  return launch_persistent<FluxCfg<N>>(k_face_flux<N>, tiles, a.grid_face > 0 ? a.grid_face : 148, a, s, &cfg,
+                                       &blocks);
 }
 
 template <int N>
