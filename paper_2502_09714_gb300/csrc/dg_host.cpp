@@ -227,8 +227,21 @@ std::vector<double> build_tables(int N) {
         const float x = static_cast<float>(t[T.VvT + l * NQP + q]);
         const float h = tf32_round(x);
         t[T.PhiH + tc_canon(q, l, KP)] = h;
-        t[T.PhiL + tc_canon(q, l, KP)] = x - h;
+        t[T.PhiL + tc_canon(q, l, KP)] = tf32_round(x - h);
       }
+    const int KQ = tc_kq(N);
+    for (int l = 0; l < L; ++l)
+      for (int q = 0; q < NQ; ++q) {
+        const float x = static_cast<float>(t[T.Vw + q * LP + l]);
+        const float h = tf32_round(x);
+        t[T.PrjH + l * KQ + q] = h;
+        t[T.PrjL + l * KQ + q] = tf32_round(x - h);
+      }
+    for (int l = 0; l < L; ++l) {
+      double sum = 0.0;
+      for (int q = 0; q < NQ; ++q) sum += t[T.Vw + q * LP + l];
+      t[T.PrjS + l] = sum;
+    }
   }
   ref::Rule1 tr = ref::time_rule(NT);
   for (int z = 0; z < NT; ++z) {

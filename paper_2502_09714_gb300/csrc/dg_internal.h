@@ -45,6 +45,9 @@ __host__ __device__ constexpr int round8(int x) { return (x + 7) & ~7; }
 // elements, 128 bytes; consecutive along K, then 8-row groups), split into a
 // TF32 high part and an FP32 remainder.
 __host__ __device__ constexpr bool tc_volume(int N) { return N >= 2 && N <= 4; }
+// K extent (volume nodes rounded up to 32) of the tensor-core projection, whose
+// A operand w_q phi_l(x_q) sits in tensor memory: lane l, column q.
+__host__ __device__ constexpr int tc_kq(int N) { return (n_vol_nodes(N) + 31) / 32 * 32; }
 __host__ __device__ constexpr int tc_kp(int N) { return round8(n_modes(N)); }
 __host__ __device__ constexpr int tc_canon(int row, int k, int kp) {
   return (row >> 3) * (kp / 4 * 32) + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
@@ -61,7 +64,10 @@ struct TableLayout {
   int VfT;    // [4][L][NFP] phi_l at face node i of local face f
   int Vfw;    // [4][NF][LP] beta_i phi_k(x_i) at face node i of local face f (beta sums to 1)
   int PhiH;   // [128 x KP]  canonical tensor-core operand: TF32 part of phi_l(x_q) (rows q >= NQ zero)
-  int PhiL;   // [128 x KP]  phi_l(x_q) minus its TF32 part
+  int PhiL;   // [128 x KP]  phi_l(x_q) minus its TF32 part, rounded to TF32
+  int PrjH;   // [128][KQ]   TF32 part of w_q phi_l(x_q), row l, column q (zero beyond L and NQ)
+  int PrjL;   // [128][KQ]   w_q phi_l(x_q) minus its TF32 part, rounded to TF32
+  int PrjS;   // [LP]        sum_q w_q phi_l(x_q), summed in double
   int tz;     // [NT]        time nodes in [0,1]
   int gz;     // [NT]        time weights (sum 1)
   int total;
@@ -81,6 +87,9 @@ __host__ __device__ constexpr TableLayout table_layout(int N) {
   t.Vfw = o; o = round4(o + 4 * NF * LP);
   t.PhiH = o; o = round4(o + (tc_volume(N) ? 128 * tc_kp(N) : 0));
   t.PhiL = o; o = round4(o + (tc_volume(N) ? 128 * tc_kp(N) : 0));
+  t.PrjH = o; o = round4(o + (tc_volume(N) ? 128 * tc_kq(N) : 0));
+  t.PrjL = o; o = round4(o + (tc_volume(N) ? 128 * tc_kq(N) : 0));
+  t.PrjS = o; o = round4(o + (tc_volume(N) ? LP : 0));
   t.tz = o;  o += NT;
   t.gz = o;  o += NT;
   t.total = round4(o);

@@ -867,6 +867,96 @@ __device__ __forceinline__ void corrector_tail(const StepArgs& a, int64_t e0, in
     if (bad) atomicOr(a.status, kStatusNonFinite);
 }
 
+// Second half of the tensor-core corrector, after the projection (That already in
+// the modal inputs sM, the damage source in column 9 of sA): modal derivative,
+// scaled face fluxes, strain/velocity rows, face term and update.
+template <int N, int TE, int KS_FACE>
+__device__ __forceinline__ void corrector_tail_tc(const StepArgs& a, int64_t e0, int ne, const float* sKtB,
+                                                  const float* sVfw, const float* sQ, const float* sM, float* sA,
+                                                  float* sH, float* sF, float* sPart, const float* sFraw,
+                                                  const float* sGeo) {
+  using D = Dim<N>;
+  constexpr int L = D::L, NF = D::NF, LP = D::LP, QS = D::QS, FFS = D::FFS;
+  constexpr int NV = 3 * TE, NM = 2 * NV, NFC = 9 * TE;
+  // modal derivative: H_e'[k][col] = sum_l int phi_l d phi_k/d xi_e' M_e'[l][col], e' = 0..2 in one pass
+  {
+    constexpr int MQ = LP / 4, NQQ = NM / 4, TILES = MQ * NQQ;
+    for (int w = threadIdx.x; w < 3 * TILES; w += blockDim.x) {
+      const int ep = w / TILES, r = w - ep * TILES;
+      const int ni = r % NQQ, mi = r / NQQ;
+      const float* A = sKtB + ep * L * LP + 4 * mi;
+      const float* B = sM + ep * L * NM + 4 * ni;
+      float acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 5
+      for (int l = 0; l < L; ++l) {
+        const float4 av = *reinterpret_cast<const float4*>(A + l * LP);
+        const float4 bv = *reinterpret_cast<const float4*>(B + l * NM);
+        const float x[4] = {av.x, av.y, av.z, av.w}, y[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(x[i], y[j], acc[i][j]);
+      }
+      float* h = sH + ep * LP * NM;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4*>(h + (4 * mi + i) * NM + 4 * ni) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    }
+  }
+  // face fluxes of the tile's elements, signed and scaled by |S_f| / |J|
+  for (int w = threadIdx.x; w < TE * 4 * NF * 9; w += blockDim.x) {
+    const int e = w / (4 * NF * 9), r = w - e * 4 * NF * 9;
+    const int f = r / (NF * 9), r2 = r - f * NF * 9;
+    const int i = r2 / 9, p = r2 - 9 * i;
+    sF[(f * NF + i) * NFC + e * 9 + p] = e < ne ? sGeo[e * 32 + 17 + f] * sFraw[(e * 4 + f) * FFS + i * 9 + p] : 0.f;
+  }
+  __syncthreads();
+  // strain rows -(v_i d_j phi + v_j d_i phi)/2 and velocity rows from the modal derivatives
+  for (int w = threadIdx.x; w < TE * L; w += blockDim.x) {
+    const int k = w / TE, e = w - k * TE;
+    const float* ti = sGeo + e * 32;
+    float hd[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int mc = 0; mc < 3; ++mc)
+        hd[d][mc] = ti[0 * 3 + d] * sH[(0 * LP + k) * NM + e * 3 + mc] + ti[1 * 3 + d] * sH[(1 * LP + k) * NM + e * 3 + mc] +
+                    ti[2 * 3 + d] * sH[(2 * LP + k) * NM + e * 3 + mc];
+    float* ao = sA + (e * L + k) * 10;
+    ao[0] -= hd[0][0];
+    ao[1] -= hd[1][1];
+    ao[2] -= hd[2][2];
+    ao[3] -= 0.5f * (hd[1][0] + hd[0][1]);
+    ao[4] -= 0.5f * (hd[2][1] + hd[1][2]);
+    ao[5] -= 0.5f * (hd[0][2] + hd[2][0]);
+#pragma unroll
+    for (int mc = 0; mc < 3; ++mc)
+      ao[6 + mc] += sH[(0 * LP + k) * NM + NV + e * 3 + mc] + sH[(1 * LP + k) * NM + NV + e * 3 + mc] +
+                    sH[(2 * LP + k) * NM + NV + e * 3 + mc];
+  }
+  __syncthreads();
+  block_gemm<KS_FACE>(sVfw, LP, sF, NFC, LP, NFC, 4 * NF, sPart, [&](int k, int col, float v) {
+    if (k < L) {
+      const int e = col / 9, p = col - 9 * e;
+      sA[(e * L + k) * 10 + p] -= v;
+    }
+  });
+  if (KS_FACE == 1) __syncthreads();
+  // update
+  bool bad = false;
+  for (int w = threadIdx.x; w < ne * L * 10; w += blockDim.x) {
+    const int e = w / (L * 10), r = w - e * (L * 10);
+    const float v = sQ[e * QS + r] + sA[e * L * 10 + r];
+    bad |= !isfinite(v);
+    a.q_out[(e0 + e) * QS + r] = v;
+  }
+  if (bad) atomicOr(a.status, kStatusNonFinite);
+}
+
 template <int N, bool TSM>
 __global__ void __launch_bounds__(256) k_corrector(StepArgs a) {
   using C = CorrCfg<N, TSM>;
@@ -1054,28 +1144,34 @@ struct CorrTcCfg : Dim<N> {
   static constexpr int THREADS = 512;
   static constexpr int GROUPS = THREADS / 128;             // warp groups reading TMEM (4 warps each)
   static constexpr int KP = tc_kp(N);
+  static constexpr int KQ = tc_kq(N);                      // K of the projection (volume nodes, padded)
   static constexpr int NCOL = D::NT * 8;                   // columns per element
-  static constexpr int NBC = TE * NCOL;                    // MMA N
-  static constexpr int TMEM_COLS = NBC <= 32 ? 32 : (NBC <= 64 ? 64 : (NBC <= 128 ? 128 : 256));
+  static constexpr int NBC = TE * NCOL;                    // MMA N of the volume evaluation
   static constexpr int NV = 3 * TE, NB = 10 * TE, NM = 2 * NV, NFC = 9 * TE;
-  static constexpr int KS_PRJ = N >= 4 ? 2 : 1, KS_FACE = N >= 4 ? 2 : 1;
+  static constexpr int NPC = (NB + 15) / 16 * 16;          // MMA N of the projection
+  static constexpr int KS_FACE = N >= 4 ? 2 : 1;
+  // tensor memory: volume-node values | projection A (TF32 high, remainder) | projection D
+  static constexpr int COL_AH = (NBC + 31) / 32 * 32, COL_AL = COL_AH + KQ, COL_DP = COL_AL + KQ;
+  static constexpr int TMEM_NEED = COL_DP + NPC;
+  static constexpr int TMEM_COLS = TMEM_NEED <= 128 ? 128 : (TMEM_NEED <= 256 ? 256 : 512);
   static constexpr int oPhiH = 0;
   static constexpr int oPhiL = oPhiH + 128 * KP;
-  static constexpr int oVw = oPhiL + 128 * KP;
-  static constexpr int oKtB = round4(oVw + D::NQ * D::LP);
+  static constexpr int oKtB = round4(oPhiL + 128 * KP);
   static constexpr int oVfw = round4(oKtB + 3 * D::L * D::LP);
-  // GEMM operand (TF32 high parts and remainders); once the MMA has completed the
-  // region holds the nodal terms, then the split-K partial sums and the modal outputs
-  static constexpr int oBeH = round4(oVfw + 4 * D::NF * D::LP);   // [NBC x KP] canonical
+  // GEMM operand region (TF32 high parts and remainders): the volume operand [NBC x KP],
+  // then the projection operand [NPC x KQ] (the nodal terms), then the modal outputs,
+  // the scaled face fluxes and the face GEMM's partial sums
+  // The projection operand's core matrices are 36 floats apart along K (4 floats of
+  // padding), so that the 32 volume nodes written by one warp land in 32 banks.
+  static constexpr int PLBO = 36, PGS = KQ / 4 * PLBO, BP = NPC / 8 * PGS;
+  static constexpr int oBeH = round4(oVfw + 4 * D::NF * D::LP);
+  static constexpr int BE_SIZE = (2 * NBC * KP > 2 * BP ? 2 * NBC * KP : 2 * BP);
+  static constexpr int BE_END = oBeH + BE_SIZE;
   static constexpr int oBeL = oBeH + NBC * KP;
-  static constexpr int BE_END = oBeL + NBC * KP;
-  static constexpr int BN = D::NQ * nb_stride(TE), BF = 4 * D::NF * NFC;
-  static constexpr int B_SIZE = round4(BN > BF ? BN : BF);
-  static constexpr int P1 = KS_PRJ * D::LP * NB, P2 = KS_FACE * D::LP * NFC, P3 = 3 * D::LP * NM;
-  static constexpr int PART = round4(P1 > P2 ? (P1 > P3 ? P1 : P3) : (P2 > P3 ? P2 : P3));
-  static constexpr int oB = oBeH;
-  static constexpr int oPart = oB + B_SIZE;                // also the modal outputs H ([3][LP][NM])
-  static constexpr int oH = oPart;
+  static constexpr int oBpH = oBeH, oBpL = oBeH + BP;
+  static constexpr int oH = oBeH;                          // [3][LP][NM]
+  static constexpr int oF = round4(oH + 3 * D::LP * NM);   // [4 NF][NFC]
+  static constexpr int oPart = round4(oF + 4 * D::NF * NFC);
   static constexpr int oM = BE_END;                        // [3][L][NM] modal GEMM inputs
   static constexpr int oA = oM + 3 * D::L * NM;            // [TE][L][10] update accumulator
   // two tile buffers filled by asynchronous copies (the next tile's while this one computes):
@@ -1085,9 +1181,15 @@ struct CorrTcCfg : Dim<N> {
   static constexpr int BUF = bG + TE * GRAW;
   static constexpr int oBuf = round4(oA + TE * D::L * 10);
   static constexpr int oGeo = oBuf + 2 * BUF;              // [TE][32]: Theta^{-1}, material, face scales
-  static constexpr int SMEM = oGeo + TE * 32;
-  static_assert(oBeH + B_SIZE + PART <= BE_END, "nodal terms and partial sums fit the operand region");
-  static_assert(D::NQ <= 128 && NBC % 16 == 0 && NBC <= 256, "tensor-core tile shape");
+  static constexpr int oC = oGeo + TE * 32;                // [TE][10] nodal terms at node 0
+  static constexpr int SMEM = round4(oC + TE * 10);
+  static_assert(oPart + KS_FACE * D::LP * NFC <= BE_END, "modal outputs, face fluxes and partials fit");
+  static_assert(D::NQ <= 128 && NBC % 16 == 0 && NBC <= 256 && NPC <= 256 && KQ % 32 == 0, "tensor-core shapes");
+  static_assert(D::L <= 64 && NB <= 40 && NB % 8 == 0 && TE * 4 <= THREADS / 32, "projection read-out: warps 0, 1 of each group");
+  __host__ __device__ static constexpr int prj_canon(int n, int q) {
+    return (n >> 3) * PGS + (q >> 2) * PLBO + (n & 7) * 4 + (q & 3);
+  }
+  static_assert(TMEM_NEED <= 512, "tensor memory columns");
   static_assert(SMEM * 4 <= 227 * 1024, "tensor-core corrector shared memory");
 };
 
@@ -1095,7 +1197,8 @@ template <int N>
 __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepArgs a) {
   using C = CorrTcCfg<N>;
   constexpr int L = C::L, NQ = C::NQ, NF = C::NF, NT = C::NT, LP = C::LP, QS = C::QS, DS = C::DS;
-  constexpr int AOFF = C::AOFF, TE = C::TE, KP = C::KP, NCOL = C::NCOL, NBC = C::NBC, NB = C::NB, NM = C::NM;
+  constexpr int AOFF = C::AOFF, TE = C::TE, KP = C::KP, KQ = C::KQ, NCOL = C::NCOL, NBC = C::NBC, NM = C::NM;
+  constexpr int NV = C::NV, NPC = C::NPC;
   constexpr TableLayout T = table_layout(N);
   constexpr int kWaitLimit = 1 << 24;
   extern __shared__ float4 smem4[];
@@ -1104,13 +1207,15 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
   __shared__ uint32_t tmem_base;
   float* sPhiH = sm + C::oPhiH;
   float* sPhiL = sm + C::oPhiL;
-  const float* sVw = sm + C::oVw;
   const float* sKtB = sm + C::oKtB;
   const float* sVfw = sm + C::oVfw;
   float* sBeH = sm + C::oBeH;
   float* sBeL = sm + C::oBeL;
   float* sM = sm + C::oM;
-  float* sB = sm + C::oB;
+  float* sBpH = sm + C::oBpH;
+  float* sBpL = sm + C::oBpL;
+  float* sF = sm + C::oF;
+  float* sC = sm + C::oC;
   float* sA = sm + C::oA;
   float* sH = sm + C::oH;
   float* sPart = sm + C::oPart;
@@ -1121,7 +1226,6 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   copy_to_smem(sPhiH, tb + T.PhiH, 128 * KP);
   copy_to_smem(sPhiL, tb + T.PhiL, 128 * KP);
-  copy_to_smem(sm + C::oVw, tb + T.Vw, NQ * LP);
   copy_to_smem(sm + C::oKtB, tb + T.KtB, 3 * L * LP);
   copy_to_smem(sm + C::oVfw, tb + T.Vfw, 4 * NF * LP);
   float tz[NT], gz[NT];
@@ -1136,6 +1240,29 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_base;
+  // projection operand A = w_q phi_l(x_q) (TF32 part, remainder) into tensor memory
+  // once: lane l, columns q.  Warp w of the first group writes lanes [32 w, 32 w + 32).
+  if (warp < 4) {
+    const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      const float* src = tb + (part ? T.PrjL : T.PrjH) + (32 * warp + lane) * KQ;
+#pragma unroll 1
+      for (int c0 = 0; c0 < KQ; c0 += 32) {
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 x = __ldg(reinterpret_cast<const float4*>(src + c0) + j);
+          v[4 * j] = x.x; v[4 * j + 1] = x.y; v[4 * j + 2] = x.z; v[4 * j + 3] = x.w;
+        }
+        tc::st_x32(tmem + lane_base + (part ? C::COL_AL : C::COL_AH) + c0, v);
+      }
+    }
+    tc::wait_st();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
   uint32_t phase = 0;
   bool failed = false;
 
@@ -1256,7 +1383,7 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
           const float h = tc::tf32_hi(x);
           const int idx = tc_canon(e * NCOL + z * 8 + c, l, KP);
           sBeH[idx] = h;
-          sBeL[idx] = x - h;
+          sBeL[idx] = tc::tf32_hi(x - h);
         }
       }
     }
@@ -1287,7 +1414,13 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
       break;
     }
     tc::fence_after();
-    // volume nodes: CDM stress and rate at the time nodes, time integral
+    // volume nodes: stress and damage rate at the time nodes, time integral; the nodal
+    // terms become the projection's B operand (row e*10 + c, column q), split like the
+    // volume operand.  Rows [NB, NPC) are zero.
+    for (int w = tid; w < (NPC - C::NB) / 8 * C::PGS; w += blockDim.x) {
+      sBpH[C::NB / 8 * C::PGS + w] = 0.f;
+      sBpL[C::NB / 8 * C::PGS + w] = 0.f;
+    }
     {
       const int q = 32 * (warp & 3) + lane;
       const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
@@ -1297,8 +1430,10 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
         float v[NCOL];
         tc::ld_cols<NCOL>(tmem + lane_base + e * NCOL, v);
         tc::wait_ld();
-        if (q < NQ) {
-          const bool live = e < ne;
+        float out[10];
+#pragma unroll
+        for (int c = 0; c < 10; ++c) out[c] = 0.f;
+        if (q < NQ && e < ne) {
           const float* gm = sGeo + e * 32;
           MatF m;
           m.rho = gm[9]; m.lam0 = gm[10]; m.mu0 = gm[11]; m.gamma_r = gm[12];
@@ -1314,21 +1449,83 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
             rb = fmaf(gz[z], r, rb);
           }
           const float S[3][3] = {{sb[0], sb[3], sb[5]}, {sb[3], sb[1], sb[4]}, {sb[5], sb[4], sb[2]}};
-          float* bq = sB + q * nb_stride(TE) + e * 10;
 #pragma unroll
           for (int ep = 0; ep < 3; ++ep)
 #pragma unroll
             for (int mc = 0; mc < 3; ++mc)
-              bq[ep * 3 + mc] =
-                  live ? -m.rho_inv * (ti[ep * 3 + 0] * S[mc][0] + ti[ep * 3 + 1] * S[mc][1] + ti[ep * 3 + 2] * S[mc][2])
-                       : 0.f;
-          bq[9] = live ? rb : 0.f;
+              out[ep * 3 + mc] =
+                  -m.rho_inv * (ti[ep * 3 + 0] * S[mc][0] + ti[ep * 3 + 1] * S[mc][1] + ti[ep * 3 + 2] * S[mc][2]);
+          out[9] = rb;
+        }
+        if (q == 0) {
+#pragma unroll
+          for (int c = 0; c < 10; ++c) sC[e * 10 + c] = out[c];
+        }
+        // the terms enter the projection less their value at node 0, which comes back
+        // through the row sums of w_q phi_l(x_q): a smooth field keeps its full precision
+        tc::named_barrier(1 + (warp >> 2), 128);
+        if (q < KQ) {
+#pragma unroll
+          for (int c = 0; c < 10; ++c) {
+            const float x = q < NQ ? out[c] - sC[e * 10 + c] : 0.f;
+            const int idx = C::prj_canon(e * 10 + c, q);
+            const float h = tc::tf32_hi(x);
+            sBpH[idx] = h;
+            sBpL[idx] = tc::tf32_hi(x - h);
+          }
+        }
+      }
+    }
+    // projection on the tensor cores: D[l][n] = sum_q w_q phi_l(x_q) B[n][q], 3xTF32
+    tc::fence_smem_to_async();
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      constexpr uint32_t idesc = tc::idesc_tf32(128, NPC);
+      const uint32_t bH = tc::smem_u32(sBpH), bL = tc::smem_u32(sBpL);
+      constexpr uint32_t lbo = 4u * C::PLBO, sbo = 4u * C::PGS;
+#pragma unroll
+      for (int ks = 0; ks < KQ / 8; ++ks) {
+        const uint32_t off = ks * 2 * lbo;   // 8 K-elements = 2 core matrices
+        const uint32_t aH = tmem + C::COL_AH + 8 * ks, aL = tmem + C::COL_AL + 8 * ks;
+        tc::mma_tf32_ta(tmem + C::COL_DP, aH, tc::desc_kmajor_strided(bH + off, lbo, sbo), idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32_ta(tmem + C::COL_DP, aH, tc::desc_kmajor_strided(bL + off, lbo, sbo), idesc, 1u);
+        tc::mma_tf32_ta(tmem + C::COL_DP, aL, tc::desc_kmajor_strided(bH + off, lbo, sbo), idesc, 1u);
+      }
+      tc::commit(&mbar);
+    }
+    {
+      const bool ok2 = tc::wait_parity(&mbar, phase, kWaitLimit);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok2)) {
+        failed = true;
+        break;
+      }
+    }
+    tc::fence_after();
+    // read-out: warps 0, 1 of group g hold modes [0, 64) of element g
+    if ((warp & 3) < 2) {
+      const int l = 32 * (warp & 3) + lane, e = warp >> 2;
+      float v[40];
+      tc::ld_cols<40>(tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + C::COL_DP, v);
+      tc::wait_ld();
+      if (l < L) {
+        const float sl = __ldg(tb + T.PrjS + l);
+        const float* ce = sC + e * 10;
+#pragma unroll
+        for (int ee = 0; ee < TE; ++ee) {
+          if (ee == e) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) sM[((c / 3) * L + l) * NM + NV + ee * 3 + c % 3] = fmaf(ce[c], sl, v[ee * 10 + c]);
+            sA[(ee * L + l) * 10 + 9] += fmaf(ce[9], sl, v[ee * 10 + 9]);
+          }
         }
       }
     }
     tc::fence_before();
     __syncthreads();
-    corrector_tail<N, TE, C::KS_PRJ, C::KS_FACE>(a, e0, ne, sVw, sKtB, sVfw, sQ, sM, sB, sA, sH, sPart, sFraw, sGeo);
+    corrector_tail_tc<N, TE, C::KS_FACE>(a, e0, ne, sKtB, sVfw, sQ, sM, sA, sH, sF, sPart, sFraw, sGeo);
   }
   tc::cp_async_wait<0>();                    // no copy may still be in flight at exit
   if (failed) {
@@ -1343,7 +1540,7 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
 // ---------------------------------------------------------------------------
 template <class Cfg, class Kern>
 cudaError_t launch_persistent(Kern kern, int64_t tiles, int grid_hint, const StepArgs& a, cudaStream_t s,
-                              bool* configured, int* max_blocks) {
+                              bool* configured, int* max_blocks, int cap_per_sm = 0) {
   const size_t smem = sizeof(float) * Cfg::SMEM;
   if (!*configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -1351,6 +1548,7 @@ cudaError_t launch_persistent(Kern kern, int64_t tiles, int grid_hint, const Ste
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, smem);
     if (e != cudaSuccess) return e;
+    if (cap_per_sm > 0 && per_sm > cap_per_sm) per_sm = cap_per_sm;
     *max_blocks = per_sm > 0 ? per_sm : 1;
     *configured = true;
   }
@@ -1403,8 +1601,9 @@ cudaError_t launch_corrector_impl(const StepArgs& a, cudaStream_t s) {
   if constexpr (tc_volume(N)) {
     if (!(table_residency_mask() & 8)) {
       const int64_t tiles = (a.E + CorrTcCfg<N>::TE - 1) / CorrTcCfg<N>::TE;
+      // resident CTAs of an SM share its 512 tensor-memory columns
       return launch_persistent<CorrTcCfg<N>>(k_corrector_tc<N>, tiles, a.grid_corr > 0 ? a.grid_corr : 148, a, s,
-                                             &cfg[2], &blocks[2]);
+                                             &cfg[2], &blocks[2], 512 / CorrTcCfg<N>::TMEM_COLS);
     }
   }
   const int64_t tiles = (a.E + CorrCfg<N, true>::TE - 1) / CorrCfg<N, true>::TE;

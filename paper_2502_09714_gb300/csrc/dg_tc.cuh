@@ -13,16 +13,20 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Shared-memory matrix descriptor of a K-major operand without swizzle whose
-// rows hold kp elements: core matrices (8 rows x 16 bytes) are consecutive
-// along K (leading byte offset 128) and 8-row groups are kp*32 bytes apart.
-__device__ __forceinline__ uint64_t desc_kmajor(uint32_t addr, int kp) {
-  const uint32_t lbo = 128u, sbo = static_cast<uint32_t>(kp) * 32u;
+// Shared-memory matrix descriptor of a K-major operand without swizzle: core
+// matrices (8 rows x 16 bytes) lbo bytes apart along K, 8-row groups sbo bytes apart.
+__device__ __forceinline__ uint64_t desc_kmajor_strided(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
   d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
   d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
   d |= 1ull << 46;   // descriptor version
   return d;
+}
+
+// The dense case: rows of kp elements, core matrices consecutive along K (128 bytes
+// apart), 8-row groups kp*32 bytes apart.
+__device__ __forceinline__ uint64_t desc_kmajor(uint32_t addr, int kp) {
+  return desc_kmajor_strided(addr, 128u, static_cast<uint32_t>(kp) * 32u);
 }
 
 // Instruction descriptor of kind::tf32 with FP32 accumulation, both operands K-major.
@@ -36,6 +40,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
       "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// The same MMA with the A operand in tensor memory (lane = row of A, column = K).
+__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -112,6 +125,20 @@ __device__ __forceinline__ void ld_x8(uint32_t taddr, float* v) {
 }
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 32 lanes x 32 bits, 32 columns: thread i of the warp writes v[0..31] to columns
+// [col, col + 32) of TMEM lane (warp's lane base + i).
+__device__ __forceinline__ void st_x32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]),
+      "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]),
+      "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
+      : "memory");
+}
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Load n (a multiple of 8, at most 40) consecutive columns.
 template <int NCOL>
 __device__ __forceinline__ void ld_cols(uint32_t taddr, float* v) {
@@ -144,6 +171,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Round to the nearest TF32 value (the high part of a 3xTF32 split).
+// Barrier over the nthreads threads (whole warps) that name barrier id (1..15).
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 __device__ __forceinline__ float tf32_hi(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
