@@ -206,61 +206,77 @@ __device__ __forceinline__ void copy_to_smem(float* dst, const float* src, int n
 }
 
 // Block GEMM: C[m][n] = sum_k A[k*lda + m] B[k*ldb + n], m < M, n < Nc (both
-// multiples of 4, rows 16-byte aligned).  Work items are (m-quad, n-quad,
-// k-split); out(m, n, value) receives each entry once.  With KS > 1 the split
-// sums go through `partial` (KS*M*Nc floats) and the call contains two
-// __syncthreads, so every thread of the block must make it.
-template <int KS, class Out>
-__device__ __forceinline__ void block_gemm(const float* __restrict__ A, int lda,
-                                           const float* __restrict__ B, int ldb, int M, int Nc,
-                                           int K, float* partial, Out out) {
-  const int mq = M >> 2, nq = Nc >> 2, tiles = mq * nq;
+// multiples of 4, rows 16-byte aligned), on threads t of [0, nt).  Work items are
+// (m-quad, n-quad, k-split); out(m, n, value) receives each entry once.  With
+// KS > 1 the split sums go through `partial` (KS*M*Nc floats) and the call runs
+// bar() twice, so every one of the nt threads must make it.
+template <int KS, int NJ = 4, class Out, class Bar>
+__device__ __forceinline__ void block_gemm_part(const float* __restrict__ A, int lda,
+                                                const float* __restrict__ B, int ldb, int M, int Nc,
+                                                int K, float* partial, Out out, int t, int nt, Bar bar) {
+  static_assert(NJ == 4 || NJ == 2, "4 rows x 4 or 2 columns per work item");
+  const int mq = M >> 2, nq = Nc / NJ, tiles = mq * nq;
   const int kchunk = (K + KS - 1) / KS;
-  for (int w = threadIdx.x; w < tiles * KS; w += blockDim.x) {
+  for (int w = t; w < tiles * KS; w += nt) {
     const int ks = w / tiles, r = w - ks * tiles;
-    const int mi = r / nq, ni = r - mi * nq;   // column quad fastest: the partial stores of a warp are contiguous
-    float acc[4][4];
+    const int mi = r / nq, ni = r - mi * nq;   // column group fastest: the partial stores of a warp are contiguous
+    float acc[4][NJ];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+      for (int j = 0; j < NJ; ++j) acc[i][j] = 0.f;
     const int k0 = ks * kchunk;
     const int k1 = min(K, k0 + kchunk);
     const float* ap = A + 4 * mi;
-    const float* bp = B + 4 * ni;
+    const float* bp = B + NJ * ni;
 #pragma unroll 4
     for (int k = k0; k < k1; ++k) {
       const float4 a = *reinterpret_cast<const float4*>(ap + k * lda);
-      const float4 b = *reinterpret_cast<const float4*>(bp + k * ldb);
+      float bv[NJ];
+      if constexpr (NJ == 4) {
+        const float4 b = *reinterpret_cast<const float4*>(bp + k * ldb);
+        bv[0] = b.x; bv[1] = b.y; bv[2] = b.z; bv[3] = b.w;
+      } else {
+        const float2 b = *reinterpret_cast<const float2*>(bp + k * ldb);
+        bv[0] = b.x; bv[1] = b.y;
+      }
       const float av[4] = {a.x, a.y, a.z, a.w};
-      const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < NJ; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
     if (KS == 1) {
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) out(4 * mi + i, 4 * ni + j, acc[i][j]);
+        for (int j = 0; j < NJ; ++j) out(4 * mi + i, NJ * ni + j, acc[i][j]);
     } else {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4*>(partial + (ks * M + 4 * mi + i) * Nc + 4 * ni) =
-            make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      for (int i = 0; i < 4; ++i) {
+        float* pp = partial + (ks * M + 4 * mi + i) * Nc + NJ * ni;
+        if constexpr (NJ == 4) *reinterpret_cast<float4*>(pp) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        else *reinterpret_cast<float2*>(pp) = make_float2(acc[i][0], acc[i][1]);
+      }
     }
   }
   if (KS > 1) {
-    __syncthreads();
-    for (int w = threadIdx.x; w < M * Nc; w += blockDim.x) {
+    bar();
+    for (int w = t; w < M * Nc; w += nt) {
       float v = 0.f;
 #pragma unroll
       for (int ks = 0; ks < KS; ++ks) v += partial[ks * M * Nc + w];
       out(w / Nc, w % Nc, v);
     }
-    __syncthreads();
+    bar();
   }
+}
+
+// The same over the whole block.
+template <int KS, class Out>
+__device__ __forceinline__ void block_gemm(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
+                                           int M, int Nc, int K, float* partial, Out out) {
+  block_gemm_part<KS>(A, lda, B, ldb, M, Nc, K, partial, out, threadIdx.x, blockDim.x, [] { __syncthreads(); });
 }
 
 // ===========================================================================
@@ -867,56 +883,49 @@ __device__ __forceinline__ void corrector_tail(const StepArgs& a, int64_t e0, in
     if (bad) atomicOr(a.status, kStatusNonFinite);
 }
 
-// Second half of the tensor-core corrector, after the projection (That already in
-// the modal inputs sM, the damage source in column 9 of sA): modal derivative,
-// scaled face fluxes, strain/velocity rows, face term and update.
-template <int N, int TE, int KS_FACE>
-__device__ __forceinline__ void corrector_tail_tc(const StepArgs& a, int64_t e0, int ne, const float* sKtB,
-                                                  const float* sVfw, const float* sQ, const float* sM, float* sA,
-                                                  float* sH, float* sF, float* sPart, const float* sFraw,
-                                                  const float* sGeo) {
+// Phases of the tensor-core corrector that run on the SIMT cores while an MMA is in
+// flight.  The modal derivative takes one half of the modal inputs at a time:
+// H_e'[k][c0 + j] = sum_l int phi_l d phi_k / d xi_e' M_e'[l][c0 + j], e' = 0..2,
+// j < 3 TE (c0 = 0: time-integrated velocity, c0 = 3 TE: the projected terms That).
+template <int N, int TE>
+__device__ __forceinline__ void modal_derivative_half(const float* sKtB, const float* sM, float* sH, int c0, int t,
+                                                      int nt) {
   using D = Dim<N>;
-  constexpr int L = D::L, NF = D::NF, LP = D::LP, QS = D::QS, FFS = D::FFS;
-  constexpr int NV = 3 * TE, NM = 2 * NV, NFC = 9 * TE;
-  // modal derivative: H_e'[k][col] = sum_l int phi_l d phi_k/d xi_e' M_e'[l][col], e' = 0..2 in one pass
-  {
-    constexpr int MQ = LP / 4, NQQ = NM / 4, TILES = MQ * NQQ;
-    for (int w = threadIdx.x; w < 3 * TILES; w += blockDim.x) {
-      const int ep = w / TILES, r = w - ep * TILES;
-      const int ni = r % NQQ, mi = r / NQQ;
-      const float* A = sKtB + ep * L * LP + 4 * mi;
-      const float* B = sM + ep * L * NM + 4 * ni;
-      float acc[4][4];
+  constexpr int L = D::L, LP = D::LP, NV = 3 * TE, NM = 2 * NV;
+  constexpr int MQ = LP / 4, NP = NV / 2, TILES = MQ * NP;   // 4 rows x 2 columns per thread
+  for (int w = t; w < 3 * TILES; w += nt) {
+    const int ep = w / TILES, r = w - ep * TILES;
+    const int mi = r / NP, ni = r - mi * NP;
+    const float* A = sKtB + ep * L * LP + 4 * mi;
+    const float* B = sM + ep * L * NM + c0 + 2 * ni;
+    float acc[4][2];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0.f;
 #pragma unroll 5
-      for (int l = 0; l < L; ++l) {
-        const float4 av = *reinterpret_cast<const float4*>(A + l * LP);
-        const float4 bv = *reinterpret_cast<const float4*>(B + l * NM);
-        const float x[4] = {av.x, av.y, av.z, av.w}, y[4] = {bv.x, bv.y, bv.z, bv.w};
+    for (int l = 0; l < L; ++l) {
+      const float4 av = *reinterpret_cast<const float4*>(A + l * LP);
+      const float2 bv = *reinterpret_cast<const float2*>(B + l * NM);
+      const float x[4] = {av.x, av.y, av.z, av.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(x[i], y[j], acc[i][j]);
+      for (int i = 0; i < 4; ++i) {
+        acc[i][0] = fmaf(x[i], bv.x, acc[i][0]);
+        acc[i][1] = fmaf(x[i], bv.y, acc[i][1]);
       }
-      float* h = sH + ep * LP * NM;
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4*>(h + (4 * mi + i) * NM + 4 * ni) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
     }
+    float* h = sH + ep * LP * NM + c0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      *reinterpret_cast<float2*>(h + (4 * mi + i) * NM + 2 * ni) = make_float2(acc[i][0], acc[i][1]);
   }
-  // face fluxes of the tile's elements, signed and scaled by |S_f| / |J|
-  for (int w = threadIdx.x; w < TE * 4 * NF * 9; w += blockDim.x) {
-    const int e = w / (4 * NF * 9), r = w - e * 4 * NF * 9;
-    const int f = r / (NF * 9), r2 = r - f * NF * 9;
-    const int i = r2 / 9, p = r2 - 9 * i;
-    sF[(f * NF + i) * NFC + e * 9 + p] = e < ne ? sGeo[e * 32 + 17 + f] * sFraw[(e * 4 + f) * FFS + i * 9 + p] : 0.f;
-  }
-  __syncthreads();
-  // strain rows -(v_i d_j phi + v_j d_i phi)/2 and velocity rows from the modal derivatives
-  for (int w = threadIdx.x; w < TE * L; w += blockDim.x) {
+}
+
+// Strain rows -(v_i d_j phi + v_j d_i phi)/2 from the velocity half of H (element fastest:
+// the lanes of a warp spread over the banks of sH).
+template <int N, int TE>
+__device__ __forceinline__ void strain_rows(const float* sH, const float* sGeo, float* sA, int t, int nt) {
+  using D = Dim<N>;
+  constexpr int L = D::L, LP = D::LP, NM = 6 * TE;
+  for (int w = t; w < TE * L; w += nt) {
     const int k = w / TE, e = w - k * TE;
     const float* ti = sGeo + e * 32;
     float hd[3][3];
@@ -933,28 +942,22 @@ __device__ __forceinline__ void corrector_tail_tc(const StepArgs& a, int64_t e0,
     ao[3] -= 0.5f * (hd[1][0] + hd[0][1]);
     ao[4] -= 0.5f * (hd[2][1] + hd[1][2]);
     ao[5] -= 0.5f * (hd[0][2] + hd[2][0]);
+  }
+}
+
+// Velocity rows: the sum over e' of the That half of H.
+template <int N, int TE>
+__device__ __forceinline__ void velocity_rows(const float* sH, float* sA) {
+  using D = Dim<N>;
+  constexpr int L = D::L, LP = D::LP, NV = 3 * TE, NM = 2 * NV;
+  for (int w = threadIdx.x; w < TE * L; w += blockDim.x) {
+    const int k = w / TE, e = w - k * TE;
+    float* ao = sA + (e * L + k) * 10;
 #pragma unroll
     for (int mc = 0; mc < 3; ++mc)
       ao[6 + mc] += sH[(0 * LP + k) * NM + NV + e * 3 + mc] + sH[(1 * LP + k) * NM + NV + e * 3 + mc] +
                     sH[(2 * LP + k) * NM + NV + e * 3 + mc];
   }
-  __syncthreads();
-  block_gemm<KS_FACE>(sVfw, LP, sF, NFC, LP, NFC, 4 * NF, sPart, [&](int k, int col, float v) {
-    if (k < L) {
-      const int e = col / 9, p = col - 9 * e;
-      sA[(e * L + k) * 10 + p] -= v;
-    }
-  });
-  if (KS_FACE == 1) __syncthreads();
-  // update
-  bool bad = false;
-  for (int w = threadIdx.x; w < ne * L * 10; w += blockDim.x) {
-    const int e = w / (L * 10), r = w - e * (L * 10);
-    const float v = sQ[e * QS + r] + sA[e * L * 10 + r];
-    bad |= !isfinite(v);
-    a.q_out[(e0 + e) * QS + r] = v;
-  }
-  if (bad) atomicOr(a.status, kStatusNonFinite);
 }
 
 template <int N, bool TSM>
@@ -1149,18 +1152,18 @@ struct CorrTcCfg : Dim<N> {
   static constexpr int NBC = TE * NCOL;                    // MMA N of the volume evaluation
   static constexpr int NV = 3 * TE, NB = 10 * TE, NM = 2 * NV, NFC = 9 * TE;
   static constexpr int NPC = (NB + 15) / 16 * 16;          // MMA N of the projection
-  static constexpr int KS_FACE = N >= 4 ? 2 : 1;
-  // tensor memory: volume-node values | projection A (TF32 high, remainder) | projection D
-  static constexpr int COL_AH = (NBC + 31) / 32 * 32, COL_AL = COL_AH + KQ, COL_DP = COL_AL + KQ;
-  static constexpr int TMEM_NEED = COL_DP + NPC;
+  static constexpr int KS_FACE = N >= 4 ? 2 : 1, NJ_FACE = 2;   // face GEMM: k-split, columns per item
+  // tensor memory: volume-node values (then the projection's D) | projection A (TF32
+  // high part, remainder) | volume A phi_l(x_q) (TF32 high part, remainder)
+  static constexpr int COL_DP = 0;
+  static constexpr int COL_AH = (NBC + 31) / 32 * 32, COL_AL = COL_AH + KQ;
+  static constexpr int COL_PH = COL_AL + KQ, COL_PL = COL_PH + KP;
+  static constexpr int TMEM_NEED = COL_PL + KP;
   static constexpr int TMEM_COLS = TMEM_NEED <= 128 ? 128 : (TMEM_NEED <= 256 ? 256 : 512);
-  static constexpr int oPhiH = 0;
-  static constexpr int oPhiL = oPhiH + 128 * KP;
-  static constexpr int oKtB = round4(oPhiL + 128 * KP);
+  static constexpr int oKtB = 0;
   static constexpr int oVfw = round4(oKtB + 3 * D::L * D::LP);
   // GEMM operand region (TF32 high parts and remainders): the volume operand [NBC x KP],
-  // then the projection operand [NPC x KQ] (the nodal terms), then the modal outputs,
-  // the scaled face fluxes and the face GEMM's partial sums
+  // then the projection operand [NPC x KQ] (the nodal terms)
   // The projection operand's core matrices are 36 floats apart along K (4 floats of
   // padding), so that the 32 volume nodes written by one warp land in 32 banks.
   static constexpr int PLBO = 36, PGS = KQ / 4 * PLBO, BP = NPC / 8 * PGS;
@@ -1169,23 +1172,29 @@ struct CorrTcCfg : Dim<N> {
   static constexpr int BE_END = oBeH + BE_SIZE;
   static constexpr int oBeL = oBeH + NBC * KP;
   static constexpr int oBpH = oBeH, oBpL = oBeH + BP;
-  static constexpr int oH = oBeH;                          // [3][LP][NM]
+  // outside the operand region, for the phases that overlap an MMA: modal outputs,
+  // scaled face fluxes, the face GEMM's partial sums
+  static constexpr int oH = BE_END;                        // [3][LP][NM]
   static constexpr int oF = round4(oH + 3 * D::LP * NM);   // [4 NF][NFC]
   static constexpr int oPart = round4(oF + 4 * D::NF * NFC);
-  static constexpr int oM = BE_END;                        // [3][L][NM] modal GEMM inputs
+  static constexpr int oM = oPart + KS_FACE * D::LP * NFC; // [3][L][NM] modal GEMM inputs
   static constexpr int oA = oM + 3 * D::L * NM;            // [TE][L][10] update accumulator
   // two tile buffers filled by asynchronous copies (the next tile's while this one computes):
   // state, predictor output, face fluxes, raw geometry (GeomF, MatF, face ids)
   static constexpr int GRAW = 48;
+  // and the face ids of the tile after next (whose face fluxes this buffer's successor fetches)
   static constexpr int bQ = 0, bD = TE * D::QS, bF = bD + TE * D::DS, bG = bF + TE * 4 * D::FFS;
-  static constexpr int BUF = bG + TE * GRAW;
+  static constexpr int bI = bG + TE * GRAW;
+  static constexpr int BUF = bI + TE * 4;
   static constexpr int oBuf = round4(oA + TE * D::L * 10);
   static constexpr int oGeo = oBuf + 2 * BUF;              // [TE][32]: Theta^{-1}, material, face scales
   static constexpr int oC = oGeo + TE * 32;                // [TE][10] nodal terms at node 0
+  // the last warp issues the MMAs; the others (the workers) run the SIMT phases meanwhile
+  static constexpr int WORKERS = THREADS - 32, ISSUER = THREADS - 32;
   static constexpr int SMEM = round4(oC + TE * 10);
-  static_assert(oPart + KS_FACE * D::LP * NFC <= BE_END, "modal outputs, face fluxes and partials fit");
   static_assert(D::NQ <= 128 && NBC % 16 == 0 && NBC <= 256 && NPC <= 256 && KQ % 32 == 0, "tensor-core shapes");
   static_assert(D::L <= 64 && NB <= 40 && NB % 8 == 0 && TE * 4 <= THREADS / 32, "projection read-out: warps 0, 1 of each group");
+  static_assert(NPC <= NBC && KP <= 40, "projection D inside the volume D; volume A in one row of stores");
   __host__ __device__ static constexpr int prj_canon(int n, int q) {
     return (n >> 3) * PGS + (q >> 2) * PLBO + (n & 7) * 4 + (q & 3);
   }
@@ -1198,15 +1207,13 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
   using C = CorrTcCfg<N>;
   constexpr int L = C::L, NQ = C::NQ, NF = C::NF, NT = C::NT, LP = C::LP, QS = C::QS, DS = C::DS;
   constexpr int AOFF = C::AOFF, TE = C::TE, KP = C::KP, KQ = C::KQ, NCOL = C::NCOL, NBC = C::NBC, NM = C::NM;
-  constexpr int NV = C::NV, NPC = C::NPC;
+  constexpr int NV = C::NV, NPC = C::NPC, NFC = C::NFC;
   constexpr TableLayout T = table_layout(N);
   constexpr int kWaitLimit = 1 << 24;
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
-  float* sPhiH = sm + C::oPhiH;
-  float* sPhiL = sm + C::oPhiL;
   const float* sKtB = sm + C::oKtB;
   const float* sVfw = sm + C::oVfw;
   float* sBeH = sm + C::oBeH;
@@ -1224,8 +1231,6 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
   const float* tb = a.tables;
   const float dt = a.dt;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  copy_to_smem(sPhiH, tb + T.PhiH, 128 * KP);
-  copy_to_smem(sPhiL, tb + T.PhiL, 128 * KP);
   copy_to_smem(sm + C::oKtB, tb + T.KtB, 3 * L * LP);
   copy_to_smem(sm + C::oVfw, tb + T.Vfw, 4 * NF * LP);
   float tz[NT], gz[NT];
@@ -1258,28 +1263,52 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
         tc::st_x32(tmem + lane_base + (part ? C::COL_AL : C::COL_AH) + c0, v);
       }
     }
-    tc::wait_st();
+  } else if (warp < 8) {
+    // volume operand A = phi_l(x_q) (TF32 part, remainder): lane q, columns l, read from
+    // the canonical tables (four consecutive l of a node are contiguous)
+    const int q = 32 * (warp - 4) + lane;
+    const uint32_t lane_base = static_cast<uint32_t>(32 * (warp - 4)) << 16;
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      const float* src = tb + (part ? T.PhiL : T.PhiH);
+      float v[KP];
+#pragma unroll
+      for (int j = 0; j < KP / 4; ++j) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(src + tc_canon(q, 4 * j, KP)));
+        v[4 * j] = x.x; v[4 * j + 1] = x.y; v[4 * j + 2] = x.z; v[4 * j + 3] = x.w;
+      }
+      tc::st_cols<KP>(tmem + lane_base + (part ? C::COL_PL : C::COL_PH), v);
+    }
   }
+  if (warp < 8) tc::wait_st();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   uint32_t phase = 0;
   bool failed = false;
 
-  // one batch of asynchronous copies of a tile: state, predictor output, face fluxes,
-  // geometry, material and face ids
-  auto issue = [&](int64_t tl, float* buf) {
+  // one batch of asynchronous copies of a tile on threads t of [0, nt): state, predictor
+  // output, face fluxes (at the face ids `ids` of the tile), geometry, material, face
+  // ids, and the face ids of this CTA's following tile
+  const int64_t ntiles = (a.E + TE - 1) / TE;
+  auto issue = [&](int64_t tl, float* buf, const int* ids, int t, int nt) {
     const int64_t e0 = tl * TE;
     const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
-    for (int w = tid; w < ne * QS / 4; w += blockDim.x) tc::cp_async16(buf + C::bQ + 4 * w, a.q_in + e0 * QS + 4 * w);
-    for (int w = tid; w < ne * DS / 4; w += blockDim.x) tc::cp_async16(buf + C::bD + 4 * w, a.d + e0 * DS + 4 * w);
-    for (int w = tid; w < ne * FFS; w += blockDim.x) {     // ne * 4 faces * FFS/4 chunks
+    for (int w = t; w < ne * QS / 4; w += nt) tc::cp_async16(buf + C::bQ + 4 * w, a.q_in + e0 * QS + 4 * w);
+    for (int w = t; w < ne * DS / 4; w += nt) tc::cp_async16(buf + C::bD + 4 * w, a.d + e0 * DS + 4 * w);
+    for (int w = t; w < ne * FFS; w += nt) {     // ne * 4 faces * FFS/4 chunks
       const int e = w / FFS, r = w - e * FFS;
       const int f = r / (FFS / 4), c = r - f * (FFS / 4);
-      const int64_t fid = a.elem_face[(e0 + e) * 4 + f] >> 1;
+      const int64_t fid = ids[e * 4 + f] >> 1;
       tc::cp_async16(buf + C::bF + (e * 4 + f) * FFS + 4 * c, a.ff + fid * FFS + 4 * c);
     }
-    for (int w = tid; w < ne * 11; w += blockDim.x) {
+    const int64_t n0 = (tl + gridDim.x) * TE;
+    const int nn = n0 < a.E ? static_cast<int>(min(static_cast<int64_t>(TE), a.E - n0)) : 0;
+    for (int w = t; w < ne * 11 + nn; w += nt) {
+      if (w >= ne * 11) {
+        tc::cp_async16(buf + C::bI + 4 * (w - ne * 11), a.elem_face + (n0 + w - ne * 11) * 4);
+        continue;
+      }
       const int e = w / 11, k = w - 11 * e;
       float* g = buf + C::bG + e * GRAW;
       if (k < 8) tc::cp_async16(g + 4 * k, reinterpret_cast<const float*>(a.geom + e0 + e) + 4 * k);
@@ -1288,8 +1317,8 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
     }
   };
 
-  const int64_t ntiles = (a.E + TE - 1) / TE;
-  if (static_cast<int64_t>(blockIdx.x) < ntiles) issue(blockIdx.x, sm + C::oBuf);
+  if (static_cast<int64_t>(blockIdx.x) < ntiles)
+    issue(blockIdx.x, sm + C::oBuf, a.elem_face + static_cast<int64_t>(blockIdx.x) * TE * 4, tid, blockDim.x);
   tc::cp_async_commit();
   int it = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -1390,23 +1419,38 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
     tc::fence_smem_to_async();
     tc::fence_before();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == C::ISSUER) {
       tc::fence_after();
       constexpr uint32_t idesc = tc::idesc_tf32(128, NBC);
-      const uint32_t aH = tc::smem_u32(sPhiH), aL = tc::smem_u32(sPhiL);
       const uint32_t bH = tc::smem_u32(sBeH), bL = tc::smem_u32(sBeL);
 #pragma unroll
       for (int ks = 0; ks < KP / 8; ++ks) {
         const uint32_t off = ks * 256;   // 8 K-elements = 2 core matrices
-        tc::mma_tf32(tmem, tc::desc_kmajor(aH + off, KP), tc::desc_kmajor(bH + off, KP), idesc, ks > 0 ? 1u : 0u);
-        tc::mma_tf32(tmem, tc::desc_kmajor(aH + off, KP), tc::desc_kmajor(bL + off, KP), idesc, 1u);
-        tc::mma_tf32(tmem, tc::desc_kmajor(aL + off, KP), tc::desc_kmajor(bH + off, KP), idesc, 1u);
+        const uint32_t aH = tmem + C::COL_PH + 8 * ks, aL = tmem + C::COL_PL + 8 * ks;
+        tc::mma_tf32_ta(tmem, aH, tc::desc_kmajor(bH + off, KP), idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32_ta(tmem, aH, tc::desc_kmajor(bL + off, KP), idesc, 1u);
+        tc::mma_tf32_ta(tmem, aL, tc::desc_kmajor(bH + off, KP), idesc, 1u);
       }
       tc::commit(&mbar);
     }
-    // while the tensor cores run: the next tile's copies into the other buffer
-    if (tile + gridDim.x < ntiles) issue(tile + gridDim.x, sm + C::oBuf + ((it + 1) & 1) * C::BUF);
-    tc::cp_async_commit();
+    // while the tensor cores run, on the worker warps: the face term (scaled face fluxes,
+    // face GEMM), which needs no volume result
+    if (tid < C::WORKERS) {
+      auto bar = [] { tc::named_barrier(5, C::WORKERS); };
+      for (int w = tid; w < TE * 4 * NF * 9; w += C::WORKERS) {
+        const int e = w / (4 * NF * 9), r = w - e * 4 * NF * 9;
+        const int f = r / (NF * 9), r2 = r - f * NF * 9;
+        const int i = r2 / 9, p = r2 - 9 * i;
+        sF[(f * NF + i) * NFC + e * 9 + p] = e < ne ? sGeo[e * 32 + 17 + f] * sFraw[(e * 4 + f) * FFS + i * 9 + p] : 0.f;
+      }
+      bar();
+      block_gemm_part<C::KS_FACE, C::NJ_FACE>(sVfw, LP, sF, NFC, LP, NFC, 4 * NF, sPart, [&](int k, int col, float v) {
+        if (k < L) {
+          const int e = col / 9, p = col - 9 * e;
+          sA[(e * L + k) * 10 + p] -= v;
+        }
+      }, tid, C::WORKERS, bar);
+    }
     const bool ok = tc::wait_parity(&mbar, phase, kWaitLimit);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
@@ -1480,7 +1524,7 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
     tc::fence_smem_to_async();
     tc::fence_before();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == C::ISSUER) {
       tc::fence_after();
       constexpr uint32_t idesc = tc::idesc_tf32(128, NPC);
       const uint32_t bH = tc::smem_u32(sBpH), bL = tc::smem_u32(sBpL);
@@ -1495,6 +1539,17 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
       }
       tc::commit(&mbar);
     }
+    // while the tensor cores run, on the worker warps: the next tile's copies into the
+    // other buffer, the velocity half of the modal derivative, strain rows
+    if (tid < C::WORKERS) {
+      if (tile + gridDim.x < ntiles)
+        issue(tile + gridDim.x, sm + C::oBuf + ((it + 1) & 1) * C::BUF, reinterpret_cast<const int*>(buf + C::bI), tid,
+              C::WORKERS);
+      modal_derivative_half<N, TE>(sKtB, sM, sH, 0, tid, C::WORKERS);
+      tc::named_barrier(5, C::WORKERS);
+      strain_rows<N, TE>(sH, sGeo, sA, tid, C::WORKERS);
+    }
+    tc::cp_async_commit();
     {
       const bool ok2 = tc::wait_parity(&mbar, phase, kWaitLimit);
       phase ^= 1u;
@@ -1525,7 +1580,19 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
     }
     tc::fence_before();
     __syncthreads();
-    corrector_tail_tc<N, TE, C::KS_FACE>(a, e0, ne, sKtB, sVfw, sQ, sM, sA, sH, sF, sPart, sFraw, sGeo);
+    modal_derivative_half<N, TE>(sKtB, sM, sH, NV, tid, blockDim.x);
+    __syncthreads();
+    velocity_rows<N, TE>(sH, sA);
+    __syncthreads();
+    // update
+    bool bad = false;
+    for (int w = tid; w < ne * L * 10; w += blockDim.x) {
+      const int e = w / (L * 10), r = w - e * (L * 10);
+      const float v = sQ[e * QS + r] + sA[e * L * 10 + r];
+      bad |= !isfinite(v);
+      a.q_out[(e0 + e) * QS + r] = v;
+    }
+    if (bad) atomicOr(a.status, kStatusNonFinite);
   }
   tc::cp_async_wait<0>();                    // no copy may still be in flight at exit
   if (failed) {

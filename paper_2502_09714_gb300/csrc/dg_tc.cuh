@@ -137,7 +137,34 @@ __device__ __forceinline__ void st_x32(uint32_t taddr, const float* v) {
       "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
       : "memory");
 }
+__device__ __forceinline__ void st_x16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+      : "memory");
+}
+__device__ __forceinline__ void st_x8(uint32_t taddr, const float* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "f"(v[0]),
+               "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
 __device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Store n (a multiple of 8, at most 40) consecutive columns.
+template <int NCOL>
+__device__ __forceinline__ void st_cols(uint32_t taddr, const float* v) {
+  static_assert(NCOL % 8 == 0 && NCOL <= 40, "column count");
+  int c = 0;
+  if constexpr (NCOL >= 32) {
+    st_x32(taddr, v);
+    c = 32;
+  } else if constexpr (NCOL >= 16) {
+    st_x16(taddr, v);
+    c = 16;
+  }
+  if constexpr (NCOL % 32 == 8 || NCOL % 16 == 8) st_x8(taddr + c, v + c);
+}
 
 // Load n (a multiple of 8, at most 40) consecutive columns.
 template <int NCOL>
