@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
             float c = 1.f;
 #pragma unroll
             for (int o = 1; o <= N; ++o) {
-              c *= tau / static_cast<float>(o);
+              c *= tau * (1.f / static_cast<float>(o));   // constant after unrolling: no division
               const float* to = t0 + o * NGG * 12;
               const float4 b0 = *reinterpret_cast<const float4*>(to);
               const float4 b1 = *reinterpret_cast<const float4*>(to + 4);
@@ -1024,7 +1024,7 @@ __global__ void __launch_bounds__(256) k_corrector(StepArgs a) {
       float c = dt;
 #pragma unroll
       for (int o = 1; o <= N; ++o) {
-        c *= dt / static_cast<float>(o + 1);
+        c *= dt * (1.f / static_cast<float>(o + 1));
         if (l < n_modes(N - o)) {
           const float* dd = de + d_offset(N, o) + l * 9;
           float* ch = sCh + (row_hi(N, o) + l) * 8 * TE + e * 8;
@@ -1102,7 +1102,7 @@ __global__ void __launch_bounds__(256) k_corrector(StepArgs a) {
           float c = 1.f;
 #pragma unroll
           for (int o = 1; o <= N; ++o) {
-            c *= tz[z] / static_cast<float>(o);
+            c *= tz[z] * (1.f / static_cast<float>(o));
 #pragma unroll
             for (int p = 0; p < 6; ++p) eps[p] = fmaf(c, ah[o - 1][n][p], eps[p]);
           }
@@ -1144,7 +1144,7 @@ template <int N>
 struct CorrTcCfg : Dim<N> {
   using D = Dim<N>;
   static constexpr int TE = 4;
-  static constexpr int THREADS = 512;
+  static constexpr int THREADS = 512;                      // 16 warps (the item maps below assume it)
   static constexpr int GROUPS = THREADS / 128;             // warp groups reading TMEM (4 warps each)
   static constexpr int KP = tc_kp(N);
   static constexpr int KQ = tc_kq(N);                      // K of the projection (volume nodes, padded)
@@ -1180,12 +1180,13 @@ struct CorrTcCfg : Dim<N> {
   static constexpr int oM = oPart + KS_FACE * D::LP * NFC; // [3][L][NM] modal GEMM inputs
   static constexpr int oA = oM + 3 * D::L * NM;            // [TE][L][10] update accumulator
   // two tile buffers filled by asynchronous copies (the next tile's while this one computes):
-  // state, predictor output, face fluxes, raw geometry (GeomF, MatF, face ids)
-  static constexpr int GRAW = 48;
-  // and the face ids of the tile after next (whose face fluxes this buffer's successor fetches)
+  // state, predictor output, face fluxes, GeomF, MatF, face ids, and the face ids of
+  // the CTA's tile after that one (whose face fluxes the next copy fetches)
   static constexpr int bQ = 0, bD = TE * D::QS, bF = bD + TE * D::DS, bG = bF + TE * 4 * D::FFS;
-  static constexpr int bI = bG + TE * GRAW;
+  static constexpr int bM = bG + TE * 32, bE = bM + TE * 8, bI = bE + TE * 4;
   static constexpr int BUF = bI + TE * 4;
+  static_assert(D::QS % 4 == 0 && D::DS % 4 == 0 && D::FFS % 4 == 0 && sizeof(GeomF) == 128 && sizeof(MatF) == 32,
+                "16-byte copies");
   static constexpr int oBuf = round4(oA + TE * D::L * 10);
   static constexpr int oGeo = oBuf + 2 * BUF;              // [TE][32]: Theta^{-1}, material, face scales
   static constexpr int oC = oGeo + TE * 32;                // [TE][10] nodal terms at node 0
@@ -1194,6 +1195,7 @@ struct CorrTcCfg : Dim<N> {
   static constexpr int SMEM = round4(oC + TE * 10);
   static_assert(D::NQ <= 128 && NBC % 16 == 0 && NBC <= 256 && NPC <= 256 && KQ % 32 == 0, "tensor-core shapes");
   static_assert(D::L <= 64 && NB <= 40 && NB % 8 == 0 && TE * 4 <= THREADS / 32, "projection read-out: warps 0, 1 of each group");
+  static_assert(THREADS == 512 && 21 * TE <= 128, "work maps of the tile's first stage");
   static_assert(NPC <= NBC && KP <= 40, "projection D inside the volume D; volume A in one row of stores");
   __host__ __device__ static constexpr int prj_canon(int n, int q) {
     return (n >> 3) * PGS + (q >> 2) * PLBO + (n & 7) * 4 + (q & 3);
@@ -1227,7 +1229,7 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
   float* sH = sm + C::oH;
   float* sPart = sm + C::oPart;
   float* sGeo = sm + C::oGeo;
-  constexpr int FFS = C::FFS, GRAW = C::GRAW;
+  constexpr int FFS = C::FFS;
   const float* tb = a.tables;
   const float dt = a.dt;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1287,13 +1289,15 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
   uint32_t phase = 0;
   bool failed = false;
 
-  // one batch of asynchronous copies of a tile on threads t of [0, nt): state, predictor
-  // output, face fluxes (at the face ids `ids` of the tile), geometry, material, face
+  // one batch of 16-byte asynchronous copies of a tile on threads t of [0, nt): state,
+  // predictor output, face fluxes (at the face ids `ids` of the tile), GeomF, MatF, face
   // ids, and the face ids of this CTA's following tile
   const int64_t ntiles = (a.E + TE - 1) / TE;
   auto issue = [&](int64_t tl, float* buf, const int* ids, int t, int nt) {
     const int64_t e0 = tl * TE;
     const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
+    const int64_t n0 = (tl + gridDim.x) * TE;
+    const int nn = n0 < a.E ? static_cast<int>(min(static_cast<int64_t>(TE), a.E - n0)) : 0;
     for (int w = t; w < ne * QS / 4; w += nt) tc::cp_async16(buf + C::bQ + 4 * w, a.q_in + e0 * QS + 4 * w);
     for (int w = t; w < ne * DS / 4; w += nt) tc::cp_async16(buf + C::bD + 4 * w, a.d + e0 * DS + 4 * w);
     for (int w = t; w < ne * FFS; w += nt) {     // ne * 4 faces * FFS/4 chunks
@@ -1302,18 +1306,15 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
       const int64_t fid = ids[e * 4 + f] >> 1;
       tc::cp_async16(buf + C::bF + (e * 4 + f) * FFS + 4 * c, a.ff + fid * FFS + 4 * c);
     }
-    const int64_t n0 = (tl + gridDim.x) * TE;
-    const int nn = n0 < a.E ? static_cast<int>(min(static_cast<int64_t>(TE), a.E - n0)) : 0;
     for (int w = t; w < ne * 11 + nn; w += nt) {
       if (w >= ne * 11) {
         tc::cp_async16(buf + C::bI + 4 * (w - ne * 11), a.elem_face + (n0 + w - ne * 11) * 4);
         continue;
       }
       const int e = w / 11, k = w - 11 * e;
-      float* g = buf + C::bG + e * GRAW;
-      if (k < 8) tc::cp_async16(g + 4 * k, reinterpret_cast<const float*>(a.geom + e0 + e) + 4 * k);
-      else if (k < 10) tc::cp_async16(g + 32 + 4 * (k - 8), reinterpret_cast<const float*>(a.mat + e0 + e) + 4 * (k - 8));
-      else tc::cp_async16(g + 40, a.elem_face + (e0 + e) * 4);
+      if (k < 8) tc::cp_async16(buf + C::bG + e * 32 + 4 * k, reinterpret_cast<const float*>(a.geom + e0 + e) + 4 * k);
+      else if (k < 10) tc::cp_async16(buf + C::bM + e * 8 + 4 * (k - 8), reinterpret_cast<const float*>(a.mat + e0 + e) + 4 * (k - 8));
+      else tc::cp_async16(buf + C::bE + e * 4, a.elem_face + (e0 + e) * 4);
     }
   };
 
@@ -1337,22 +1338,23 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
     // per element: Theta^{-1} [0,9), material [9,17), signed |S_f|/|J| [17,21)
     for (int w = tid; w < TE * 21; w += blockDim.x) {
       const int e = w / 21, c = w - 21 * e;
-      const float* g = sGraw + e * GRAW;
+      const float* g = sGraw + e * 32;
       float v = 0.f;
       if (e < ne) {
         if (c < 9) {
           v = g[c];
         } else if (c < 17) {
-          v = g[32 + c - 9];
+          v = buf[C::bM + e * 8 + c - 9];
         } else {
           const int f = c - 17;
-          v = g[12 + 4 * f + 3] * ((__float_as_int(g[40 + f]) & 1) ? -1.f : 1.f);
+          v = g[12 + 4 * f + 3] * ((__float_as_int(buf[C::bE + e * 4 + f]) & 1) ? -1.f : 1.f);
         }
       }
       sGeo[e * 32 + c] = v;
     }
-    // time-integrated velocity (modal), the first 3 TE columns of each [L][NM] block of sM
-    for (int w = tid; w < L * TE; w += blockDim.x) {
+    // time-integrated velocity (modal), the first 3 TE columns of each [L][NM] block of sM,
+    // on threads from 128 on (the per-element data above runs on the first ones)
+    for (int w = (tid + C::THREADS - 128) % C::THREADS; w < L * TE; w += blockDim.x) {
       const int l = w / TE, e = w - l * TE;
       float iv[3] = {0.f, 0.f, 0.f};
       if (e < ne) {
@@ -1364,7 +1366,7 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
         float ci = dt;
 #pragma unroll
         for (int o = 1; o <= N; ++o) {
-          ci *= dt / static_cast<float>(o + 1);
+          ci *= dt * (1.f / static_cast<float>(o + 1));
           if (l < n_modes(N - o)) {
             const float* dd = de + d_offset(N, o) + l * 9 + 6;
 #pragma unroll
@@ -1381,8 +1383,19 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
     // alpha, 0.  Lane (c, l mod 4) of a warp holds one channel of one mode for all time
     // nodes, so each store of a warp fills one core matrix without bank conflicts.
     {
+      float cf[NT][N];                       // t_z^o / o!, o = 1..N
+#pragma unroll
+      for (int z = 0; z < NT; ++z) {
+        float cc = 1.f;
+#pragma unroll
+        for (int o = 1; o <= N; ++o) {
+          cc *= tz[z] * (1.f / static_cast<float>(o));
+          cf[z][o - 1] = cc;
+        }
+      }
       const int c = lane & 7, l4 = lane >> 3;
-      for (int pi = warp; pi < TE * (KP / 4); pi += C::THREADS / 32) {
+      // warps 9..15 and 0 (little or no work above) take the third round of items
+      for (int pi = (warp + 7) % 16; pi < TE * (KP / 4); pi += C::THREADS / 32) {
         const int e = pi / (KP / 4), lq = pi - e * (KP / 4);
         const int l = lq * 4 + l4;
         float base = 0.f, dd[N + 1];
@@ -1403,12 +1416,9 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
         }
 #pragma unroll
         for (int z = 0; z < NT; ++z) {
-          float x = base, cc = 1.f;
+          float x = base;
 #pragma unroll
-          for (int o = 1; o <= N; ++o) {
-            cc *= tz[z] / static_cast<float>(o);
-            x = fmaf(cc, dd[o], x);
-          }
+          for (int o = 1; o <= N; ++o) x = fmaf(cf[z][o - 1], dd[o], x);
           const float h = tc::tf32_hi(x);
           const int idx = tc_canon(e * NCOL + z * 8 + c, l, KP);
           sBeH[idx] = h;
@@ -1437,11 +1447,16 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
     // face GEMM), which needs no volume result
     if (tid < C::WORKERS) {
       auto bar = [] { tc::named_barrier(5, C::WORKERS); };
-      for (int w = tid; w < TE * 4 * NF * 9; w += C::WORKERS) {
-        const int e = w / (4 * NF * 9), r = w - e * 4 * NF * 9;
-        const int f = r / (NF * 9), r2 = r - f * NF * 9;
-        const int i = r2 / 9, p = r2 - 9 * i;
-        sF[(f * NF + i) * NFC + e * 9 + p] = e < ne ? sGeo[e * 32 + 17 + f] * sFraw[(e * 4 + f) * FFS + i * 9 + p] : 0.f;
+      // one 9-float row (element e, face f, node i) per thread, element fastest: the rows
+      // of a warp start 9 floats + a multiple of 36 apart, on distinct banks
+      for (int w = tid; w < TE * 4 * NF; w += C::WORKERS) {
+        const int e = w % TE, fi = w / TE;
+        const int f = fi / NF, i = fi - f * NF;
+        float* dst = sF + fi * NFC + e * 9;
+        const float sc = e < ne ? sGeo[e * 32 + 17 + f] : 0.f;
+        const float* src = sFraw + (e * 4 + f) * FFS + i * 9;
+#pragma unroll
+        for (int p = 0; p < 9; ++p) dst[p] = e < ne ? sc * src[p] : 0.f;
       }
       bar();
       block_gemm_part<C::KS_FACE, C::NJ_FACE>(sVfw, LP, sF, NFC, LP, NFC, 4 * NF, sPart, [&](int k, int col, float v) {

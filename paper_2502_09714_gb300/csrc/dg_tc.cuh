@@ -197,16 +197,17 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
 
-// Round to the nearest TF32 value (the high part of a 3xTF32 split).
 // Barrier over the nthreads threads (whole warps) that name barrier id (1..15).
 __device__ __forceinline__ void named_barrier(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// The nearest TF32 value (the high part of a 3xTF32 split): x rounded to 10
+// mantissa bits, ties away from zero, by integer arithmetic on the bit pattern (a
+// full-rate add and mask instead of a conversion).  A non-finite x stays non-finite
+// (a NaN may come back as an infinity).
 __device__ __forceinline__ float tf32_hi(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 }  // namespace tc
