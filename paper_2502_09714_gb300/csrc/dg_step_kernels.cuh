@@ -494,11 +494,13 @@ struct FluxCfg : Dim<N> {
   // fall on the same banks are shifted by 16 bytes
   static constexpr int goff(int g) { return g * GP + 4 * (g / (32 / GP)); }
   static constexpr int VROW = round4(goff(NG - 1) + GP);
-  static constexpr int META = 28;                           // per face: n, |S|/|J|, cp-, cp+, tag, local faces, materials
+  // per face: n, |S|/|J|, cp-, cp+, tag, local faces, materials, side 0's mode-0 row
+  static constexpr int META = 40;
   static constexpr int oV = 0;                              // [4][L][VROW] phi_l at the face nodes
   static constexpr int oRaw = round4(oV + 4 * D::L * VROW);  // [TF][2][RAW]
-  static constexpr int oMeta = oRaw + TF * 2 * RAW;         // [TF][META]
-  static constexpr int oTr = round4(oMeta + TF * META);     // [TF][2][N+1][NGG][12] traces per order
+  static constexpr int oMeta = oRaw + TF * 2 * RAW;         // [2][TF][META], this tile's and the next one's
+  static constexpr int oFR = oMeta + 2 * TF * META;         // [2][TF] int4 face records of the next two tiles
+  static constexpr int oTr = round4(oFR + 2 * TF * 4);      // [TF][2][N+1][NGG][12] traces per order
   static constexpr int SMEM = oTr + TF * 2 * (N + 1) * NGG * 12;
   static_assert(TF >= 1 && UPK <= KT, "trace units per kind");
   static_assert(THREADS > 256 || SMEM * 4 * 2 <= 227 * 1024, "two face CTAs per SM");
@@ -537,18 +539,19 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
     sV[(lf * L + l) * C::VROW + C::goff(g) + n] = (n < G && node < NF) ? __ldg(tb + T.VfT + (lf * L + l) * NFP + node) : 0.f;
   }
 
+  // Copies of a tile's face data: per face the normal, both cells' P speeds and
+  // materials (into the meta buffer mt0); per side the state and the predictor output
+  // as stored (into sRaw).  Face records from fr (shared or global memory).
   const int64_t ntiles = (a.F + TF - 1) / TF;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t f0 = tile * TF;
+  int4* sFR = reinterpret_cast<int4*>(sm + C::oFR);
+  auto issue = [&](int64_t tl, const int4* fr, float* mt0, int t, int nt) {
+    const int64_t f0 = tl * TF;
     const int nf = static_cast<int>(min(static_cast<int64_t>(TF), a.F - f0));
-    __syncthreads();
-    // one batch of asynchronous copies: per face the normal, both cells' P speeds and
-    // materials; per side the state and the predictor output as stored
     constexpr int CH = C::RAW_USED / 4;          // 16-byte chunks per side
-    for (int w = tid; w < TF * (2 * CH + 8); w += C::THREADS) {
+    for (int w = t; w < TF * (2 * CH + 8); w += nt) {
       const int fc = w / (2 * CH + 8), r = w - fc * (2 * CH + 8);
       if (fc >= nf) continue;
-      const int4 fa = a.faces[f0 + fc];
+      const int4 fa = fr[fc];
       const bool bnd = fa.z < 0;
       if (r < 2 * CH) {
         const int side = r / CH, ch = r - side * CH;
@@ -558,7 +561,7 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
         if (ch < QS / 4) tc::cp_async16(dst, a.q_in + e * QS + 4 * ch);
         else tc::cp_async16(dst, a.d + e * DS + 4 * (ch - QS / 4));
       } else {
-        float* mt = sMeta + fc * META;
+        float* mt = mt0 + fc * META;
         const int k = r - 2 * CH;
         const int64_t ep = bnd ? fa.x : fa.z;
         if (k == 0) tc::cp_async16(mt, &a.geom[fa.x].face[fa.y][0]);
@@ -575,8 +578,32 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
         }
       }
     }
-    tc::cp_async_wait_all();
+  };
+  // face records of tile tl into slot b
+  auto issue_records = [&](int64_t tl, int b, int t, int nt) {
+    const int64_t f0 = tl * TF;
+    const int nf = static_cast<int>(min(static_cast<int64_t>(TF), a.F - f0));
+    for (int w = t; w < nf; w += nt) tc::cp_async16(sFR + b * TF + w, a.faces + f0 + w);
+  };
+
+  if (static_cast<int64_t>(blockIdx.x) < ntiles)
+    issue(blockIdx.x, a.faces + static_cast<int64_t>(blockIdx.x) * TF, sm + C::oMeta, tid, C::THREADS);
+  if (static_cast<int64_t>(blockIdx.x) + gridDim.x < ntiles) issue_records(blockIdx.x + gridDim.x, 1, tid, C::THREADS);
+  tc::cp_async_commit();
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int64_t f0 = tile * TF;
+    const int nf = static_cast<int>(min(static_cast<int64_t>(TF), a.F - f0));
+    float* sMeta = sm + C::oMeta + (it & 1) * TF * META;
+    __syncthreads();                           // the previous tile's flux phase is done
+    tc::cp_async_wait<0>();                    // this tile's copies (and the next tile's face records)
     __syncthreads();
+    // side 0's mode-0 row (the cell mean) for the boundary flux, kept with the face data:
+    // the next tile's copies overwrite the state during the flux phase
+    for (int w = tid; w < TF * 10; w += C::THREADS) {
+      const int fc = w / 10, c = w - 10 * fc;
+      sMeta[fc * META + 28 + c] = sRaw[(2 * fc) * RAW + c];
+    }
 
     // traces: warps 0-3 order 0 (G nodes x 4 columns), warps 4-7 orders 1..N (G nodes x 3 fields)
     {
@@ -647,6 +674,13 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
       }
     }
     __syncthreads();
+    // the next tile's copies (its face records landed with this tile's data), then the
+    // records of the tile after it, while the flux runs
+    if (tile + gridDim.x < ntiles)
+      issue(tile + gridDim.x, sFR + ((it + 1) & 1) * TF, sm + C::oMeta + ((it + 1) & 1) * TF * META, tid, C::THREADS);
+    if (tile + 2 * static_cast<int64_t>(gridDim.x) < ntiles)
+      issue_records(tile + 2 * static_cast<int64_t>(gridDim.x), it & 1, tid, C::THREADS);
+    tc::cp_async_commit();
 
     // flux at the face nodes, time-integrated: two threads per (face, node), each
     // over half of the time nodes, combined by a shuffle
@@ -672,7 +706,7 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
         }
         float lam = 0.f, mu = 0.f, cpb = 0.f, csb = 0.f, k_p = 0.f;
         if (bc != 0) {
-          effective_lame(a.law, sRaw + (2 * fc) * RAW, mm, &lam, &mu);   // row 0 of the state: the cell-mean modes
+          effective_lame(a.law, mt + 28, mm, &lam, &mu);   // side 0's cell-mean modes
           cpb = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * mm.rho_inv);
           csb = sqrtf(fmaxf(mu, 0.f) * mm.rho_inv);
           k_p = lam + 2.f * mu > 0.f ? cpb / (lam + 2.f * mu) : 0.f;
@@ -731,6 +765,7 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
       }
     }
   }
+  tc::cp_async_wait<0>();                      // no copy may still be in flight at exit
 }
 
 // ===========================================================================
