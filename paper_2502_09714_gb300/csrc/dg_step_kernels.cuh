@@ -293,15 +293,19 @@ struct PredCfg : Dim<N> {
   static constexpr int oVvT = 0;
   static constexpr int oVw = TSM ? round4(oVvT + D::L * D::NQP) : 0;
   static constexpr int oKtA = TSM ? round4(oVw + D::NQ * D::LP) : 0;
+  // staged state rows, stride QSP: off the bank period, so that lanes on different
+  // elements read different banks
+  static constexpr int QSP = D::QS % 32 == 0 ? D::QS + 4 : D::QS;
   static constexpr int oQ = TSM ? round4(oKtA + 3 * D::L * D::LP) : 0;
-  static constexpr int oC0 = oQ + TE * D::QS;              // [L][8 TE] strains at t_n
+  static constexpr int oC0 = oQ + TE * QSP;                // [L][8 TE] strains at t_n
   static constexpr int oR = oC0 + D::L * 8 * TE;           // [NQ][TE] damage rate at the nodes
   static constexpr int oP0 = round4(oR + D::NQ * TE);      // [L][CW] CK input
   static constexpr int oP1 = oP0 + D::L * CW;              // [L][CW] CK output
   static constexpr int oPart = oP1 + D::L * CW;            // split-K partial sums
   static constexpr int PART = KS_SRC * D::LP * TE;
   static constexpr int oCoef = oPart + PART;               // [TE][16]
-  static constexpr int SMEM = oCoef + 16 * TE;
+  static constexpr int oGM = round4(oCoef + 16 * TE);      // [TE][40] GeomF, MatF as copied
+  static constexpr int SMEM = oGM + 40 * TE;
   static constexpr bool FITS = SMEM * 4 <= 227 * 1024;
   static_assert(FITS || TSM, "predictor shared memory");
 };
@@ -324,6 +328,7 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
   float* sP1 = sm + C::oP1;
   float* sPart = sm + C::oPart;
   float* sCoef = sm + C::oCoef;
+  float* sGM = sm + C::oGM;
   if (TSM) {
     copy_to_smem(sm + C::oVvT, a.tables + T.VvT, L * NQP);
     copy_to_smem(sm + C::oVw, a.tables + T.Vw, NQ * LP);
@@ -335,41 +340,46 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
     const int64_t e0 = tile * TE;
     const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
     __syncthreads();
-    {
-      const float4* src = reinterpret_cast<const float4*>(a.q_in + e0 * QS);
-      float4* dst = reinterpret_cast<float4*>(sQ);
-      for (int w = threadIdx.x; w < TE * QS / 4; w += blockDim.x)
-        dst[w] = w < ne * QS / 4 ? __ldg(src + w) : make_float4(0.f, 0.f, 0.f, 0.f);
+    // one batch of asynchronous copies: the tile's state rows, GeomF and MatF
+    for (int w = threadIdx.x; w < TE * QS / 4; w += blockDim.x) {
+      const int e = w / (QS / 4), c = w - e * (QS / 4);
+      if (e < ne) tc::cp_async16(sQ + e * C::QSP + 4 * c, a.q_in + (e0 + e) * QS + 4 * c);
+      else *reinterpret_cast<float4*>(sQ + e * C::QSP + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    for (int w = threadIdx.x; w < ne * 10; w += blockDim.x) {
+      const int e = w / 10, k = w - 10 * e;
+      if (k < 8) tc::cp_async16(sGM + e * 40 + 4 * k, reinterpret_cast<const float*>(a.geom + e0 + e) + 4 * k);
+      else tc::cp_async16(sGM + e * 40 + 32 + 4 * (k - 8), reinterpret_cast<const float*>(a.mat + e0 + e) + 4 * (k - 8));
+    }
+    tc::cp_async_wait_all();
     __syncthreads();
     // per element: effective moduli at the cell mean (Eq. "effective-cdb", mu sign from Eq. "cdb-model")
     if (threadIdx.x < ne) {
       const int e = threadIdx.x;
       const int64_t ge = e0 + e;
-      const MatF m = a.mat[ge];
+      const MatF m = *reinterpret_cast<const MatF*>(sGM + e * 40 + 32);
       float lam, mu;
-      effective_lame(a.law, sQ + e * QS, m, &lam, &mu);
+      effective_lame(a.law, sQ + e * C::QSP, m, &lam, &mu);
       if (!(mu > 0.f) || !(lam + 2.f * mu > 0.f)) atomicOr(a.status, kStatusNonHyperbolic);
       a.cp[ge] = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * m.rho_inv);
       float* c = sCoef + e * 16;
       c[0] = lam * m.rho_inv;
       c[1] = mu * m.rho_inv;
-      const GeomF* g = a.geom + ge;
-      for (int k = 0; k < 9; ++k) c[2 + k] = g->tinv[k];
+      const float* g = sGM + e * 40;           // GeomF starts with Theta^{-1}
+      for (int k = 0; k < 9; ++k) c[2 + k] = g[k];
     }
     // coefficient arrays: strains at t_n [l][e*8 + c] and the CK input [l][e*12 + p]
     for (int w = threadIdx.x; w < L * TE; w += blockDim.x) {
       const int l = w / TE, e = w - l * TE;
-      const float* q = sQ + e * QS + l * 10;
-      float* c0 = sC0 + l * 8 * TE + e * 8;
-      float* p0 = sP0 + l * CW + e * 12;
-#pragma unroll
-      for (int p = 0; p < 6; ++p) c0[p] = q[p];
-      c0[6] = q[9];
-      c0[7] = 0.f;
-#pragma unroll
-      for (int p = 0; p < 9; ++p) p0[p] = q[p];
-      p0[9] = p0[10] = p0[11] = 0.f;
+      const float2* q2 = reinterpret_cast<const float2*>(sQ + e * C::QSP + l * 10);
+      const float2 q01 = q2[0], q23 = q2[1], q45 = q2[2], q67 = q2[3], q89 = q2[4];
+      float4* c0 = reinterpret_cast<float4*>(sC0 + l * 8 * TE + e * 8);
+      float4* p0 = reinterpret_cast<float4*>(sP0 + l * CW + e * 12);
+      c0[0] = make_float4(q01.x, q01.y, q23.x, q23.y);
+      c0[1] = make_float4(q45.x, q45.y, q89.y, 0.f);
+      p0[0] = make_float4(q01.x, q01.y, q23.x, q23.y);
+      p0[1] = make_float4(q45.x, q45.y, q67.x, q67.y);
+      p0[2] = make_float4(q89.x, 0.f, 0.f, 0.f);
     }
     __syncthreads();
 
@@ -395,7 +405,7 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
           acc[1][p] = fmaf(ph.y, cv[p], acc[1][p]);
         }
       }
-      const MatF m = a.mat[e0 + (e < ne ? e : 0)];
+      const MatF m = *reinterpret_cast<const MatF*>(sGM + (e < ne ? e : 0) * 40 + 32);
 #pragma unroll
       for (int n = 0; n < 2; ++n) {
         const int q = 2 * j + n;
