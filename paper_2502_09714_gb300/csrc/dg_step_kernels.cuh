@@ -418,8 +418,10 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
       if (k < L && e < ne) a.d[(e0 + e) * DS + C::AOFF + k] = v;
     });
 
-    // Cauchy-Kovalevskaya: D^i_kp = -sum_e Kt^e_kl D^{i-1}_lq (Theta^{-1}_ed B^d_pq)
-#pragma unroll 1
+    // Cauchy-Kovalevskaya: D^i_kp = -sum_e Kt^e_kl D^{i-1}_lq (Theta^{-1}_ed B^d_pq); the
+    // order loop is unrolled so that the mode counts are constants and the inner loop
+    // can be software-pipelined
+#pragma unroll
     for (int i = 1; i <= N; ++i) {
       const int Lin = n_modes(N - i + 1), Lout = n_modes(N - i);
       const float* pin = (i & 1) ? sP0 : sP1;
@@ -430,6 +432,7 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
         float g[3][9];
 #pragma unroll
         for (int f = 0; f < 9; ++f) g[0][f] = g[1][f] = g[2][f] = 0.f;
+#pragma unroll 4
         for (int l = 0; l < Lin; ++l) {
           const float k0 = sKtA[(0 * L + l) * LP + k], k1 = sKtA[(1 * L + l) * LP + k], k2 = sKtA[(2 * L + l) * LP + k];
           const float4 p0 = *reinterpret_cast<const float4*>(pin + l * CW + e * 12);
