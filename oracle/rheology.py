@@ -4,9 +4,11 @@ last axis: (eps_xx, eps_yy, eps_zz, eps_xy, eps_yz, eps_zx, v_x, v_y, v_z, alpha
 (Eq. "nonlinear hyper pdes"), tensor shear strains.
 
 Material arrays `mat` have last axis (rho, lambda0, mu0, gamma_r, xi0, C_d) for
-the CDM and (rho, lambda0, mu0, gamma_b, tau_b, unused) for the IVM
+the CDM, (rho, lambda0, mu0, gamma_b, tau_b, unused) for the IVM
 (Eq. "ivm-model", Murnaghan coefficients l0 = m0 = n0 = 0 as the paper sets
-them).  The law-generic entry points take law = "cdm" (default) or "ivm".
+them) and (rho, lambda0, mu0, beta, unused, unused) for the nonlinear shear law
+of the 1-D Riemann verification (Sec. 3.1, Eq. "1d Riemann eqs").  The
+law-generic entry points take law = "cdm" (default), "ivm" or "nlshear".
 """
 from __future__ import annotations
 
@@ -122,20 +124,68 @@ def ivm_effective_lame(u, mat):
     return (1.0 - alpha) * mat[..., 1], (1.0 - alpha) * mat[..., 2]
 
 
+def shear_magnitude(u):
+    """gamma = sqrt(I2 / 2): for a plane shear state (eps_xy = eps_yx the only
+    nonzero strains) I2 = 2 eps_xy^2 and gamma = |eps_xy|."""
+    _, I2, _, _ = invariants(u)
+    return np.sqrt(0.5 * I2)
+
+
+def nlshear_stress(u, mat):
+    """Stress of the nonlinear shear law (reading R19):
+    sigma = lambda0 I1 delta + 2 mu0 (1 - beta gamma) eps,  gamma = sqrt(I2 / 2).
+    It is the isotropic law whose plane shear response is the relation of
+    Eq. "1d Riemann eqs", sigma_xy = 2 mu (1 - beta eps_xy) eps_xy for eps_xy >= 0;
+    alpha plays no part."""
+    lam0, mu0, beta = mat[..., 1], mat[..., 2], mat[..., 3]
+    e = strain_tensor(u)
+    I1 = e[..., 0, 0] + e[..., 1, 1] + e[..., 2, 2]
+    g = shear_magnitude(u)
+    sh = 2.0 * mu0 * (1.0 - beta * g)
+    return (lam0 * I1)[..., None, None] * np.eye(3) + sh[..., None, None] * e
+
+
+def nlshear_damage_rate(u, mat):
+    """No damage variable evolves under the nonlinear shear law: r_alpha = 0."""
+    return np.zeros(u.shape[:-1])
+
+
+def nlshear_energy(u, mat):
+    """Energy density whose strain gradient is nlshear_stress (derived, not
+    printed): W = lambda0/2 I1^2 + mu0 I2 - (sqrt(2)/3) mu0 beta I2^(3/2), since
+    d I2^(3/2) / d eps = 3 sqrt(I2) eps and sqrt(2) sqrt(I2) = 2 gamma."""
+    lam0, mu0, beta = mat[..., 1], mat[..., 2], mat[..., 3]
+    I1, I2, _, _ = invariants(u)
+    return 0.5 * lam0 * I1 * I1 + mu0 * I2 - (np.sqrt(2.0) / 3.0) * mu0 * beta * I2 ** 1.5
+
+
+def nlshear_effective_lame(u, mat):
+    """Secant moduli at the state (reading R19): lambda_eff = lambda0,
+    mu_eff = mu0 (1 - beta gamma), so that sigma(u) = lambda_eff I1 delta + 2 mu_eff eps."""
+    return mat[..., 1] + 0.0 * u[..., 0], mat[..., 2] * (1.0 - mat[..., 3] * shear_magnitude(u))
+
+
+_LAWS = {
+    "cdm": (cdm_stress, cdm_damage_rate, cdm_energy, effective_lame),
+    "ivm": (ivm_stress, ivm_damage_rate, ivm_energy, ivm_effective_lame),
+    "nlshear": (nlshear_stress, nlshear_damage_rate, nlshear_energy, nlshear_effective_lame),
+}
+
+
 def stress(u, mat, law="cdm"):
-    return ivm_stress(u, mat) if law == "ivm" else cdm_stress(u, mat)
+    return _LAWS[law][0](u, mat)
 
 
 def damage_rate(u, mat, law="cdm"):
-    return ivm_damage_rate(u, mat) if law == "ivm" else cdm_damage_rate(u, mat)
+    return _LAWS[law][1](u, mat)
 
 
 def energy(u, mat, law="cdm"):
-    return ivm_energy(u, mat) if law == "ivm" else cdm_energy(u, mat)
+    return _LAWS[law][2](u, mat)
 
 
 def effective_lame_law(u, mat, law="cdm"):
-    return ivm_effective_lame(u, mat) if law == "ivm" else effective_lame(u, mat)
+    return _LAWS[law][3](u, mat)
 
 
 def flux(u, mat, law="cdm"):

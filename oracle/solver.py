@@ -21,8 +21,10 @@ One step from t_n to t_{n+1} = t_n + dt, in the order of Appendix A:
      ("Free surface and absorbing boundary conditions", oracle/boundary.py);
   9. update of Eq. "time-integrated" with M = I (orthonormal basis).
 Point sources enter step 9 as strain-rate deltas; receivers sample velocity.
-The pointwise law is the CDM of Eq. "cdb-model" (law="cdm", default) or the IVM
-of Eq. "ivm-model" without Murnaghan terms (law="ivm").
+The pointwise law is the CDM of Eq. "cdb-model" (law="cdm", default), the IVM
+of Eq. "ivm-model" without Murnaghan terms (law="ivm") or the nonlinear shear
+law of the 1-D Riemann verification (law="nlshear", Eq. "1d Riemann eqs",
+reading R19), whose effective moduli in step 2 are its secant moduli.
 
 State layout inside the oracle: Q[E, L, 10] (mode, field), modes of the
 Dubiner basis mapped onto each element with its vertices in increasing vertex
@@ -97,7 +99,7 @@ class Oracle:
                         else np.asarray(face_bc, dtype=np.int8)[rows, vorder])
         if np.any((self.face_bc < 0) | (self.face_bc > 2)):
             raise MeshError("face tags must be 0 (interior), 1 (free surface) or 2 (absorbing)")
-        if law not in ("cdm", "ivm"):
+        if law not in ("cdm", "ivm", "nlshear"):
             raise ValueError(f"unknown rheology {law}")
         self.law = law
         self.cfl = cfl
@@ -389,6 +391,8 @@ class Oracle:
         u = self.evaluate(Q, pts)
         mat = self.mat[:, None, :]
         I1, I2, s, xi = invariants(u)
+        if self.law == "nlshear":
+            return 0.0
         if self.law == "ivm":
             dWda = -(0.5 * mat[..., 1] * I1 * I1 + mat[..., 2] * I2)
         else:

@@ -15,7 +15,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .mesh import periodic_cube_mesh
+from .mesh import kuhn_box_mesh, periodic_cube_mesh
 
 FIELD_NAMES = ("exx", "eyy", "ezz", "exy", "eyz", "ezx", "vx", "vy", "vz", "alpha")
 
@@ -131,3 +131,29 @@ def workload_small_layered(n=4, order=3, side=4000.0, m0=C2_M0, seed=1, sort_by_
         cz = w["mesh"].centroids()[:, 2]
         w["material"] = two_layer_material(cz, z_top=side, layer_thickness=600.0 * side / 4000.0)
     return w
+
+
+# 1-D Riemann problem of the nonlinear shear law (Sec. 3.1): rho = mu = 1 and beta = 10
+# as the paper sets them, lambda0 = 1 (not stated; it only sets the P speed), and a
+# strain step at rest (eps_xy 0.01 | 0.02), inside the hyperbolic range of the law
+RIEMANN_LEFT = (0.01, 0.0)      # (eps_xy, v_y) for x < 0
+RIEMANN_RIGHT = (0.02, 0.0)     # (eps_xy, v_y) for x >= 0
+RIEMANN_MATERIAL = (1.0, 1.0, 1.0, 10.0)   # rho, lambda0, mu0, beta
+
+
+def workload_riemann(nx, order=2, half_length=1.2, t_end=0.5):
+    """Quasi-1-D mesh for the plane shear Riemann problem: nx cells on
+    [-half_length, half_length] in x (x = 0 a grid plane), 3 cells of the same
+    width in y and z, periodic in all three directions, Kuhn 6-tet split.  The
+    periodic seam at x = +-half_length starts a second wave fan; with speeds
+    below 1 neither fan reaches |x| < half_length - t_end before t_end, the
+    window `eval_half_width` where the solution is compared."""
+    h = 2.0 * half_length / nx
+    xs = np.linspace(-half_length, half_length, nx + 1)
+    yz = np.linspace(0.0, 3.0 * h, 4)
+    mesh = kuhn_box_mesh(xs, yz, yz, periodic=(True, True, True), sort_by_vid=True)
+    mat = np.zeros((mesh.n_elem, 6))
+    mat[:, :4] = RIEMANN_MATERIAL
+    return {"name": f"plane shear Riemann problem nx={nx} N={order}", "mesh": mesh, "material": mat,
+            "order": order, "left": RIEMANN_LEFT, "right": RIEMANN_RIGHT, "t_end": t_end, "h": h,
+            "eval_half_width": half_length - t_end - 0.1}
