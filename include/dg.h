@@ -110,11 +110,17 @@ typedef struct {
  * On success *out owns the context (free with dg_destroy). */
 dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out);
 
-/* Pointwise law of the step: DG_LAW_CDM (default; Eq. "cdb-model") or DG_LAW_IVM
+/* Pointwise law of the step: DG_LAW_CDM (default; Eq. "cdb-model"), DG_LAW_IVM
  * (Eq. "ivm-model" with the Murnaghan coefficients l0 = m0 = n0 = 0, effective Lame
- * parameters of Eq. "effective-ivm").  Changing the law invalidates the material:
- * call dg_set_material again before dg_step.  DG_E_ARG for another value. */
-enum { DG_LAW_CDM = 0, DG_LAW_IVM = 1 };
+ * parameters of Eq. "effective-ivm") or DG_LAW_NLSHEAR, the nonlinear shear law of
+ * the 1-D Riemann verification (Sec. 3.1, Eq. "1d Riemann eqs"):
+ *     sigma = lambda0 I1 delta + 2 mu0 (1 - beta gamma) eps,  gamma = sqrt(I2 / 2),
+ * whose plane shear response is sigma_xy = 2 mu0 (1 - beta eps_xy) eps_xy for
+ * eps_xy >= 0; alpha does not evolve, and the predictor and boundary Jacobians use
+ * the secant moduli lambda0 and mu0 (1 - beta gamma) at the cell mean.  Changing
+ * the law invalidates the material: call dg_set_material again before dg_step.
+ * DG_E_ARG for another value. */
+enum { DG_LAW_CDM = 0, DG_LAW_IVM = 1, DG_LAW_NLSHEAR = 2 };
 dg_status dg_set_rheology(dg_ctx* ctx, int law);
 
 /* Per-element material [n_elem][6] = (rho, lambda0, mu0, gamma_r, xi0, C_d):
@@ -127,7 +133,8 @@ dg_status dg_set_rheology(dg_ctx* ctx, int law);
  * shared by the members.  Under DG_LAW_IVM the rows are
  * (rho, lambda0, mu0, gamma_b, tau_b, unused) with gamma_b > 0 [Pa] the scale of
  * the storage energy and tau_b > 0 [s] the damage time scale, and
- * member_xi0_cd must be NULL.
+ * member_xi0_cd must be NULL.  Under DG_LAW_NLSHEAR the rows are
+ * (rho, lambda0, mu0, beta, unused, unused) with beta >= 0, member_xi0_cd NULL.
  * Also fixes the default time step dt = cfl * min_e 2 r_in(e) / ((2N+1) c_p(e)),
  * r_in the inradius, c_p = sqrt((lambda0 + 2 mu0)/rho). */
 dg_status dg_set_material(dg_ctx* ctx, const double* mat, const double* member_xi0_cd);

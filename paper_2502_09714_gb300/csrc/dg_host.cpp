@@ -40,7 +40,7 @@ struct FaceKeyHash {
 
 struct dg_ctx {
   int N = 0, L = 0, M = 1;
-  int law = 0;                       // 0 = CDM, 1 = IVM
+  int law = 0;                       // 0 = CDM, 1 = IVM, 2 = nonlinear shear
   int64_t E = 0;                     // mesh elements
   int64_t EV = 0;                    // element copies on the device: E x members, member fastest
   double cfl = 0.5;
@@ -660,7 +660,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
 
 dg_status dg_set_rheology(dg_ctx* ctx, int law) {
   if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
-  if (law != DG_LAW_CDM && law != DG_LAW_IVM) return fail(ctx, DG_E_ARG, "unknown rheology");
+  if (law != DG_LAW_CDM && law != DG_LAW_IVM && law != DG_LAW_NLSHEAR) return fail(ctx, DG_E_ARG, "unknown rheology");
   if (law != ctx->law) ctx->has_material = false;   // the material slots change meaning
   ctx->law = law;
   return DG_OK;
@@ -680,6 +680,15 @@ dg_status dg_set_material(dg_ctx* ctx, const double* mat, const double* member_x
     const double rho = m[0], lam = m[1], mu = m[2], gr = m[3];
     if (!(rho > 0) || !(mu > 0) || !(lam + 2 * mu > 0))
       return fail(ctx, DG_E_ARG, "invalid material of element " + std::to_string(e));
+    if (ctx->law == DG_LAW_NLSHEAR) {
+      // (rho, lambda0, mu0, beta, -, -): beta in gamma_r
+      if (!(m[3] >= 0)) return fail(ctx, DG_E_ARG, "the shear law needs beta >= 0, element " + std::to_string(e));
+      const MatF f{float(rho), float(lam), float(mu), float(m[3]), 0.f, 0.f, float(1.0 / rho), 0.f};
+      for (int64_t k = 0; k < M; ++k) mf[e * M + k] = f;
+      const double cp = std::sqrt((lam + 2 * mu) / rho);
+      dt = std::min(dt, ctx->cfl * 2.0 * ctx->rin[e] / ((2 * ctx->N + 1) * cp));
+      continue;
+    }
     if (ctx->law == DG_LAW_IVM) {
       // (rho, lambda0, mu0, gamma_b, tau_b, -): gamma_b in gamma_r, 1/(gamma_b tau_b) in C_d
       if (!(m[3] > 0) || !(m[4] > 0)) return fail(ctx, DG_E_ARG, "IVM needs gamma_b > 0 and tau_b > 0, element " + std::to_string(e));

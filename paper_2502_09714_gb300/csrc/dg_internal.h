@@ -143,7 +143,8 @@ struct StepArgs {
   float dt;
   unsigned* status;
   int grid_pred, grid_face, grid_corr;   // persistent grid sizes (0: one CTA per tile)
-  int law;                // pointwise law: 0 = CDM (Eq. "cdb-model"), 1 = IVM (Eq. "ivm-model")
+  int law;                // pointwise law: 0 = CDM (Eq. "cdb-model"), 1 = IVM (Eq. "ivm-model"),
+                          // 2 = nonlinear shear (Eq. "1d Riemann eqs")
 };
 
 // Kernel launchers, one per compiled degree (dg_step_n<N>.cu), and their

@@ -103,13 +103,33 @@ __device__ __forceinline__ void ivm_point(const float e[6], float alpha, const M
   *rate = m.cd * (0.5f * m.lam0 * I1 * I1 + m.mu0 * I2 - m.gamma_r * s * s);
 }
 
-// The pointwise law selected for the step: 0 = CDM, 1 = IVM.
+// Nonlinear shear law of the 1-D Riemann verification (Eq. "1d Riemann eqs"):
+// sigma = lambda0 I1 delta + 2 mu0 (1 - beta gamma) eps, gamma = sqrt(I2 / 2), which in
+// plane shear is sigma_xy = 2 mu0 (1 - beta eps_xy) eps_xy for eps_xy >= 0; beta is
+// held in gamma_r and alpha does not evolve.
+__device__ __forceinline__ void nlshear_point(const float e[6], const MatF& m, float sig[6], float* rate) {
+  const float I1 = e[0] + e[1] + e[2];
+  const float I2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + 2.f * (e[3] * e[3] + e[4] * e[4] + e[5] * e[5]);
+  const float sh = 2.f * m.mu0 * (1.f - m.gamma_r * sqrtf(0.5f * I2));
+  const float iso = m.lam0 * I1;
+  sig[0] = iso + sh * e[0];
+  sig[1] = iso + sh * e[1];
+  sig[2] = iso + sh * e[2];
+  sig[3] = sh * e[3];
+  sig[4] = sh * e[4];
+  sig[5] = sh * e[5];
+  *rate = 0.f;
+}
+
+// The pointwise law selected for the step: 0 = CDM, 1 = IVM, 2 = nonlinear shear.
 __device__ __forceinline__ void law_point(int law, const float e[6], float alpha, const MatF& m, float sig[6],
                                           float* rate) {
   if (law == 1) ivm_point(e, alpha, m, sig, rate);
+  else if (law == 2) nlshear_point(e, m, sig, rate);
   else cdm_point(e, alpha, m, sig, rate);
 }
 __device__ __forceinline__ float law_rate(int law, const float e[6], float alpha, const MatF& m) {
+  if (law == 2) return 0.f;
   if (law == 1) {
     float sig[6], r;
     ivm_point(e, alpha, m, sig, &r);
@@ -136,8 +156,8 @@ __device__ __forceinline__ void normal_flux(int law, const float u[10], const Ma
 }
 
 // Effective Lame parameters at a cell mean (CDM: Eq. "effective-cdb" with the sign
-// of the xi0 term taken from Eq. "cdb-model"; IVM: Eq. "effective-ivm"); q0 holds the
-// ten mode-0 coefficients.
+// of the xi0 term taken from Eq. "cdb-model"; IVM: Eq. "effective-ivm"; nonlinear
+// shear: the secant moduli); q0 holds the ten mode-0 coefficients.
 __device__ __forceinline__ void effective_lame(int law, const float* q0, const MatF& m, float* lam, float* mu) {
   const float r6 = 2.449489742783178f;   // phi_0 = sqrt(6): cell mean = Q_0 sqrt(6)
   if (law == 1) {
@@ -149,6 +169,12 @@ __device__ __forceinline__ void effective_lame(int law, const float* q0, const M
   float u[6];
 #pragma unroll
   for (int p = 0; p < 6; ++p) u[p] = q0[p] * r6;
+  if (law == 2) {                        // secant moduli of the nonlinear shear law
+    const float I2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + 2.f * (u[3] * u[3] + u[4] * u[4] + u[5] * u[5]);
+    *lam = m.lam0;
+    *mu = m.mu0 * (1.f - m.gamma_r * sqrtf(0.5f * I2));
+    return;
+  }
   const float alpha = q0[9] * r6;
   const float I1 = u[0] + u[1] + u[2];
   const float I2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + 2.f * (u[3] * u[3] + u[4] * u[4] + u[5] * u[5]);

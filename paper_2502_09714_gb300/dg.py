@@ -181,8 +181,9 @@ class Solver:
             self.set_rheology(law)
 
     def set_rheology(self, law):
-        """law: "cdm" (Eq. "cdb-model") or "ivm" (Eq. "ivm-model"); set the material after."""
-        self._chk(self.lib.dg_set_rheology(self.ctx, {"cdm": 0, "ivm": 1}[law]))
+        """law: "cdm" (Eq. "cdb-model"), "ivm" (Eq. "ivm-model") or "nlshear" (the
+        nonlinear shear law of the 1-D Riemann verification); set the material after."""
+        self._chk(self.lib.dg_set_rheology(self.ctx, {"cdm": 0, "ivm": 1, "nlshear": 2}[law]))
 
     # ------------------------------------------------------------------
     def _chk(self, status):
