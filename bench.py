@@ -372,13 +372,14 @@ def run_ensemble(args, dgpkg, torch, stream, steps=10, warmup=3):
 
 
 def _kernel_name(kind, N):
-    """Name of the CUDA kernel that runs `kind` at degree N (the corrector's
-    volume evaluation runs on the tensor cores for 2 <= N <= 4 unless bit 3 of
-    DG_KERNEL_VARIANT selects the all-SIMT corrector)."""
+    """Name of the CUDA kernel that runs `kind` at degree N under the CDM (the
+    kernels' last template argument 0: compiled for the CDM alone).  The
+    corrector's volume evaluation runs on the tensor cores for 2 <= N <= 4
+    unless bit 3 of DG_KERNEL_VARIANT selects the all-SIMT corrector."""
     variant = int(os.environ.get("DG_KERNEL_VARIANT", "1"))
     if kind == "corrector" and 2 <= N <= 4 and not (variant & 8):
-        return f"k_corrector_tc<{N}>"
-    return f"k_{kind}<{N}>"
+        return f"k_corrector_tc<{N}, 0>"
+    return f"k_{kind}<{N}, 0>"
 
 
 def _kernel_source_digest():

@@ -121,14 +121,23 @@ __device__ __forceinline__ void nlshear_point(const float e[6], const MatF& m, f
   *rate = 0.f;
 }
 
-// The pointwise law selected for the step: 0 = CDM, 1 = IVM, 2 = nonlinear shear.
+// The pointwise law of the step: 0 = CDM, 1 = IVM, 2 = nonlinear shear.  Every law-
+// dependent helper and kernel takes LAW: 0 compiles the CDM alone (the kernels run with
+// it whenever the CDM is selected), -1 dispatches on the run-time value `law`.
+template <int LAW>
 __device__ __forceinline__ void law_point(int law, const float e[6], float alpha, const MatF& m, float sig[6],
                                           float* rate) {
-  if (law == 1) ivm_point(e, alpha, m, sig, rate);
-  else if (law == 2) nlshear_point(e, m, sig, rate);
-  else cdm_point(e, alpha, m, sig, rate);
+  if constexpr (LAW == 0) {
+    cdm_point(e, alpha, m, sig, rate);
+  } else {
+    if (law == 1) ivm_point(e, alpha, m, sig, rate);
+    else if (law == 2) nlshear_point(e, m, sig, rate);
+    else cdm_point(e, alpha, m, sig, rate);
+  }
 }
+template <int LAW>
 __device__ __forceinline__ float law_rate(int law, const float e[6], float alpha, const MatF& m) {
+  if constexpr (LAW == 0) return cdm_rate(e, m);
   if (law == 2) return 0.f;
   if (law == 1) {
     float sig[6], r;
@@ -140,9 +149,10 @@ __device__ __forceinline__ float law_rate(int law, const float e[6], float alpha
 
 // Normal flux F^d(u) n_d of the 9 wave fields (Eq. "nonlinear hyper pdes"):
 // strain rows -(v_i n_j + v_j n_i)/2, velocity rows -sigma_ij n_j / rho.
+template <int LAW>
 __device__ __forceinline__ void normal_flux(int law, const float u[10], const MatF& m, const float n[3], float F[9]) {
   float sig[6], r;
-  law_point(law, u, u[9], m, sig, &r);
+  law_point<LAW>(law, u, u[9], m, sig, &r);
   const float vx = u[6], vy = u[7], vz = u[8];
   F[0] = -vx * n[0];
   F[1] = -vy * n[1];
@@ -158,7 +168,9 @@ __device__ __forceinline__ void normal_flux(int law, const float u[10], const Ma
 // Effective Lame parameters at a cell mean (CDM: Eq. "effective-cdb" with the sign
 // of the xi0 term taken from Eq. "cdb-model"; IVM: Eq. "effective-ivm"; nonlinear
 // shear: the secant moduli); q0 holds the ten mode-0 coefficients.
+template <int LAW>
 __device__ __forceinline__ void effective_lame(int law, const float* q0, const MatF& m, float* lam, float* mu) {
+  if constexpr (LAW == 0) law = 0;
   const float r6 = 2.449489742783178f;   // phi_0 = sqrt(6): cell mean = Q_0 sqrt(6)
   if (law == 1) {
     const float f = 1.f - q0[9] * r6;
@@ -336,7 +348,7 @@ struct PredCfg : Dim<N> {
   static_assert(FITS || TSM, "predictor shared memory");
 };
 
-template <int N, bool TSM>
+template <int N, bool TSM, int LAW>
 __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
   using C = PredCfg<N, TSM>;
   constexpr int L = C::L, NQ = C::NQ, NQP = C::NQP, LP = C::LP, QS = C::QS, DS = C::DS, TE = C::TE;
@@ -385,7 +397,7 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
       const int64_t ge = e0 + e;
       const MatF m = *reinterpret_cast<const MatF*>(sGM + e * 40 + 32);
       float lam, mu;
-      effective_lame(a.law, sQ + e * C::QSP, m, &lam, &mu);
+      effective_lame<LAW>(a.law, sQ + e * C::QSP, m, &lam, &mu);
       if (!(mu > 0.f) || !(lam + 2.f * mu > 0.f)) atomicOr(a.status, kStatusNonHyperbolic);
       a.cp[ge] = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * m.rho_inv);
       float* c = sCoef + e * 16;
@@ -435,7 +447,7 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
 #pragma unroll
       for (int n = 0; n < 2; ++n) {
         const int q = 2 * j + n;
-        if (q < NQ) sR[q * TE + e] = e < ne ? law_rate(a.law, acc[n], acc[n][6], m) : 0.f;
+        if (q < NQ) sR[q * TE + e] = e < ne ? law_rate<LAW>(a.law, acc[n], acc[n][6], m) : 0.f;
       }
     }
     __syncthreads();
@@ -553,7 +565,7 @@ __device__ __forceinline__ void load_group(const float* v, float* out) {
   if constexpr (C::G == 5) out[4] = v[4];
 }
 
-template <int N>
+template <int N, int LAW>
 __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS) k_face_flux(StepArgs a) {
   using C = FluxCfg<N>;
   constexpr int L = C::L, NF = C::NF, NFP = C::NFP, NT = C::NT, QS = C::QS, DS = C::DS, AOFF = C::AOFF;
@@ -745,7 +757,7 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
         }
         float lam = 0.f, mu = 0.f, cpb = 0.f, csb = 0.f, k_p = 0.f;
         if (bc != 0) {
-          effective_lame(a.law, mt + 28, mm, &lam, &mu);   // side 0's cell-mean modes
+          effective_lame<LAW>(a.law, mt + 28, mm, &lam, &mu);   // side 0's cell-mean modes
           cpb = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * mm.rho_inv);
           csb = sqrtf(fmaxf(mu, 0.f) * mm.rho_inv);
           k_p = lam + 2.f * mu > 0.f ? cpb / (lam + 2.f * mu) : 0.f;
@@ -786,8 +798,8 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
             boundary_flux(bc, um, n, lam, mu, mm.rho_inv, cpb, csb, k_p, F);
           } else {
             float Fm[9], Fp[9];
-            normal_flux(a.law, um, mm, n, Fm);
-            normal_flux(a.law, up, mp, n, Fp);
+            normal_flux<LAW>(a.law, um, mm, n, Fm);
+            normal_flux<LAW>(a.law, up, mp, n, Fp);
 #pragma unroll
             for (int p = 0; p < 9; ++p) F[p] = 0.5f * (Fm[p] + Fp[p]) + 0.5f * Cs * (um[p] - up[p]);
           }
@@ -1034,7 +1046,7 @@ __device__ __forceinline__ void velocity_rows(const float* sH, float* sA) {
   }
 }
 
-template <int N, bool TSM>
+template <int N, bool TSM, int LAW>
 __global__ void __launch_bounds__(256) k_corrector(StepArgs a) {
   using C = CorrCfg<N, TSM>;
   constexpr int L = C::L, NQ = C::NQ, NQP = C::NQP, NF = C::NF, NT = C::NT, LP = C::LP;
@@ -1182,7 +1194,7 @@ __global__ void __launch_bounds__(256) k_corrector(StepArgs a) {
           }
           const float alpha = fmaf(tz[z], a0[n][7], a0[n][6]);
           float sig[6], r;
-          law_point(a.law, eps, alpha, m, sig, &r);
+          law_point<LAW>(a.law, eps, alpha, m, sig, &r);
 #pragma unroll
           for (int p = 0; p < 6; ++p) sb[p] = fmaf(gz[z], sig[p], sb[p]);
           rb = fmaf(gz[z], r, rb);
@@ -1278,7 +1290,7 @@ struct CorrTcCfg : Dim<N> {
   static_assert(SMEM * 4 <= 227 * 1024, "tensor-core corrector shared memory");
 };
 
-template <int N>
+template <int N, int LAW>
 __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepArgs a) {
   using C = CorrTcCfg<N>;
   constexpr int L = C::L, NQ = C::NQ, NF = C::NF, NT = C::NT, LP = C::LP, QS = C::QS, DS = C::DS;
@@ -1576,7 +1588,7 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
 #pragma unroll
           for (int z = 0; z < NT; ++z) {
             float sig[6], r;
-            law_point(a.law, v + z * 8, v[z * 8 + 6], m, sig, &r);
+            law_point<LAW>(a.law, v + z * 8, v[z * 8 + 6], m, sig, &r);
 #pragma unroll
             for (int p = 0; p < 6; ++p) sb[p] = fmaf(gz[z], sig[p], sb[p]);
             rb = fmaf(gz[z], r, rb);
@@ -1729,45 +1741,61 @@ inline int table_residency_mask() {
   return mask;
 }
 
-template <int N>
-cudaError_t launch_predictor_impl(const StepArgs& a, cudaStream_t s) {
+template <int N, int LAW>
+cudaError_t launch_predictor_law(const StepArgs& a, cudaStream_t s) {
   static bool cfg[2] = {false, false};
   static int blocks[2] = {1, 1};
   const int64_t tiles = (a.E + PredCfg<N, true>::TE - 1) / PredCfg<N, true>::TE;
   if constexpr (PredCfg<N, true>::FITS) {
     if (table_residency_mask() & 1)
-      return launch_persistent<PredCfg<N, true>>(k_predictor<N, true>, tiles, a.grid_pred, a, s, &cfg[1], &blocks[1]);
+      return launch_persistent<PredCfg<N, true>>(k_predictor<N, true, LAW>, tiles, a.grid_pred, a, s, &cfg[1],
+                                                 &blocks[1]);
   }
-  return launch_persistent<PredCfg<N, false>>(k_predictor<N, false>, tiles, 0, a, s, &cfg[0], &blocks[0]);
+  return launch_persistent<PredCfg<N, false>>(k_predictor<N, false, LAW>, tiles, 0, a, s, &cfg[0], &blocks[0]);
 }
 
-template <int N>
-cudaError_t launch_faces_impl(const StepArgs& a, cudaStream_t s) {
+template <int N, int LAW>
+cudaError_t launch_faces_law(const StepArgs& a, cudaStream_t s) {
   static bool cfg = false;
   static int blocks = 1;
   const int64_t tiles = (a.F + FluxCfg<N>::TF - 1) / FluxCfg<N>::TF;
-  return launch_persistent<FluxCfg<N>>(k_face_flux<N>, tiles, a.grid_face > 0 ? a.grid_face : 148, a, s, &cfg,
+  return launch_persistent<FluxCfg<N>>(k_face_flux<N, LAW>, tiles, a.grid_face > 0 ? a.grid_face : 148, a, s, &cfg,
                                        &blocks);
 }
 
-template <int N>
-cudaError_t launch_corrector_impl(const StepArgs& a, cudaStream_t s) {
+template <int N, int LAW>
+cudaError_t launch_corrector_law(const StepArgs& a, cudaStream_t s) {
   static bool cfg[3] = {false, false, false};
   static int blocks[3] = {1, 1, 1};
   if constexpr (tc_volume(N)) {
     if (!(table_residency_mask() & 8)) {
       const int64_t tiles = (a.E + CorrTcCfg<N>::TE - 1) / CorrTcCfg<N>::TE;
       // resident CTAs of an SM share its 512 tensor-memory columns
-      return launch_persistent<CorrTcCfg<N>>(k_corrector_tc<N>, tiles, a.grid_corr > 0 ? a.grid_corr : 148, a, s,
-                                             &cfg[2], &blocks[2], 512 / CorrTcCfg<N>::TMEM_COLS);
+      return launch_persistent<CorrTcCfg<N>>(k_corrector_tc<N, LAW>, tiles, a.grid_corr > 0 ? a.grid_corr : 148, a,
+                                             s, &cfg[2], &blocks[2], 512 / CorrTcCfg<N>::TMEM_COLS);
     }
   }
   const int64_t tiles = (a.E + CorrCfg<N, true>::TE - 1) / CorrCfg<N, true>::TE;
   if constexpr (CorrCfg<N, true>::FITS) {
     if (table_residency_mask() & 4)
-      return launch_persistent<CorrCfg<N, true>>(k_corrector<N, true>, tiles, a.grid_corr, a, s, &cfg[1], &blocks[1]);
+      return launch_persistent<CorrCfg<N, true>>(k_corrector<N, true, LAW>, tiles, a.grid_corr, a, s, &cfg[1],
+                                                 &blocks[1]);
   }
-  return launch_persistent<CorrCfg<N, false>>(k_corrector<N, false>, tiles, 0, a, s, &cfg[0], &blocks[0]);
+  return launch_persistent<CorrCfg<N, false>>(k_corrector<N, false, LAW>, tiles, 0, a, s, &cfg[0], &blocks[0]);
+}
+
+// The CDM runs on kernels compiled for it alone; the other laws on the dispatching ones.
+template <int N>
+cudaError_t launch_predictor_impl(const StepArgs& a, cudaStream_t s) {
+  return a.law == 0 ? launch_predictor_law<N, 0>(a, s) : launch_predictor_law<N, -1>(a, s);
+}
+template <int N>
+cudaError_t launch_faces_impl(const StepArgs& a, cudaStream_t s) {
+  return a.law == 0 ? launch_faces_law<N, 0>(a, s) : launch_faces_law<N, -1>(a, s);
+}
+template <int N>
+cudaError_t launch_corrector_impl(const StepArgs& a, cudaStream_t s) {
+  return a.law == 0 ? launch_corrector_law<N, 0>(a, s) : launch_corrector_law<N, -1>(a, s);
 }
 
 }  // namespace dg
