@@ -953,6 +953,7 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
   StepArgs a{};
   a.E = ctx->EV;
   a.F = ctx->F;
+  a.has_boundary = ctx->F > ctx->F_interior;
   a.d = ctx->d;
   a.cp = ctx->cp;
   a.ff = ctx->ff;
@@ -1037,6 +1038,7 @@ bool noalloc_view(const dg_ctx* ctx, NoAllocView* v) {
   v->faces = ctx->faces;
   v->elem_face = ctx->elem_face;
   v->F = ctx->F;
+  v->has_boundary = ctx->F > ctx->F_interior;
   v->tables = ctx->tables;
   v->dt_cfl = ctx->dt_cfl;
   v->has_material = ctx->has_material;

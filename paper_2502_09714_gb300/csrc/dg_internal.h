@@ -145,6 +145,7 @@ struct StepArgs {
   int grid_pred, grid_face, grid_corr;   // persistent grid sizes (0: one CTA per tile)
   int law;                // pointwise law: 0 = CDM (Eq. "cdb-model"), 1 = IVM (Eq. "ivm-model"),
                           // 2 = nonlinear shear (Eq. "1d Riemann eqs")
+  int has_boundary;       // nonzero when the mesh has absorbing or free-surface faces
 };
 
 // Kernel launchers, one per compiled degree (dg_step_n<N>.cu), and their
@@ -192,6 +193,7 @@ struct NoAllocView {
   const int4* faces;
   const int* elem_face;
   int64_t F;
+  bool has_boundary;
   const float* tables;
   double dt_cfl;
   bool has_material;

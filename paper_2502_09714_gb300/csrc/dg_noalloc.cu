@@ -83,6 +83,7 @@ extern "C" dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_ou
   StepArgs a{};
   a.E = v.E;
   a.F = v.F;
+  a.has_boundary = v.has_boundary;
   a.ff = ff;
   a.faces = v.faces;
   a.elem_face = v.elem_face;

@@ -565,7 +565,8 @@ __device__ __forceinline__ void load_group(const float* v, float* out) {
   if constexpr (C::G == 5) out[4] = v[4];
 }
 
-template <int N, int LAW>
+// BND: the mesh has boundary faces (false compiles their flux out).
+template <int N, int LAW, bool BND>
 __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS) k_face_flux(StepArgs a) {
   using C = FluxCfg<N>;
   constexpr int L = C::L, NF = C::NF, NFP = C::NFP, NT = C::NT, QS = C::QS, DS = C::DS, AOFF = C::AOFF;
@@ -664,7 +665,7 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
         const int g = r / 3, c = r - 3 * g;
         const int fc = s2 >> 1, side = s2 & 1;
         const float* mt = sMeta + fc * META;
-        if (fc < nf && !(side && mt[6] != 0.f)) {
+        if (fc < nf && !(side && BND && mt[6] != 0.f)) {
           const int lf = static_cast<int>(side ? mt[24] : mt[7]);
           const float* V = sV + lf * L * C::VROW + C::goff(g);
           const float* R = sRaw + s2 * RAW;
@@ -745,7 +746,7 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
       if (fc < nf) {
         const float* mt = sMeta + fc * META;
         const float n[3] = {mt[0], mt[1], mt[2]};
-        const int bc = static_cast<int>(mt[6]);
+        const int bc = BND ? static_cast<int>(mt[6]) : 0;
         MatF mm, mp;
         {
           const float* m0 = mt + 8;
@@ -1756,11 +1757,13 @@ cudaError_t launch_predictor_law(const StepArgs& a, cudaStream_t s) {
 
 template <int N, int LAW>
 cudaError_t launch_faces_law(const StepArgs& a, cudaStream_t s) {
-  static bool cfg = false;
-  static int blocks = 1;
+  static bool cfg[2] = {false, false};
+  static int blocks[2] = {1, 1};
   const int64_t tiles = (a.F + FluxCfg<N>::TF - 1) / FluxCfg<N>::TF;
-  return launch_persistent<FluxCfg<N>>(k_face_flux<N, LAW>, tiles, a.grid_face > 0 ? a.grid_face : 148, a, s, &cfg,
-                                       &blocks);
+  const int grid = a.grid_face > 0 ? a.grid_face : 148;
+  if (a.has_boundary)
+    return launch_persistent<FluxCfg<N>>(k_face_flux<N, LAW, true>, tiles, grid, a, s, &cfg[1], &blocks[1]);
+  return launch_persistent<FluxCfg<N>>(k_face_flux<N, LAW, false>, tiles, grid, a, s, &cfg[0], &blocks[0]);
 }
 
 template <int N, int LAW>
