@@ -142,3 +142,58 @@ class ShearRiemann:
                 e, w = self.eR, self.vR
             eps[k], v[k] = e, w
         return eps, v
+
+
+class ShearSimpleWave:
+    """Exact right-going simple wave of the same plane shear system (derived here,
+    not printed in the paper), for convergence on smooth nonlinear solutions.
+
+    The states lie on the integral curve of the 2-family through (eps_bar, v_bar),
+    v = v_bar - G(eps_bar, eps), and eps is constant along the straight
+    characteristics dx/dt = c(eps): eps(x, t) = eps0(xi) with x = xi + c(eps0(xi)) t.
+    Initial strain eps0(x) = eps_bar + amp sin(2 pi x / length), periodic in x;
+    exact until the characteristics cross (t < t_break)."""
+
+    def __init__(self, eps_bar=0.01, amp=0.002, v_bar=0.0, length=1.0, rho=1.0, mu=1.0, beta=10.0):
+        self.r = ShearRiemann((eps_bar, 0.0), (eps_bar, 0.0), rho=rho, mu=mu, beta=beta)
+        self.eps_bar, self.amp, self.v_bar, self.length = float(eps_bar), float(amp), float(v_bar), float(length)
+        if eps_bar - amp < 0 or not self.r.dsigma(eps_bar + amp) > 0:
+            raise ValueError("the wave must stay in 0 <= eps < 1 / (2 beta)")
+        k = 2 * math.pi / self.length
+        xi = np.linspace(0.0, self.length, 4001)
+        e = self.eps0(xi)
+        dc = np.array([self.dc(x) for x in e]) * self.amp * k * np.cos(k * xi)
+        self.t_break = float("inf") if np.min(dc) >= 0 else float(-1.0 / np.min(dc))
+
+    def eps0(self, x):
+        return self.eps_bar + self.amp * np.sin(2 * math.pi * np.asarray(x) / self.length)
+
+    def dc(self, e):
+        """d c / d eps = sigma''(eps) / (4 rho c) with sigma'' = -4 mu beta (eps > 0)."""
+        return -4.0 * self.r.mu * self.r.beta / (4.0 * self.r.rho * self.r.c(e)) if self.r.beta else 0.0
+
+    def v_of(self, e):
+        return self.v_bar - self.r.G(self.eps_bar, e)
+
+    def sample(self, x, t):
+        """(eps, v) at the points x and time 0 <= t < t_break: the foot xi of the
+        characteristic through (x, t) by Newton on xi + c(eps0(xi)) t = x (mod length)."""
+        if not t < self.t_break:
+            raise ValueError("the characteristics have crossed: no smooth solution")
+        x = np.asarray(x, dtype=np.float64)
+        k = 2 * math.pi / self.length
+        c0 = self.r.c(self.eps_bar)
+        xi = x - c0 * t
+        for _ in range(60):
+            e = self.eps0(xi)
+            c = np.sqrt(np.maximum(2.0 * self.r.mu * (1.0 - 2.0 * self.r.beta * np.abs(e)), 0.0) / (2.0 * self.r.rho))
+            dcde = np.where(c > 0, -self.r.mu * self.r.beta / (self.r.rho * np.maximum(c, 1e-300)), 0.0)
+            f = xi + c * t - x
+            df = 1.0 + dcde * self.amp * k * np.cos(k * xi) * t
+            step = f / df
+            xi = xi - step
+            if np.max(np.abs(step)) < 1e-15 * self.length:
+                break
+        eps = self.eps0(xi)
+        v = np.array([self.v_of(ev) for ev in np.ravel(eps)]).reshape(eps.shape)
+        return eps, v

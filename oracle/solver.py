@@ -79,9 +79,11 @@ def stf_integral(src, t):
 
 class Oracle:
     def __init__(self, elem_xyz, elem_vid, order, material, face_bc=None, cfl=0.5, face_rows=None,
-                 law="cdm"):
+                 law="cdm", picard_iterations=0):
         """face_rows: elements whose face tables are built (default all); step()
-        can only produce new states for those elements."""
+        can only produce new states for those elements.  picard_iterations > 0
+        refines the CK predictor by that many discrete Picard iterations
+        (Sec. 6.1's proposed extension, reading R20); 0 keeps the CK predictor."""
         xyz = np.asarray(elem_xyz, dtype=np.float64)
         vid = np.asarray(elem_vid, dtype=np.int64)
         # Reading R15: each element's reference map lists its vertices by
@@ -102,6 +104,8 @@ class Oracle:
         if law not in ("cdm", "ivm", "nlshear"):
             raise ValueError(f"unknown rheology {law}")
         self.law = law
+        self.picard_iterations = int(picard_iterations)
+        self.flag_nonhyperbolic = False
         self.cfl = cfl
         self._reference()
         self._geometry()
@@ -275,6 +279,43 @@ class Oracle:
             D.append(Di)
         return np.stack(D, axis=0), cp, (lam, mu)
 
+    def picard(self, D, rows, dt, iterations):
+        """Discrete Picard iteration on the element-local evolution (reading R20):
+        with q(t) = sum_i t^i/i! D^i the predictor's polynomial, one iteration
+        evaluates R(q) = -div F(q) + S(q) at the Gauss time nodes t_z of the step,
+          R_kp(t_z) = -sum_e sum_l Kt[e,k,l] Fhat*_{l,e,p}(t_z) + Shat_kp(t_z),
+        Fhat* the volume-rule projection of Theta^{-1}_{ed} F^d(q_h) and Shat that
+        of the source (the damage rate), fits the interpolating polynomial
+        sum_j t^j/j! R^j through the N + 1 values, and sets D^{j+1} = R^j.  Each
+        D^o is then truncated as the CK's is (degree N - o for the wave fields,
+        first order for alpha), so the output keeps the predictor's form.  For a
+        linear flux the CK coefficients are a fixed point."""
+        N, L = self.N, self.L
+        mat = self.mat[rows]
+        Jinv = self.Jinv[rows]
+        tz = self.qt_x * dt
+        V = np.array([[t ** j / math.factorial(j) for j in range(N + 1)] for t in tz])   # [z, j]
+        Vinv = np.linalg.inv(V)
+        deg = np.array([sum(m) for m in mode_list(N)])
+        D = np.array(D, copy=True)
+        for _ in range(iterations):
+            U = np.einsum("zi,inlp->nzlp", V, D, optimize=True)
+            u = np.einsum("ql,nzlp->nzqp", self.Vv, U, optimize=True)
+            F = flux(u, mat[:, None, None, :], self.law)                       # [n,z,q,3(d),10]
+            Fs = np.einsum("ned,nzqdp->nzqep", Jinv, F, optimize=True)
+            Fh = np.einsum("q,ql,nzqep->nzlep", self.qv_w, self.Vv, Fs, optimize=True)
+            R = -np.einsum("ekl,nzlep->nzkp", self.Kt, Fh, optimize=True)
+            r = damage_rate(u, mat[:, None, None, :], self.law)                # [n,z,q]
+            R[..., 9] += np.einsum("q,ql,nzq->nzl", self.qv_w, self.Vv, r, optimize=True)
+            Rj = np.einsum("jz,nzkp->jnkp", Vinv, R, optimize=True)
+            for o in range(1, N + 1):
+                Do = Rj[o - 1].copy()
+                Do[:, deg > N - o, :9] = 0.0
+                if o > 1:
+                    Do[..., 9] = 0.0
+                D[o] = Do
+        return D
+
     def step(self, Q, dt, t=0.0, rows=None):
         """Advance Q[E,L,10] by dt; returns the new state (all elements, or only
         `rows` when given, as an array [len(rows),L,10])."""
@@ -285,6 +326,8 @@ class Oracle:
         pos = -np.ones(self.E, dtype=np.int64)
         pos[need] = np.arange(need.size)
         D, cp, (lam_eff, mu_eff) = self.predictor(Q, need)
+        if self.picard_iterations > 0:
+            D = self.picard(D, need, dt, self.picard_iterations)
         tz = self.qt_x * dt
         gz = self.qt_w * dt
         N = self.N
