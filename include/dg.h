@@ -123,6 +123,21 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out);
 enum { DG_LAW_CDM = 0, DG_LAW_IVM = 1, DG_LAW_NLSHEAR = 2 };
 dg_status dg_set_rheology(dg_ctx* ctx, int law);
 
+/* Predictor of the step: DG_PREDICTOR_CK (default; the linearised Cauchy-Kovalevskaya
+ * procedure of Appendix A.1, Eqs. "CKIter-ref-matrix" and "CKIter-ref-source") or
+ * DG_PREDICTOR_PICARD, the discrete Picard iteration Sec. 6.1 proposes in its place:
+ * `iterations` (1..16) sweeps that start from the CK coefficients, evaluate the
+ * element-local rate -div F(q) + S(q) of the predictor's polynomial at the N + 1
+ * time nodes of the step (flux and damage rate projected by the volume rule) and
+ * replace D^{j+1} by the j-th Taylor coefficient of the polynomial through those
+ * values; each D^o keeps the CK's form (degree N - o for the wave fields, first
+ * order for alpha).  It restores order N + 1 on smooth nonlinear solutions, at
+ * several times the cost of a step.  Degrees 1..4 (DG_E_ORDER for 5); DG_E_ARG for
+ * another kind or iteration count.  The iterations run in the same launch sequence
+ * (dg_step and dg_step_noalloc); dg_profile_read counts them under the predictor. */
+enum { DG_PREDICTOR_CK = 0, DG_PREDICTOR_PICARD = 1 };
+dg_status dg_set_predictor(dg_ctx* ctx, int kind, int iterations);
+
 /* Per-element material [n_elem][6] = (rho, lambda0, mu0, gamma_r, xi0, C_d):
  * density, Lame parameters of the intact rock, damage modulus gamma_r [Pa],
  * damage onset xi0 (Eq. "cdb-model") and damage-rate coefficient C_d [1/(Pa s)].

@@ -41,6 +41,7 @@ struct FaceKeyHash {
 struct dg_ctx {
   int N = 0, L = 0, M = 1;
   int law = 0;                       // 0 = CDM, 1 = IVM, 2 = nonlinear shear
+  int picard_iters = 0;              // Picard iterations after the CK predictor (0: CK alone)
   int64_t E = 0;                     // mesh elements
   int64_t EV = 0;                    // element copies on the device: E x members, member fastest
   double cfl = 0.5;
@@ -247,6 +248,34 @@ std::vector<double> build_tables(int N) {
   for (int z = 0; z < NT; ++z) {
     t[T.tz + z] = tr.x[z];
     t[T.gz + z] = tr.w[z];
+  }
+  // Tfit = V^{-1}, V[z][j] = tz_z^j / j!, by Gauss-Jordan elimination with partial pivoting
+  {
+    std::vector<double> A(NT * 2 * NT, 0.0);
+    for (int z = 0; z < NT; ++z) {
+      double p = 1.0, f = 1.0;
+      for (int j = 0; j < NT; ++j) {
+        A[z * 2 * NT + j] = p / f;
+        p *= tr.x[z];
+        f *= (j + 1);
+      }
+      A[z * 2 * NT + NT + z] = 1.0;
+    }
+    for (int c = 0; c < NT; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < NT; ++r)
+        if (std::fabs(A[r * 2 * NT + c]) > std::fabs(A[piv * 2 * NT + c])) piv = r;
+      for (int k = 0; k < 2 * NT; ++k) std::swap(A[c * 2 * NT + k], A[piv * 2 * NT + k]);
+      const double d = A[c * 2 * NT + c];
+      for (int k = 0; k < 2 * NT; ++k) A[c * 2 * NT + k] /= d;
+      for (int r = 0; r < NT; ++r) {
+        if (r == c) continue;
+        const double m = A[r * 2 * NT + c];
+        for (int k = 0; k < 2 * NT; ++k) A[r * 2 * NT + k] -= m * A[c * 2 * NT + k];
+      }
+    }
+    for (int j = 0; j < NT; ++j)
+      for (int z = 0; z < NT; ++z) t[T.Tfit + j * NT + z] = A[j * 2 * NT + NT + z];
   }
   return t;
 }
@@ -658,6 +687,19 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
   return DG_OK;
 }
 
+dg_status dg_set_predictor(dg_ctx* ctx, int kind, int iterations) {
+  if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
+  if (kind == DG_PREDICTOR_CK) {
+    ctx->picard_iters = 0;
+    return DG_OK;
+  }
+  if (kind != DG_PREDICTOR_PICARD || iterations < 1 || iterations > 16)
+    return fail(ctx, DG_E_ARG, "unknown predictor or iteration count");
+  if (ctx->N > 4) return fail(ctx, DG_E_ORDER, "the Picard predictor supports degrees 1..4");
+  ctx->picard_iters = iterations;
+  return DG_OK;
+}
+
 dg_status dg_set_rheology(dg_ctx* ctx, int law) {
   if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
   if (law != DG_LAW_CDM && law != DG_LAW_IVM && law != DG_LAW_NLSHEAR) return fail(ctx, DG_E_ARG, "unknown rheology");
@@ -963,6 +1005,7 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
   a.grid_face = ctx->grid_face;
   a.grid_corr = ctx->grid_corr;
   a.law = ctx->law;
+  a.picard_iters = ctx->picard_iters;
   a.geom = ctx->geom;
   a.mat = ctx->matf;
   a.nbr = ctx->nbr;
@@ -975,6 +1018,10 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
     a.q_in = ctx->q[ctx->cur];
     a.q_out = ctx->q[1 - ctx->cur];
     DG_CUDA(ctx, launch_predictor(ctx->N, a, ctx->stream));
+    if (a.picard_iters > 0) {
+      DG_CUDA(ctx, launch_picard(ctx->N, a, ctx->stream));
+      ++launches;
+    }
     DG_CUDA(ctx, mark(0));
     DG_CUDA(ctx, launch_faces(ctx->N, a, ctx->stream));
     DG_CUDA(ctx, mark(4));
@@ -1043,6 +1090,7 @@ bool noalloc_view(const dg_ctx* ctx, NoAllocView* v) {
   v->dt_cfl = ctx->dt_cfl;
   v->has_material = ctx->has_material;
   v->law = ctx->law;
+  v->picard_iters = ctx->picard_iters;
   return true;
 }
 
@@ -1077,6 +1125,17 @@ cudaError_t launch_corrector(int N, const StepArgs& a, cudaStream_t s) {
     case 3: return launch_corrector_t<3>(a, s);
     case 4: return launch_corrector_t<4>(a, s);
     case 5: return launch_corrector_t<5>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_picard(int N, const StepArgs& a, cudaStream_t s) {
+  switch (N) {
+    case 1: return launch_picard_t<1>(a, s);
+    case 2: return launch_picard_t<2>(a, s);
+    case 3: return launch_picard_t<3>(a, s);
+    case 4: return launch_picard_t<4>(a, s);
+    case 5: return launch_picard_t<5>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -70,6 +70,8 @@ struct TableLayout {
   int PrjS;   // [LP]        sum_q w_q phi_l(x_q), summed in double
   int tz;     // [NT]        time nodes in [0,1]
   int gz;     // [NT]        time weights (sum 1)
+  int Tfit;   // [NT][NT]    Tfit[j][z]: the inverse of tz_z^j / j!, the Taylor coefficients at
+              //             t = 0 of the polynomial through values at the time nodes
   int total;
 };
 
@@ -92,6 +94,7 @@ __host__ __device__ constexpr TableLayout table_layout(int N) {
   t.PrjS = o; o = round4(o + (tc_volume(N) ? LP : 0));
   t.tz = o;  o += NT;
   t.gz = o;  o += NT;
+  t.Tfit = o; o += NT * NT;
   t.total = round4(o);
   return t;
 }
@@ -146,6 +149,7 @@ struct StepArgs {
   int law;                // pointwise law: 0 = CDM (Eq. "cdb-model"), 1 = IVM (Eq. "ivm-model"),
                           // 2 = nonlinear shear (Eq. "1d Riemann eqs")
   int has_boundary;       // nonzero when the mesh has absorbing or free-surface faces
+  int picard_iters;       // Picard iterations after the CK predictor (0: the CK alone)
 };
 
 // Kernel launchers, one per compiled degree (dg_step_n<N>.cu), and their
@@ -153,9 +157,11 @@ struct StepArgs {
 template <int N> cudaError_t launch_predictor_t(const StepArgs& a, cudaStream_t s);
 template <int N> cudaError_t launch_faces_t(const StepArgs& a, cudaStream_t s);
 template <int N> cudaError_t launch_corrector_t(const StepArgs& a, cudaStream_t s);
+template <int N> cudaError_t launch_picard_t(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_predictor(int N, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_faces(int N, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_corrector(int N, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_picard(int N, const StepArgs& a, cudaStream_t s);
 
 // Auxiliary kernels (dg_aux.cu).
 // State conversion between the ABI layout [M][E][10][L] (FP64 or FP32) and the
@@ -198,6 +204,7 @@ struct NoAllocView {
   double dt_cfl;
   bool has_material;
   int law;
+  int picard_iters;
 };
 
 }  // namespace dg

@@ -98,10 +98,12 @@ extern "C" dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_ou
   a.dt = static_cast<float>(dt);
   a.status = status;
   a.law = v.law;
+  a.picard_iters = v.picard_iters;
   // the array keeps the previous call's contents: the status word must start at zero
   if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned), v.stream)) != cudaSuccess ||
       (e = launch_state_in(v.N, v.E, 1, q_in, 0, qa, v.stream)) != cudaSuccess ||
       (e = launch_predictor(v.N, a, v.stream)) != cudaSuccess ||
+      (a.picard_iters > 0 && (e = launch_picard(v.N, a, v.stream)) != cudaSuccess) ||
       (e = launch_faces(v.N, a, v.stream)) != cudaSuccess ||
       (e = launch_corrector(v.N, a, v.stream)) != cudaSuccess ||
       (e = launch_state_out(v.N, v.E, 1, qb, q_out, 0, v.stream)) != cudaSuccess)

@@ -517,6 +517,224 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
 }
 
 // ===========================================================================
+// Picard predictor (the extension Sec. 6.1 proposes in place of the linearised
+// CK): starting from the CK output in a.d, each iteration evaluates the
+// element-local rate R(q) = -div F(q) + S(q) of the predictor's polynomial
+// q(t) = sum_o t^o/o! D^o at the N + 1 time nodes of the step, with the volume-
+// rule projection of Theta^{-1} F(q) and of the damage rate and the divergence
+// through the Kt tables, and replaces D^{j+1} by the j-th Taylor coefficient of
+// the polynomial through those values.  Each D^o keeps the CK's form (degree
+// N - o for the wave fields, D^1 only for alpha).  Persistent CTAs of 512 threads,
+// TE elements per tile, all iterations in shared memory; everything SIMT.
+// ===========================================================================
+template <int N>
+struct PicardCfg : Dim<N> {
+  using D = Dim<N>;
+  static constexpr int TE = 4;
+  static constexpr int THREADS = 512;
+  static constexpr int CU = TE * 12;                       // node-value columns: (element, 10 fields + 2 pad)
+  static constexpr int CF = TE * 28;                       // flux columns: (element, e' 0..2 x 9 fields, rate)
+  static constexpr int FST = CF + 4;                       // row stride of the nodal fluxes
+  static constexpr int QSP = D::QS % 32 == 0 ? D::QS + 4 : D::QS;
+  static constexpr int VQ = round4(D::NQ);                 // volume nodes padded to a multiple of 4
+  static constexpr int oVvT = 0;                           // [L][VQ] phi_l(x_q), zero beyond NQ
+  static constexpr int oVw = round4(oVvT + D::L * VQ);     // [NQ][LP]
+  static constexpr int oKtA = round4(oVw + D::NQ * D::LP); // [3][L][LP]
+  static constexpr int oQ = round4(oKtA + 3 * D::L * D::LP);   // [TE][QSP] state at t_n
+  static constexpr int oD = oQ + TE * QSP;                 // [TE][DS] Taylor coefficients being refined
+  static constexpr int oGeo = round4(oD + TE * D::DS);     // [TE][40] GeomF, MatF as copied
+  static constexpr int oUt = oGeo + TE * 40;               // [L][CU] modal values at one time node
+  static constexpr int oU = round4(oUt + D::L * CU);       // [VQ][CU] node values; later [LP][CF] projections
+  static constexpr int U_SIZE = (VQ * CU > D::LP * CF ? VQ * CU : D::LP * CF);
+  static constexpr int oF = round4(oU + U_SIZE);           // [VQ][FST] nodal reference fluxes and rate
+  static constexpr int oDn = oF + VQ * FST;                // [TE][DS] new coefficients (same layout as oD)
+  static constexpr int oTc = oDn + TE * D::DS;             // [NT][N+1] t_z^o / o!, then [NT][NT] the fit
+  static constexpr int SMEM = round4(oTc + D::NT * (N + 1) + D::NT * D::NT);
+  static constexpr bool FITS = SMEM * 4 <= 227 * 1024;    // N = 5 does not fit
+  static_assert(D::LP % 4 == 0 && CU % 4 == 0 && CF % 4 == 0 && FST % 4 == 0, "block GEMM shapes");
+};
+
+template <int N, int LAW>
+__global__ void __launch_bounds__(512, 1) k_picard(StepArgs a) {
+  using C = PicardCfg<N>;
+  constexpr int L = C::L, NQ = C::NQ, NQP = C::NQP, LP = C::LP, NT = C::NT, QS = C::QS, DS = C::DS;
+  constexpr int AOFF = C::AOFF, TE = C::TE, CU = C::CU, CF = C::CF, FST = C::FST, QSP = C::QSP, VQ = C::VQ;
+  constexpr int L1 = n_modes(N - 1);
+  constexpr TableLayout T = table_layout(N);
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  float* sVvT = sm + C::oVvT;
+  float* sVw = sm + C::oVw;
+  float* sKtA = sm + C::oKtA;
+  float* sQ = sm + C::oQ;
+  float* sD = sm + C::oD;
+  float* sGM = sm + C::oGeo;
+  float* sUt = sm + C::oUt;
+  float* sU = sm + C::oU;
+  float* sFh = sm + C::oU;                                 // the projections reuse the node-value rows
+  float* sF = sm + C::oF;
+  float* sDn = sm + C::oDn;
+  float* sCz = sm + C::oTc;                                // [NT][N+1]
+  float* sFit = sCz + NT * (N + 1);                        // [NT][NT], sFit[j][z]
+  const float* tb = a.tables;
+  const float dt = a.dt;
+  for (int w = threadIdx.x; w < L * VQ; w += blockDim.x) {
+    const int l = w / VQ, q = w - l * VQ;
+    sVvT[w] = q < NQ ? __ldg(tb + T.VvT + l * NQP + q) : 0.f;
+  }
+  copy_to_smem(sVw, tb + T.Vw, NQ * LP);
+  copy_to_smem(sKtA, tb + T.KtA, 3 * L * LP);
+  // Taylor weights t_z^o / o! and the fit Tfit[j][z] / dt^j
+  if (threadIdx.x < NT) {
+    const int z = threadIdx.x;
+    const float tz = __ldg(tb + T.tz + z) * dt;
+    float c = 1.f;
+    for (int o = 0; o <= N; ++o) {
+      sCz[z * (N + 1) + o] = c;
+      c *= tz / static_cast<float>(o + 1);
+    }
+    float sc = 1.f;
+    for (int j = 0; j < NT; ++j) {
+      for (int zz = 0; zz < NT; ++zz) {
+        if (zz == z) sFit[j * NT + zz] = __ldg(tb + T.Tfit + j * NT + zz) * sc;
+      }
+      sc /= dt;
+    }
+  }
+
+  const int64_t ntiles = (a.E + TE - 1) / TE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * TE;
+    const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
+    __syncthreads();
+    for (int w = threadIdx.x; w < TE * QS / 4; w += blockDim.x) {
+      const int e = w / (QS / 4), c = w - e * (QS / 4);
+      if (e < ne) tc::cp_async16(sQ + e * QSP + 4 * c, a.q_in + (e0 + e) * QS + 4 * c);
+      else *reinterpret_cast<float4*>(sQ + e * QSP + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int w = threadIdx.x; w < TE * DS / 4; w += blockDim.x) {
+      const int e = w / (DS / 4), c = w - e * (DS / 4);
+      if (e < ne) tc::cp_async16(sD + e * DS + 4 * c, a.d + (e0 + e) * DS + 4 * c);
+      else *reinterpret_cast<float4*>(sD + e * DS + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int w = threadIdx.x; w < ne * 10; w += blockDim.x) {
+      const int e = w / 10, k = w - 10 * e;
+      if (k < 8) tc::cp_async16(sGM + e * 40 + 4 * k, reinterpret_cast<const float*>(a.geom + e0 + e) + 4 * k);
+      else tc::cp_async16(sGM + e * 40 + 32 + 4 * (k - 8), reinterpret_cast<const float*>(a.mat + e0 + e) + 4 * (k - 8));
+    }
+    tc::cp_async_wait_all();
+    __syncthreads();
+
+#pragma unroll 1
+    for (int iter = 0; iter < a.picard_iters; ++iter) {
+      for (int w = threadIdx.x; w < TE * DS; w += blockDim.x) sDn[w] = 0.f;
+#pragma unroll 1
+      for (int z = 0; z < NT; ++z) {
+        // modal values of q(t_z): (element, field) columns; alpha to first order
+        for (int w = threadIdx.x; w < L * TE; w += blockDim.x) {
+          const int l = w / TE, e = w - l * TE;
+          const float* q = sQ + e * QSP + l * 10;
+          const float* de = sD + e * DS;
+          float u[12];
+#pragma unroll
+          for (int c = 0; c < 10; ++c) u[c] = q[c];
+          u[10] = u[11] = 0.f;
+#pragma unroll
+          for (int o = 1; o <= N; ++o) {
+            if (l < n_modes(N - o)) {
+#pragma unroll
+              for (int c = 0; c < 9; ++c) u[c] = fmaf(sCz[z * (N + 1) + o], de[d_offset(N, o) + l * 9 + c], u[c]);
+            }
+          }
+          u[9] = fmaf(sCz[z * (N + 1) + 1], de[AOFF + l], u[9]);
+          float4* dst = reinterpret_cast<float4*>(sUt + l * CU + e * 12);
+          dst[0] = make_float4(u[0], u[1], u[2], u[3]);
+          dst[1] = make_float4(u[4], u[5], u[6], u[7]);
+          dst[2] = make_float4(u[8], u[9], 0.f, 0.f);
+        }
+        __syncthreads();
+        // node values U[q][col] = sum_l phi_l(x_q) Ut[l][col]
+        block_gemm<1>(sVvT, VQ, sUt, CU, VQ, CU, L, nullptr, [&](int q, int col, float v) { sU[q * CU + col] = v; });
+        __syncthreads();
+        // reference fluxes Theta^{-1}_{e'd} F^d and the damage rate at every node
+        for (int w = threadIdx.x; w < NQ * TE; w += blockDim.x) {
+          const int q = w / TE, e = w - q * TE;
+          float* f = sF + q * FST + e * 28;
+          if (e >= ne) {
+#pragma unroll
+            for (int p = 0; p < 28; ++p) f[p] = 0.f;
+            continue;
+          }
+          const float* u = sU + q * CU + e * 12;
+          const float* gm = sGM + e * 40;
+          const MatF m = *reinterpret_cast<const MatF*>(gm + 32);
+          float sig[6], r;
+          law_point<LAW>(a.law, u, u[9], m, sig, &r);
+          const float S[3][3] = {{sig[0], sig[3], sig[5]}, {sig[3], sig[1], sig[4]}, {sig[5], sig[4], sig[2]}};
+          const float v[3] = {u[6], u[7], u[8]};
+#pragma unroll
+          for (int ep = 0; ep < 3; ++ep) {
+            const float th[3] = {gm[ep * 3 + 0], gm[ep * 3 + 1], gm[ep * 3 + 2]};   // Theta^{-1}[e'][d]
+            float* fe = f + ep * 9;
+            // strain rows: -(v_i th_j + v_j th_i) / 2 ; velocity rows: -(sigma th)_i / rho
+            fe[0] = -v[0] * th[0];
+            fe[1] = -v[1] * th[1];
+            fe[2] = -v[2] * th[2];
+            fe[3] = -0.5f * (v[0] * th[1] + v[1] * th[0]);
+            fe[4] = -0.5f * (v[1] * th[2] + v[2] * th[1]);
+            fe[5] = -0.5f * (v[2] * th[0] + v[0] * th[2]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) fe[6 + i] = -m.rho_inv * (S[i][0] * th[0] + S[i][1] * th[1] + S[i][2] * th[2]);
+          }
+          f[27] = r;
+        }
+        __syncthreads();
+        // projections by the volume rule: Fh[l][col] = sum_q w_q phi_l(x_q) F[q][col]
+        block_gemm<1>(sVw, LP, sF, FST, LP, CF, NQ, nullptr, [&](int l, int col, float v) { sFh[l * CF + col] = v; });
+        __syncthreads();
+        // R(t_z) = -sum_e' Kt^{e'} Fh_{e'} + Shat, folded into the Taylor fit of every order
+        for (int w = threadIdx.x; w < L * TE; w += blockDim.x) {
+          const int k = w / TE, e = w - k * TE;
+          float* dn = sDn + e * DS;
+          if (k < L1) {
+            float acc[9];
+#pragma unroll
+            for (int p = 0; p < 9; ++p) acc[p] = 0.f;
+#pragma unroll 5
+            for (int l = 0; l < L; ++l) {
+              const float* fh = sFh + l * CF + e * 28;
+#pragma unroll
+              for (int ep = 0; ep < 3; ++ep) {
+                const float kt = sKtA[(ep * L + l) * LP + k];
+#pragma unroll
+                for (int p = 0; p < 9; ++p) acc[p] = fmaf(kt, fh[ep * 9 + p], acc[p]);
+              }
+            }
+#pragma unroll
+            for (int o = 1; o <= N; ++o) {
+              if (k < n_modes(N - o)) {
+#pragma unroll
+                for (int p = 0; p < 9; ++p) dn[d_offset(N, o) + k * 9 + p] -= sFit[(o - 1) * NT + z] * acc[p];
+              }
+            }
+          }
+          dn[AOFF + k] += sFit[z] * sFh[k * CF + e * 28 + 27];
+        }
+        __syncthreads();
+      }
+      for (int w = threadIdx.x; w < TE * DS; w += blockDim.x) sD[w] = sDn[w];
+      __syncthreads();
+    }
+    bool bad = false;
+    for (int w = threadIdx.x; w < ne * DS; w += blockDim.x) {
+      bad |= !isfinite(sD[w]);
+      a.d[e0 * DS + w] = sD[w];
+    }
+    if (bad) atomicOr(a.status, kStatusNonFinite);
+  }
+}
+
+// ===========================================================================
 // Faces: Rusanov flux at the space-time nodes of each interior face, once per
 // face; boundary faces (side 1 absent, tag in the fourth entry) take the
 // absorbing or free-surface flux.  Persistent CTAs of 256 threads, two per SM.  Per tile of
@@ -1787,6 +2005,14 @@ cudaError_t launch_corrector_law(const StepArgs& a, cudaStream_t s) {
   return launch_persistent<CorrCfg<N, false>>(k_corrector<N, false, LAW>, tiles, 0, a, s, &cfg[0], &blocks[0]);
 }
 
+template <int N, int LAW>
+cudaError_t launch_picard_law(const StepArgs& a, cudaStream_t s) {
+  static bool cfg = false;
+  static int blocks = 1;
+  const int64_t tiles = (a.E + PicardCfg<N>::TE - 1) / PicardCfg<N>::TE;
+  return launch_persistent<PicardCfg<N>>(k_picard<N, LAW>, tiles, 148, a, s, &cfg, &blocks);
+}
+
 // The CDM runs on kernels compiled for it alone; the other laws on the dispatching ones.
 template <int N>
 cudaError_t launch_predictor_impl(const StepArgs& a, cudaStream_t s) {
@@ -1799,6 +2025,12 @@ cudaError_t launch_faces_impl(const StepArgs& a, cudaStream_t s) {
 template <int N>
 cudaError_t launch_corrector_impl(const StepArgs& a, cudaStream_t s) {
   return a.law == 0 ? launch_corrector_law<N, 0>(a, s) : launch_corrector_law<N, -1>(a, s);
+}
+template <int N>
+cudaError_t launch_picard_impl(const StepArgs& a, cudaStream_t s) {
+  if constexpr (PicardCfg<N>::FITS)
+    return a.law == 0 ? launch_picard_law<N, 0>(a, s) : launch_picard_law<N, -1>(a, s);
+  return cudaErrorNotSupported;
 }
 
 }  // namespace dg
@@ -1813,5 +2045,8 @@ cudaError_t launch_corrector_impl(const StepArgs& a, cudaStream_t s) {
   }                                                                                             \
   template <> cudaError_t launch_corrector_t<N>(const StepArgs& a, cudaStream_t s) {           \
     return launch_corrector_impl<N>(a, s);                                                      \
+  }                                                                                             \
+  template <> cudaError_t launch_picard_t<N>(const StepArgs& a, cudaStream_t s) {              \
+    return launch_picard_impl<N>(a, s);                                                         \
   }                                                                                             \
   }

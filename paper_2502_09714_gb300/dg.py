@@ -24,7 +24,7 @@ EXPORTS = (
     "dg_set_state_device", "dg_get_state", "dg_get_state_f32", "dg_get_state_device", "dg_step",
     "dg_receivers", "dg_receivers_read", "dg_dt", "dg_time", "dg_n_modes", "dg_get_stats",
     "dg_profile_enable", "dg_profile_read", "dg_reference_table", "dg_last_error", "dg_destroy",
-    "dg_step_noalloc", "dg_set_rheology",
+    "dg_step_noalloc", "dg_set_rheology", "dg_set_predictor",
 )
 
 
@@ -80,6 +80,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "dg_mesh_create": ([C.POINTER(MeshDesc), C.POINTER(vp)], C.c_int),
         "dg_set_material": ([vp, C.POINTER(dbl), C.POINTER(dbl)], C.c_int),
         "dg_set_rheology": ([vp, C.c_int], C.c_int),
+        "dg_set_predictor": ([vp, C.c_int, C.c_int], C.c_int),
         "dg_set_source": ([vp, C.POINTER(PointSource), i64], C.c_int),
         "dg_set_state": ([vp, C.POINTER(dbl), dbl], C.c_int),
         "dg_set_state_f32": ([vp, C.POINTER(C.c_float), dbl], C.c_int),
@@ -184,6 +185,11 @@ class Solver:
         """law: "cdm" (Eq. "cdb-model"), "ivm" (Eq. "ivm-model") or "nlshear" (the
         nonlinear shear law of the 1-D Riemann verification); set the material after."""
         self._chk(self.lib.dg_set_rheology(self.ctx, {"cdm": 0, "ivm": 1, "nlshear": 2}[law]))
+
+    def set_predictor(self, kind="ck", iterations=0):
+        """kind: "ck" (the linearised Cauchy-Kovalevskaya procedure) or "picard"
+        (`iterations` discrete Picard sweeps after it, Sec. 6.1's extension)."""
+        self._chk(self.lib.dg_set_predictor(self.ctx, {"ck": 0, "picard": 1}[kind], int(iterations)))
 
     # ------------------------------------------------------------------
     def _chk(self, status):
