@@ -192,7 +192,8 @@ def _config(w, args):
     return {"workload": w["name"], "elements": w["mesh"].n_elem, "order": w["order"],
             "modes": n_modes(w["order"]), "fields": 10, "sources": len(w["sources"]),
             "receivers": int(len(w["receivers"])), "l2_policy": "inputs larger than L2 "
-            "(state 2x and predictor buffers > 129 MB at N=4); no flush", "parallelism": f"replicas{args.gpus}"}
+            "(state 2x and predictor buffers > 129 MB at N=4); no flush", "parallelism": f"replicas{args.gpus}",
+            "predictor": f"picard{args.picard_iterations}" if getattr(args, "picard_iterations", 0) > 0 else "ck"}
 
 
 def main():
@@ -209,6 +210,9 @@ def main():
                     help="c2: 196,608-tet two-layer cube (the benchmark); c3: ~4.35 M-tet regional-shaped box")
     ap.add_argument("--ensemble-members", type=int, default=0,
                     help="also time the ensemble workload (N=3, this many members) against one member")
+    ap.add_argument("--picard-iterations", type=int, default=0,
+                    help="run the Picard predictor with this many iterations after the CK one (0: CK alone); "
+                         "the flop counts stay the CK step's")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -234,6 +238,8 @@ def main():
     bc = mesh.face_bc if np.any(mesh.face_bc != 0) else None
     s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, N, face_bc=bc, cfl=w["cfl"], stream=stream)
     s.set_material(mat)
+    if args.picard_iterations > 0:
+        s.set_predictor("picard", args.picard_iterations)
     s.set_sources(w["sources"])
     s.set_receivers(w["receivers"])
     s.set_state(np.zeros((E, 10, L), np.float32), 0.0)
