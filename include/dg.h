@@ -247,8 +247,9 @@ dg_status dg_get_stats(const dg_ctx* ctx, dg_stats* out);
 /* Per-kernel timing: when enabled, dg_step records CUDA events around each
  * kernel on the context's stream; dg_profile_read returns, per kernel kind,
  * the number of launches and the summed device milliseconds since the last
- * enable.  Kinds: 0 predictor, 1 corrector (volume terms, face projection and
- * update), 2 point source, 3 receivers, 4 face fluxes. */
+ * enable.  Kinds: 0 predictor (with the Picard iterations when they run),
+ * 1 corrector (volume terms, face projection and update), 2 point source,
+ * 3 receivers, 4 face fluxes. */
 typedef struct {
   int64_t launches;
   double total_ms;
