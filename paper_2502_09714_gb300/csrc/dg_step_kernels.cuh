@@ -690,35 +690,37 @@ __global__ void __launch_bounds__(512, 1) k_picard(StepArgs a) {
         }
         __syncthreads();
         // projections by the volume rule: Fh[l][col] = sum_q w_q phi_l(x_q) F[q][col]
-        block_gemm<1>(sVw, LP, sF, FST, LP, CF, NQ, nullptr, [&](int l, int col, float v) { sFh[l * CF + col] = v; });
+        // 4 x 2 work items: (LP/4) x (CF/2) of them fill the block
+        block_gemm_part<1, 2>(sVw, LP, sF, FST, LP, CF, NQ, nullptr, [&](int l, int col, float v) { sFh[l * CF + col] = v; },
+                              threadIdx.x, blockDim.x, [] { __syncthreads(); });
         __syncthreads();
         // R(t_z) = -sum_e' Kt^{e'} Fh_{e'} + Shat, folded into the Taylor fit of every order
-        for (int w = threadIdx.x; w < L * TE; w += blockDim.x) {
-          const int k = w / TE, e = w - k * TE;
+        // items (mode, element, group of 3 fields)
+        for (int w = threadIdx.x; w < L * TE * 3; w += blockDim.x) {
+          const int pg = w % 3, ke = w / 3;
+          const int k = ke / TE, e = ke - k * TE;
           float* dn = sDn + e * DS;
           if (k < L1) {
-            float acc[9];
-#pragma unroll
-            for (int p = 0; p < 9; ++p) acc[p] = 0.f;
+            float acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll 5
             for (int l = 0; l < L; ++l) {
-              const float* fh = sFh + l * CF + e * 28;
+              const float* fh = sFh + l * CF + e * 28 + 3 * pg;
 #pragma unroll
               for (int ep = 0; ep < 3; ++ep) {
                 const float kt = sKtA[(ep * L + l) * LP + k];
 #pragma unroll
-                for (int p = 0; p < 9; ++p) acc[p] = fmaf(kt, fh[ep * 9 + p], acc[p]);
+                for (int j = 0; j < 3; ++j) acc[j] = fmaf(kt, fh[ep * 9 + j], acc[j]);
               }
             }
 #pragma unroll
             for (int o = 1; o <= N; ++o) {
               if (k < n_modes(N - o)) {
 #pragma unroll
-                for (int p = 0; p < 9; ++p) dn[d_offset(N, o) + k * 9 + p] -= sFit[(o - 1) * NT + z] * acc[p];
+                for (int j = 0; j < 3; ++j) dn[d_offset(N, o) + k * 9 + 3 * pg + j] -= sFit[(o - 1) * NT + z] * acc[j];
               }
             }
           }
-          dn[AOFF + k] += sFit[z] * sFh[k * CF + e * 28 + 27];
+          if (pg == 0) dn[AOFF + k] += sFit[z] * sFh[k * CF + e * 28 + 27];
         }
         __syncthreads();
       }
