@@ -195,6 +195,17 @@ dg_status dg_get_state_device(dg_ctx* ctx, float* q_dev_out, double* t_out);
  * and state (DG_E_STATE). */
 dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt);
 
+/* One step from a host state to a host state: q_in and q_out are FP32 host
+ * arrays [members][n_elem][10][L] (they may be the same array).  Equivalent to
+ * dg_set_state_f32(q_in, current time), dg_step(1, dt), dg_get_state_f32(q_out),
+ * with the same arithmetic, but with one member the transfers overlap the
+ * step: the elements are cut into chunks, the upload of one chunk runs while the
+ * previous one is predicted and the download of one chunk while the corrector
+ * works on the next (page-locked host arrays are needed for the overlap;
+ * pageable ones work without it).  Advances the time by dt.  Requires the
+ * material (DG_E_STATE); errors as dg_step. */
+dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt);
+
 /* One step that allocates no memory, for callers that cannot call
  * cudaMalloc while they step (a host process under a fixed device-memory
  * budget, code running between the capture of other work, or an embedding

@@ -1,5 +1,7 @@
 // Auxiliary kernels of libdg: state conversion between the ABI layout and the
 // internal layout, point-source injection and receiver sampling.
+#include <cstdint>
+
 #include "dg_internal.h"
 
 namespace dg {
@@ -40,11 +42,14 @@ __global__ void k_state_out(int64_t E, int M, const float* q, int qs, void* dst,
   }
 }
 
-__global__ void k_sources(int L, int qs, int n_src, const SourceDev* src, const float* amp, int64_t step, float* q) {
+// Sources whose element copy lies in [e_lo, e_hi) (all of them for the full range).
+__global__ void k_sources(int L, int qs, int n_src, const SourceDev* src, const float* amp, int64_t step, float* q,
+                          int64_t e_lo, int64_t e_hi) {
   const int s = blockIdx.x;
   if (s >= n_src) return;
-  const float a = amp[step * n_src + s];
   const int64_t e = src[s].elem;
+  if (e < e_lo || e >= e_hi) return;
+  const float a = amp[step * n_src + s];
   for (int w = threadIdx.x; w < 6 * L; w += blockDim.x) {
     const int p = w / L, l = w % L;
     atomicAdd(&q[e * qs + l * kFields + p], -a * src[s].phi_eps[p * L + l]);
@@ -99,7 +104,13 @@ cudaError_t launch_state_out(int N, int64_t E, int M, const float* q, void* dst,
 
 cudaError_t launch_sources(int N, int n_src, const SourceDev* src, const float* amp, int64_t step,
                            float* q, cudaStream_t s) {
-  k_sources<<<n_src, 128, 0, s>>>(n_modes(N), q_stride(N), n_src, src, amp, step, q);
+  k_sources<<<n_src, 128, 0, s>>>(n_modes(N), q_stride(N), n_src, src, amp, step, q, 0, INT64_MAX);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sources_range(int N, int n_src, const SourceDev* src, const float* amp, int64_t step,
+                                 float* q, int64_t e_lo, int64_t e_hi, cudaStream_t s) {
+  k_sources<<<n_src, 128, 0, s>>>(n_modes(N), q_stride(N), n_src, src, amp, step, q, e_lo, e_hi);
   return cudaGetLastError();
 }
 

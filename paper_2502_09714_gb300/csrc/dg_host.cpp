@@ -71,6 +71,8 @@ struct dg_ctx {
   int64_t F = 0;            // faces in the flux list: interior first, then boundary
   int64_t F_interior = 0;
   int grid_pred = 0, grid_face = 0, grid_corr = 0;
+  cudaStream_t copy_stream = nullptr;     // host transfers of dg_step_host (created on first use)
+  std::vector<cudaEvent_t> xfer_events;   // [2 x chunks + 1] for dg_step_host
   GeomF* geom = nullptr;
   MatF* matf = nullptr;
   int* nbr = nullptr;
@@ -438,6 +440,8 @@ void dg_destroy(dg_ctx* ctx) {
   if (ctx->status_host) cudaFreeHost(ctx->status_host);
   if (ctx->amp_host) cudaFreeHost(ctx->amp_host);
   for (cudaEvent_t ev : ctx->events) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : ctx->xfer_events) cudaEventDestroy(ev);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   delete ctx;
 }
 
@@ -925,13 +929,12 @@ static double stf_integral(const dg_point_source& s, double t) {
   return 0.5 * (1.0 + std::erf(tau / (s.f0_or_sigma * std::sqrt(2.0))));
 }
 
-dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
-  if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
-  if (n_steps < 0) return fail(ctx, DG_E_ARG, "negative step count");
-  if (!ctx->has_material || !ctx->has_state) return fail(ctx, DG_E_STATE, "material and state must be set before dg_step");
-  if (dt <= 0) dt = ctx->dt_cfl;
-  if (!std::isfinite(dt)) return fail(ctx, DG_E_ARG, "non-finite dt");
-  if (n_steps == 0) return DG_OK;
+namespace {
+
+// Per-call preparation of a run of n_steps steps of size dt: the sources' amplitude
+// per step (exact time integrals of the moment-rate function) and room for the
+// receivers' traces.
+dg_status prepare_steps(dg_ctx* ctx, int64_t n_steps, double dt) {
   const int nsrc = static_cast<int>(ctx->source_host.size());     // sources x members
   const int R = static_cast<int>(ctx->rec_host.size());           // receivers x members
   const int M = ctx->M;
@@ -973,6 +976,24 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
       ctx->traces = nt;
       ctx->trace_cap = cap;
     }
+  }
+  return DG_OK;
+}
+
+}  // namespace
+
+dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
+  if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
+  if (n_steps < 0) return fail(ctx, DG_E_ARG, "negative step count");
+  if (!ctx->has_material || !ctx->has_state) return fail(ctx, DG_E_STATE, "material and state must be set before dg_step");
+  if (dt <= 0) dt = ctx->dt_cfl;
+  if (!std::isfinite(dt)) return fail(ctx, DG_E_ARG, "non-finite dt");
+  if (n_steps == 0) return DG_OK;
+  const int nsrc = static_cast<int>(ctx->source_host.size());     // sources x members
+  const int R = static_cast<int>(ctx->rec_host.size());           // receivers x members
+  {
+    dg_status st = prepare_steps(ctx, n_steps, dt);
+    if (st != DG_OK) return st;
   }
   DG_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream));
   // events for per-kernel timing
@@ -1060,6 +1081,153 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
       }
     }
   }
+  const unsigned st = *ctx->status_host;
+  if (st & kStatusNonFinite) return fail(ctx, DG_E_NONFINITE, "non-finite value in the state");
+  if (st & kStatusNonHyperbolic) return fail(ctx, DG_E_NONHYPERBOLIC, "effective moduli lost hyperbolicity");
+  if (st & kStatusIndex) return fail(ctx, DG_E_MESH, "neighbour index out of range");
+  if (st & kStatusTimeout) return fail(ctx, DG_E_CUDA, "a bounded wait on the tensor cores timed out");
+  return DG_OK;
+}
+
+// One step from a host state to a host state, with the transfers overlapped: the
+// element range is cut into chunks; the host-to-device copy of chunk k+1 runs
+// (on a copy stream) while chunk k is converted and predicted, and the
+// device-to-host copy of chunk k while the corrector works on chunk k+1.  Every
+// element's arithmetic is the same as dg_step's.
+dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) {
+  if (!ctx || !q_in || !q_out) return fail(ctx, DG_E_ARG, "NULL argument");
+  if (!ctx->has_material) return fail(ctx, DG_E_STATE, "material must be set before dg_step_host");
+  if (ctx->M != 1) {                        // members: the plain sequence
+    dg_status st = dg_set_state_f32(ctx, q_in, ctx->t);
+    if (st == DG_OK) st = dg_step(ctx, 1, dt);
+    double t = 0.0;
+    return st == DG_OK ? dg_get_state_f32(ctx, q_out, &t) : st;
+  }
+  if (dt <= 0) dt = ctx->dt_cfl;
+  if (!std::isfinite(dt)) return fail(ctx, DG_E_ARG, "non-finite dt");
+  const int nsrc = static_cast<int>(ctx->source_host.size());
+  const int R = static_cast<int>(ctx->rec_host.size());
+  {
+    dg_status st = prepare_steps(ctx, 1, dt);
+    if (st != DG_OK) return st;
+  }
+  const int64_t E = ctx->E, L = ctx->L;
+  const size_t row = static_cast<size_t>(kFields * L);          // floats per element, host layout
+  const int64_t qs = q_stride(ctx->N), ds = d_stride(ctx->N);
+  {
+    dg_status st = ensure_staging(ctx, sizeof(float) * row * E);
+    if (st != DG_OK) return st;
+  }
+  // chunks of a multiple of 16 elements, at least 4096 each, at most 8 (16 measured slower)
+  int64_t chunk = std::max<int64_t>(4096, (E + 7) / 8);
+  chunk = (chunk + 15) / 16 * 16;
+  const int C = static_cast<int>((E + chunk - 1) / chunk);
+  if (!ctx->copy_stream) DG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  while (ctx->xfer_events.size() < static_cast<size_t>(2 * C + 1)) {
+    cudaEvent_t ev;
+    DG_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    ctx->xfer_events.push_back(ev);
+  }
+  cudaEvent_t* evH = ctx->xfer_events.data();
+  cudaEvent_t* evC = evH + C;
+  cudaEvent_t evStart = evH[2 * C];
+  float* staging = static_cast<float*>(ctx->staging);
+  const int cur = ctx->cur;
+  float* qi = ctx->q[cur];
+  float* qo = ctx->q[1 - cur];
+  StepArgs a{};
+  a.E = ctx->EV;
+  a.F = ctx->F;
+  a.has_boundary = ctx->F > ctx->F_interior;
+  a.q_in = qi;
+  a.q_out = qo;
+  a.d = ctx->d;
+  a.cp = ctx->cp;
+  a.ff = ctx->ff;
+  a.faces = ctx->faces;
+  a.elem_face = ctx->elem_face;
+  a.grid_pred = ctx->grid_pred;
+  a.grid_face = ctx->grid_face;
+  a.grid_corr = ctx->grid_corr;
+  a.law = ctx->law;
+  a.picard_iters = ctx->picard_iters;
+  a.geom = ctx->geom;
+  a.mat = ctx->matf;
+  a.nbr = ctx->nbr;
+  a.tables = ctx->tables;
+  a.dt = static_cast<float>(dt);
+  a.status = ctx->status;
+  auto part = [&](int k) {
+    const int64_t e0 = k * chunk;
+    StepArgs c = a;
+    c.E = std::min<int64_t>(chunk, E - e0);
+    c.q_in = qi + e0 * qs;
+    c.q_out = qo + e0 * qs;
+    c.d = a.d + e0 * ds;
+    c.cp = a.cp + e0;
+    c.geom = a.geom + e0;
+    c.mat = a.mat + e0;
+    c.nbr = a.nbr + e0 * 4;
+    c.elem_face = a.elem_face + e0 * 4;
+    return c;
+  };
+  DG_CUDA(ctx, cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream));
+  // the copies may not touch the staging buffer before earlier work on it is done
+  DG_CUDA(ctx, cudaEventRecord(evStart, ctx->stream));
+  DG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, evStart, 0));
+  for (int k = 0; k < C; ++k) {
+    const int64_t e0 = k * chunk, ne = std::min<int64_t>(chunk, E - e0);
+    DG_CUDA(ctx, cudaMemcpyAsync(staging + e0 * row, q_in + e0 * row, sizeof(float) * row * ne,
+                                 cudaMemcpyHostToDevice, ctx->copy_stream));
+    DG_CUDA(ctx, cudaEventRecord(evH[k], ctx->copy_stream));
+  }
+  int64_t launches = 0;
+  for (int k = 0; k < C; ++k) {
+    const StepArgs c = part(k);
+    const int64_t e0 = k * chunk;
+    DG_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, evH[k], 0));
+    DG_CUDA(ctx, launch_state_in(ctx->N, c.E, 1, staging + e0 * row, 0, qi + e0 * qs, ctx->stream));
+    DG_CUDA(ctx, launch_predictor(ctx->N, c, ctx->stream));
+    launches += 1;
+    if (c.picard_iters > 0) {
+      DG_CUDA(ctx, launch_picard(ctx->N, c, ctx->stream));
+      ++launches;
+    }
+  }
+  DG_CUDA(ctx, launch_faces(ctx->N, a, ctx->stream));
+  ++launches;
+  for (int k = 0; k < C; ++k) {
+    const StepArgs c = part(k);
+    const int64_t e0 = k * chunk;
+    DG_CUDA(ctx, launch_corrector(ctx->N, c, ctx->stream));
+    ++launches;
+    if (nsrc > 0) {
+      DG_CUDA(ctx, launch_sources_range(ctx->N, nsrc, ctx->source_dev, ctx->amp_dev, 0, qo, e0, e0 + c.E, ctx->stream));
+      ++launches;
+    }
+    DG_CUDA(ctx, launch_state_out(ctx->N, c.E, 1, qo + e0 * qs, staging + e0 * row, 0, ctx->stream));
+    DG_CUDA(ctx, cudaEventRecord(evC[k], ctx->stream));
+  }
+  for (int k = 0; k < C; ++k) {
+    const int64_t e0 = k * chunk, ne = std::min<int64_t>(chunk, E - e0);
+    DG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, evC[k], 0));
+    DG_CUDA(ctx, cudaMemcpyAsync(q_out + e0 * row, staging + e0 * row, sizeof(float) * row * ne,
+                                 cudaMemcpyDeviceToHost, ctx->copy_stream));
+  }
+  if (R > 0 && ctx->n_rec < 65536) {
+    DG_CUDA(ctx, launch_receivers(ctx->N, R, ctx->rec_dev, qo, ctx->traces + 3 * R * ctx->n_rec, ctx->stream));
+    ++ctx->n_rec;
+    ++launches;
+  }
+  DG_CUDA(ctx, cudaMemcpyAsync(ctx->status_host, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+  DG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  DG_CUDA(ctx, cudaStreamSynchronize(ctx->copy_stream));
+  ctx->cur = 1 - cur;
+  ctx->has_state = true;
+  ctx->t += dt;
+  ctx->stats.steps += 1;
+  ctx->stats.kernel_launches += launches;
+  ctx->stats.element_updates += ctx->EV;
   const unsigned st = *ctx->status_host;
   if (st & kStatusNonFinite) return fail(ctx, DG_E_NONFINITE, "non-finite value in the state");
   if (st & kStatusNonHyperbolic) return fail(ctx, DG_E_NONHYPERBOLIC, "effective moduli lost hyperbolicity");

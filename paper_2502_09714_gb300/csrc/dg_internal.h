@@ -179,6 +179,9 @@ struct SourceDev {
 // Adds -amp[step * n_src + s] * phi_eps to the strain modes of each source element.
 cudaError_t launch_sources(int N, int n_src, const SourceDev* src, const float* amp, int64_t step,
                            float* q, cudaStream_t s);
+// The sources whose element copy lies in [e_lo, e_hi).
+cudaError_t launch_sources_range(int N, int n_src, const SourceDev* src, const float* amp, int64_t step,
+                                 float* q, int64_t e_lo, int64_t e_hi, cudaStream_t s);
 
 struct ReceiverDev {
   int64_t elem;

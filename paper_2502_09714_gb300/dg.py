@@ -24,7 +24,7 @@ EXPORTS = (
     "dg_set_state_device", "dg_get_state", "dg_get_state_f32", "dg_get_state_device", "dg_step",
     "dg_receivers", "dg_receivers_read", "dg_dt", "dg_time", "dg_n_modes", "dg_get_stats",
     "dg_profile_enable", "dg_profile_read", "dg_reference_table", "dg_last_error", "dg_destroy",
-    "dg_step_noalloc", "dg_set_rheology", "dg_set_predictor",
+    "dg_step_noalloc", "dg_set_rheology", "dg_set_predictor", "dg_step_host",
 )
 
 
@@ -81,6 +81,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "dg_set_material": ([vp, C.POINTER(dbl), C.POINTER(dbl)], C.c_int),
         "dg_set_rheology": ([vp, C.c_int], C.c_int),
         "dg_set_predictor": ([vp, C.c_int, C.c_int], C.c_int),
+        "dg_step_host": ([vp, vp, vp, C.c_double], C.c_int),
         "dg_set_source": ([vp, C.POINTER(PointSource), i64], C.c_int),
         "dg_set_state": ([vp, C.POINTER(dbl), dbl], C.c_int),
         "dg_set_state_f32": ([vp, C.POINTER(C.c_float), dbl], C.c_int),
@@ -271,6 +272,18 @@ class Solver:
 
     def step(self, n_steps=1, dt=0.0):
         self._chk(self.lib.dg_step(self.ctx, int(n_steps), float(dt)))
+
+    def step_host(self, q_in, q_out, dt=0.0):
+        """One step from the host state q_in to the host state q_out (float32
+        arrays [E,10,L], [M,E,10,L] with several members; page-locked memory,
+        e.g. numpy views of pinned torch tensors, lets the transfers overlap the
+        step)."""
+        a = q_in.numpy() if hasattr(q_in, "numpy") else q_in
+        b = q_out.numpy() if hasattr(q_out, "numpy") else q_out
+        assert a.dtype == np.float32 and b.dtype == np.float32
+        assert a.flags.c_contiguous and b.flags.c_contiguous and b.flags.writeable
+        assert tuple(a.shape) == self._shape() and tuple(b.shape) == self._shape()
+        self._chk(self.lib.dg_step_host(self.ctx, C.c_void_p(a.ctypes.data), C.c_void_p(b.ctypes.data), float(dt)))
 
     def step_noalloc(self, q_in, q_out, dt=0.0):
         """One step from q_in to q_out (CUDA float32 tensors [E,10,L], or raw
