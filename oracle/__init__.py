@@ -15,7 +15,9 @@ wave, energy decay, the brute-force monomial-basis re-derivation of one step,
 invariance under relabelling/rotation/translation and monotone damage; for the
 nonlinear shear law of the 1-D Riemann verification, its energy, plane-shear
 reduction and secant moduli, and the exact Riemann solution's jump conditions,
-invariants and linear limit.
+invariants and linear limit; for the discrete adjoint (oracle/adjoint.py), its
+pointwise derivatives, its step transpose and its misfit gradient against
+central differences of the forward law, step and run.
 """
 from .basis import eval_basis, mode_list, n_modes
 from .quadrature import gauss_jacobi, gauss_legendre_01, tet_rule, tri_rule

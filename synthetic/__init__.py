@@ -9,11 +9,11 @@ from .mesh import Mesh, kuhn_box_mesh, periodic_cube_mesh
 from .workloads import (
     FIELD_NAMES, rock_material, two_layer_material, uniform_material,
     dip_slip_source, receiver_grid, workload_c1, workload_c2, workload_c4, workload_small_layered,
-    workload_riemann,
+    workload_riemann, workload_adjoint,
 )
 
 __all__ = [
     "Mesh", "kuhn_box_mesh", "periodic_cube_mesh", "FIELD_NAMES", "rock_material",
     "two_layer_material", "uniform_material", "dip_slip_source", "receiver_grid",
-    "workload_c1", "workload_c2", "workload_c4", "workload_small_layered", "workload_riemann",
+    "workload_c1", "workload_c2", "workload_c4", "workload_small_layered", "workload_riemann", "workload_adjoint",
 ]

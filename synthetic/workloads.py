@@ -157,3 +157,29 @@ def workload_riemann(nx, order=2, half_length=1.2, t_end=0.5):
     return {"name": f"plane shear Riemann problem nx={nx} N={order}", "mesh": mesh, "material": mat,
             "order": order, "left": RIEMANN_LEFT, "right": RIEMANN_RIGHT, "t_end": t_end, "h": h,
             "eval_half_width": half_length - t_end - 0.1}
+
+
+def workload_adjoint(n=24, side=4000.0, order=3, n_receivers=32, steps=800, m0=C2_M0, seed=5):
+    """The adjoint workload: a periodic jittered cube of n^3 x 6 tets (82,944 at
+    n = 24) at degree 3 in homogeneous rock, the c2 dip-slip point source, 32
+    receivers on a jittered 4 x 8 grid at three quarters of the height, and
+    per-element damage parameters drawn with `seed`: xi0 ~ U[-1.0, -0.6] and
+    log C_d ~ U[log 3e-5, log 3e-4] ("material").  The reference run that makes
+    the traces to be fitted uses "material_ref": xi0 + 0.05 N(0, 1) and
+    C_d exp(0.3 N(0, 1)), drawn with seed + 1."""
+    mesh = periodic_cube_mesh(n, side, jitter=0.1, seed=1, sort_by_vid=True)
+    E = mesh.n_elem
+    rng = np.random.default_rng(seed)
+    mat = rock_material(E)
+    mat[:, 4] = rng.uniform(-1.0, -0.6, size=E)
+    mat[:, 5] = np.exp(rng.uniform(np.log(3e-5), np.log(3e-4), size=E))
+    rng2 = np.random.default_rng(seed + 1)
+    ref = mat.copy()
+    ref[:, 4] += 0.05 * rng2.normal(size=E)
+    ref[:, 5] *= np.exp(0.3 * rng2.normal(size=E))
+    src = dip_slip_source([0.5 * side, 0.5 * side, 0.5 * side], m0)
+    h = side / n
+    rec = receiver_grid(4, 8, (side, side), z=0.75 * side, jitter=min(0.5 * h, side / 32.0), seed=seed + 2)
+    return {"name": f"c5 adjoint on the {E}-tet jittered cube N={order}", "mesh": mesh,
+            "material": mat, "material_ref": ref, "order": order, "cfl": 0.5, "steps": steps,
+            "snapshots": 40, "sources": [src], "receivers": rec[:n_receivers]}
