@@ -278,6 +278,62 @@ dg_status dg_profile_read(dg_ctx* ctx, dg_kernel_time* out, int cap, int* n_kind
  * full table.  DG_E_ORDER for an unsupported degree, DG_E_ARG otherwise. */
 dg_status dg_reference_table(int order, int which, double* out, int64_t cap, int64_t* count);
 
+/* Gradient of the receiver misfit by the discrete adjoint of the step.
+ * Starting from the context's state Q^0 at time t0, n_steps steps of size dt
+ * (dt <= 0 selects dg_dt) give the misfit
+ *     J = 1/2 sum_{k=1..n_steps} dt sum_r |v_r(Q^k) - ref[k-1][r]|^2,
+ * v_r the velocity at receiver r of dg_receivers (FP64 sum).  The call returns
+ * J in *misfit and, when the pointers are not NULL, dJ/dxi0 and dJ/dC_d per
+ * element (grad_xi0, grad_cd: [n_elem] FP64, the damage onset and rate
+ * coefficient of Eq. "cdb-model" in dg_set_material's rows) and dJ/dQ^0
+ * (grad_q0: [n_elem][10][L] FP64, the state layout).
+ * The gradient is that of the FP32 step the library takes (predictor, face
+ * fluxes, corrector, point sources): each product of the step is transposed,
+ * including the dependence of the star matrices on the effective Lame
+ * parameters of the cell mean (Eq. "effective-cdb") and of the Rusanov speed
+ * C = max(cp-, cp+) (Eq. "rusanov-flux") on both cells.  At the non-smooth points
+ * the damage rate max(0, .) has derivative zero on its flat side, and a tie of
+ * the two P speeds splits the derivative of the max in halves.  The
+ * parameter-gradient sums over steps and the misfit are FP64.
+ * The step history is kept by binomial checkpointing (revolve): `snapshots`
+ * state copies in all (one holds Q^0), so that the forward steps number
+ * dg_revolve_cost(n_steps, snapshots) + 1; each adjoint step recomputes its own
+ * predictor.  ref: host FP32 [n_steps][R][3], R receivers.  The context's state,
+ * time and recorded traces are left unchanged.  info: NULL or the counts and
+ * device milliseconds of the forward steps, the adjoint steps (predictor
+ * recompute, adjoint kernels and misfit terms) and the snapshot copies.
+ * Requires the CDM law, the CK predictor, one member, no boundary faces
+ * (DG_E_UNSUPPORTED otherwise), material, state and at least one receiver
+ * (DG_E_STATE); DG_E_ARG for n_steps outside 1..2^20, snapshots outside
+ * 1..4096 or a plan of more than 2^27 forward steps; DG_E_OOM if the
+ * snapshots (snapshots x n_elem x 4 ceil(10 L / 4) floats) do not fit;
+ * DG_E_NONFINITE / DG_E_NONHYPERBOLIC as dg_step. */
+typedef struct {
+  int64_t forward_steps;
+  int64_t adjoint_steps;
+  double forward_ms;
+  double adjoint_ms;
+  double copy_ms;
+} dg_adjoint_info;
+dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const float* ref, int snapshots,
+                              double* misfit, double* grad_xi0, double* grad_cd, double* grad_q0,
+                              dg_adjoint_info* info);
+
+/* The binomial checkpointing plan behind dg_adjoint_gradient, for inspection
+ * (host only, no device needed).  Reversing n_steps steps with `snapshots`
+ * state slots (slot 0 holds the initial state) takes
+ *     T = t n - C(s + 1 + t, t - 1)  forward steps,  s = snapshots - 1,
+ * t the least integer with C(s + 1 + t, t) >= n (T = n (n - 1) / 2 for s = 0);
+ * dg_revolve_cost returns T (-1 for bad arguments).  dg_revolve_plan writes
+ * *forward_steps = T and up to cap actions as triples (kind, a, b): kind 0
+ * advance the current state from step a to step b, 1 store the current state
+ * (step b) in slot a, 2 restore slot a (step b), 3 the adjoint of step a; the
+ * full count goes to *n_actions.  DG_E_ARG for n_steps outside 1..2^20,
+ * snapshots outside 1..4096 or T > 2^27. */
+dg_status dg_revolve_plan(int64_t n_steps, int snapshots, int64_t* forward_steps, int64_t* actions,
+                          int64_t cap, int64_t* n_actions);
+int64_t dg_revolve_cost(int64_t n_steps, int snapshots);
+
 const char* dg_last_error(const dg_ctx* ctx);
 void dg_destroy(dg_ctx* ctx);
 

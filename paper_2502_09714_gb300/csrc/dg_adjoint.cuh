@@ -1,0 +1,635 @@
+// Discrete adjoint of one CK step under the CDM law (Eq. "cdb-model"), FP32,
+// templated on the degree N.  With lam = dJ/dQ^{k+1}, the two kernels give
+// dJ/dQ^k and add dJ/dxi0 and dJ/dC_d of the step
+//     Q^{k+1} = Q^k + vol(U) + src(U) - face(U, U_nbr, C) / |J|
+// (Eqs. "time-integrated", "3rd term", "rhs term", "2nd term", "rusanov-flux";
+// U the Taylor expansion of the CK predictor, Eqs. "CKIter-ref-matrix" and
+// "CKIter-ref-source"), every product of the forward step transposed:
+//
+//   k_adj_face   once per interior face: lam of the face term -> lam of both
+//                traces at the space-time face nodes through the Rusanov
+//                flux (flux Jacobians of both sides, C = max of the two P
+//                speeds), folded into Taylor orders and projected onto the
+//                modes of each side; lam of C and the xi0 part per side.
+//   k_adj_elem   once per element: volume flux and damage-rate source
+//                transposed at the space-time volume nodes, the records of its
+//                four faces gathered, the CK recursion transposed from order N
+//                down to 0 (star matrices through the effective Lame
+//                parameters of the cell mean, damage-rate source of D^1), and
+//                the cell-mean terms; writes dJ/dQ^k = lam + dJ/dD^0 and adds
+//                the element's parameter gradient in FP64.
+//
+// Conventions at the non-smooth points: the damage rate has derivative zero
+// where I1 sqrt(I2) - xi0 I2 <= 0, xi and sqrt(I2) have derivative zero below
+// I2 = 1e-30, and a tie of the two P speeds splits the derivative of the max in
+// halves.  The predictor output D and the speeds cp of Q^k come from the
+// forward predictor kernel, launched on Q^k just before.
+#pragma once
+
+#include "dg_internal.h"
+
+namespace dg {
+namespace adj {
+
+template <int N>
+struct ADim {
+  static constexpr int L = n_modes(N), NQ = n_vol_nodes(N), NF = n_face_nodes(N), NT = N + 1;
+  static constexpr int LP = lp_of(N), NQP = nqp_of(N), NFP = nfp_of(N);
+  static constexpr int QS = q_stride(N), DS = d_stride(N), AOFF = d_alpha_offset(N);
+  static constexpr int RS = adj_rec_stride(N);
+  static constexpr int LDS = QS + DS;           // lam of D^0..D^N in the (Q, D) layout
+};
+
+// sqrt(I2), xi = I1 / sqrt(I2) and their derivatives in the six strain entries
+// (zero below I2 = 1e-30); dI2 counts each shear entry twice.
+struct Inv {
+  float I1, I2, s, xi, ds[6], dxi[6];
+};
+__device__ __forceinline__ Inv invariants(const float* e) {
+  Inv v;
+  v.I1 = e[0] + e[1] + e[2];
+  v.I2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] + 2.f * (e[3] * e[3] + e[4] * e[4] + e[5] * e[5]);
+  if (v.I2 > 1e-30f) {
+    const float rs = rsqrtf(v.I2);
+    v.s = v.I2 * rs;
+    v.xi = v.I1 * rs;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      v.ds[p] = (p < 3 ? 1.f : 2.f) * e[p] * rs;        // dI2/(2 s)
+      v.dxi[p] = (p < 3 ? rs : 0.f) - v.xi * rs * v.ds[p];
+    }
+  } else {
+    v.s = v.xi = 0.f;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) v.ds[p] = v.dxi[p] = 0.f;
+  }
+  return v;
+}
+
+// Adds to lu[10] the gradient of sum_p ls[p] sigma_p(u) (sigma_p the six
+// independent entries xx yy zz xy yz zx of the CDM stress); returns its xi0 part.
+__device__ __forceinline__ float stress_vjp(const float* u, const MatF& m, const float ls[6], float lu[10]) {
+  const Inv v = invariants(u);
+  const float ag = u[9] * m.gamma_r;
+  const float sh = 2.f * (m.mu0 + ag * m.xi0) - ag * v.xi;
+  const float tr = ls[0] + ls[1] + ls[2];
+  float le = 0.f;
+#pragma unroll
+  for (int p = 0; p < 6; ++p) le = fmaf(ls[p], u[p], le);
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    const float diso = (p < 3 ? m.lam0 : 0.f) - ag * v.ds[p];
+    lu[p] += tr * diso - le * ag * v.dxi[p] + sh * ls[p];
+  }
+  lu[9] += -tr * m.gamma_r * v.s + le * m.gamma_r * (2.f * m.xi0 - v.xi);
+  return 2.f * le * ag;
+}
+
+// Adds to lu[0..5] the gradient of lr * r(u) (CDM damage rate); adds its xi0
+// and C_d parts to *gx and *gc.
+__device__ __forceinline__ void rate_vjp(const float* u, const MatF& m, float lr, float lu[10], float* gx,
+                                         float* gc) {
+  const Inv v = invariants(u);
+  const float arg = v.I1 * v.s - m.xi0 * v.I2;
+  if (!(arg > 0.f)) return;
+  const float k = lr * m.cd * m.gamma_r;
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    const float d1 = p < 3 ? 1.f : 0.f, d2 = (p < 3 ? 2.f : 4.f) * u[p];
+    lu[p] += k * (d1 * v.s + v.I1 * v.ds[p] - m.xi0 * d2);
+  }
+  *gx -= k * v.I2;
+  *gc += lr * m.gamma_r * arg;
+}
+
+// Adds to lu[10] the gradient of sum_{d,p} lF[d][p] F^d_p(u) (flux of Eq.
+// "nonlinear hyper pdes", lF [3][9] row-major); returns its xi0 part.
+__device__ __forceinline__ float flux_vjp(const float* u, const MatF& m, const float* lF, float lu[10]) {
+  // strain rows F^d_(ij) = -(v_i delta_jd + v_j delta_id) / 2
+  lu[6] += -lF[0 * 9 + 0] - 0.5f * (lF[1 * 9 + 3] + lF[2 * 9 + 5]);
+  lu[7] += -lF[1 * 9 + 1] - 0.5f * (lF[0 * 9 + 3] + lF[2 * 9 + 4]);
+  lu[8] += -lF[2 * 9 + 2] - 0.5f * (lF[1 * 9 + 4] + lF[0 * 9 + 5]);
+  // velocity rows F^d_(v_i) = -sigma_id / rho
+  const float r = -m.rho_inv;
+  const float ls[6] = {r * lF[0 * 9 + 6], r * lF[1 * 9 + 7], r * lF[2 * 9 + 8],
+                       r * (lF[1 * 9 + 6] + lF[0 * 9 + 7]), r * (lF[2 * 9 + 7] + lF[1 * 9 + 8]),
+                       r * (lF[0 * 9 + 8] + lF[2 * 9 + 6])};
+  return stress_vjp(u, m, ls, lu);
+}
+
+// Adds to lu[10] the gradient of sum_p lf[p] (F(u) n)_p (the normal flux of the
+// face kernel); returns its xi0 part.
+__device__ __forceinline__ float normal_flux_vjp(const float* u, const MatF& m, const float n[3], const float lf[9],
+                                                 float lu[10]) {
+  lu[6] += -lf[0] * n[0] - 0.5f * (lf[3] * n[1] + lf[5] * n[2]);
+  lu[7] += -lf[1] * n[1] - 0.5f * (lf[3] * n[0] + lf[4] * n[2]);
+  lu[8] += -lf[2] * n[2] - 0.5f * (lf[4] * n[1] + lf[5] * n[0]);
+  const float r = -m.rho_inv;
+  const float ls[6] = {r * lf[6] * n[0], r * lf[7] * n[1], r * lf[8] * n[2], r * (lf[6] * n[1] + lf[7] * n[0]),
+                       r * (lf[7] * n[2] + lf[8] * n[1]), r * (lf[6] * n[2] + lf[8] * n[0])};
+  return stress_vjp(u, m, ls, lu);
+}
+
+// Block-wide sum of one float per thread into a shared double (atomic).
+__device__ __forceinline__ void block_add(double* acc, float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(acc, static_cast<double>(v));
+}
+
+// Taylor coefficient t^o / o! of order o at time node z (t = tz dt).
+template <int N>
+__device__ __forceinline__ float taylor(const float* tb, const TableLayout& T, int z, int o, float dt) {
+  const float t = __ldg(tb + T.tz + z) * dt;
+  float c = 1.f;
+  for (int j = 1; j <= o; ++j) c *= t / static_cast<float>(j);
+  return c;
+}
+
+// U[z][l][p] (p < 10) of one element from Q [L][10] and D (GPU layout).
+template <int N>
+__device__ __forceinline__ void taylor_values(const float* sQ, const float* sD, float* sU, const float* tb,
+                                              const TableLayout& T, float dt, int t0, int nt) {
+  using A = ADim<N>;
+  for (int w = t0; w < A::NT * A::L * 10; w += nt) {
+    const int z = w / (A::L * 10), r = w - z * A::L * 10, l = r / 10, p = r - l * 10;
+    float u = sQ[l * 10 + p];
+    if (p == 9) {
+      u = fmaf(__ldg(tb + T.tz + z) * dt, sD[A::AOFF + l], u);
+    } else {
+      for (int o = 1; o <= N; ++o)
+        if (l < n_modes(N - o)) u = fmaf(taylor<N>(tb, T, z, o, dt), sD[d_offset(N, o) + l * 9 + p], u);
+    }
+    sU[w] = u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Faces
+// ---------------------------------------------------------------------------
+template <int N>
+struct FaceSmem {
+  using A = ADim<N>;
+  static constexpr int oLam = 0;                              // [2][L][10]
+  static constexpr int oQ = oLam + 2 * A::L * 10;             // [2][QS]
+  static constexpr int oD = oQ + 2 * A::QS;                   // [2][DS]
+  static constexpr int oU = oD + 2 * A::DS;                   // [2][NT][L][10]
+  static constexpr int oTr = oU + 2 * A::NT * A::L * 10;      // [2][NT][NF][10] traces
+  static constexpr int oLff = oTr + 2 * A::NT * A::NF * 10;   // [NF][9]
+  static constexpr int oLu = oLff + A::NF * 9;                // [2][NT][NF][10] lam of the traces
+  static constexpr int oLo = oLu + 2 * A::NT * A::NF * 10;    // [2][NT(orders)][NF][10]
+  static constexpr int total = oLo + 2 * A::NT * A::NF * 10;
+};
+
+template <int N>
+__global__ void __launch_bounds__(128) k_adj_face(AdjArgs a) {
+  using A = ADim<N>;
+  using S = FaceSmem<N>;
+  constexpr int L = A::L, NF = A::NF, NT = A::NT;
+  extern __shared__ __align__(16) float smem[];
+  __shared__ double sRed[4];
+  const TableLayout T = table_layout(N);
+  const float* tb = a.tables;
+  const float dt = a.dt;
+  for (int64_t f = blockIdx.x; f < a.F; f += gridDim.x) {
+    const int4 fc = a.faces[f];
+    const int64_t e[2] = {fc.x, fc.z};
+    const int lf[2] = {fc.y, fc.w};
+    __syncthreads();
+    for (int w = threadIdx.x; w < 2 * L * 10; w += blockDim.x) {
+      const int sd = w / (L * 10), r = w - sd * L * 10;
+      smem[S::oLam + w] = a.lam_in[e[sd] * A::QS + r];
+      smem[S::oQ + sd * A::QS + r] = a.q[e[sd] * A::QS + r];
+    }
+    for (int w = threadIdx.x; w < 2 * A::DS; w += blockDim.x) {
+      const int sd = w / A::DS, r = w - sd * A::DS;
+      smem[S::oD + w] = a.d[e[sd] * A::DS + r];
+    }
+    if (threadIdx.x < 4) sRed[threadIdx.x] = 0.0;
+    __syncthreads();
+    for (int sd = 0; sd < 2; ++sd)
+      taylor_values<N>(smem + S::oQ + sd * A::QS, smem + S::oD + sd * A::DS, smem + S::oU + sd * NT * L * 10, tb,
+                       T, dt, threadIdx.x, blockDim.x);
+    // lam of the time-integrated face flux:
+    //   lff[i][p] = -(a0 sum_k Vfw[f0][i][k] lam0[k][p] - a1 sum_k Vfw[f1][i][k] lam1[k][p])
+    const float a0 = a.geom[e[0]].face[lf[0]][3], a1 = a.geom[e[1]].face[lf[1]][3];
+    for (int w = threadIdx.x; w < NF * 9; w += blockDim.x) {
+      const int i = w / 9, p = w - i * 9;
+      float s0 = 0.f, s1 = 0.f;
+      for (int k = 0; k < L; ++k) {
+        s0 = fmaf(__ldg(tb + T.Vfw + (lf[0] * NF + i) * A::LP + k), smem[S::oLam + k * 10 + p], s0);
+        s1 = fmaf(__ldg(tb + T.Vfw + (lf[1] * NF + i) * A::LP + k), smem[S::oLam + L * 10 + k * 10 + p], s1);
+      }
+      smem[S::oLff + w] = -(a0 * s0 - a1 * s1);
+    }
+    __syncthreads();
+    // traces of both sides at the space-time face nodes
+    for (int w = threadIdx.x; w < 2 * NT * NF * 10; w += blockDim.x) {
+      const int sd = w / (NT * NF * 10), r = w - sd * NT * NF * 10;
+      const int z = r / (NF * 10), r2 = r - z * NF * 10, i = r2 / 10, p = r2 - i * 10;
+      const float* U = smem + S::oU + (sd * NT + z) * L * 10;
+      float s = 0.f;
+      for (int l = 0; l < L; ++l) s = fmaf(__ldg(tb + T.VfT + (lf[sd] * L + l) * A::NFP + i), U[l * 10 + p], s);
+      smem[S::oTr + w] = s;
+    }
+    __syncthreads();
+    // the Rusanov flux transposed at each space-time node
+    const MatF m0 = a.mat[e[0]], m1 = a.mat[e[1]];
+    const float n[3] = {a.geom[e[0]].face[lf[0]][0], a.geom[e[0]].face[lf[0]][1], a.geom[e[0]].face[lf[0]][2]};
+    const float cp0 = a.cp[e[0]], cp1 = a.cp[e[1]];
+    const float C = fmaxf(cp0, cp1);
+    float pC = 0.f, px0 = 0.f, px1 = 0.f;
+    for (int w = threadIdx.x; w < NT * NF; w += blockDim.x) {
+      const int z = w / NF, i = w - z * NF;
+      const float g = __ldg(tb + T.gz + z) * dt;
+      const float* um = smem + S::oTr + (0 * NT * NF + w) * 10;
+      const float* up = smem + S::oTr + (1 * NT * NF + w) * 10;
+      float lfs[9];
+#pragma unroll
+      for (int p = 0; p < 9; ++p) lfs[p] = g * smem[S::oLff + i * 9 + p];
+      float lm[10], lp[10];
+#pragma unroll
+      for (int p = 0; p < 10; ++p) lm[p] = lp[p] = 0.f;
+      px0 += 0.5f * normal_flux_vjp(um, m0, n, lfs, lm);
+      px1 += 0.5f * normal_flux_vjp(up, m1, n, lfs, lp);
+      float* om = smem + S::oLu + (0 * NT * NF + w) * 10;
+      float* op = smem + S::oLu + (1 * NT * NF + w) * 10;
+#pragma unroll
+      for (int p = 0; p < 9; ++p) {
+        om[p] = 0.5f * lm[p] + 0.5f * C * lfs[p];
+        op[p] = 0.5f * lp[p] - 0.5f * C * lfs[p];
+        pC = fmaf(0.5f * lfs[p], um[p] - up[p], pC);
+      }
+      om[9] = 0.5f * lm[9];
+      op[9] = 0.5f * lp[9];
+    }
+    block_add(&sRed[0], pC);
+    block_add(&sRed[1], px0);
+    block_add(&sRed[2], px1);
+    __syncthreads();
+    // fold the time nodes into Taylor orders: Lo[o][i][p] = sum_z t_z^o / o! Lu[z][i][p]
+    for (int w = threadIdx.x; w < 2 * NT * NF * 10; w += blockDim.x) {
+      const int sd = w / (NT * NF * 10), r = w - sd * NT * NF * 10;
+      const int o = r / (NF * 10), r2 = r - o * NF * 10;
+      float s = 0.f;
+      for (int z = 0; z < NT; ++z)
+        s = fmaf(taylor<N>(tb, T, z, o, dt), smem[S::oLu + (sd * NT + z) * NF * 10 + r2], s);
+      smem[S::oLo + w] = s;
+    }
+    __syncthreads();
+    // project onto the modes of each side and write the record in the (Q, D) layout
+    for (int w = threadIdx.x; w < 2 * A::LDS; w += blockDim.x) {
+      const int sd = w / A::LDS, r = w - sd * A::LDS;
+      int o, l, p;
+      bool live = true;
+      if (r < A::QS) {
+        o = 0; l = r / 10; p = r - l * 10;
+        live = l < L;
+      } else {
+        const int rd = r - A::QS;
+        if (rd >= A::AOFF) {
+          o = 1; l = rd - A::AOFF; p = 9;
+          live = l < L;
+        } else {
+          o = 1;
+          while (o < N && rd >= d_offset(N, o + 1)) ++o;
+          const int ro = rd - d_offset(N, o);
+          l = ro / 9; p = ro - l * 9;
+        }
+      }
+      float s = 0.f;
+      if (live) {
+        const float* Lo = smem + S::oLo + (sd * NT + o) * NF * 10;
+        for (int i = 0; i < NF; ++i) s = fmaf(__ldg(tb + T.VfT + (lf[sd] * L + l) * A::NFP + i), Lo[i * 10 + p], s);
+      }
+      a.rec[(f * 2 + sd) * A::RS + r] = s;
+    }
+    if (threadIdx.x < 2) {
+      const int sd = threadIdx.x;
+      // C = max(cp0, cp1): its derivative goes to the larger speed, in halves at a tie
+      const float share = cp0 > cp1 ? (sd == 0 ? 1.f : 0.f) : (cp0 < cp1 ? (sd == 1 ? 1.f : 0.f) : 0.5f);
+      float* tail = a.rec + (f * 2 + sd) * A::RS + A::LDS;
+      tail[0] = share * static_cast<float>(sRed[0]);
+      tail[1] = static_cast<float>(sRed[1 + sd]);
+      tail[2] = 0.f;
+      tail[3] = 0.f;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Elements
+// ---------------------------------------------------------------------------
+template <int N>
+struct ElemSmem {
+  using A = ADim<N>;
+  static constexpr int oLam = 0;                          // [L][10] lam^{k+1}
+  static constexpr int oQ = oLam + A::L * 10;             // [QS]
+  static constexpr int oD = oQ + A::QS;                   // [DS]
+  static constexpr int oU = oD + A::DS;                   // [NT][L][10]
+  static constexpr int oX = oU + A::NT * A::L * 10;       // [NQ][28]: w_q dphi_k/dx_d lam_kp (27), w_q phi_k lam_k9
+  static constexpr int oLu = oX + A::NQ * 28;             // [NT][NQ][10] lam of the nodal values
+  static constexpr int oLD = oLu + A::NT * A::NQ * 10;    // [QS + DS] lam of D^0..D^N
+  static constexpr int oH = oLD + A::LDS;                 // [3][L][9]
+  static constexpr int total = oH + 3 * A::L * 9;
+};
+
+template <int N>
+__global__ void __launch_bounds__(128) k_adj_elem(AdjArgs a) {
+  using A = ADim<N>;
+  using S = ElemSmem<N>;
+  constexpr int L = A::L, NQ = A::NQ, NT = A::NT;
+  extern __shared__ __align__(16) float smem[];
+  __shared__ double sRed[4];          // xi0, C_d, lam/rho, mu/rho
+  __shared__ float sGeo[16];          // Theta^{-1} [e][d], lambda_eff/rho, mu_eff/rho
+  const TableLayout T = table_layout(N);
+  const float* tb = a.tables;
+  const float dt = a.dt;
+  float* sLD = smem + S::oLD;
+  for (int64_t e = blockIdx.x; e < a.E; e += gridDim.x) {
+    __syncthreads();
+    for (int w = threadIdx.x; w < L * 10; w += blockDim.x) {
+      smem[S::oLam + w] = a.lam_in[e * A::QS + w];
+      smem[S::oQ + w] = a.q[e * A::QS + w];
+    }
+    for (int w = threadIdx.x; w < A::DS; w += blockDim.x) smem[S::oD + w] = a.d[e * A::DS + w];
+    for (int w = threadIdx.x; w < A::LDS; w += blockDim.x) sLD[w] = 0.f;
+    const MatF m = a.mat[e];
+    if (threadIdx.x < 9) sGeo[threadIdx.x] = a.geom[e].tinv[threadIdx.x];
+    if (threadIdx.x < 4) sRed[threadIdx.x] = 0.0;
+    __syncthreads();
+    taylor_values<N>(smem + S::oQ, smem + S::oD, smem + S::oU, tb, T, dt, threadIdx.x, blockDim.x);
+    // per volume node q: X[q][d][p] = sum_k w_q dphi_k/dx_d(x_q) lam[k][p], X[q][27] = sum_k w_q phi_k lam[k][9]
+    for (int w = threadIdx.x; w < NQ * 10; w += blockDim.x) {
+      const int q = w / 10, p = w - q * 10;
+      if (p < 9) {
+        float g[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < L; ++k) {
+          const float lk = smem[S::oLam + k * 10 + p];
+#pragma unroll
+          for (int ee = 0; ee < 3; ++ee) g[ee] = fmaf(__ldg(tb + T.Gw + (ee * NQ + q) * A::LP + k), lk, g[ee]);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          smem[S::oX + q * 28 + d * 9 + p] = g[0] * sGeo[0 * 3 + d] + g[1] * sGeo[1 * 3 + d] + g[2] * sGeo[2 * 3 + d];
+      } else {
+        float s = 0.f;
+        for (int k = 0; k < L; ++k) s = fmaf(__ldg(tb + T.Vw + q * A::LP + k), smem[S::oLam + k * 10 + 9], s);
+        smem[S::oX + q * 28 + 27] = s;
+      }
+    }
+    __syncthreads();
+    // the volume flux and the damage-rate source transposed at each space-time volume node
+    float px = 0.f, pc = 0.f;
+    for (int w = threadIdx.x; w < NT * NQ; w += blockDim.x) {
+      const int z = w / NQ, q = w - z * NQ;
+      const float g = __ldg(tb + T.gz + z) * dt;
+      const float* U = smem + S::oU + z * L * 10;
+      float u[10];
+#pragma unroll
+      for (int p = 0; p < 10; ++p) u[p] = 0.f;
+      for (int l = 0; l < L; ++l) {
+        const float ph = __ldg(tb + T.VvT + l * A::NQP + q);
+#pragma unroll
+        for (int p = 0; p < 10; ++p) u[p] = fmaf(ph, U[l * 10 + p], u[p]);
+      }
+      float lF[27];
+#pragma unroll
+      for (int c = 0; c < 27; ++c) lF[c] = g * smem[S::oX + q * 28 + c];
+      float lu[10];
+#pragma unroll
+      for (int p = 0; p < 10; ++p) lu[p] = 0.f;
+      px += flux_vjp(u, m, lF, lu);
+      rate_vjp(u, m, g * smem[S::oX + q * 28 + 27], lu, &px, &pc);
+      float* o = smem + S::oLu + w * 10;
+#pragma unroll
+      for (int p = 0; p < 10; ++p) o[p] = lu[p];
+    }
+    __syncthreads();
+    // lam of U(t_z), folded into lam of D^o: sum_z t_z^o/o! sum_q phi_l(x_q) Lu[z][q][p]
+    for (int w = threadIdx.x; w < A::LDS; w += blockDim.x) {
+      int o, l, p;
+      bool live = true;
+      if (w < A::QS) {
+        o = 0; l = w / 10; p = w - l * 10;
+        live = l < L;
+      } else {
+        const int rd = w - A::QS;
+        if (rd >= A::AOFF) {
+          o = 1; l = rd - A::AOFF; p = 9;
+          live = l < L;
+        } else {
+          o = 1;
+          while (o < N && rd >= d_offset(N, o + 1)) ++o;
+          const int ro = rd - d_offset(N, o);
+          l = ro / 9; p = ro - l * 9;
+        }
+      }
+      float s = 0.f;
+      if (live) {
+        for (int z = 0; z < NT; ++z) {
+          const float* Lu = smem + S::oLu + z * NQ * 10;
+          float t = 0.f;
+          for (int q = 0; q < NQ; ++q) t = fmaf(__ldg(tb + T.VvT + l * A::NQP + q), Lu[q * 10 + p], t);
+          s = fmaf(taylor<N>(tb, T, z, o, dt), t, s);
+        }
+        // the element's four face records
+        for (int fl = 0; fl < 4; ++fl) {
+          const int ef = a.elem_face[e * 4 + fl];
+          s += a.rec[static_cast<int64_t>(ef) * A::RS + w];
+        }
+      }
+      sLD[w] = s;
+    }
+    if (threadIdx.x < 4) {
+      const int ef = a.elem_face[e * 4 + threadIdx.x];
+      const float* tail = a.rec + static_cast<int64_t>(ef) * A::RS + A::LDS;
+      atomicAdd(&sRed[2], static_cast<double>(tail[0]));   // lam of cp (scaled below)
+      atomicAdd(&sRed[0], static_cast<double>(tail[1]));   // xi0 part of the face fluxes
+    }
+    block_add(&sRed[0], px);
+    block_add(&sRed[1], pc);
+    // effective Lame parameters of the cell mean (the forward predictor's rule)
+    float lam_eff, mu_eff;
+    {
+      const float r6 = 2.449489742783178f;
+      float ub[10];
+#pragma unroll
+      for (int p = 0; p < 10; ++p) ub[p] = smem[S::oQ + p] * r6;
+      const Inv v = invariants(ub);
+      lam_eff = m.lam0 - ub[9] * m.gamma_r * v.xi * (1.f / 3.f);
+      mu_eff = m.mu0 + ub[9] * m.xi0 * m.gamma_r - 0.5f * ub[9] * m.gamma_r * v.xi;
+    }
+    if (threadIdx.x == 0) {
+      sGeo[9] = lam_eff * m.rho_inv;
+      sGeo[10] = mu_eff * m.rho_inv;
+    }
+    __syncthreads();
+    // the cp part: cp = sqrt((lambda + 2 mu) / rho)
+    const double lam_cp = sRed[2];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const float cp = a.cp[e];
+      const float dc = (lam_eff + 2.f * mu_eff > 0.f && cp > 0.f) ? static_cast<float>(lam_cp) * 0.5f * m.rho_inv / cp : 0.f;
+      sRed[2] = static_cast<double>(dc) * m.rho;        // in units of lam/rho: d/d(lam/rho) = rho d/dlam
+      sRed[3] = static_cast<double>(2.f * dc) * m.rho;
+    }
+    __syncthreads();
+
+    // Cauchy-Kovalevskaya recursion transposed, order N down to 1
+    const float lr = sGeo[9], mr = sGeo[10];
+    for (int i = N; i >= 1; --i) {
+      const int Lout = n_modes(N - i), Lin = n_modes(N - i + 1);
+      const float* lDi = sLD + A::QS + d_offset(N, i);       // [Lout][9]
+      const float* Dprev = i == 1 ? smem + S::oQ : smem + S::oD + d_offset(N, i - 1);
+      const int sp = i == 1 ? 10 : 9;
+      float* lDprev = i == 1 ? sLD : sLD + A::QS + d_offset(N, i - 1);
+      const int lsp = i == 1 ? 10 : 9;
+      float plr = 0.f, pmr = 0.f;
+      for (int k = threadIdx.x; k < Lout; k += blockDim.x) {
+        float lv[9];
+#pragma unroll
+        for (int p = 0; p < 9; ++p) lv[p] = lDi[k * 9 + p];
+        // Psi_d = B^d^T lam (q < 9)
+        float psi[3][9];
+        psi[0][6] = -lv[0]; psi[0][7] = -0.5f * lv[3]; psi[0][8] = -0.5f * lv[5];
+        psi[1][6] = -0.5f * lv[3]; psi[1][7] = -lv[1]; psi[1][8] = -0.5f * lv[4];
+        psi[2][6] = -0.5f * lv[5]; psi[2][7] = -0.5f * lv[4]; psi[2][8] = -lv[2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float ld = lv[6 + d];
+          psi[d][0] = psi[d][1] = psi[d][2] = -lr * ld;
+          psi[d][3] = psi[d][4] = psi[d][5] = 0.f;
+        }
+        psi[0][0] += -2.f * mr * lv[6]; psi[0][3] += -2.f * mr * lv[7]; psi[0][5] += -2.f * mr * lv[8];
+        psi[1][3] += -2.f * mr * lv[6]; psi[1][1] += -2.f * mr * lv[7]; psi[1][4] += -2.f * mr * lv[8];
+        psi[2][5] += -2.f * mr * lv[6]; psi[2][4] += -2.f * mr * lv[7]; psi[2][2] += -2.f * mr * lv[8];
+#pragma unroll
+        for (int ee = 0; ee < 3; ++ee)
+#pragma unroll
+          for (int q = 0; q < 9; ++q)
+            smem[S::oH + (ee * L + k) * 9 + q] =
+                sGeo[ee * 3 + 0] * psi[0][q] + sGeo[ee * 3 + 1] * psi[1][q] + sGeo[ee * 3 + 2] * psi[2][q];
+        // the star matrices' dependence on lambda/rho and mu/rho:
+        // Gx[d][q] = sum_e Theta^{-1}_ed sum_l Kt^e_kl D^{i-1}_lq
+        float gk[3][9];
+#pragma unroll
+        for (int ee = 0; ee < 3; ++ee)
+#pragma unroll
+          for (int q = 0; q < 9; ++q) gk[ee][q] = 0.f;
+        for (int l = 0; l < Lin; ++l) {
+#pragma unroll
+          for (int ee = 0; ee < 3; ++ee) {
+            const float kt = __ldg(tb + T.KtA + (ee * L + l) * A::LP + k);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) gk[ee][q] = fmaf(kt, Dprev[l * sp + q], gk[ee][q]);
+          }
+        }
+        float gx[3][9];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int q = 0; q < 9; ++q)
+            gx[d][q] = sGeo[0 * 3 + d] * gk[0][q] + sGeo[1 * 3 + d] * gk[1][q] + sGeo[2 * 3 + d] * gk[2][q];
+        // d/d(lam/rho): B^d_{6+d, q<3} = -lam/rho; d/d(mu/rho): B^d_{6+i, sym(i,d)} = -2 mu/rho
+#pragma unroll
+        for (int d = 0; d < 3; ++d) plr += (gx[d][0] + gx[d][1] + gx[d][2]) * lv[6 + d];
+        pmr += 2.f * (gx[0][0] * lv[6] + gx[0][3] * lv[7] + gx[0][5] * lv[8] +
+                      gx[1][3] * lv[6] + gx[1][1] * lv[7] + gx[1][4] * lv[8] +
+                      gx[2][5] * lv[6] + gx[2][4] * lv[7] + gx[2][2] * lv[8]);
+      }
+      block_add(&sRed[2], plr);
+      block_add(&sRed[3], pmr);
+      __syncthreads();
+      // lam D^{i-1}_lq -= sum_e sum_k Kt^e_kl H[e][k][q]
+      for (int w = threadIdx.x; w < Lin * 9; w += blockDim.x) {
+        const int l = w / 9, q = w - l * 9;
+        float s = 0.f;
+        for (int k = 0; k < Lout; ++k)
+#pragma unroll
+          for (int ee = 0; ee < 3; ++ee)
+            s = fmaf(__ldg(tb + T.KtA + (ee * L + l) * A::LP + k), smem[S::oH + (ee * L + k) * 9 + q], s);
+        lDprev[l * lsp + q] -= s;
+      }
+      __syncthreads();
+    }
+    // damage-rate source of D^1 from the state at t_n: lam_r(q) = sum_k w_q phi_k(x_q) lam D^1_k9
+    {
+      float* sLu0 = smem + S::oLu;                           // [NQ][6] (reuses the nodal lam)
+      float pxr = 0.f, pcr = 0.f;
+      for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
+        float u[10];
+#pragma unroll
+        for (int p = 0; p < 10; ++p) u[p] = 0.f;
+        float lrq = 0.f;
+        for (int l = 0; l < L; ++l) {
+          const float ph = __ldg(tb + T.VvT + l * A::NQP + q);
+#pragma unroll
+          for (int p = 0; p < 6; ++p) u[p] = fmaf(ph, smem[S::oQ + l * 10 + p], u[p]);
+          lrq = fmaf(__ldg(tb + T.Vw + q * A::LP + l), sLD[A::QS + A::AOFF + l], lrq);
+        }
+        float lu[10];
+#pragma unroll
+        for (int p = 0; p < 10; ++p) lu[p] = 0.f;
+        rate_vjp(u, m, lrq, lu, &pxr, &pcr);
+#pragma unroll
+        for (int p = 0; p < 6; ++p) sLu0[q * 6 + p] = lu[p];
+      }
+      block_add(&sRed[0], pxr);
+      block_add(&sRed[1], pcr);
+      __syncthreads();
+      for (int w = threadIdx.x; w < L * 6; w += blockDim.x) {
+        const int l = w / 6, p = w - l * 6;
+        float s = 0.f;
+        for (int q = 0; q < NQ; ++q) s = fmaf(__ldg(tb + T.VvT + l * A::NQP + q), sLu0[q * 6 + p], s);
+        sLD[l * 10 + p] += s;
+      }
+      __syncthreads();
+    }
+    // the cell mean: lambda_eff and mu_eff (and through them cp) at ubar = sqrt(6) Q_0
+    if (threadIdx.x == 0) {
+      const float r6 = 2.449489742783178f;
+      float ub[10];
+#pragma unroll
+      for (int p = 0; p < 10; ++p) ub[p] = smem[S::oQ + p] * r6;
+      const Inv v = invariants(ub);
+      const float al = static_cast<float>(sRed[2]) * m.rho_inv;   // d/dlambda_eff
+      const float am = static_cast<float>(sRed[3]) * m.rho_inv;   // d/dmu_eff
+      const float wv = al * (1.f / 3.f) + 0.5f * am;
+      const float ag = ub[9] * m.gamma_r;
+#pragma unroll
+      for (int p = 0; p < 6; ++p) sLD[p] += r6 * (-ag * wv * v.dxi[p]);
+      sLD[9] += r6 * (-m.gamma_r * v.xi * wv + am * m.xi0 * m.gamma_r);
+      sRed[0] += static_cast<double>(am * ag);
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < A::QS; w += blockDim.x)
+      a.lam_out[e * A::QS + w] = w < L * 10 ? smem[S::oLam + w] + sLD[w] : 0.f;
+    if (threadIdx.x == 0) {
+      a.g_xi0[e] += sRed[0];
+      a.g_cd[e] += sRed[1];
+    }
+  }
+}
+
+}  // namespace adj
+
+template <int N>
+cudaError_t launch_adjoint_t(const AdjArgs& a, cudaStream_t s) {
+  using SF = adj::FaceSmem<N>;
+  using SE = adj::ElemSmem<N>;
+  const size_t bf = sizeof(float) * SF::total, be = sizeof(float) * SE::total;
+  cudaError_t err = cudaFuncSetAttribute(adj::k_adj_face<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bf));
+  if (err != cudaSuccess) return err;
+  err = cudaFuncSetAttribute(adj::k_adj_elem<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(be));
+  if (err != cudaSuccess) return err;
+  const int gf = static_cast<int>(a.F < 152 * 64 ? a.F : 152 * 64);
+  const int ge = static_cast<int>(a.E < 152 * 64 ? a.E : 152 * 64);
+  if (gf > 0) adj::k_adj_face<N><<<gf, 128, bf, s>>>(a);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  if (ge > 0) adj::k_adj_elem<N><<<ge, 128, be, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dg

@@ -14,6 +14,7 @@
 
 #include "dg_internal.h"
 #include "dg_reference.h"
+#include "dg_revolve.h"
 
 using namespace dg;
 
@@ -1228,6 +1229,236 @@ dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) 
   ctx->stats.steps += 1;
   ctx->stats.kernel_launches += launches;
   ctx->stats.element_updates += ctx->EV;
+  const unsigned st = *ctx->status_host;
+  if (st & kStatusNonFinite) return fail(ctx, DG_E_NONFINITE, "non-finite value in the state");
+  if (st & kStatusNonHyperbolic) return fail(ctx, DG_E_NONHYPERBOLIC, "effective moduli lost hyperbolicity");
+  if (st & kStatusIndex) return fail(ctx, DG_E_MESH, "neighbour index out of range");
+  if (st & kStatusTimeout) return fail(ctx, DG_E_CUDA, "a bounded wait on the tensor cores timed out");
+  return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Discrete adjoint with binomial checkpointing
+// ---------------------------------------------------------------------------
+dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const float* ref, int snapshots,
+                              double* misfit, double* grad_xi0, double* grad_cd, double* grad_q0,
+                              dg_adjoint_info* info) {
+  if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
+  if (n_steps < 1 || n_steps > (int64_t(1) << 20)) return fail(ctx, DG_E_ARG, "n_steps must be in 1..2^20");
+  if (!ref || !misfit) return fail(ctx, DG_E_ARG, "NULL reference traces or misfit");
+  if (snapshots < 1 || snapshots > 4096) return fail(ctx, DG_E_ARG, "snapshots must be in 1..4096");
+  if (!ctx->has_material || !ctx->has_state) return fail(ctx, DG_E_STATE, "material and state must be set");
+  if (ctx->law != 0) return fail(ctx, DG_E_UNSUPPORTED, "the adjoint covers the CDM law");
+  if (ctx->picard_iters > 0) return fail(ctx, DG_E_UNSUPPORTED, "the adjoint covers the CK predictor");
+  if (ctx->M != 1) return fail(ctx, DG_E_UNSUPPORTED, "the adjoint covers one member");
+  if (ctx->F > ctx->F_interior) return fail(ctx, DG_E_UNSUPPORTED, "the adjoint covers meshes without boundary faces");
+  const int R = static_cast<int>(ctx->rec_host.size());
+  if (R < 1) return fail(ctx, DG_E_STATE, "the misfit needs receivers (dg_receivers)");
+  if (dt <= 0) dt = ctx->dt_cfl;
+  if (!std::isfinite(dt)) return fail(ctx, DG_E_ARG, "non-finite dt");
+  const int s_free = snapshots - 1;
+  if (revolve_cost(n_steps, s_free) > kMaxRevolveSteps)
+    return fail(ctx, DG_E_ARG, "too few snapshots for this many steps");
+  int64_t fw_plan = 0;
+  const std::vector<RevolveAction> plan = revolve_plan(n_steps, snapshots, &fw_plan);
+  {
+    dg_status st = prepare_steps(ctx, n_steps, dt);
+    if (st != DG_OK) return st;
+  }
+  const int N = ctx->N;
+  const int64_t E = ctx->EV, QS = q_stride(N);
+  const size_t state_bytes = sizeof(float) * static_cast<size_t>(E * QS);
+  const int nsrc = static_cast<int>(ctx->source_host.size());
+
+  // device buffers of the call: snapshot slots, two current states, the state after the
+  // last step, two adjoint states, face records, gradients, misfit, reference traces
+  std::vector<void*> bufs;
+  auto take = [&](size_t bytes) -> void* {
+    void* p = dev_alloc(ctx, bytes);
+    if (p) bufs.push_back(p);
+    return p;
+  };
+  auto release = [&]() {
+    for (void* p : bufs) dev_free(ctx, p);
+    bufs.clear();
+  };
+  float* slots = static_cast<float*>(take(state_bytes * static_cast<size_t>(snapshots)));
+  float* work[2] = {static_cast<float*>(take(state_bytes)), static_cast<float*>(take(state_bytes))};
+  float* last = static_cast<float*>(take(state_bytes));
+  float* lam[2] = {static_cast<float*>(take(state_bytes)), static_cast<float*>(take(state_bytes))};
+  float* rec = static_cast<float*>(take(sizeof(float) * static_cast<size_t>(ctx->F_interior * 2 * adj_rec_stride(N))));
+  double* g = static_cast<double*>(take(sizeof(double) * static_cast<size_t>(2 * E + 1)));
+  float* ref_dev = static_cast<float*>(take(sizeof(float) * static_cast<size_t>(n_steps * R * 3)));
+  if (!slots || !work[0] || !work[1] || !last || !lam[0] || !lam[1] || !rec || !g || !ref_dev) {
+    release();
+    return fail(ctx, DG_E_OOM, "adjoint buffers");
+  }
+  double* g_xi0 = g;
+  double* g_cd = g + E;
+  double* J = g + 2 * E;
+#define ADJ_CUDA(call)                                         \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) {                                   \
+      release();                                               \
+      return cuda_fail(ctx, e_, #call);                        \
+    }                                                          \
+  } while (0)
+  ADJ_CUDA(cudaMemcpyAsync(ref_dev, ref, sizeof(float) * n_steps * R * 3, cudaMemcpyHostToDevice, ctx->stream));
+  ADJ_CUDA(cudaMemsetAsync(g, 0, sizeof(double) * (2 * E + 1), ctx->stream));
+  ADJ_CUDA(cudaMemsetAsync(lam[0], 0, state_bytes, ctx->stream));
+  ADJ_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream));
+  ADJ_CUDA(cudaMemcpyAsync(slots, ctx->q[ctx->cur], state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+
+  StepArgs a{};
+  a.E = E;
+  a.F = ctx->F;
+  a.has_boundary = 0;
+  a.d = ctx->d;
+  a.cp = ctx->cp;
+  a.ff = ctx->ff;
+  a.faces = ctx->faces;
+  a.elem_face = ctx->elem_face;
+  a.grid_pred = ctx->grid_pred;
+  a.grid_face = ctx->grid_face;
+  a.grid_corr = ctx->grid_corr;
+  a.law = 0;
+  a.picard_iters = 0;
+  a.geom = ctx->geom;
+  a.mat = ctx->matf;
+  a.nbr = ctx->nbr;
+  a.tables = ctx->tables;
+  a.dt = static_cast<float>(dt);
+  a.status = ctx->status;
+  AdjArgs b{};
+  b.E = E;
+  b.F = ctx->F_interior;
+  b.d = ctx->d;
+  b.cp = ctx->cp;
+  b.rec = rec;
+  b.g_xi0 = g_xi0;
+  b.g_cd = g_cd;
+  b.geom = ctx->geom;
+  b.mat = ctx->matf;
+  b.faces = ctx->faces;
+  b.elem_face = ctx->elem_face;
+  b.tables = ctx->tables;
+  b.dt = static_cast<float>(dt);
+
+  int64_t launches = 0;
+  // one forward step of the state in `in` (step index s) into `out`
+  auto forward = [&](const float* in, float* out, int64_t s) -> cudaError_t {
+    a.q_in = in;
+    a.q_out = out;
+    cudaError_t e = launch_predictor(N, a, ctx->stream);
+    if (e == cudaSuccess) e = launch_faces(N, a, ctx->stream);
+    if (e == cudaSuccess) e = launch_corrector(N, a, ctx->stream);
+    launches += 3;
+    if (e == cudaSuccess && nsrc > 0) {
+      e = launch_sources(N, nsrc, ctx->source_dev, ctx->amp_dev, s, out, ctx->stream);
+      ++launches;
+    }
+    return e;
+  };
+  // per-action timing (info requested): one event after each action
+  std::vector<cudaEvent_t> evs;
+  std::vector<int> ev_kind;
+  if (info) {
+    evs.resize(plan.size() + 1);
+    for (auto& ev : evs) ADJ_CUDA(cudaEventCreate(&ev));
+    ADJ_CUDA(cudaEventRecord(evs[0], ctx->stream));
+  }
+  int cb = 0;
+  int64_t cur_step = -1, fw_done = 0, adj_done = 0;
+  int li = 0;                       // lam[li] holds dJ/dQ^{j+1} before the adjoint of step j
+  bool seeded = false;
+  for (size_t ai = 0; ai < plan.size(); ++ai) {
+    const RevolveAction& act = plan[ai];
+    switch (act.kind) {
+      case kRestore:
+        if (cur_step != act.b) {
+          ADJ_CUDA(cudaMemcpyAsync(work[cb], slots + static_cast<size_t>(act.a) * E * QS, state_bytes,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+          cur_step = act.b;
+        }
+        break;
+      case kStore:
+        ADJ_CUDA(cudaMemcpyAsync(slots + static_cast<size_t>(act.a) * E * QS, work[cb], state_bytes,
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+        break;
+      case kAdvance:
+        for (int64_t s = act.a; s < act.b; ++s) {
+          ADJ_CUDA(forward(work[cb], work[1 - cb], s));
+          cb = 1 - cb;
+          ++fw_done;
+        }
+        cur_step = act.b;
+        break;
+      case kAdjoint: {
+        const int64_t j = act.a;
+        if (!seeded) {
+          // the state after the last step and its misfit term seed dJ/dQ^n
+          ADJ_CUDA(forward(work[cb], last, j));
+          ++fw_done;
+          ADJ_CUDA(launch_misfit(N, R, ctx->rec_dev, last, ref_dev + (n_steps - 1) * R * 3, static_cast<float>(dt),
+                                 J, lam[li], ctx->stream));
+          ++launches;
+          seeded = true;
+        }
+        a.q_in = work[cb];
+        ADJ_CUDA(launch_predictor(N, a, ctx->stream));
+        b.q = work[cb];
+        b.lam_in = lam[li];
+        b.lam_out = lam[1 - li];
+        ADJ_CUDA(launch_adjoint(N, b, ctx->stream));
+        launches += 3;
+        if (j >= 1) {
+          ADJ_CUDA(launch_misfit(N, R, ctx->rec_dev, work[cb], ref_dev + (j - 1) * R * 3, static_cast<float>(dt), J,
+                                 lam[1 - li], ctx->stream));
+          ++launches;
+        }
+        li = 1 - li;
+        ++adj_done;
+        break;
+      }
+    }
+    if (info) ADJ_CUDA(cudaEventRecord(evs[ai + 1], ctx->stream));
+  }
+  // results
+  double Jh = 0.0;
+  ADJ_CUDA(cudaMemcpyAsync(&Jh, J, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (grad_xi0) ADJ_CUDA(cudaMemcpyAsync(grad_xi0, g_xi0, sizeof(double) * E, cudaMemcpyDeviceToHost, ctx->stream));
+  if (grad_cd) ADJ_CUDA(cudaMemcpyAsync(grad_cd, g_cd, sizeof(double) * E, cudaMemcpyDeviceToHost, ctx->stream));
+  if (grad_q0) {
+    const size_t n = static_cast<size_t>(E) * kFields * ctx->L;
+    dg_status st = ensure_staging(ctx, n * 8);
+    if (st != DG_OK) {
+      release();
+      return st;
+    }
+    ADJ_CUDA(launch_state_out(N, ctx->E, 1, lam[li], ctx->staging, 1, ctx->stream));
+    ADJ_CUDA(cudaMemcpyAsync(grad_q0, ctx->staging, n * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  ADJ_CUDA(cudaMemcpyAsync(ctx->status_host, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+  ADJ_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (info) {
+    info->forward_steps = fw_done;
+    info->adjoint_steps = adj_done;
+    info->forward_ms = info->adjoint_ms = info->copy_ms = 0.0;
+    for (size_t ai = 0; ai < plan.size(); ++ai) {
+      float ms = 0.f;
+      ADJ_CUDA(cudaEventElapsedTime(&ms, evs[ai], evs[ai + 1]));
+      const int k = plan[ai].kind;
+      if (k == kAdvance) info->forward_ms += ms;
+      else if (k == kAdjoint) info->adjoint_ms += ms;
+      else info->copy_ms += ms;
+    }
+    for (auto& ev : evs) cudaEventDestroy(ev);
+  }
+#undef ADJ_CUDA
+  release();
+  *misfit = Jh;
+  ctx->stats.kernel_launches += launches;
   const unsigned st = *ctx->status_host;
   if (st & kStatusNonFinite) return fail(ctx, DG_E_NONFINITE, "non-finite value in the state");
   if (st & kStatusNonHyperbolic) return fail(ctx, DG_E_NONHYPERBOLIC, "effective moduli lost hyperbolicity");

@@ -190,6 +190,35 @@ struct ReceiverDev {
 cudaError_t launch_receivers(int N, int n_rec, const ReceiverDev* rec, const float* q,
                              float* traces_row, cudaStream_t s);
 
+// Discrete adjoint of one step (dg_adjoint.cu).  A face record holds, per face
+// and side, lam of that side's D^0..D^N in the (Q, D) layout (q_stride floats of
+// order 0, then d_stride floats of the higher orders) and four scalars: lam of the
+// side's P speed and the xi0 part of the side's flux.
+__host__ __device__ constexpr int adj_rec_stride(int N) { return q_stride(N) + d_stride(N) + 4; }
+struct AdjArgs {
+  int64_t E, F;           // elements, interior faces
+  const float* q;         // Q^k [E][q_stride]
+  const float* d;         // predictor output of Q^k [E][d_stride]
+  const float* cp;        // effective P speeds of Q^k [E]
+  const float* lam_in;    // dJ/dQ^{k+1} [E][q_stride]
+  float* lam_out;         // dJ/dQ^k [E][q_stride]
+  float* rec;             // [F][2][adj_rec_stride]
+  double* g_xi0;          // [E] dJ/dxi0, accumulated
+  double* g_cd;           // [E] dJ/dC_d, accumulated
+  const GeomF* geom;
+  const MatF* mat;
+  const int4* faces;
+  const int* elem_face;
+  const float* tables;
+  float dt;
+};
+template <int N> cudaError_t launch_adjoint_t(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint(int N, const AdjArgs& a, cudaStream_t s);
+// Receiver misfit at one state: res = v_r(q) - ref[r] for every receiver and
+// component; adds 0.5 dt res^2 to *J (FP64) and dt phi_l(xi_r) res to lam[e_r].
+cudaError_t launch_misfit(int N, int n_rec, const ReceiverDev* rec, const float* q, const float* ref, float dt,
+                          double* J, float* lam, cudaStream_t s);
+
 // Read-only view of a context for the allocation-free step (dg_noalloc.cu).
 struct NoAllocView {
   int N;

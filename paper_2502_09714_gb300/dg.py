@@ -25,6 +25,7 @@ EXPORTS = (
     "dg_receivers", "dg_receivers_read", "dg_dt", "dg_time", "dg_n_modes", "dg_get_stats",
     "dg_profile_enable", "dg_profile_read", "dg_reference_table", "dg_last_error", "dg_destroy",
     "dg_step_noalloc", "dg_set_rheology", "dg_set_predictor", "dg_step_host",
+    "dg_adjoint_gradient", "dg_revolve_plan", "dg_revolve_cost",
 )
 
 
@@ -61,6 +62,11 @@ class Stats(C.Structure):
 
 class KernelTime(C.Structure):
     _fields_ = [("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
+class AdjointInfo(C.Structure):
+    _fields_ = [("forward_steps", C.c_int64), ("adjoint_steps", C.c_int64), ("forward_ms", C.c_double),
+                ("adjoint_ms", C.c_double), ("copy_ms", C.c_double)]
 
 
 _LIB = None
@@ -102,6 +108,10 @@ def load_library(path: str | None = None) -> C.CDLL:
         "dg_last_error": ([vp], C.c_char_p),
         "dg_destroy": ([vp], None),
         "dg_step_noalloc": ([vp, vp, vp, dbl], C.c_int),
+        "dg_adjoint_gradient": ([vp, i64, dbl, C.POINTER(C.c_float), C.c_int, C.POINTER(dbl), C.POINTER(dbl),
+                                 C.POINTER(dbl), C.POINTER(dbl), C.POINTER(AdjointInfo)], C.c_int),
+        "dg_revolve_plan": ([i64, C.c_int, C.POINTER(i64), C.POINTER(i64), i64, C.POINTER(i64)], C.c_int),
+        "dg_revolve_cost": ([i64, C.c_int], i64),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -127,6 +137,23 @@ def reference_table(order: int, which: int) -> np.ndarray:
     out = np.empty(count.value)
     _check(lib, None, lib.dg_reference_table(order, which, _ptr(out, C.c_double), out.size, C.byref(count)))
     return out
+
+
+def revolve_plan(n_steps: int, snapshots: int):
+    """(forward steps, actions [n, 3] of (kind, a, b)) of the checkpointing plan
+    (kind 0 advance a -> b, 1 store slot a <- step b, 2 restore slot a (step b),
+    3 adjoint of step a)."""
+    lib = load_library()
+    fw, n = C.c_int64(0), C.c_int64(0)
+    _check(lib, None, lib.dg_revolve_plan(int(n_steps), int(snapshots), C.byref(fw), None, 0, C.byref(n)))
+    acts = np.empty((n.value, 3), dtype=np.int64)
+    _check(lib, None, lib.dg_revolve_plan(int(n_steps), int(snapshots), C.byref(fw), _ptr(acts, C.c_int64),
+                                          n.value, C.byref(n)))
+    return fw.value, acts
+
+
+def revolve_cost(n_steps: int, snapshots: int) -> int:
+    return int(load_library().dg_revolve_cost(int(n_steps), int(snapshots)))
 
 
 def _check(lib, ctx, status):
@@ -321,6 +348,32 @@ class Solver:
         self._chk(self.lib.dg_get_stats(self.ctx, C.byref(s)))
         return {"steps": s.steps, "kernel_launches": s.kernel_launches, "element_updates": s.element_updates}
 
+    def adjoint_gradient(self, ref, n_steps, dt=0.0, snapshots=40, grad_state=False, info=False):
+        """Receiver misfit J of n_steps steps from the current state against
+        ref [n_steps, R, 3] and its gradient by the discrete adjoint with
+        binomial checkpointing (`snapshots` state copies).  Returns
+        (J, dJ/dxi0 [E], dJ/dC_d [E]) plus dJ/dQ^0 [E, 10, L] with grad_state and
+        the run's counts and device times (a dict) with info.  The state, time and
+        traces of the solver are left unchanged."""
+        r = np.ascontiguousarray(ref, dtype=np.float32)
+        assert r.shape == (int(n_steps), self.R, 3), r.shape
+        J = C.c_double(0.0)
+        gx = np.empty(self.E)
+        gc = np.empty(self.E)
+        gq = np.empty((self.E, 10, self.L)) if grad_state else None
+        inf = AdjointInfo()
+        self._chk(self.lib.dg_adjoint_gradient(self.ctx, int(n_steps), float(dt), _ptr(r, C.c_float), int(snapshots),
+                                               C.byref(J), _ptr(gx, C.c_double), _ptr(gc, C.c_double),
+                                               _ptr(gq, C.c_double) if gq is not None else None,
+                                               C.byref(inf) if info else None))
+        out = [J.value, gx, gc]
+        if grad_state:
+            out.append(gq)
+        if info:
+            out.append({"forward_steps": inf.forward_steps, "adjoint_steps": inf.adjoint_steps,
+                        "forward_ms": inf.forward_ms, "adjoint_ms": inf.adjoint_ms, "copy_ms": inf.copy_ms})
+        return tuple(out)
+
     def profile(self, on=True):
         self._chk(self.lib.dg_profile_enable(self.ctx, int(on)))
 
@@ -330,3 +383,32 @@ class Solver:
         self._chk(self.lib.dg_profile_read(self.ctx, out, 5, C.byref(n)))
         names = ("predictor", "corrector", "source", "receivers", "faces")
         return {names[k]: {"launches": out[k].launches, "total_ms": out[k].total_ms} for k in range(n.value)}
+
+
+def misfit_function():
+    """torch.autograd.Function of the receiver misfit in the per-element damage
+    parameters: MisfitFn.apply(xi0, cd, solver, material, ref, n_steps, dt,
+    snapshots) sets rows 4 and 5 of `material` [E, 6] from the tensors xi0 [E]
+    and cd [E] (FP64), runs dg_adjoint_gradient from the solver's current state
+    and returns J as a 0-d FP64 tensor; backward gives grad_J * dJ/dxi0 and
+    grad_J * dJ/dC_d.  The gradient is computed with J (one call of the adjoint),
+    so backward only scales it."""
+    import torch
+
+    class MisfitFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, xi0, cd, solver, material, ref, n_steps, dt, snapshots):
+            mat = np.array(material, dtype=np.float64, copy=True)
+            mat[:, 4] = xi0.detach().cpu().numpy()
+            mat[:, 5] = cd.detach().cpu().numpy()
+            solver.set_material(mat)
+            J, gx, gc = solver.adjoint_gradient(ref, n_steps, dt, snapshots)
+            ctx.save_for_backward(torch.from_numpy(gx).to(xi0.device), torch.from_numpy(gc).to(cd.device))
+            return torch.tensor(J, dtype=torch.float64, device=xi0.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            gx, gc = ctx.saved_tensors
+            return grad * gx, grad * gc, None, None, None, None, None, None
+
+    return MisfitFn

@@ -164,7 +164,8 @@ def workload_adjoint(n=24, side=4000.0, order=3, n_receivers=32, steps=800, m0=C
     n = 24) at degree 3 in homogeneous rock, the c2 dip-slip point source, 32
     receivers on a jittered 4 x 8 grid at three quarters of the height, and
     per-element damage parameters drawn with `seed`: xi0 ~ U[-1.0, -0.6] and
-    log C_d ~ U[log 3e-5, log 3e-4] ("material").  The reference run that makes
+    log C_d ~ U[log 2e-6, log 2e-5] ("material"), which keeps the damage near the
+    source below ~0.3 over the 800 steps.  The reference run that makes
     the traces to be fitted uses "material_ref": xi0 + 0.05 N(0, 1) and
     C_d exp(0.3 N(0, 1)), drawn with seed + 1."""
     mesh = periodic_cube_mesh(n, side, jitter=0.1, seed=1, sort_by_vid=True)
@@ -172,7 +173,7 @@ def workload_adjoint(n=24, side=4000.0, order=3, n_receivers=32, steps=800, m0=C
     rng = np.random.default_rng(seed)
     mat = rock_material(E)
     mat[:, 4] = rng.uniform(-1.0, -0.6, size=E)
-    mat[:, 5] = np.exp(rng.uniform(np.log(3e-5), np.log(3e-4), size=E))
+    mat[:, 5] = np.exp(rng.uniform(np.log(2e-6), np.log(2e-5), size=E))
     rng2 = np.random.default_rng(seed + 1)
     ref = mat.copy()
     ref[:, 4] += 0.05 * rng2.normal(size=E)

@@ -146,8 +146,8 @@ def test_misfit_gradient_against_finite_differences():
     rng = np.random.default_rng(21)
     deg = np.array([sum(mm) for mm in mode_list(N)])
     Q0 = rng.normal(size=(m.n_elem, o.L, 10)) * (0.5 ** deg)[None, :, None]
-    Q0[..., :6] *= 1e-3
-    Q0[..., 6:9] *= 3.0
+    Q0[..., :6] *= 2e-4
+    Q0[..., 6:9] *= 0.6
     Q0[..., 9] = 0.0
     for oo in (o, oref):
         oo.set_receivers(w["receivers"])
