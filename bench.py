@@ -210,6 +210,11 @@ def main():
                     help="c2: 196,608-tet two-layer cube (the benchmark); c3: ~4.35 M-tet regional-shaped box")
     ap.add_argument("--ensemble-members", type=int, default=0,
                     help="also time the ensemble workload (N=3, this many members) against one member")
+    ap.add_argument("--adjoint-steps", type=int, default=800,
+                    help="steps of the adjoint workload (82,944 tets, N=3, 40 snapshots) whose gradient is "
+                         "timed against its forward step; 0 skips it")
+    ap.add_argument("--adjoint-n", type=int, default=24,
+                    help="cells per cube side of the adjoint workload (24 -> 82,944 tets)")
     ap.add_argument("--picard-iterations", type=int, default=0,
                     help="run the Picard predictor with this many iterations after the CK one (0: CK alone); "
                          "the flop counts stay the CK step's")
@@ -329,6 +334,8 @@ def main():
     }
     if args.ensemble_members > 1:
         line["ensemble"] = run_ensemble(args, dgpkg, torch, stream)
+    if args.adjoint_steps > 0:
+        line["adjoint"] = run_adjoint(args, dgpkg, torch, stream)
     if not args.no_cpu_baseline and world == 1:
         v, sample, threads, _ = cpu_baseline(w, steps=1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
@@ -373,6 +380,54 @@ def run_ensemble(args, dgpkg, torch, stream, steps=10, warmup=3):
     return {"workload": w["name"], "members": M, "order": N, "elements": E, "steps": steps,
             "member_updates_per_s": rate[M], "single_member_updates_per_s": rate[1],
             "per_member_ratio": rate[M] / rate[1]}
+
+
+def run_adjoint(args, dgpkg, torch, stream, snapshots=40, fwd_steps=50):
+    """Cost of the receiver-misfit gradient (discrete adjoint with binomial
+    checkpointing) on the adjoint workload against the forward step of the same
+    mesh: the reference traces come from an untimed run with the perturbed
+    parameters; the forward step is timed over fwd_steps steps, the gradient as
+    one dg_adjoint_gradient call after a short warm-up call."""
+    from synthetic import workload_adjoint
+    n = args.adjoint_steps
+    w = workload_adjoint(n=args.adjoint_n, steps=n)
+    mesh, N = w["mesh"], w["order"]
+    E, L = mesh.n_elem, n_modes(N)
+    s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, N, cfl=w["cfl"], stream=stream)
+    zero = np.zeros((E, 10, L), np.float32)
+    s.set_material(w["material_ref"])
+    s.set_sources(w["sources"])
+    s.set_receivers(w["receivers"])
+    s.set_state(zero, 0.0)
+    dt = s.dt
+    s.step(n, dt)
+    ref = s.read_receivers()[:n]
+    s.set_material(w["material"])
+    s.set_state(zero, 0.0)
+    s.step(5, dt)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(fwd_steps, dt)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(ev1) / fwd_steps
+    s.set_state(zero, 0.0)
+    k = min(n, 20)
+    s.adjoint_gradient(ref[:k], k, dt, snapshots=min(snapshots, k))
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    J, gx, gc, info = s.adjoint_gradient(ref, n, dt, snapshots=snapshots, info=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    total = ev0.elapsed_time(ev1)
+    s.close()
+    adj = info["adjoint_ms"] / info["adjoint_steps"]
+    return {"workload": w["name"], "elements": E, "order": N, "steps": n, "snapshots": snapshots,
+            "forward_ms_per_step": fwd_ms, "adjoint_ms_per_step": adj, "adjoint_to_forward_step": adj / fwd_ms,
+            "forward_steps_run": info["forward_steps"], "snapshot_copy_ms": info["copy_ms"],
+            "gradient_ms": total, "gradient_to_forward_run": total / (n * fwd_ms), "misfit": J,
+            "max_abs_grad_xi0": float(np.abs(gx).max()), "max_abs_grad_cd": float(np.abs(gc).max())}
 
 
 def _kernel_name(kind, N):

@@ -137,30 +137,65 @@ __device__ __forceinline__ void block_add(double* acc, float v) {
   if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(acc, static_cast<double>(v));
 }
 
-// Taylor coefficient t^o / o! of order o at time node z (t = tz dt).
+// Taylor coefficients c[z][o] = (tz_z dt)^o / o! and time weights gz_z dt of the
+// step, once per CTA.
 template <int N>
-__device__ __forceinline__ float taylor(const float* tb, const TableLayout& T, int z, int o, float dt) {
-  const float t = __ldg(tb + T.tz + z) * dt;
-  float c = 1.f;
-  for (int j = 1; j <= o; ++j) c *= t / static_cast<float>(j);
-  return c;
+__device__ __forceinline__ void time_tables(const float* tb, const TableLayout& T, float dt, float* sC, float* sG) {
+  constexpr int NT = N + 1;
+  if (threadIdx.x < NT) {
+    const int z = threadIdx.x;
+    const float t = __ldg(tb + T.tz + z) * dt;
+    float c = 1.f;
+    for (int o = 0; o < NT; ++o) {
+      if (o > 0) c *= t / static_cast<float>(o);
+      sC[z * NT + o] = c;
+    }
+    sG[z] = __ldg(tb + T.gz + z) * dt;
+  }
 }
 
-// U[z][l][p] (p < 10) of one element from Q [L][10] and D (GPU layout).
+// Modes of Taylor order o held for field p: the wave fields of D^o have the
+// modes of degree <= N - o, alpha has orders 0 and 1 on all modes.
 template <int N>
-__device__ __forceinline__ void taylor_values(const float* sQ, const float* sD, float* sU, const float* tb,
-                                              const TableLayout& T, float dt, int t0, int nt) {
-  using A = ADim<N>;
-  for (int w = t0; w < A::NT * A::L * 10; w += nt) {
-    const int z = w / (A::L * 10), r = w - z * A::L * 10, l = r / 10, p = r - l * 10;
-    float u = sQ[l * 10 + p];
-    if (p == 9) {
-      u = fmaf(__ldg(tb + T.tz + z) * dt, sD[A::AOFF + l], u);
-    } else {
-      for (int o = 1; o <= N; ++o)
-        if (l < n_modes(N - o)) u = fmaf(taylor<N>(tb, T, z, o, dt), sD[d_offset(N, o) + l * 9 + p], u);
+__host__ __device__ constexpr int order_modes(int o, int p) {
+  return p == 9 ? (o <= 1 ? n_modes(N) : 0) : n_modes(N - o);
+}
+// Offset of (o, l, p) in the (Q, D) layout of one element (Q stride q_stride(N)).
+template <int N>
+__device__ __forceinline__ int ld_index(int o, int l, int p) {
+  if (o == 0) return l * 10 + p;
+  if (p == 9) return q_stride(N) + d_alpha_offset(N) + l;
+  return q_stride(N) + d_offset(N, o) + l * 9 + p;
+}
+
+// For every node x of a basis table V[l][x] (row stride ldv, NX nodes) and field
+// p: the value of the predictor's polynomial at the NT time nodes,
+//     u[z][x][p] = sum_o c[z][o] sum_l V[l][x] D^o_lp,
+// taking the sum over modes once per Taylor order.
+template <int N, int NX>
+__device__ __forceinline__ void node_values(const float* V, int ldv, const float* sQ, const float* sD,
+                                            const float* sC, float* out) {
+  constexpr int NT = N + 1;
+  for (int w = threadIdx.x; w < NX * 10; w += blockDim.x) {
+    const int x = w / 10, p = w - x * 10;
+    const float* vx = V + x;
+    float t[NT];
+#pragma unroll
+    for (int o = 0; o < NT; ++o) {
+      const int lim = order_modes<N>(o, p);
+      const float* src = o == 0 ? sQ + p : (p == 9 ? sD + d_alpha_offset(N) : sD + d_offset(N, o) + p);
+      const int st = o == 0 ? 10 : (p == 9 ? 1 : 9);
+      float acc = 0.f;
+      for (int l = 0; l < lim; ++l) acc = fmaf(__ldg(vx + l * ldv), src[l * st], acc);
+      t[o] = acc;
     }
-    sU[w] = u;
+#pragma unroll
+    for (int z = 0; z < NT; ++z) {
+      float u = 0.f;
+#pragma unroll
+      for (int o = 0; o < NT; ++o) u = fmaf(sC[z * NT + o], t[o], u);
+      out[(z * NX + x) * 10 + p] = u;
+    }
   }
 }
 
@@ -173,12 +208,10 @@ struct FaceSmem {
   static constexpr int oLam = 0;                              // [2][L][10]
   static constexpr int oQ = oLam + 2 * A::L * 10;             // [2][QS]
   static constexpr int oD = oQ + 2 * A::QS;                   // [2][DS]
-  static constexpr int oU = oD + 2 * A::DS;                   // [2][NT][L][10]
-  static constexpr int oTr = oU + 2 * A::NT * A::L * 10;      // [2][NT][NF][10] traces
+  static constexpr int oTr = oD + 2 * A::DS;                  // [2][NT][NF][10] traces
   static constexpr int oLff = oTr + 2 * A::NT * A::NF * 10;   // [NF][9]
   static constexpr int oLu = oLff + A::NF * 9;                // [2][NT][NF][10] lam of the traces
-  static constexpr int oLo = oLu + 2 * A::NT * A::NF * 10;    // [2][NT(orders)][NF][10]
-  static constexpr int total = oLo + 2 * A::NT * A::NF * 10;
+  static constexpr int total = oLu + 2 * A::NT * A::NF * 10;
 };
 
 template <int N>
@@ -188,121 +221,100 @@ __global__ void __launch_bounds__(128) k_adj_face(AdjArgs a) {
   constexpr int L = A::L, NF = A::NF, NT = A::NT;
   extern __shared__ __align__(16) float smem[];
   __shared__ double sRed[4];
+  __shared__ float sC[NT * NT], sG[NT];
   const TableLayout T = table_layout(N);
   const float* tb = a.tables;
-  const float dt = a.dt;
+  time_tables<N>(tb, T, a.dt, sC, sG);
   for (int64_t f = blockIdx.x; f < a.F; f += gridDim.x) {
     const int4 fc = a.faces[f];
-    const int64_t e[2] = {fc.x, fc.z};
-    const int lf[2] = {fc.y, fc.w};
+    const int64_t e0 = fc.x, e1 = fc.z;
+    const int lf0 = fc.y, lf1 = fc.w;
     __syncthreads();
     for (int w = threadIdx.x; w < 2 * L * 10; w += blockDim.x) {
       const int sd = w / (L * 10), r = w - sd * L * 10;
-      smem[S::oLam + w] = a.lam_in[e[sd] * A::QS + r];
-      smem[S::oQ + sd * A::QS + r] = a.q[e[sd] * A::QS + r];
+      smem[S::oLam + w] = a.lam_in[(sd ? e1 : e0) * A::QS + r];
+      smem[S::oQ + sd * A::QS + r] = a.q[(sd ? e1 : e0) * A::QS + r];
     }
     for (int w = threadIdx.x; w < 2 * A::DS; w += blockDim.x) {
       const int sd = w / A::DS, r = w - sd * A::DS;
-      smem[S::oD + w] = a.d[e[sd] * A::DS + r];
+      smem[S::oD + w] = a.d[(sd ? e1 : e0) * A::DS + r];
     }
     if (threadIdx.x < 4) sRed[threadIdx.x] = 0.0;
     __syncthreads();
+    // traces of both sides at the space-time face nodes
     for (int sd = 0; sd < 2; ++sd)
-      taylor_values<N>(smem + S::oQ + sd * A::QS, smem + S::oD + sd * A::DS, smem + S::oU + sd * NT * L * 10, tb,
-                       T, dt, threadIdx.x, blockDim.x);
+      node_values<N, NF>(tb + T.VfT + (sd ? lf1 : lf0) * L * A::NFP, A::NFP, smem + S::oQ + sd * A::QS,
+                         smem + S::oD + sd * A::DS, sC, smem + S::oTr + sd * NT * NF * 10);
     // lam of the time-integrated face flux:
     //   lff[i][p] = -(a0 sum_k Vfw[f0][i][k] lam0[k][p] - a1 sum_k Vfw[f1][i][k] lam1[k][p])
-    const float a0 = a.geom[e[0]].face[lf[0]][3], a1 = a.geom[e[1]].face[lf[1]][3];
+    const float a0 = a.geom[e0].face[lf0][3], a1 = a.geom[e1].face[lf1][3];
     for (int w = threadIdx.x; w < NF * 9; w += blockDim.x) {
       const int i = w / 9, p = w - i * 9;
       float s0 = 0.f, s1 = 0.f;
       for (int k = 0; k < L; ++k) {
-        s0 = fmaf(__ldg(tb + T.Vfw + (lf[0] * NF + i) * A::LP + k), smem[S::oLam + k * 10 + p], s0);
-        s1 = fmaf(__ldg(tb + T.Vfw + (lf[1] * NF + i) * A::LP + k), smem[S::oLam + L * 10 + k * 10 + p], s1);
+        s0 = fmaf(__ldg(tb + T.Vfw + (lf0 * NF + i) * A::LP + k), smem[S::oLam + k * 10 + p], s0);
+        s1 = fmaf(__ldg(tb + T.Vfw + (lf1 * NF + i) * A::LP + k), smem[S::oLam + L * 10 + k * 10 + p], s1);
       }
       smem[S::oLff + w] = -(a0 * s0 - a1 * s1);
     }
     __syncthreads();
-    // traces of both sides at the space-time face nodes
-    for (int w = threadIdx.x; w < 2 * NT * NF * 10; w += blockDim.x) {
-      const int sd = w / (NT * NF * 10), r = w - sd * NT * NF * 10;
-      const int z = r / (NF * 10), r2 = r - z * NF * 10, i = r2 / 10, p = r2 - i * 10;
-      const float* U = smem + S::oU + (sd * NT + z) * L * 10;
-      float s = 0.f;
-      for (int l = 0; l < L; ++l) s = fmaf(__ldg(tb + T.VfT + (lf[sd] * L + l) * A::NFP + i), U[l * 10 + p], s);
-      smem[S::oTr + w] = s;
-    }
-    __syncthreads();
-    // the Rusanov flux transposed at each space-time node
-    const MatF m0 = a.mat[e[0]], m1 = a.mat[e[1]];
-    const float n[3] = {a.geom[e[0]].face[lf[0]][0], a.geom[e[0]].face[lf[0]][1], a.geom[e[0]].face[lf[0]][2]};
-    const float cp0 = a.cp[e[0]], cp1 = a.cp[e[1]];
+    // the Rusanov flux transposed at each space-time node, one side per item
+    const float n[3] = {a.geom[e0].face[lf0][0], a.geom[e0].face[lf0][1], a.geom[e0].face[lf0][2]};
+    const float cp0 = a.cp[e0], cp1 = a.cp[e1];
     const float C = fmaxf(cp0, cp1);
     float pC = 0.f, px0 = 0.f, px1 = 0.f;
-    for (int w = threadIdx.x; w < NT * NF; w += blockDim.x) {
-      const int z = w / NF, i = w - z * NF;
-      const float g = __ldg(tb + T.gz + z) * dt;
-      const float* um = smem + S::oTr + (0 * NT * NF + w) * 10;
-      const float* up = smem + S::oTr + (1 * NT * NF + w) * 10;
+    for (int w = threadIdx.x; w < 2 * NT * NF; w += blockDim.x) {
+      const int sd = w / (NT * NF), r = w - sd * NT * NF;
+      const int z = r / NF, i = r - z * NF;
+      const float g = sG[z];
+      const float* u = smem + S::oTr + w * 10;
       float lfs[9];
 #pragma unroll
       for (int p = 0; p < 9; ++p) lfs[p] = g * smem[S::oLff + i * 9 + p];
-      float lm[10], lp[10];
+      float lu[10];
 #pragma unroll
-      for (int p = 0; p < 10; ++p) lm[p] = lp[p] = 0.f;
-      px0 += 0.5f * normal_flux_vjp(um, m0, n, lfs, lm);
-      px1 += 0.5f * normal_flux_vjp(up, m1, n, lfs, lp);
-      float* om = smem + S::oLu + (0 * NT * NF + w) * 10;
-      float* op = smem + S::oLu + (1 * NT * NF + w) * 10;
+      for (int p = 0; p < 10; ++p) lu[p] = 0.f;
+      const MatF m = a.mat[sd ? e1 : e0];
+      const float gx = 0.5f * normal_flux_vjp(u, m, n, lfs, lu);
+      const float cs = sd ? -0.5f * C : 0.5f * C;
+      float* o = smem + S::oLu + w * 10;
 #pragma unroll
-      for (int p = 0; p < 9; ++p) {
-        om[p] = 0.5f * lm[p] + 0.5f * C * lfs[p];
-        op[p] = 0.5f * lp[p] - 0.5f * C * lfs[p];
-        pC = fmaf(0.5f * lfs[p], um[p] - up[p], pC);
+      for (int p = 0; p < 9; ++p) o[p] = 0.5f * lu[p] + cs * lfs[p];
+      o[9] = 0.5f * lu[9];
+      if (sd == 0) {
+        px0 += gx;
+        const float* up = smem + S::oTr + (NT * NF + r) * 10;
+#pragma unroll
+        for (int p = 0; p < 9; ++p) pC = fmaf(0.5f * lfs[p], u[p] - up[p], pC);
+      } else {
+        px1 += gx;
       }
-      om[9] = 0.5f * lm[9];
-      op[9] = 0.5f * lp[9];
     }
     block_add(&sRed[0], pC);
     block_add(&sRed[1], px0);
     block_add(&sRed[2], px1);
     __syncthreads();
-    // fold the time nodes into Taylor orders: Lo[o][i][p] = sum_z t_z^o / o! Lu[z][i][p]
-    for (int w = threadIdx.x; w < 2 * NT * NF * 10; w += blockDim.x) {
-      const int sd = w / (NT * NF * 10), r = w - sd * NT * NF * 10;
-      const int o = r / (NF * 10), r2 = r - o * NF * 10;
-      float s = 0.f;
-      for (int z = 0; z < NT; ++z)
-        s = fmaf(taylor<N>(tb, T, z, o, dt), smem[S::oLu + (sd * NT + z) * NF * 10 + r2], s);
-      smem[S::oLo + w] = s;
-    }
-    __syncthreads();
-    // project onto the modes of each side and write the record in the (Q, D) layout
-    for (int w = threadIdx.x; w < 2 * A::LDS; w += blockDim.x) {
-      const int sd = w / A::LDS, r = w - sd * A::LDS;
-      int o, l, p;
-      bool live = true;
-      if (r < A::QS) {
-        o = 0; l = r / 10; p = r - l * 10;
-        live = l < L;
-      } else {
-        const int rd = r - A::QS;
-        if (rd >= A::AOFF) {
-          o = 1; l = rd - A::AOFF; p = 9;
-          live = l < L;
-        } else {
-          o = 1;
-          while (o < N && rd >= d_offset(N, o + 1)) ++o;
-          const int ro = rd - d_offset(N, o);
-          l = ro / 9; p = ro - l * 9;
+    // lam of D^o_lp of each side: sum_i phi_l(x_i) sum_z c[z][o] Lu[z][i][p]
+    for (int w = threadIdx.x; w < 2 * L * 10; w += blockDim.x) {
+      const int sd = w / (L * 10), r = w - sd * L * 10, l = r / 10, p = r - l * 10;
+      const float* V = tb + T.VfT + ((sd ? lf1 : lf0) * L + l) * A::NFP;
+      const float* Lu = smem + S::oLu + sd * NT * NF * 10 + p;
+      float acc[NT];
+#pragma unroll
+      for (int o = 0; o < NT; ++o) acc[o] = 0.f;
+      for (int i = 0; i < NF; ++i) {
+        const float v = __ldg(V + i);
+#pragma unroll
+        for (int z = 0; z < NT; ++z) {
+          const float lz = v * Lu[(z * NF + i) * 10];
+#pragma unroll
+          for (int o = 0; o < NT; ++o) acc[o] = fmaf(sC[z * NT + o], lz, acc[o]);
         }
       }
-      float s = 0.f;
-      if (live) {
-        const float* Lo = smem + S::oLo + (sd * NT + o) * NF * 10;
-        for (int i = 0; i < NF; ++i) s = fmaf(__ldg(tb + T.VfT + (lf[sd] * L + l) * A::NFP + i), Lo[i * 10 + p], s);
-      }
-      a.rec[(f * 2 + sd) * A::RS + r] = s;
+      float* out = a.rec + (f * 2 + sd) * A::RS;
+#pragma unroll
+      for (int o = 0; o < NT; ++o)
+        if (l < order_modes<N>(o, p)) out[ld_index<N>(o, l, p)] = acc[o];
     }
     if (threadIdx.x < 2) {
       const int sd = threadIdx.x;
@@ -324,12 +336,12 @@ template <int N>
 struct ElemSmem {
   using A = ADim<N>;
   static constexpr int oLam = 0;                          // [L][10] lam^{k+1}
-  static constexpr int oQ = oLam + A::L * 10;             // [QS]
+  static constexpr int oQ = round4(oLam + A::L * 10);     // [QS]
   static constexpr int oD = oQ + A::QS;                   // [DS]
-  static constexpr int oU = oD + A::DS;                   // [NT][L][10]
-  static constexpr int oX = oU + A::NT * A::L * 10;       // [NQ][28]: w_q dphi_k/dx_d lam_kp (27), w_q phi_k lam_k9
-  static constexpr int oLu = oX + A::NQ * 28;             // [NT][NQ][10] lam of the nodal values
-  static constexpr int oLD = oLu + A::NT * A::NQ * 10;    // [QS + DS] lam of D^0..D^N
+  static constexpr int oU = oD + A::DS;                   // [NT][NQ][10] nodal values, then their lam
+  static constexpr int oLu = oU;                          //   (each node's lam replaces its value)
+  static constexpr int oX = round4(oU + A::NT * A::NQ * 10);   // [NQ][28]: w_q dphi_k/dx_d lam_kp (27), w_q phi_k lam_k9
+  static constexpr int oLD = oX + A::NQ * 28;             // [QS + DS] lam of D^0..D^N
   static constexpr int oH = oLD + A::LDS;                 // [3][L][9]
   static constexpr int total = oH + 3 * A::L * 9;
 };
@@ -342,9 +354,10 @@ __global__ void __launch_bounds__(128) k_adj_elem(AdjArgs a) {
   extern __shared__ __align__(16) float smem[];
   __shared__ double sRed[4];          // xi0, C_d, lam/rho, mu/rho
   __shared__ float sGeo[16];          // Theta^{-1} [e][d], lambda_eff/rho, mu_eff/rho
+  __shared__ float sC[NT * NT], sG[NT];
   const TableLayout T = table_layout(N);
   const float* tb = a.tables;
-  const float dt = a.dt;
+  time_tables<N>(tb, T, a.dt, sC, sG);
   float* sLD = smem + S::oLD;
   for (int64_t e = blockIdx.x; e < a.E; e += gridDim.x) {
     __syncthreads();
@@ -358,24 +371,34 @@ __global__ void __launch_bounds__(128) k_adj_elem(AdjArgs a) {
     if (threadIdx.x < 9) sGeo[threadIdx.x] = a.geom[e].tinv[threadIdx.x];
     if (threadIdx.x < 4) sRed[threadIdx.x] = 0.0;
     __syncthreads();
-    taylor_values<N>(smem + S::oQ, smem + S::oD, smem + S::oU, tb, T, dt, threadIdx.x, blockDim.x);
-    // per volume node q: X[q][d][p] = sum_k w_q dphi_k/dx_d(x_q) lam[k][p], X[q][27] = sum_k w_q phi_k lam[k][9]
-    for (int w = threadIdx.x; w < NQ * 10; w += blockDim.x) {
-      const int q = w / 10, p = w - q * 10;
-      if (p < 9) {
-        float g[3] = {0.f, 0.f, 0.f};
-        for (int k = 0; k < L; ++k) {
-          const float lk = smem[S::oLam + k * 10 + p];
-#pragma unroll
-          for (int ee = 0; ee < 3; ++ee) g[ee] = fmaf(__ldg(tb + T.Gw + (ee * NQ + q) * A::LP + k), lk, g[ee]);
+    node_values<N, NQ>(tb + T.VvT, A::NQP, smem + S::oQ, smem + S::oD, sC, smem + S::oU);
+    // per volume node q: X[q][d][p] = sum_k w_q dphi_k/dx_d(x_q) lam[k][p], X[q][27] = sum_k w_q phi_k lam[k][9];
+    // one item per node and pair of fields (8, 9 pairs the last wave field with alpha)
+    for (int w = threadIdx.x; w < NQ * 5; w += blockDim.x) {
+      const int q = w / 5, pp = w - q * 5, p0 = 2 * pp;
+      float g0[3] = {0.f, 0.f, 0.f}, g1[3] = {0.f, 0.f, 0.f};
+      const float* gw = tb + T.Gw + q * A::LP;
+      const float* vw = tb + T.Vw + q * A::LP;
+      for (int k = 0; k < L; ++k) {
+        const float2 lk = *reinterpret_cast<const float2*>(smem + S::oLam + k * 10 + p0);
+        const float ga = __ldg(gw + k), gb = __ldg(gw + NQ * A::LP + k), gc = __ldg(gw + 2 * NQ * A::LP + k);
+        g0[0] = fmaf(ga, lk.x, g0[0]); g0[1] = fmaf(gb, lk.x, g0[1]); g0[2] = fmaf(gc, lk.x, g0[2]);
+        if (pp < 4) {
+          g1[0] = fmaf(ga, lk.y, g1[0]); g1[1] = fmaf(gb, lk.y, g1[1]); g1[2] = fmaf(gc, lk.y, g1[2]);
+        } else {
+          g1[0] = fmaf(__ldg(vw + k), lk.y, g1[0]);
         }
+      }
+      float* xq = smem + S::oX + q * 28;
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        xq[d * 9 + p0] = g0[0] * sGeo[0 * 3 + d] + g0[1] * sGeo[1 * 3 + d] + g0[2] * sGeo[2 * 3 + d];
+      if (pp < 4) {
 #pragma unroll
         for (int d = 0; d < 3; ++d)
-          smem[S::oX + q * 28 + d * 9 + p] = g[0] * sGeo[0 * 3 + d] + g[1] * sGeo[1 * 3 + d] + g[2] * sGeo[2 * 3 + d];
+          xq[d * 9 + p0 + 1] = g1[0] * sGeo[0 * 3 + d] + g1[1] * sGeo[1 * 3 + d] + g1[2] * sGeo[2 * 3 + d];
       } else {
-        float s = 0.f;
-        for (int k = 0; k < L; ++k) s = fmaf(__ldg(tb + T.Vw + q * A::LP + k), smem[S::oLam + k * 10 + 9], s);
-        smem[S::oX + q * 28 + 27] = s;
+        xq[27] = g1[0];
       }
     }
     __syncthreads();
@@ -383,63 +406,67 @@ __global__ void __launch_bounds__(128) k_adj_elem(AdjArgs a) {
     float px = 0.f, pc = 0.f;
     for (int w = threadIdx.x; w < NT * NQ; w += blockDim.x) {
       const int z = w / NQ, q = w - z * NQ;
-      const float g = __ldg(tb + T.gz + z) * dt;
-      const float* U = smem + S::oU + z * L * 10;
+      const float g = sG[z];
       float u[10];
 #pragma unroll
-      for (int p = 0; p < 10; ++p) u[p] = 0.f;
-      for (int l = 0; l < L; ++l) {
-        const float ph = __ldg(tb + T.VvT + l * A::NQP + q);
-#pragma unroll
-        for (int p = 0; p < 10; ++p) u[p] = fmaf(ph, U[l * 10 + p], u[p]);
+      for (int p = 0; p < 10; p += 2) {
+        const float2 v2 = *reinterpret_cast<const float2*>(smem + S::oU + w * 10 + p);
+        u[p] = v2.x;
+        u[p + 1] = v2.y;
       }
-      float lF[27];
+      float lF[28];
 #pragma unroll
-      for (int c = 0; c < 27; ++c) lF[c] = g * smem[S::oX + q * 28 + c];
+      for (int c = 0; c < 28; c += 4) {
+        const float4 v4 = *reinterpret_cast<const float4*>(smem + S::oX + q * 28 + c);
+        lF[c] = g * v4.x; lF[c + 1] = g * v4.y; lF[c + 2] = g * v4.z; lF[c + 3] = g * v4.w;
+      }
       float lu[10];
 #pragma unroll
       for (int p = 0; p < 10; ++p) lu[p] = 0.f;
       px += flux_vjp(u, m, lF, lu);
-      rate_vjp(u, m, g * smem[S::oX + q * 28 + 27], lu, &px, &pc);
+      rate_vjp(u, m, lF[27], lu, &px, &pc);
       float* o = smem + S::oLu + w * 10;
 #pragma unroll
-      for (int p = 0; p < 10; ++p) o[p] = lu[p];
+      for (int p = 0; p < 10; p += 2) *reinterpret_cast<float2*>(o + p) = make_float2(lu[p], lu[p + 1]);
     }
     __syncthreads();
-    // lam of U(t_z), folded into lam of D^o: sum_z t_z^o/o! sum_q phi_l(x_q) Lu[z][q][p]
-    for (int w = threadIdx.x; w < A::LDS; w += blockDim.x) {
-      int o, l, p;
-      bool live = true;
-      if (w < A::QS) {
-        o = 0; l = w / 10; p = w - l * 10;
-        live = l < L;
-      } else {
-        const int rd = w - A::QS;
-        if (rd >= A::AOFF) {
-          o = 1; l = rd - A::AOFF; p = 9;
-          live = l < L;
-        } else {
-          o = 1;
-          while (o < N && rd >= d_offset(N, o + 1)) ++o;
-          const int ro = rd - d_offset(N, o);
-          l = ro / 9; p = ro - l * 9;
-        }
-      }
-      float s = 0.f;
-      if (live) {
+    // lam of D^o_lp = sum_z c[z][o] sum_q phi_l(x_q) Lu[z][q][p], plus the four face records;
+    // one item per mode and pair of fields
+    for (int w = threadIdx.x; w < L * 5; w += blockDim.x) {
+      const int l = w / 5, p0 = 2 * (w - l * 5);
+      const float* V = tb + T.VvT + l * A::NQP;
+      const float* Lu = smem + S::oLu + p0;
+      float a0[NT], a1[NT];
+#pragma unroll
+      for (int z = 0; z < NT; ++z) a0[z] = a1[z] = 0.f;
+      for (int q = 0; q < NQ; ++q) {
+        const float v = __ldg(V + q);
+#pragma unroll
         for (int z = 0; z < NT; ++z) {
-          const float* Lu = smem + S::oLu + z * NQ * 10;
-          float t = 0.f;
-          for (int q = 0; q < NQ; ++q) t = fmaf(__ldg(tb + T.VvT + l * A::NQP + q), Lu[q * 10 + p], t);
-          s = fmaf(taylor<N>(tb, T, z, o, dt), t, s);
-        }
-        // the element's four face records
-        for (int fl = 0; fl < 4; ++fl) {
-          const int ef = a.elem_face[e * 4 + fl];
-          s += a.rec[static_cast<int64_t>(ef) * A::RS + w];
+          const float2 lz = *reinterpret_cast<const float2*>(Lu + (z * NQ + q) * 10);
+          a0[z] = fmaf(v, lz.x, a0[z]);
+          a1[z] = fmaf(v, lz.y, a1[z]);
         }
       }
-      sLD[w] = s;
+      int ef[4];
+#pragma unroll
+      for (int fl = 0; fl < 4; ++fl) ef[fl] = a.elem_face[e * 4 + fl];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int p = p0 + h;
+        const float* acc = h ? a1 : a0;
+#pragma unroll
+        for (int o = 0; o < NT; ++o) {
+          if (l >= order_modes<N>(o, p)) continue;
+          float s = 0.f;
+#pragma unroll
+          for (int z = 0; z < NT; ++z) s = fmaf(sC[z * NT + o], acc[z], s);
+          const int idx = ld_index<N>(o, l, p);
+#pragma unroll
+          for (int fl = 0; fl < 4; ++fl) s += a.rec[static_cast<int64_t>(ef[fl]) * A::RS + idx];
+          sLD[idx] = s;
+        }
+      }
     }
     if (threadIdx.x < 4) {
       const int ef = a.elem_face[e * 4 + threadIdx.x];
@@ -475,7 +502,6 @@ __global__ void __launch_bounds__(128) k_adj_elem(AdjArgs a) {
       sRed[3] = static_cast<double>(2.f * dc) * m.rho;
     }
     __syncthreads();
-
     // Cauchy-Kovalevskaya recursion transposed, order N down to 1
     const float lr = sGeo[9], mr = sGeo[10];
     for (int i = N; i >= 1; --i) {
