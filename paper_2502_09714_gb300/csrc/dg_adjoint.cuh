@@ -27,6 +27,7 @@
 #pragma once
 
 #include "dg_internal.h"
+#include "dg_tc.cuh"
 
 namespace dg {
 namespace adj {
@@ -174,7 +175,7 @@ __device__ __forceinline__ int ld_index(int o, int l, int p) {
 // taking the sum over modes once per Taylor order.
 template <int N, int NX>
 __device__ __forceinline__ void node_values(const float* V, int ldv, const float* sQ, const float* sD,
-                                            const float* sC, float* out) {
+                                            const float* sC, float* out, float* out0 = nullptr) {
   constexpr int NT = N + 1;
   for (int w = threadIdx.x; w < NX * 10; w += blockDim.x) {
     const int x = w / 10, p = w - x * 10;
@@ -189,6 +190,7 @@ __device__ __forceinline__ void node_values(const float* V, int ldv, const float
       for (int l = 0; l < lim; ++l) acc = fmaf(__ldg(vx + l * ldv), src[l * st], acc);
       t[o] = acc;
     }
+    if (out0 != nullptr && p < 6) out0[x * 6 + p] = t[0];   // the strains at t_n
 #pragma unroll
     for (int z = 0; z < NT; ++z) {
       float u = 0.f;
@@ -205,17 +207,18 @@ __device__ __forceinline__ void node_values(const float* V, int ldv, const float
 template <int N>
 struct FaceSmem {
   using A = ADim<N>;
-  static constexpr int oLam = 0;                              // [2][L][10]
-  static constexpr int oQ = oLam + 2 * A::L * 10;             // [2][QS]
+  static constexpr int oLam = 0;                              // [2][QS] lam^{k+1} of both sides
+  static constexpr int oQ = oLam + 2 * A::QS;                 // [2][QS]
   static constexpr int oD = oQ + 2 * A::QS;                   // [2][DS]
   static constexpr int oTr = oD + 2 * A::DS;                  // [2][NT][NF][10] traces
-  static constexpr int oLff = oTr + 2 * A::NT * A::NF * 10;   // [NF][9]
-  static constexpr int oLu = oLff + A::NF * 9;                // [2][NT][NF][10] lam of the traces
+  static constexpr int oLff = round4(oTr + 2 * A::NT * A::NF * 10);   // [NF][9]
+  static constexpr int oLu = round4(oLff + A::NF * 9);        // [2][NT][NF][10] lam of the traces,
+                                                              //   then folded into Taylor orders
   static constexpr int total = oLu + 2 * A::NT * A::NF * 10;
 };
 
 template <int N>
-__global__ void __launch_bounds__(128) k_adj_face(AdjArgs a) {
+__global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
   using A = ADim<N>;
   using S = FaceSmem<N>;
   constexpr int L = A::L, NF = A::NF, NT = A::NT;
@@ -230,15 +233,18 @@ __global__ void __launch_bounds__(128) k_adj_face(AdjArgs a) {
     const int64_t e0 = fc.x, e1 = fc.z;
     const int lf0 = fc.y, lf1 = fc.w;
     __syncthreads();
-    for (int w = threadIdx.x; w < 2 * L * 10; w += blockDim.x) {
-      const int sd = w / (L * 10), r = w - sd * L * 10;
-      smem[S::oLam + w] = a.lam_in[(sd ? e1 : e0) * A::QS + r];
-      smem[S::oQ + sd * A::QS + r] = a.q[(sd ? e1 : e0) * A::QS + r];
+    // one batch of 16-byte asynchronous copies: lam, Q and D of both sides
+    for (int w = threadIdx.x; w < A::QS / 2; w += blockDim.x) {
+      const int sd = w / (A::QS / 4), c = 4 * (w - sd * (A::QS / 4));
+      const int64_t es = sd ? e1 : e0;
+      tc::cp_async16(smem + S::oLam + sd * A::QS + c, a.lam_in + es * A::QS + c);
+      tc::cp_async16(smem + S::oQ + sd * A::QS + c, a.q + es * A::QS + c);
     }
-    for (int w = threadIdx.x; w < 2 * A::DS; w += blockDim.x) {
-      const int sd = w / A::DS, r = w - sd * A::DS;
-      smem[S::oD + w] = a.d[(sd ? e1 : e0) * A::DS + r];
+    for (int w = threadIdx.x; w < A::DS / 2; w += blockDim.x) {
+      const int sd = w / (A::DS / 4), c = 4 * (w - sd * (A::DS / 4));
+      tc::cp_async16(smem + S::oD + sd * A::DS + c, a.d + (sd ? e1 : e0) * A::DS + c);
     }
+    tc::cp_async_wait_all();
     if (threadIdx.x < 4) sRed[threadIdx.x] = 0.0;
     __syncthreads();
     // traces of both sides at the space-time face nodes
@@ -253,7 +259,7 @@ __global__ void __launch_bounds__(128) k_adj_face(AdjArgs a) {
       float s0 = 0.f, s1 = 0.f;
       for (int k = 0; k < L; ++k) {
         s0 = fmaf(__ldg(tb + T.Vfw + (lf0 * NF + i) * A::LP + k), smem[S::oLam + k * 10 + p], s0);
-        s1 = fmaf(__ldg(tb + T.Vfw + (lf1 * NF + i) * A::LP + k), smem[S::oLam + L * 10 + k * 10 + p], s1);
+        s1 = fmaf(__ldg(tb + T.Vfw + (lf1 * NF + i) * A::LP + k), smem[S::oLam + A::QS + k * 10 + p], s1);
       }
       smem[S::oLff + w] = -(a0 * s0 - a1 * s1);
     }
@@ -294,27 +300,45 @@ __global__ void __launch_bounds__(128) k_adj_face(AdjArgs a) {
     block_add(&sRed[1], px0);
     block_add(&sRed[2], px1);
     __syncthreads();
-    // lam of D^o_lp of each side: sum_i phi_l(x_i) sum_z c[z][o] Lu[z][i][p]
-    for (int w = threadIdx.x; w < 2 * L * 10; w += blockDim.x) {
-      const int sd = w / (L * 10), r = w - sd * L * 10, l = r / 10, p = r - l * 10;
-      const float* V = tb + T.VfT + ((sd ? lf1 : lf0) * L + l) * A::NFP;
-      const float* Lu = smem + S::oLu + sd * NT * NF * 10 + p;
-      float acc[NT];
+    // fold the time nodes into Taylor orders in place: Lo[o][i][p] = sum_z c[z][o] Lu[z][i][p]
+    for (int w = threadIdx.x; w < 2 * NF * 10; w += blockDim.x) {
+      const int sd = w / (NF * 10), r = w - sd * NF * 10;
+      float* base = smem + S::oLu + sd * NT * NF * 10 + r;
+      float lz[NT];
 #pragma unroll
-      for (int o = 0; o < NT; ++o) acc[o] = 0.f;
+      for (int z = 0; z < NT; ++z) lz[z] = base[z * NF * 10];
+#pragma unroll
+      for (int o = 0; o < NT; ++o) {
+        float acc = 0.f;
+#pragma unroll
+        for (int z = 0; z < NT; ++z) acc = fmaf(sC[z * NT + o], lz[z], acc);
+        base[o * NF * 10] = acc;
+      }
+    }
+    __syncthreads();
+    // lam of D^o_lp of each side = sum_i phi_l(x_i) Lo[o][i][p]; one item per mode and pair of fields
+    for (int w = threadIdx.x; w < 2 * L * 5; w += blockDim.x) {
+      const int sd = w / (L * 5), r = w - sd * L * 5, l = r / 5, p0 = 2 * (r - l * 5);
+      const float* V = tb + T.VfT + ((sd ? lf1 : lf0) * L + l) * A::NFP;
+      const float* Lo = smem + S::oLu + sd * NT * NF * 10 + p0;
+      float a0[NT], a1[NT];
+#pragma unroll
+      for (int o = 0; o < NT; ++o) a0[o] = a1[o] = 0.f;
       for (int i = 0; i < NF; ++i) {
         const float v = __ldg(V + i);
 #pragma unroll
-        for (int z = 0; z < NT; ++z) {
-          const float lz = v * Lu[(z * NF + i) * 10];
-#pragma unroll
-          for (int o = 0; o < NT; ++o) acc[o] = fmaf(sC[z * NT + o], lz, acc[o]);
+        for (int o = 0; o < NT; ++o) {
+          const float2 lo = *reinterpret_cast<const float2*>(Lo + (o * NF + i) * 10);
+          a0[o] = fmaf(v, lo.x, a0[o]);
+          a1[o] = fmaf(v, lo.y, a1[o]);
         }
       }
       float* out = a.rec + (f * 2 + sd) * A::RS;
 #pragma unroll
-      for (int o = 0; o < NT; ++o)
-        if (l < order_modes<N>(o, p)) out[ld_index<N>(o, l, p)] = acc[o];
+      for (int o = 0; o < NT; ++o) {
+        if (l < order_modes<N>(o, p0)) out[ld_index<N>(o, l, p0)] = a0[o];
+        if (l < order_modes<N>(o, p0 + 1)) out[ld_index<N>(o, l, p0 + 1)] = a1[o];
+      }
     }
     if (threadIdx.x < 2) {
       const int sd = threadIdx.x;
@@ -343,11 +367,13 @@ struct ElemSmem {
   static constexpr int oX = round4(oU + A::NT * A::NQ * 10);   // [NQ][28]: w_q dphi_k/dx_d lam_kp (27), w_q phi_k lam_k9
   static constexpr int oLD = oX + A::NQ * 28;             // [QS + DS] lam of D^0..D^N
   static constexpr int oH = oLD + A::LDS;                 // [3][L][9]
-  static constexpr int total = oH + 3 * A::L * 9;
+  static constexpr int oU0 = oH + 3 * A::L * 9;           // [NQ][6] strains at the volume nodes at t_n
+  static constexpr int oR = round4(oU0 + A::NQ * 6);      // [4][RS] the element's four face records
+  static constexpr int total = oR + 4 * A::RS;
 };
 
 template <int N>
-__global__ void __launch_bounds__(128) k_adj_elem(AdjArgs a) {
+__global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
   using A = ADim<N>;
   using S = ElemSmem<N>;
   constexpr int L = A::L, NQ = A::NQ, NT = A::NT;
@@ -361,17 +387,28 @@ __global__ void __launch_bounds__(128) k_adj_elem(AdjArgs a) {
   float* sLD = smem + S::oLD;
   for (int64_t e = blockIdx.x; e < a.E; e += gridDim.x) {
     __syncthreads();
-    for (int w = threadIdx.x; w < L * 10; w += blockDim.x) {
-      smem[S::oLam + w] = a.lam_in[e * A::QS + w];
-      smem[S::oQ + w] = a.q[e * A::QS + w];
+    // one batch of 16-byte asynchronous copies: lam, Q, D and the four face records
+    {
+      const int4 ef4 = reinterpret_cast<const int4*>(a.elem_face)[e];
+      for (int w = threadIdx.x; w < A::QS / 4; w += blockDim.x) {
+        tc::cp_async16(smem + S::oLam + 4 * w, a.lam_in + e * A::QS + 4 * w);
+        tc::cp_async16(smem + S::oQ + 4 * w, a.q + e * A::QS + 4 * w);
+      }
+      for (int w = threadIdx.x; w < A::DS / 4; w += blockDim.x)
+        tc::cp_async16(smem + S::oD + 4 * w, a.d + e * A::DS + 4 * w);
+      for (int w = threadIdx.x; w < A::RS; w += blockDim.x) {
+        const int fl = w / (A::RS / 4), c = 4 * (w - fl * (A::RS / 4));
+        const int ef = fl == 0 ? ef4.x : (fl == 1 ? ef4.y : (fl == 2 ? ef4.z : ef4.w));
+        tc::cp_async16(smem + S::oR + fl * A::RS + c, a.rec + static_cast<int64_t>(ef) * A::RS + c);
+      }
     }
-    for (int w = threadIdx.x; w < A::DS; w += blockDim.x) smem[S::oD + w] = a.d[e * A::DS + w];
     for (int w = threadIdx.x; w < A::LDS; w += blockDim.x) sLD[w] = 0.f;
+    tc::cp_async_wait_all();
     const MatF m = a.mat[e];
     if (threadIdx.x < 9) sGeo[threadIdx.x] = a.geom[e].tinv[threadIdx.x];
     if (threadIdx.x < 4) sRed[threadIdx.x] = 0.0;
     __syncthreads();
-    node_values<N, NQ>(tb + T.VvT, A::NQP, smem + S::oQ, smem + S::oD, sC, smem + S::oU);
+    node_values<N, NQ>(tb + T.VvT, A::NQP, smem + S::oQ, smem + S::oD, sC, smem + S::oU, smem + S::oU0);
     // per volume node q: X[q][d][p] = sum_k w_q dphi_k/dx_d(x_q) lam[k][p], X[q][27] = sum_k w_q phi_k lam[k][9];
     // one item per node and pair of fields (8, 9 pairs the last wave field with alpha)
     for (int w = threadIdx.x; w < NQ * 5; w += blockDim.x) {
@@ -448,29 +485,24 @@ __global__ void __launch_bounds__(128) k_adj_elem(AdjArgs a) {
           a1[z] = fmaf(v, lz.y, a1[z]);
         }
       }
-      int ef[4];
-#pragma unroll
-      for (int fl = 0; fl < 4; ++fl) ef[fl] = a.elem_face[e * 4 + fl];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int p = p0 + h;
-        const float* acc = h ? a1 : a0;
 #pragma unroll
         for (int o = 0; o < NT; ++o) {
           if (l >= order_modes<N>(o, p)) continue;
           float s = 0.f;
 #pragma unroll
-          for (int z = 0; z < NT; ++z) s = fmaf(sC[z * NT + o], acc[z], s);
+          for (int z = 0; z < NT; ++z) s = fmaf(sC[z * NT + o], h ? a1[z] : a0[z], s);
           const int idx = ld_index<N>(o, l, p);
 #pragma unroll
-          for (int fl = 0; fl < 4; ++fl) s += a.rec[static_cast<int64_t>(ef[fl]) * A::RS + idx];
+          for (int fl = 0; fl < 4; ++fl) s += smem[S::oR + fl * A::RS + idx];
           sLD[idx] = s;
         }
       }
     }
     if (threadIdx.x < 4) {
-      const int ef = a.elem_face[e * 4 + threadIdx.x];
-      const float* tail = a.rec + static_cast<int64_t>(ef) * A::RS + A::LDS;
+      const float* tail = smem + S::oR + threadIdx.x * A::RS + A::LDS;
       atomicAdd(&sRed[2], static_cast<double>(tail[0]));   // lam of cp (scaled below)
       atomicAdd(&sRed[0], static_cast<double>(tail[1]));   // xi0 part of the face fluxes
     }
@@ -512,57 +544,56 @@ __global__ void __launch_bounds__(128) k_adj_elem(AdjArgs a) {
       float* lDprev = i == 1 ? sLD : sLD + A::QS + d_offset(N, i - 1);
       const int lsp = i == 1 ? 10 : 9;
       float plr = 0.f, pmr = 0.f;
-      for (int k = threadIdx.x; k < Lout; k += blockDim.x) {
+      for (int w = threadIdx.x; w < Lout * 9; w += blockDim.x) {
+        const int k = w / 9, q = w - k * 9;
         float lv[9];
 #pragma unroll
         for (int p = 0; p < 9; ++p) lv[p] = lDi[k * 9 + p];
-        // Psi_d = B^d^T lam (q < 9)
-        float psi[3][9];
-        psi[0][6] = -lv[0]; psi[0][7] = -0.5f * lv[3]; psi[0][8] = -0.5f * lv[5];
-        psi[1][6] = -0.5f * lv[3]; psi[1][7] = -lv[1]; psi[1][8] = -0.5f * lv[4];
-        psi[2][6] = -0.5f * lv[5]; psi[2][7] = -0.5f * lv[4]; psi[2][8] = -lv[2];
+        // column q of Psi_d = B^d^T lam
+        float ps[3];
+        if (q < 3) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const float ld = lv[6 + d];
-          psi[d][0] = psi[d][1] = psi[d][2] = -lr * ld;
-          psi[d][3] = psi[d][4] = psi[d][5] = 0.f;
+          for (int d = 0; d < 3; ++d) ps[d] = -lr * lv[6 + d] - (q == d ? 2.f * mr * lv[6 + d] : 0.f);
+        } else if (q == 3) {
+          ps[0] = -2.f * mr * lv[7]; ps[1] = -2.f * mr * lv[6]; ps[2] = 0.f;
+        } else if (q == 4) {
+          ps[0] = 0.f; ps[1] = -2.f * mr * lv[8]; ps[2] = -2.f * mr * lv[7];
+        } else if (q == 5) {
+          ps[0] = -2.f * mr * lv[8]; ps[1] = 0.f; ps[2] = -2.f * mr * lv[6];
+        } else if (q == 6) {
+          ps[0] = -lv[0]; ps[1] = -0.5f * lv[3]; ps[2] = -0.5f * lv[5];
+        } else if (q == 7) {
+          ps[0] = -0.5f * lv[3]; ps[1] = -lv[1]; ps[2] = -0.5f * lv[4];
+        } else {
+          ps[0] = -0.5f * lv[5]; ps[1] = -0.5f * lv[4]; ps[2] = -lv[2];
         }
-        psi[0][0] += -2.f * mr * lv[6]; psi[0][3] += -2.f * mr * lv[7]; psi[0][5] += -2.f * mr * lv[8];
-        psi[1][3] += -2.f * mr * lv[6]; psi[1][1] += -2.f * mr * lv[7]; psi[1][4] += -2.f * mr * lv[8];
-        psi[2][5] += -2.f * mr * lv[6]; psi[2][4] += -2.f * mr * lv[7]; psi[2][2] += -2.f * mr * lv[8];
 #pragma unroll
         for (int ee = 0; ee < 3; ++ee)
-#pragma unroll
-          for (int q = 0; q < 9; ++q)
-            smem[S::oH + (ee * L + k) * 9 + q] =
-                sGeo[ee * 3 + 0] * psi[0][q] + sGeo[ee * 3 + 1] * psi[1][q] + sGeo[ee * 3 + 2] * psi[2][q];
+          smem[S::oH + (ee * L + k) * 9 + q] = sGeo[ee * 3 + 0] * ps[0] + sGeo[ee * 3 + 1] * ps[1] + sGeo[ee * 3 + 2] * ps[2];
         // the star matrices' dependence on lambda/rho and mu/rho:
-        // Gx[d][q] = sum_e Theta^{-1}_ed sum_l Kt^e_kl D^{i-1}_lq
-        float gk[3][9];
-#pragma unroll
-        for (int ee = 0; ee < 3; ++ee)
-#pragma unroll
-          for (int q = 0; q < 9; ++q) gk[ee][q] = 0.f;
+        // Gx[d] = sum_e Theta^{-1}_ed sum_l Kt^e_kl D^{i-1}_lq
+        float gk0 = 0.f, gk1 = 0.f, gk2 = 0.f;
+        const float* kt = tb + T.KtA + k;
         for (int l = 0; l < Lin; ++l) {
-#pragma unroll
-          for (int ee = 0; ee < 3; ++ee) {
-            const float kt = __ldg(tb + T.KtA + (ee * L + l) * A::LP + k);
-#pragma unroll
-            for (int q = 0; q < 9; ++q) gk[ee][q] = fmaf(kt, Dprev[l * sp + q], gk[ee][q]);
-          }
+          const float dv = Dprev[l * sp + q];
+          gk0 = fmaf(__ldg(kt + (0 * L + l) * A::LP), dv, gk0);
+          gk1 = fmaf(__ldg(kt + (1 * L + l) * A::LP), dv, gk1);
+          gk2 = fmaf(__ldg(kt + (2 * L + l) * A::LP), dv, gk2);
         }
-        float gx[3][9];
+        float gx[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-#pragma unroll
-          for (int q = 0; q < 9; ++q)
-            gx[d][q] = sGeo[0 * 3 + d] * gk[0][q] + sGeo[1 * 3 + d] * gk[1][q] + sGeo[2 * 3 + d] * gk[2][q];
+        for (int d = 0; d < 3; ++d) gx[d] = sGeo[0 * 3 + d] * gk0 + sGeo[1 * 3 + d] * gk1 + sGeo[2 * 3 + d] * gk2;
         // d/d(lam/rho): B^d_{6+d, q<3} = -lam/rho; d/d(mu/rho): B^d_{6+i, sym(i,d)} = -2 mu/rho
-#pragma unroll
-        for (int d = 0; d < 3; ++d) plr += (gx[d][0] + gx[d][1] + gx[d][2]) * lv[6 + d];
-        pmr += 2.f * (gx[0][0] * lv[6] + gx[0][3] * lv[7] + gx[0][5] * lv[8] +
-                      gx[1][3] * lv[6] + gx[1][1] * lv[7] + gx[1][4] * lv[8] +
-                      gx[2][5] * lv[6] + gx[2][4] * lv[7] + gx[2][2] * lv[8]);
+        if (q < 3) {
+          plr += gx[0] * lv[6] + gx[1] * lv[7] + gx[2] * lv[8];
+          pmr += 2.f * (q == 0 ? gx[0] * lv[6] : (q == 1 ? gx[1] * lv[7] : gx[2] * lv[8]));
+        } else if (q == 3) {
+          pmr += 2.f * (gx[0] * lv[7] + gx[1] * lv[6]);
+        } else if (q == 4) {
+          pmr += 2.f * (gx[1] * lv[8] + gx[2] * lv[7]);
+        } else if (q == 5) {
+          pmr += 2.f * (gx[0] * lv[8] + gx[2] * lv[6]);
+        }
       }
       block_add(&sRed[2], plr);
       block_add(&sRed[3], pmr);
@@ -586,14 +617,10 @@ __global__ void __launch_bounds__(128) k_adj_elem(AdjArgs a) {
       for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
         float u[10];
 #pragma unroll
-        for (int p = 0; p < 10; ++p) u[p] = 0.f;
+        for (int p = 0; p < 6; ++p) u[p] = smem[S::oU0 + q * 6 + p];
+        u[6] = u[7] = u[8] = u[9] = 0.f;
         float lrq = 0.f;
-        for (int l = 0; l < L; ++l) {
-          const float ph = __ldg(tb + T.VvT + l * A::NQP + q);
-#pragma unroll
-          for (int p = 0; p < 6; ++p) u[p] = fmaf(ph, smem[S::oQ + l * 10 + p], u[p]);
-          lrq = fmaf(__ldg(tb + T.Vw + q * A::LP + l), sLD[A::QS + A::AOFF + l], lrq);
-        }
+        for (int l = 0; l < L; ++l) lrq = fmaf(__ldg(tb + T.Vw + q * A::LP + l), sLD[A::QS + A::AOFF + l], lrq);
         float lu[10];
 #pragma unroll
         for (int p = 0; p < 10; ++p) lu[p] = 0.f;
