@@ -176,27 +176,42 @@ __device__ __forceinline__ int ld_index(int o, int l, int p) {
 template <int N, int NX>
 __device__ __forceinline__ void node_values(const float* V, int ldv, const float* sQ, const float* sD,
                                             const float* sC, float* out, float* out0 = nullptr) {
-  constexpr int NT = N + 1;
-  for (int w = threadIdx.x; w < NX * 10; w += blockDim.x) {
-    const int x = w / 10, p = w - x * 10;
+  constexpr int NT = N + 1, NXH = (NX + 1) / 2;
+  // two nodes per item: the table's rows are padded to an even length with zeros
+  for (int w = threadIdx.x; w < NXH * 10; w += blockDim.x) {
+    const int xh = w / 10, p = w - xh * 10, x = 2 * xh;
     const float* vx = V + x;
-    float t[NT];
+    float t0[NT], t1[NT];
 #pragma unroll
     for (int o = 0; o < NT; ++o) {
       const int lim = order_modes<N>(o, p);
       const float* src = o == 0 ? sQ + p : (p == 9 ? sD + d_alpha_offset(N) : sD + d_offset(N, o) + p);
       const int st = o == 0 ? 10 : (p == 9 ? 1 : 9);
-      float acc = 0.f;
-      for (int l = 0; l < lim; ++l) acc = fmaf(__ldg(vx + l * ldv), src[l * st], acc);
-      t[o] = acc;
+      float a0 = 0.f, a1 = 0.f;
+      for (int l = 0; l < lim; ++l) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(vx + l * ldv));
+        const float c = src[l * st];
+        a0 = fmaf(v.x, c, a0);
+        a1 = fmaf(v.y, c, a1);
+      }
+      t0[o] = a0;
+      t1[o] = a1;
     }
-    if (out0 != nullptr && p < 6) out0[x * 6 + p] = t[0];   // the strains at t_n
+    const bool two = x + 1 < NX;
+    if (out0 != nullptr && p < 6) {                           // the strains at t_n
+      out0[x * 6 + p] = t0[0];
+      if (two) out0[(x + 1) * 6 + p] = t1[0];
+    }
 #pragma unroll
     for (int z = 0; z < NT; ++z) {
-      float u = 0.f;
+      float u0 = 0.f, u1 = 0.f;
 #pragma unroll
-      for (int o = 0; o < NT; ++o) u = fmaf(sC[z * NT + o], t[o], u);
-      out[(z * NX + x) * 10 + p] = u;
+      for (int o = 0; o < NT; ++o) {
+        u0 = fmaf(sC[z * NT + o], t0[o], u0);
+        u1 = fmaf(sC[z * NT + o], t1[o], u1);
+      }
+      out[(z * NX + x) * 10 + p] = u0;
+      if (two) out[(z * NX + x + 1) * 10 + p] = u1;
     }
   }
 }
