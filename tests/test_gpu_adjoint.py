@@ -117,7 +117,7 @@ def test_autograd_function():
     cd = torch.tensor(w["material"][:, 5], dtype=torch.float64, requires_grad=True)
     J = dgpkg.misfit_function().apply(xi0, cd, s, w["material"], ref, n, dt, 2)
     (3.0 * J).backward()
-    assert float(J) == pytest.approx(Jg, rel=1e-12)
+    assert float(J.detach()) == pytest.approx(Jg, rel=1e-12)
     assert np.allclose(xi0.grad.numpy(), 3.0 * gxg, rtol=1e-12, atol=0)
     assert np.allclose(cd.grad.numpy(), 3.0 * gcg, rtol=1e-12, atol=0)
 
