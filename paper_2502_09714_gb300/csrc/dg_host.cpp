@@ -1361,10 +1361,16 @@ dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const flo
     return e;
   };
   // per-action timing (info requested): one event after each action
-  std::vector<cudaEvent_t> evs;
-  std::vector<int> ev_kind;
+  struct Events {                        // destroyed on every return path
+    std::vector<cudaEvent_t> v;
+    ~Events() {
+      for (cudaEvent_t e : v)
+        if (e) cudaEventDestroy(e);
+    }
+  } ev_list;
+  std::vector<cudaEvent_t>& evs = ev_list.v;
   if (info) {
-    evs.resize(plan.size() + 1);
+    evs.assign(plan.size() + 1, nullptr);
     for (auto& ev : evs) ADJ_CUDA(cudaEventCreate(&ev));
     ADJ_CUDA(cudaEventRecord(evs[0], ctx->stream));
   }
@@ -1453,7 +1459,6 @@ dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const flo
       else if (k == kAdjoint) info->adjoint_ms += ms;
       else info->copy_ms += ms;
     }
-    for (auto& ev : evs) cudaEventDestroy(ev);
   }
 #undef ADJ_CUDA
   release();
