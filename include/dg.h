@@ -298,14 +298,16 @@ dg_status dg_reference_table(int order, int which, double* out, int64_t cap, int
  * The step history is kept by binomial checkpointing (revolve): `snapshots`
  * state copies in all (one holds Q^0), so that the forward steps number
  * dg_revolve_cost(n_steps, snapshots) + 1; each adjoint step recomputes its own
- * predictor.  ref: host FP32 [n_steps][R][3], R receivers.  The context's state,
+ * predictor.  snapshots = 0 takes as many copies as 80 % of the free device
+ * memory holds beside the call's other buffers, at most n_steps + 1 (the whole
+ * history, one forward sweep) and at most 4096.  ref: host FP32 [n_steps][R][3], R receivers.  The context's state,
  * time and recorded traces are left unchanged.  info: NULL or the counts and
  * device milliseconds of the forward steps, the adjoint steps (predictor
  * recompute, adjoint kernels and misfit terms) and the snapshot copies.
  * Requires the CDM law, the CK predictor, one member, no boundary faces
  * (DG_E_UNSUPPORTED otherwise), material, state and at least one receiver
  * (DG_E_STATE); DG_E_ARG for n_steps outside 1..2^20, snapshots outside
- * 1..4096 or a plan of more than 2^27 forward steps; DG_E_OOM if the
+ * 0..4096 or a plan of more than 2^27 forward steps; DG_E_OOM if the
  * snapshots (snapshots x n_elem x 4 ceil(10 L / 4) floats) do not fit;
  * DG_E_NONFINITE / DG_E_NONHYPERBOLIC as dg_step. */
 typedef struct {

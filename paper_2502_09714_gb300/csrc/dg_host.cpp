@@ -1246,7 +1246,7 @@ dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const flo
   if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
   if (n_steps < 1 || n_steps > (int64_t(1) << 20)) return fail(ctx, DG_E_ARG, "n_steps must be in 1..2^20");
   if (!ref || !misfit) return fail(ctx, DG_E_ARG, "NULL reference traces or misfit");
-  if (snapshots < 1 || snapshots > 4096) return fail(ctx, DG_E_ARG, "snapshots must be in 1..4096");
+  if (snapshots < 0 || snapshots > 4096) return fail(ctx, DG_E_ARG, "snapshots must be in 0..4096");
   if (!ctx->has_material || !ctx->has_state) return fail(ctx, DG_E_STATE, "material and state must be set");
   if (ctx->law != 0) return fail(ctx, DG_E_UNSUPPORTED, "the adjoint covers the CDM law");
   if (ctx->picard_iters > 0) return fail(ctx, DG_E_UNSUPPORTED, "the adjoint covers the CK predictor");
@@ -1256,6 +1256,15 @@ dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const flo
   if (R < 1) return fail(ctx, DG_E_STATE, "the misfit needs receivers (dg_receivers)");
   if (dt <= 0) dt = ctx->dt_cfl;
   if (!std::isfinite(dt)) return fail(ctx, DG_E_ARG, "non-finite dt");
+  if (snapshots == 0) {
+    // as many state copies as a fifth of the free device memory spares, at most the whole history
+    size_t free_b = 0, total_b = 0;
+    DG_CUDA(ctx, cudaMemGetInfo(&free_b, &total_b));
+    const double state_b = 4.0 * static_cast<double>(ctx->EV) * q_stride(ctx->N);
+    const double fit = (0.8 * static_cast<double>(free_b) - 6.0 * state_b -
+                        8.0 * static_cast<double>(ctx->F_interior) * adj_rec_stride(ctx->N)) / state_b;
+    snapshots = static_cast<int>(std::max(1.0, std::min({fit, static_cast<double>(n_steps + 1), 4096.0})));
+  }
   const int s_free = snapshots - 1;
   if (revolve_cost(n_steps, s_free) > kMaxRevolveSteps)
     return fail(ctx, DG_E_ARG, "too few snapshots for this many steps");

@@ -3,9 +3,10 @@
 // retained initial state.  The plan is the recursion
 //     reverse(l, r, s): advance l -> l + m, store l + m, reverse(l + m, r, s - 1),
 //                       restore l, reverse(l, l + m, s)
-// with the split m chosen to minimise the forward steps, whose optimum has the
+// with a split m that minimises the forward steps, whose optimum has the
 // closed form  T(n, s) = t n - C(s + 1 + t, t - 1),  t the least integer with
-// C(s + 1 + t, t) >= n  (T(n, 0) = n (n - 1) / 2, T(1, s) = 0).  The adjoint of
+// C(s + 1 + t, t) >= n  (T(n, 0) = n (n - 1) / 2, T(1, s) = 0).  Each level of the
+// recursion lowers s or t, so its depth stays below s + t.  The adjoint of
 // step j needs the state Q^j in hand; it recomputes its own predictor.
 #include <algorithm>
 #include <cstdint>
@@ -35,16 +36,14 @@ struct Planner {
 
   void emit(int kind, int64_t a, int64_t b) { out->push_back(RevolveAction{kind, a, b}); }
 
-  int64_t split(int64_t n, int s) const {
-    int64_t best = 1, best_cost = -1;
-    for (int64_t m = 1; m < n; ++m) {
-      const int64_t c = m + revolve_cost(n - m, s - 1) + revolve_cost(m, s);
-      if (best_cost < 0 || c < best_cost) {
-        best_cost = c;
-        best = m;
-      }
-    }
-    return best;
+  // An optimal first split: with t the repetition number of (n, s), C(s + t, t) < n at t - 1,
+  // m = max(C(s + t - 1, t - 2), n - C(s + t, t)) leaves a right part of n - m steps that s - 1
+  // slots reverse with t repetitions and a left part that s slots reverse with t - 1.
+  static int64_t split(int64_t n, int s) {
+    int64_t t = 0;
+    while (beta(s + 1, t) < n) ++t;
+    const int64_t m = std::max(beta(s + 1, t - 2), n - beta(s, t));
+    return std::min(std::max<int64_t>(m, 1), n - 1);
   }
 
   void reverse(int64_t l, int64_t r, int s, int slot_l) {

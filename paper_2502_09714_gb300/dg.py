@@ -351,7 +351,8 @@ class Solver:
     def adjoint_gradient(self, ref, n_steps, dt=0.0, snapshots=40, grad_state=False, info=False):
         """Receiver misfit J of n_steps steps from the current state against
         ref [n_steps, R, 3] and its gradient by the discrete adjoint with
-        binomial checkpointing (`snapshots` state copies).  Returns
+        binomial checkpointing (`snapshots` state copies; 0 keeps as many as the
+        free device memory holds, up to the whole history).  Returns
         (J, dJ/dxi0 [E], dJ/dC_d [E]) plus dJ/dQ^0 [E, 10, L] with grad_state and
         the run's counts and device times (a dict) with info.  The state, time and
         traces of the solver are left unchanged."""
