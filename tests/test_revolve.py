@@ -72,7 +72,8 @@ def test_cost_matches_closed_form_and_exhaustive_search(snapshots):
         assert c == _closed(n, snapshots) == _dp(n, snapshots - 1), (n, snapshots)
 
 
-@pytest.mark.parametrize("n,snapshots", [(1, 1), (7, 1), (10, 3), (33, 4), (100, 6), (257, 9), (800, 40)])
+@pytest.mark.parametrize("n,snapshots", [(1, 1), (7, 1), (10, 3), (33, 4), (100, 6), (257, 9), (800, 40),
+                                           (800, 801), (1500, 2), (16384, 10), (5000, 4096)])
 def test_plan_reverses_every_step_once(n, snapshots):
     fw, acts = dgpkg.revolve_plan(n, snapshots)
     assert fw == dgpkg.revolve_cost(n, snapshots)
