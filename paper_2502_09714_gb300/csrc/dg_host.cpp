@@ -1265,6 +1265,7 @@ dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const flo
                         8.0 * static_cast<double>(ctx->F_interior) * adj_rec_stride(ctx->N)) / state_b;
     snapshots = static_cast<int>(std::max(1.0, std::min({fit, static_cast<double>(n_steps + 1), 4096.0})));
   }
+  snapshots = static_cast<int>(std::min<int64_t>(snapshots, n_steps + 1));   // more slots are never used
   const int s_free = snapshots - 1;
   if (revolve_cost(n_steps, s_free) > kMaxRevolveSteps)
     return fail(ctx, DG_E_ARG, "too few snapshots for this many steps");
