@@ -23,8 +23,11 @@ Pins (tests/test_oracle_adjoint.py): each pointwise derivative against central
 differences of the forward law, the step adjoint against central differences
 of Oracle.step along random directions (the dot-product test), and the misfit
 gradient against central differences of whole runs, element by element.
-Meshes with boundary faces, the Picard predictor and the other laws are not
-covered.
+Boundary faces (free surface, absorbing) are covered: their flux is linear in
+the own trace with a matrix of the own cell's effective Lame parameters, whose
+derivative in those parameters is taken by a central difference of relative
+step 1e-6 (error ~1e-10 of the term).  The Picard predictor and the other laws
+are not covered.
 """
 from __future__ import annotations
 
@@ -33,6 +36,7 @@ import math
 import numpy as np
 
 from .rheology import I2_FLOOR, invariants, jacobian_eff, strain_tensor
+from .boundary import boundary_matrix
 from .solver import PHI0
 
 _PAIRS = ((0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (2, 0))
@@ -138,12 +142,11 @@ def _lame_partials(rho):
 
 def step_vjp(o, Q, dt, lam):
     """lam [E, L, 10] = dJ/dQ^{k+1}; returns (dJ/dQ^k, dJ/dxi0, dJ/dC_d) of
-    Q^{k+1} = Oracle.step(Q^k) (all elements, interior faces only, CK predictor,
-    CDM law).  Point sources add a state-independent term and drop out."""
+    Q^{k+1} = Oracle.step(Q^k) (all elements, CK predictor, CDM law; interior,
+    free-surface and absorbing faces).  Point sources add a state-independent term
+    and drop out."""
     if o.law != "cdm" or o.picard_iterations:
         raise ValueError("the oracle adjoint covers the CDM law with the CK predictor")
-    if np.any(o.nbr < 0):
-        raise ValueError("the oracle adjoint covers meshes without boundary faces")
     E, L, N = o.E, o.L, o.N
     mat = o.mat
     rows = np.arange(E)
@@ -171,29 +174,51 @@ def step_vjp(o, Q, dt, lam):
 
     # 8. face terms: new -= area/|J| sum_z gz sum_i w_i phi_k(x_i) Fs_zip
     lam_cp = np.zeros(E)
+    a_lam_b = np.zeros(E)            # boundary faces: d/d lambda_eff, d/d mu_eff of the own cell
+    a_mu_b = np.zeros(E)
     for f in range(4):
-        nb = o.nbr[:, f]
-        n = o.normal[:, f]
-        um = np.einsum("il,nzlp->nzip", o.Vf_own[f], U, optimize=True)
-        up = np.einsum("nil,nzlp->nzip", o.Vf_nbr[o.row_of, f], U[nb], optimize=True)
-        lamFs = -np.einsum("n,z,i,ik,nkp->nzip", o.area[:, f] / o.detJ, gz, o.qf_w, o.Vf_own[f], lam,
-                           optimize=True)
-        lamFs[..., 9] = 0.0
-        # d(F(u).n) / du: lam_F[d, p] = lamFs_p n_d
-        lFn = np.einsum("nzip,nd->nzidp", lamFs, n, optimize=True)
-        lm, gm = flux_vjp(um, mz, lFn)
-        lp, gp = flux_vjp(up, mat[nb][:, None, None, :], lFn)
-        C = np.maximum(cp, cp[nb])
-        lam_um = 0.5 * lm + 0.5 * C[:, None, None, None] * lamFs
-        lam_up = 0.5 * lp - 0.5 * C[:, None, None, None] * lamFs
-        lC = 0.5 * np.einsum("nzip,nzip->n", lamFs, um - up, optimize=True)
-        own = np.where(cp > cp[nb], 1.0, np.where(cp < cp[nb], 0.0, 0.5))
-        lam_cp += own * lC
-        np.add.at(lam_cp, nb, (1.0 - own) * lC)
-        g_xi0 += 0.5 * gm.sum(axis=(1, 2))
-        np.add.at(g_xi0, nb, 0.5 * gp.sum(axis=(1, 2)))
-        lamU += np.einsum("il,nzip->nzlp", o.Vf_own[f], lam_um, optimize=True)
-        np.add.at(lamU, nb, np.einsum("nil,nzip->nzlp", o.Vf_nbr[o.row_of, f], lam_up, optimize=True))
+        nb_all = o.nbr[:, f]
+        inner = nb_all >= 0
+        um_all = np.einsum("il,nzlp->nzip", o.Vf_own[f], U, optimize=True)
+        lamFs_all = -np.einsum("n,z,i,ik,nkp->nzip", o.area[:, f] / o.detJ, gz, o.qf_w, o.Vf_own[f], lam,
+                               optimize=True)
+        lamFs_all[..., 9] = 0.0
+        # interior faces: Fs = (F(u-).n + F(u+).n)/2 + C/2 (u- - u+)
+        rr = np.nonzero(inner)[0]
+        if rr.size:
+            nb = nb_all[rr]
+            n = o.normal[rr, f]
+            um = um_all[rr]
+            lamFs = lamFs_all[rr]
+            up = np.einsum("nil,nzlp->nzip", o.Vf_nbr[o.row_of[rr], f], U[nb], optimize=True)
+            # d(F(u).n) / du: lam_F[d, p] = lamFs_p n_d
+            lFn = np.einsum("nzip,nd->nzidp", lamFs, n, optimize=True)
+            lm, gm = flux_vjp(um, mat[rr][:, None, None, :], lFn)
+            lp, gp = flux_vjp(up, mat[nb][:, None, None, :], lFn)
+            C = np.maximum(cp[rr], cp[nb])
+            lam_um = 0.5 * lm + 0.5 * C[:, None, None, None] * lamFs
+            lam_up = 0.5 * lp - 0.5 * C[:, None, None, None] * lamFs
+            lC = 0.5 * np.einsum("nzip,nzip->n", lamFs, um - up, optimize=True)
+            own = np.where(cp[rr] > cp[nb], 1.0, np.where(cp[rr] < cp[nb], 0.0, 0.5))
+            np.add.at(lam_cp, rr, own * lC)
+            np.add.at(lam_cp, nb, (1.0 - own) * lC)
+            np.add.at(g_xi0, rr, 0.5 * gm.sum(axis=(1, 2)))
+            np.add.at(g_xi0, nb, 0.5 * gp.sum(axis=(1, 2)))
+            np.add.at(lamU, rr, np.einsum("il,nzip->nzlp", o.Vf_own[f], lam_um, optimize=True))
+            np.add.at(lamU, nb, np.einsum("nil,nzip->nzlp", o.Vf_nbr[o.row_of[rr], f], lam_up, optimize=True))
+        # boundary faces (Appendix A): Fs = M(lambda_eff, mu_eff) u-, M the face's flux matrix; its
+        # derivative in the effective Lame parameters by a central difference of relative step 1e-6
+        for k in np.nonzero(~inner)[0]:
+            bc, n = int(o.face_bc[k, f]), o.normal[k, f]
+            le, me, rho_k = lam_eff[k], mu_eff[k], mat[k, 0]
+            Mb = boundary_matrix(bc, n, le, me, rho_k)
+            lFs, uk = lamFs_all[k], um_all[k]
+            lamU[k] += np.einsum("il,zip,pq->zlq", o.Vf_own[f], lFs, Mb, optimize=True)
+            hl, hm = 1e-6 * abs(le) + 1e-300, 1e-6 * abs(me) + 1e-300
+            dMl = (boundary_matrix(bc, n, le + hl, me, rho_k) - boundary_matrix(bc, n, le - hl, me, rho_k)) / (2 * hl)
+            dMm = (boundary_matrix(bc, n, le, me + hm, rho_k) - boundary_matrix(bc, n, le, me - hm, rho_k)) / (2 * hm)
+            a_lam_b[k] += np.einsum("zip,pq,ziq->", lFs, dMl, uk, optimize=True)
+            a_mu_b[k] += np.einsum("zip,pq,ziq->", lFs, dMm, uk, optimize=True)
 
     # 6. Taylor expansion U(t_z) = sum_i t_z^i / i! D^i
     lamD = np.einsum("zi,nzlp->inlp", coef, lamU, optimize=True)
@@ -225,8 +250,8 @@ def step_vjp(o, Q, dt, lam):
     m2 = lam_eff + 2.0 * mu_eff
     live = m2 > 0.0
     dc = np.where(live, lam_cp / (2.0 * rho * np.where(live, cp, 1.0)), 0.0)
-    a_lam += dc
-    a_mu += 2.0 * dc
+    a_lam += dc + a_lam_b
+    a_mu += 2.0 * dc + a_mu_b
     # 2./1. effective Lame parameters at the cell mean ubar = phi_0 Q_0
     ubar = Q[:, 0, :] * PHI0
     lb, gx = lame_vjp(ubar, mat, a_lam, a_mu)

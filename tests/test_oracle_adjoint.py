@@ -176,3 +176,48 @@ def test_misfit_gradient_against_finite_differences():
     h = 1e-5
     fd = (misfit(o, Q0 + h * d, dt, ns, ref)[0] - misfit(o, Q0 - h * d, dt, ns, ref)[0]) / (2 * h)
     assert abs(fd - np.sum(lq * d)) <= 1e-6 * abs(fd)
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_step_dot_product_with_boundary_faces(N):
+    """A closed jittered box with a free-surface top and absorbing sides: the
+    step transpose, including the boundary fluxes' dependence on the effective
+    Lame parameters of the cell mean, passes the dot-product test along random
+    state, xi0 and C_d directions."""
+    from synthetic.mesh import kuhn_box_mesh
+    rng = np.random.default_rng(40 + N)
+    g = np.linspace(0.0, 4000.0, 4)
+    mesh = kuhn_box_mesh(g, g, g, periodic=(False, False, False), jitter=0.1, seed=3)
+    E = mesh.n_elem
+    mat = np.zeros((E, 6))
+    mat[:] = (2700.0, 32e9, 32e9, 3.7e10, -0.8, 1e-5)
+    mat[:, 1] *= rng.uniform(0.9, 1.1, E)
+    mat[:, 4] = rng.uniform(-1.0, -0.6, E)
+    mat[:, 5] = 10 ** rng.uniform(-6, -4, E)
+    o = Oracle(mesh.elem_xyz, mesh.elem_vid, N, mat, face_bc=mesh.face_bc)
+    assert np.any(o.nbr < 0)
+    deg = np.array([sum(m) for m in mode_list(N)])
+    Q = rng.normal(size=(E, o.L, 10)) * (0.5 ** deg)[None, :, None]
+    Q[..., :6] *= 1e-3
+    Q[..., 6:9] *= 3.0
+    Q[..., 9] *= 0.02
+    Q[:, 0, 9] = 0.05 + 0.05 * rng.uniform(size=E)
+    dt = 0.5 * o.cfl_dt()
+    lam = rng.normal(size=Q.shape)
+    lQ, gx, gc = step_vjp(o, Q, dt, lam)
+    d = rng.normal(size=Q.shape) * np.abs(Q).mean(axis=0, keepdims=True)
+    h = 1e-6
+    fd = np.sum(lam * (o.step(Q + h * d, dt) - o.step(Q - h * d, dt))) / (2 * h)
+    assert abs(fd - np.sum(lQ * d)) <= 1e-7 * abs(fd), (fd, np.sum(lQ * d))
+    # the alpha cell means alone: the boundary matrices' dependence on lambda_eff, mu_eff
+    d = np.zeros_like(Q)
+    d[:, 0, 9] = rng.uniform(0.5, 1.5, size=E) * 0.01
+    fd = np.sum(lam * (o.step(Q + h * d, dt) - o.step(Q - h * d, dt))) / (2 * h)
+    assert abs(fd - np.sum(lQ * d)) <= 1e-6 * abs(fd), (fd, np.sum(lQ * d))
+    for col, gg, hh in ((4, gx, 1e-6), (5, gc, 1e-12)):
+        dd = rng.normal(size=E)
+        step = np.outer(dd, np.eye(6)[col]) * hh
+        o1 = Oracle(mesh.elem_xyz, mesh.elem_vid, N, mat + step, face_bc=mesh.face_bc)
+        o2 = Oracle(mesh.elem_xyz, mesh.elem_vid, N, mat - step, face_bc=mesh.face_bc)
+        fd = np.sum(lam * (o1.step(Q, dt) - o2.step(Q, dt))) / (2 * hh)
+        assert abs(fd - np.sum(gg * dd)) <= 1e-6 * abs(fd), (col, fd, np.sum(gg * dd))
