@@ -304,8 +304,10 @@ dg_status dg_reference_table(int order, int which, double* out, int64_t cap, int
  * time and recorded traces are left unchanged.  info: NULL or the counts and
  * device milliseconds of the forward steps, the adjoint steps (predictor
  * recompute, adjoint kernels and misfit terms) and the snapshot copies.
- * Requires the CDM law, the CK predictor, one member, no boundary faces
- * (DG_E_UNSUPPORTED otherwise), material, state and at least one receiver
+ * Free-surface and absorbing faces are differentiated too (their flux through
+ * the own trace and the effective Lame parameters of the cell mean).
+ * Requires the CDM law, the CK predictor, one member (DG_E_UNSUPPORTED
+ * otherwise), material, state and at least one receiver
  * (DG_E_STATE); DG_E_ARG for n_steps outside 1..2^20, snapshots outside
  * 0..4096 or a plan of more than 2^27 forward steps; DG_E_OOM if the
  * snapshots (snapshots x n_elem x 4 ceil(10 L / 4) floats) do not fit;

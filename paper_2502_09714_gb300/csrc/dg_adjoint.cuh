@@ -131,6 +131,94 @@ __device__ __forceinline__ float normal_flux_vjp(const float* u, const MatF& m, 
   return stress_vjp(u, m, ls, lu);
 }
 
+// Transpose of the boundary flux of a free-surface (bc 1) or absorbing (bc 2) face
+// (Appendix A; the closed form of the forward face kernel): adds to lu[10] the gradient
+// of sum_p lf[p] F_p(u), which is linear in u, and to *dl and *dm its derivatives in the
+// effective Lame parameters lambda and mu of the cell mean (through sigma_nn, c_p, c_s
+// and k_p = c_p / (lambda + 2 mu)).
+__device__ __forceinline__ void boundary_flux_vjp(int bc, const float* u, const float n[3], float lam, float mu,
+                                                  float rho_inv, float cp, float cs, float kp, const float lf[9],
+                                                  float lu[10], float* dl, float* dm) {
+  const float En[3] = {u[0] * n[0] + u[3] * n[1] + u[5] * n[2], u[3] * n[0] + u[1] * n[1] + u[4] * n[2],
+                       u[5] * n[0] + u[4] * n[1] + u[2] * n[2]};
+  const float enn = En[0] * n[0] + En[1] * n[1] + En[2] * n[2];
+  const float I1 = u[0] + u[1] + u[2];
+  const float snn = lam * I1 + 2.f * mu * enn;
+  const float vn = u[6] * n[0] + u[7] * n[1] + u[8] * n[2];
+  float vt[3], et[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    vt[i] = u[6 + i] - vn * n[i];
+    et[i] = En[i] - enn * n[i];
+  }
+  const float h = bc == 2 ? 0.5f : 1.f;
+  // strain rows h (a n n^T + n b^T + b n^T)
+  const float la = h * (lf[0] * n[0] * n[0] + lf[1] * n[1] * n[1] + lf[2] * n[2] * n[2] + lf[3] * n[0] * n[1] +
+                        lf[4] * n[1] * n[2] + lf[5] * n[2] * n[0]);
+  const float lb[3] = {h * (2.f * lf[0] * n[0] + lf[3] * n[1] + lf[5] * n[2]),
+                       h * (2.f * lf[1] * n[1] + lf[3] * n[0] + lf[4] * n[2]),
+                       h * (2.f * lf[2] * n[2] + lf[4] * n[1] + lf[5] * n[0])};
+  float lsnn = 0.f, lvn = 0.f, lvt[3] = {0.f, 0.f, 0.f}, let[3] = {0.f, 0.f, 0.f};
+  float dlam = 0.f, dmu = 0.f, dcp = 0.f, dcs = 0.f, dkp = 0.f;
+  if (bc == 2) {
+    // velocity rows pn n_i + (-2 mu et_i rho_inv + c_s vt_i) / 2, pn = (-sigma_nn rho_inv + c_p v.n) / 2
+    const float lpn = lf[6] * n[0] + lf[7] * n[1] + lf[8] * n[2];
+    lsnn += -0.5f * rho_inv * lpn;
+    lvn += 0.5f * cp * lpn;
+    dcp += 0.5f * vn * lpn;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      let[i] += -mu * rho_inv * lf[6 + i];
+      lvt[i] += 0.5f * cs * lf[6 + i];
+      dmu += -et[i] * rho_inv * lf[6 + i];
+      dcs += 0.5f * vt[i] * lf[6 + i];
+    }
+  }
+  // b_i = -vt_i / 2 + c_s et_i ; a = -v.n + k_p sigma_nn
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    lvt[i] += -0.5f * lb[i];
+    let[i] += cs * lb[i];
+    dcs += lb[i] * et[i];
+  }
+  lvn += -la;
+  lsnn += kp * la;
+  dkp += la * snn;
+  // et_i = En_i - enn n_i ; vt_i = v_i - vn n_i ; sigma_nn = lambda I1 + 2 mu enn ; vn = v.n ; enn = En.n
+  float lEn[3], lenn = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    lEn[i] = let[i];
+    lenn -= let[i] * n[i];
+    lvn -= lvt[i] * n[i];
+  }
+  const float lI1 = lam * lsnn;
+  lenn += 2.f * mu * lsnn;
+  dlam += lsnn * I1;
+  dmu += 2.f * lsnn * enn;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    lu[6 + i] += lvt[i] + lvn * n[i];
+    lEn[i] += lenn * n[i];
+  }
+  // En_i = sum_j eps_ij n_j
+  lu[0] += lEn[0] * n[0] + lI1;
+  lu[1] += lEn[1] * n[1] + lI1;
+  lu[2] += lEn[2] * n[2] + lI1;
+  lu[3] += lEn[0] * n[1] + lEn[1] * n[0];
+  lu[4] += lEn[1] * n[2] + lEn[2] * n[1];
+  lu[5] += lEn[0] * n[2] + lEn[2] * n[0];
+  // c_p = sqrt((lambda + 2 mu) rho_inv), c_s = sqrt(mu rho_inv), k_p = c_p / (lambda + 2 mu)
+  const float m2 = lam + 2.f * mu;
+  if (cp > 0.f && m2 > 0.f) {
+    dlam += dcp * 0.5f * rho_inv / cp - dkp * 0.5f * kp / m2;
+    dmu += dcp * rho_inv / cp - dkp * kp / m2;
+  }
+  if (cs > 0.f) dmu += dcs * 0.5f * rho_inv / cs;
+  *dl += dlam;
+  *dm += dmu;
+}
+
 // Block-wide sum of one float per thread into a shared double (atomic).
 __device__ __forceinline__ void block_add(double* acc, float v) {
 #pragma unroll
@@ -238,15 +326,19 @@ __global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
   using S = FaceSmem<N>;
   constexpr int L = A::L, NF = A::NF, NT = A::NT;
   extern __shared__ __align__(16) float smem[];
-  __shared__ double sRed[4];
+  __shared__ double sRed[6];
   __shared__ float sC[NT * NT], sG[NT];
   const TableLayout T = table_layout(N);
   const float* tb = a.tables;
   time_tables<N>(tb, T, a.dt, sC, sG);
   for (int64_t f = blockIdx.x; f < a.F; f += gridDim.x) {
     const int4 fc = a.faces[f];
-    const int64_t e0 = fc.x, e1 = fc.z;
-    const int lf0 = fc.y, lf1 = fc.w;
+    // a boundary face is (element, local face, -1, tag): its side 1 is a stand-in that
+    // receives nothing
+    const bool bnd = fc.z < 0;
+    const int bc = bnd ? fc.w : 0;
+    const int64_t e0 = fc.x, e1 = bnd ? fc.x : fc.z;
+    const int lf0 = fc.y, lf1 = bnd ? fc.y : fc.w;
     __syncthreads();
     // one batch of 16-byte asynchronous copies: lam, Q and D of both sides
     for (int w = threadIdx.x; w < A::QS / 2; w += blockDim.x) {
@@ -260,7 +352,7 @@ __global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
       tc::cp_async16(smem + S::oD + sd * A::DS + c, a.d + (sd ? e1 : e0) * A::DS + c);
     }
     tc::cp_async_wait_all();
-    if (threadIdx.x < 4) sRed[threadIdx.x] = 0.0;
+    if (threadIdx.x < 6) sRed[threadIdx.x] = 0.0;
     __syncthreads();
     // traces of both sides at the space-time face nodes
     for (int sd = 0; sd < 2; ++sd)
@@ -268,7 +360,7 @@ __global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
                          smem + S::oD + sd * A::DS, sC, smem + S::oTr + sd * NT * NF * 10);
     // lam of the time-integrated face flux:
     //   lff[i][p] = -(a0 sum_k Vfw[f0][i][k] lam0[k][p] - a1 sum_k Vfw[f1][i][k] lam1[k][p])
-    const float a0 = a.geom[e0].face[lf0][3], a1 = a.geom[e1].face[lf1][3];
+    const float a0 = a.geom[e0].face[lf0][3], a1 = bnd ? 0.f : a.geom[e1].face[lf1][3];
     for (int w = threadIdx.x; w < NF * 9; w += blockDim.x) {
       const int i = w / 9, p = w - i * 9;
       float s0 = 0.f, s1 = 0.f;
@@ -279,11 +371,26 @@ __global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
       smem[S::oLff + w] = -(a0 * s0 - a1 * s1);
     }
     __syncthreads();
-    // the Rusanov flux transposed at each space-time node, one side per item
+    // the Rusanov flux (or the boundary flux) transposed at each space-time node, one side per item
     const float n[3] = {a.geom[e0].face[lf0][0], a.geom[e0].face[lf0][1], a.geom[e0].face[lf0][2]};
     const float cp0 = a.cp[e0], cp1 = a.cp[e1];
     const float C = fmaxf(cp0, cp1);
-    float pC = 0.f, px0 = 0.f, px1 = 0.f;
+    // boundary faces: effective Lame parameters of the own cell mean and the speeds of the forward flux
+    float blam = 0.f, bmu = 0.f, bcp = 0.f, bcs = 0.f, bkp = 0.f;
+    const MatF mb = a.mat[e0];
+    if (bnd) {
+      const float r6 = 2.449489742783178f;
+      float ub[10];
+#pragma unroll
+      for (int p = 0; p < 10; ++p) ub[p] = smem[S::oQ + p] * r6;
+      const Inv v = invariants(ub);
+      blam = mb.lam0 - ub[9] * mb.gamma_r * v.xi * (1.f / 3.f);
+      bmu = mb.mu0 + ub[9] * mb.xi0 * mb.gamma_r - 0.5f * ub[9] * mb.gamma_r * v.xi;
+      bcp = sqrtf(fmaxf(blam + 2.f * bmu, 0.f) * mb.rho_inv);
+      bcs = sqrtf(fmaxf(bmu, 0.f) * mb.rho_inv);
+      bkp = blam + 2.f * bmu > 0.f ? bcp / (blam + 2.f * bmu) : 0.f;
+    }
+    float pC = 0.f, px0 = 0.f, px1 = 0.f, pl = 0.f, pm = 0.f;
     for (int w = threadIdx.x; w < 2 * NT * NF; w += blockDim.x) {
       const int sd = w / (NT * NF), r = w - sd * NT * NF;
       const int z = r / NF, i = r - z * NF;
@@ -295,10 +402,17 @@ __global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
       float lu[10];
 #pragma unroll
       for (int p = 0; p < 10; ++p) lu[p] = 0.f;
+      float* o = smem + S::oLu + w * 10;
+      if (bnd) {
+        if (sd == 0) boundary_flux_vjp(bc, u, n, blam, bmu, mb.rho_inv, bcp, bcs, bkp, lfs, lu, &pl, &pm);
+#pragma unroll
+        for (int p = 0; p < 9; ++p) o[p] = lu[p];
+        o[9] = 0.f;
+        continue;
+      }
       const MatF m = a.mat[sd ? e1 : e0];
       const float gx = 0.5f * normal_flux_vjp(u, m, n, lfs, lu);
       const float cs = sd ? -0.5f * C : 0.5f * C;
-      float* o = smem + S::oLu + w * 10;
 #pragma unroll
       for (int p = 0; p < 9; ++p) o[p] = 0.5f * lu[p] + cs * lfs[p];
       o[9] = 0.5f * lu[9];
@@ -311,6 +425,8 @@ __global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
         px1 += gx;
       }
     }
+    block_add(&sRed[3], pl);
+    block_add(&sRed[4], pm);
     block_add(&sRed[0], pC);
     block_add(&sRed[1], px0);
     block_add(&sRed[2], px1);
@@ -360,10 +476,12 @@ __global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
       // C = max(cp0, cp1): its derivative goes to the larger speed, in halves at a tie
       const float share = cp0 > cp1 ? (sd == 0 ? 1.f : 0.f) : (cp0 < cp1 ? (sd == 1 ? 1.f : 0.f) : 0.5f);
       float* tail = a.rec + (f * 2 + sd) * A::RS + A::LDS;
-      tail[0] = share * static_cast<float>(sRed[0]);
-      tail[1] = static_cast<float>(sRed[1 + sd]);
-      tail[2] = 0.f;
-      tail[3] = 0.f;
+      // lam of the side's P speed, the xi0 part of its flux, and (boundary faces) the flux's
+      // derivatives in the own cell's lambda_eff and mu_eff
+      tail[0] = bnd ? 0.f : share * static_cast<float>(sRed[0]);
+      tail[1] = bnd ? 0.f : static_cast<float>(sRed[1 + sd]);
+      tail[2] = bnd && sd == 0 ? static_cast<float>(sRed[3]) : 0.f;
+      tail[3] = bnd && sd == 0 ? static_cast<float>(sRed[4]) : 0.f;
     }
   }
 }
@@ -393,7 +511,7 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
   using S = ElemSmem<N>;
   constexpr int L = A::L, NQ = A::NQ, NT = A::NT;
   extern __shared__ __align__(16) float smem[];
-  __shared__ double sRed[4];          // xi0, C_d, lam/rho, mu/rho
+  __shared__ double sRed[6];          // xi0, C_d, lam/rho, mu/rho, boundary d/dlam, d/dmu
   __shared__ float sGeo[16];          // Theta^{-1} [e][d], lambda_eff/rho, mu_eff/rho
   __shared__ float sC[NT * NT], sG[NT];
   const TableLayout T = table_layout(N);
@@ -421,7 +539,7 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
     tc::cp_async_wait_all();
     const MatF m = a.mat[e];
     if (threadIdx.x < 9) sGeo[threadIdx.x] = a.geom[e].tinv[threadIdx.x];
-    if (threadIdx.x < 4) sRed[threadIdx.x] = 0.0;
+    if (threadIdx.x < 6) sRed[threadIdx.x] = 0.0;
     __syncthreads();
     node_values<N, NQ>(tb + T.VvT, A::NQP, smem + S::oQ, smem + S::oD, sC, smem + S::oU, smem + S::oU0);
     // per volume node q: X[q][d][p] = sum_k w_q dphi_k/dx_d(x_q) lam[k][p], X[q][27] = sum_k w_q phi_k lam[k][9];
@@ -520,6 +638,8 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
       const float* tail = smem + S::oR + threadIdx.x * A::RS + A::LDS;
       atomicAdd(&sRed[2], static_cast<double>(tail[0]));   // lam of cp (scaled below)
       atomicAdd(&sRed[0], static_cast<double>(tail[1]));   // xi0 part of the face fluxes
+      atomicAdd(&sRed[4], static_cast<double>(tail[2]));   // boundary fluxes: d/dlambda_eff
+      atomicAdd(&sRed[5], static_cast<double>(tail[3]));   //                  d/dmu_eff
     }
     block_add(&sRed[0], px);
     block_add(&sRed[1], pc);
@@ -545,8 +665,9 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
     if (threadIdx.x == 0) {
       const float cp = a.cp[e];
       const float dc = (lam_eff + 2.f * mu_eff > 0.f && cp > 0.f) ? static_cast<float>(lam_cp) * 0.5f * m.rho_inv / cp : 0.f;
-      sRed[2] = static_cast<double>(dc) * m.rho;        // in units of lam/rho: d/d(lam/rho) = rho d/dlam
-      sRed[3] = static_cast<double>(2.f * dc) * m.rho;
+      // in units of lam/rho: d/d(lam/rho) = rho d/dlam
+      sRed[2] = (static_cast<double>(dc) + sRed[4]) * m.rho;
+      sRed[3] = (static_cast<double>(2.f * dc) + sRed[5]) * m.rho;
     }
     __syncthreads();
     // Cauchy-Kovalevskaya recursion transposed, order N down to 1

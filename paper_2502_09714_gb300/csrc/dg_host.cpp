@@ -1251,7 +1251,6 @@ dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const flo
   if (ctx->law != 0) return fail(ctx, DG_E_UNSUPPORTED, "the adjoint covers the CDM law");
   if (ctx->picard_iters > 0) return fail(ctx, DG_E_UNSUPPORTED, "the adjoint covers the CK predictor");
   if (ctx->M != 1) return fail(ctx, DG_E_UNSUPPORTED, "the adjoint covers one member");
-  if (ctx->F > ctx->F_interior) return fail(ctx, DG_E_UNSUPPORTED, "the adjoint covers meshes without boundary faces");
   const int R = static_cast<int>(ctx->rec_host.size());
   if (R < 1) return fail(ctx, DG_E_STATE, "the misfit needs receivers (dg_receivers)");
   if (dt <= 0) dt = ctx->dt_cfl;
@@ -1262,7 +1261,7 @@ dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const flo
     DG_CUDA(ctx, cudaMemGetInfo(&free_b, &total_b));
     const double state_b = 4.0 * static_cast<double>(ctx->EV) * q_stride(ctx->N);
     const double fit = (0.8 * static_cast<double>(free_b) - 6.0 * state_b -
-                        8.0 * static_cast<double>(ctx->F_interior) * adj_rec_stride(ctx->N)) / state_b;
+                        8.0 * static_cast<double>(ctx->F) * adj_rec_stride(ctx->N)) / state_b;
     snapshots = static_cast<int>(std::max(1.0, std::min({fit, static_cast<double>(n_steps + 1), 4096.0})));
   }
   snapshots = static_cast<int>(std::min<int64_t>(snapshots, n_steps + 1));   // more slots are never used
@@ -1296,7 +1295,7 @@ dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const flo
   float* work[2] = {static_cast<float*>(take(state_bytes)), static_cast<float*>(take(state_bytes))};
   float* last = static_cast<float*>(take(state_bytes));
   float* lam[2] = {static_cast<float*>(take(state_bytes)), static_cast<float*>(take(state_bytes))};
-  float* rec = static_cast<float*>(take(sizeof(float) * static_cast<size_t>(ctx->F_interior * 2 * adj_rec_stride(N))));
+  float* rec = static_cast<float*>(take(sizeof(float) * static_cast<size_t>(ctx->F * 2 * adj_rec_stride(N))));
   double* g = static_cast<double*>(take(sizeof(double) * static_cast<size_t>(2 * E + 1)));
   float* ref_dev = static_cast<float*>(take(sizeof(float) * static_cast<size_t>(n_steps * R * 3)));
   if (!slots || !work[0] || !work[1] || !last || !lam[0] || !lam[1] || !rec || !g || !ref_dev) {
@@ -1323,7 +1322,7 @@ dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const flo
   StepArgs a{};
   a.E = E;
   a.F = ctx->F;
-  a.has_boundary = 0;
+  a.has_boundary = ctx->F > ctx->F_interior;
   a.d = ctx->d;
   a.cp = ctx->cp;
   a.ff = ctx->ff;
@@ -1342,7 +1341,7 @@ dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const flo
   a.status = ctx->status;
   AdjArgs b{};
   b.E = E;
-  b.F = ctx->F_interior;
+  b.F = ctx->F;                       // interior faces, then boundary faces
   b.d = ctx->d;
   b.cp = ctx->cp;
   b.rec = rec;

@@ -196,7 +196,7 @@ cudaError_t launch_receivers(int N, int n_rec, const ReceiverDev* rec, const flo
 // side's P speed and the xi0 part of the side's flux.
 __host__ __device__ constexpr int adj_rec_stride(int N) { return q_stride(N) + d_stride(N) + 4; }
 struct AdjArgs {
-  int64_t E, F;           // elements, interior faces
+  int64_t E, F;           // elements, faces (interior first, then boundary)
   const float* q;         // Q^k [E][q_stride]
   const float* d;         // predictor output of Q^k [E][d_stride]
   const float* cp;        // effective P speeds of Q^k [E]

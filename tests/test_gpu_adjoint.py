@@ -89,6 +89,46 @@ def test_adjoint_parity_with_oracle(N):
     assert errs["xi0"] <= TOL_GRAD and errs["cd"] <= TOL_GRAD and errs["q0"] <= TOL_GRAD, errs
 
 
+@pytest.mark.parametrize("N", [2, 3])
+def test_adjoint_parity_with_boundary_faces(N):
+    """A closed jittered box (162 tets) with a free-surface top and absorbing
+    sides: the GPU gradient against the oracle's adjoint, whose boundary part is
+    pinned by the dot-product tests on the same kind of box."""
+    import paper_2502_09714_gb300 as dgpkg
+    from synthetic.mesh import kuhn_box_mesh
+    n = 6
+    g = np.linspace(0.0, 4000.0, 4)
+    mesh = kuhn_box_mesh(g, g, g, periodic=(False, False, False), jitter=0.1, seed=3)
+    E = mesh.n_elem
+    w = workload_adjoint(n=3, order=N, steps=n)
+    mat, mref = w["material"].copy(), w["material_ref"].copy()
+    mat[:, 5] *= 0.75
+    mref[:, 5] *= 0.75
+    rng = np.random.default_rng(50 + N)
+    rec = rng.uniform(400.0, 3600.0, size=(16, 3))
+    o = Oracle(mesh.elem_xyz, mesh.elem_vid, N, mat, face_bc=mesh.face_bc)
+    oref = Oracle(mesh.elem_xyz, mesh.elem_vid, N, mref, face_bc=mesh.face_bc)
+    for oo in (o, oref):
+        oo.set_receivers(rec)
+    deg = np.array([sum(mm) for mm in mode_list(N)])
+    Q0 = rng.normal(size=(E, o.L, 10)) * (0.5 ** deg)[None, :, None]
+    Q0[..., :6] *= 2e-4
+    Q0[..., 6:9] *= 0.6
+    Q0[..., 9] *= 0.005
+    Q0[:, 0, 9] = (0.02 + 0.03 * rng.uniform(size=E)) / math.sqrt(6.0)
+    dt = 0.5 * o.cfl_dt()
+    _, ref = oref.run(Q0, dt, n, record=True)
+    J, gx, gc, lq = misfit_gradient(o, Q0, dt, n, ref)
+    s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, N, face_bc=mesh.face_bc)
+    s.set_material(mat)
+    s.set_state(to_abi(Q0))
+    s.set_receivers(rec)
+    Jg, gxg, gcg, lqg = s.adjoint_gradient(ref, n, dt, snapshots=3, grad_state=True)
+    errs = {"xi0": _rel(gxg, gx), "cd": _rel(gcg, gc), "q0": _rel(lqg, to_abi(lq))}
+    print(N, errs)
+    assert errs["xi0"] <= TOL_GRAD and errs["cd"] <= TOL_GRAD and errs["q0"] <= TOL_GRAD, errs
+
+
 def test_snapshot_budget_and_state_untouched():
     N, n = 2, 9
     w, o, Q0, dt, ref = _case(N, n, seed=5)
