@@ -6,11 +6,14 @@
 // U the Taylor expansion of the CK predictor, Eqs. "CKIter-ref-matrix" and
 // "CKIter-ref-source"), every product of the forward step transposed:
 //
-//   k_adj_face   once per interior face: lam of the face term -> lam of both
-//                traces at the space-time face nodes through the Rusanov
-//                flux (flux Jacobians of both sides, C = max of the two P
-//                speeds), folded into Taylor orders and projected onto the
-//                modes of each side; lam of C and the xi0 part per side.
+//   k_adj_face   once per face: lam of the face term -> lam of both traces at
+//                the space-time face nodes through the Rusanov flux (flux
+//                Jacobians of both sides, C = max of the two P speeds), folded
+//                into Taylor orders and projected onto the modes of each side;
+//                lam of C and the xi0 part per side.  A free-surface or
+//                absorbing face transposes its boundary flux (Appendix A) and
+//                returns the flux's derivatives in the own cell's effective
+//                Lame parameters.
 //   k_adj_elem   once per element: volume flux and damage-rate source
 //                transposed at the space-time volume nodes, the records of its
 //                four faces gathered, the CK recursion transposed from order N
