@@ -221,3 +221,47 @@ def test_step_dot_product_with_boundary_faces(N):
         o2 = Oracle(mesh.elem_xyz, mesh.elem_vid, N, mat - step, face_bc=mesh.face_bc)
         fd = np.sum(lam * (o1.step(Q, dt) - o2.step(Q, dt))) / (2 * hh)
         assert abs(fd - np.sum(gg * dd)) <= 1e-6 * abs(fd), (col, fd, np.sum(gg * dd))
+
+
+def test_misfit_gradient_with_boundary_faces():
+    """The closed 162-tet box at N = 1 over 3 steps: the misfit gradient matches
+    central differences of whole oracle runs on 8 random elements, for xi0 and
+    C_d."""
+    from synthetic.mesh import kuhn_box_mesh
+    rng = np.random.default_rng(61)
+    g = np.linspace(0.0, 4000.0, 4)
+    mesh = kuhn_box_mesh(g, g, g, periodic=(False, False, False), jitter=0.1, seed=3)
+    E, N, ns = mesh.n_elem, 1, 3
+    w = workload_adjoint(n=3, order=N, steps=ns)
+    mat, mref = w["material"].copy(), w["material_ref"].copy()
+    rec = rng.uniform(400.0, 3600.0, size=(16, 3))
+    o = Oracle(mesh.elem_xyz, mesh.elem_vid, N, mat, face_bc=mesh.face_bc)
+    oref = Oracle(mesh.elem_xyz, mesh.elem_vid, N, mref, face_bc=mesh.face_bc)
+    for oo in (o, oref):
+        oo.set_receivers(rec)
+    deg = np.array([sum(mm) for mm in mode_list(N)])
+    Q0 = rng.normal(size=(E, o.L, 10)) * (0.5 ** deg)[None, :, None]
+    Q0[..., :6] *= 2e-4
+    Q0[..., 6:9] *= 0.6
+    Q0[..., 9] = 0.0
+    Q0[:, 0, 9] = 0.05
+    dt = 0.5 * o.cfl_dt()
+    _, ref = oref.run(Q0, dt, ns, record=True)
+    J, gx, gc, _ = misfit_gradient(o, Q0, dt, ns, ref)
+    assert J > 0
+    els = rng.choice(E, 8, replace=False)
+    for col, gg, rel_h in ((4, gx, 1e-5), (5, gc, 1e-3)):
+        fd = []
+        for e in els:
+            h = rel_h * abs(mat[e, col])
+            runs = []
+            for sgn in (1.0, -1.0):
+                mm = mat.copy()
+                mm[e, col] += sgn * h
+                oo = Oracle(mesh.elem_xyz, mesh.elem_vid, N, mm, face_bc=mesh.face_bc)
+                oo.set_receivers(rec)
+                runs.append(misfit(oo, Q0, dt, ns, ref)[0])
+            fd.append((runs[0] - runs[1]) / (2 * h))
+        fd = np.array(fd)
+        assert np.count_nonzero(fd) >= 4
+        assert np.abs(fd - gg[els]).max() <= 1e-6 * np.abs(fd).max(), (col, fd, gg[els])
