@@ -1256,7 +1256,8 @@ dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const flo
   if (dt <= 0) dt = ctx->dt_cfl;
   if (!std::isfinite(dt)) return fail(ctx, DG_E_ARG, "non-finite dt");
   if (snapshots == 0) {
-    // as many state copies as a fifth of the free device memory spares, at most the whole history
+    // as many state copies as 80 % of the free device memory holds beside the call's other
+    // buffers, at most the whole history
     size_t free_b = 0, total_b = 0;
     DG_CUDA(ctx, cudaMemGetInfo(&free_b, &total_b));
     const double state_b = 4.0 * static_cast<double>(ctx->EV) * q_stride(ctx->N);
