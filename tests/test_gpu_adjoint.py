@@ -1,6 +1,7 @@
 """GPU checks of the discrete adjoint (dg_adjoint_gradient): the misfit, its
 gradient in xi0 and C_d and the gradient in the initial state against the
-oracle's adjoint on the 384-tet cube, invariance under the snapshot budget,
+oracle's adjoint on the 384-tet cube and on a closed box with free-surface and
+absorbing faces, invariance under the snapshot budget,
 the state left untouched, the torch.autograd.Function, the refused
 configurations, and, on the 82,944-tet adjoint workload, the second-order
 Taylor remainder of the misfit along the gradient's own parameter directions.
