@@ -162,6 +162,43 @@ def cpu_baseline(workload, steps=1, max_seconds=None):
     return rows.size * steps / el, sample, threads, el
 
 
+def cpu_adjoint_baseline():
+    """The FP64 oracle's forward step and its discrete adjoint (oracle.adjoint,
+    as it stands) timed on a bounded sample of the adjoint workload: its jittered
+    cube at 4 cells per side (384 tets) and degree 3, one step each from a seeded
+    damaged state.  Returns (adjoint element-steps/s, forward element-steps/s,
+    sample text, threads)."""
+    import math
+    from oracle import Oracle, mode_list
+    from oracle.adjoint import step_vjp
+    from synthetic import workload_adjoint
+    w = workload_adjoint(n=4, order=3, steps=1)
+    mesh, N = w["mesh"], w["order"]
+    o = Oracle(mesh.elem_xyz, mesh.elem_vid, N, w["material"])
+    rng = np.random.default_rng(0)
+    deg = np.array([sum(m) for m in mode_list(N)])
+    Q = rng.normal(size=(mesh.n_elem, o.L, 10)) * (0.5 ** deg)[None, :, None]
+    Q[..., :6] *= 2e-4
+    Q[..., 6:9] *= 0.6
+    Q[..., 9] = 0.0
+    Q[:, 0, 9] = 0.03 / math.sqrt(6.0)
+    lam = rng.normal(size=Q.shape)
+    dt = 0.5 * o.cfl_dt()
+    t0 = time.perf_counter()
+    o.step(Q, dt)
+    t1 = time.perf_counter()
+    step_vjp(o, Q, dt, lam)
+    t2 = time.perf_counter()
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:          # threadpoolctl absent: the pinned BLAS thread count
+        threads = int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
+    sample = (f"{mesh.n_elem} tets of the adjoint workload's cube at n = 4, N = {N}, one forward step and one "
+              f"adjoint step, numpy FP64 with {threads} BLAS thread(s)")
+    return mesh.n_elem / (t2 - t1), mesh.n_elem / (t1 - t0), sample, threads
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
@@ -336,6 +373,11 @@ def main():
         line["ensemble"] = run_ensemble(args, dgpkg, torch, stream)
     if args.adjoint_steps > 0:
         line["adjoint"] = run_adjoint(args, dgpkg, torch, stream)
+        if not args.no_cpu_baseline and world == 1:
+            va, vf, sample, threads = cpu_adjoint_baseline()
+            line["adjoint"]["cpu_baseline"] = {
+                "value": va, "unit": "element-adjoint-steps/s", "forward_value": vf,
+                "adjoint_to_forward_step": vf / va, "cores": threads, "kind": "oracle", "sample": sample}
     if not args.no_cpu_baseline and world == 1:
         v, sample, threads, _ = cpu_baseline(w, steps=1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
