@@ -94,7 +94,7 @@ def _step_setup(N, seed, alpha_spread=True):
     return mesh, mat, o, Q, 0.5 * o.cfl_dt(), rng
 
 
-@pytest.mark.parametrize("N", [1, 2, 3])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
 def test_step_dot_product(N):
     """<lam, dQ^{k+1}> by central differences of Oracle.step equals
     <step_vjp(lam), dQ^k> along random state directions, and likewise for
