@@ -125,7 +125,7 @@ dg_status dg_set_rheology(dg_ctx* ctx, int law);
 
 /* Predictor of the step: DG_PREDICTOR_CK (default; the linearised Cauchy-Kovalevskaya
  * procedure of Appendix A.1, Eqs. "CKIter-ref-matrix" and "CKIter-ref-source") or
- * DG_PREDICTOR_PICARD, the discrete Picard iteration Sec. 6.1 proposes in its place:
+ * DG_PREDICTOR_PICARD, the discrete Picard iteration Sec. 5.1 proposes in its place:
  * `iterations` (1..16) sweeps that start from the CK coefficients, evaluate the
  * element-local rate -div F(q) + S(q) of the predictor's polynomial at the N + 1
  * time nodes of the step (flux and damage rate projected by the volume rule) and
@@ -137,6 +137,17 @@ dg_status dg_set_rheology(dg_ctx* ctx, int law);
  * (dg_step and dg_step_noalloc); dg_profile_read counts them under the predictor. */
 enum { DG_PREDICTOR_CK = 0, DG_PREDICTOR_PICARD = 1 };
 dg_status dg_set_predictor(dg_ctx* ctx, int kind, int iterations);
+
+/* Limit of the bounded waits with which the tensor-core corrector (degrees 2..4)
+ * waits for its matrix products: `polls` polls of the completion barrier per wait
+ * (0 .. 2^31 - 1), or the library's default (2^24) for a negative value.  A wait
+ * that runs out makes the corrector stop its work, wait (with the default limit)
+ * for the products in flight, free its tensor memory and return; the step then
+ * returns DG_E_CUDA ("timed out") and the state is left as computed, so the caller
+ * restores it with dg_set_state.  A limit of 0 gives up at the first wait, which
+ * is how the failure path is tested without any fault.  Not a passage of the
+ * paper: the waits belong to this library's kernels.  DG_E_ARG above 2^31 - 1. */
+dg_status dg_set_wait_limit(dg_ctx* ctx, int64_t polls);
 
 /* Per-element material [n_elem][6] = (rho, lambda0, mu0, gamma_r, xi0, C_d):
  * density, Lame parameters of the intact rock, damage modulus gamma_r [Pa],

@@ -83,7 +83,7 @@ class Oracle:
         """face_rows: elements whose face tables are built (default all); step()
         can only produce new states for those elements.  picard_iterations > 0
         refines the CK predictor by that many discrete Picard iterations
-        (Sec. 6.1's proposed extension, reading R20); 0 keeps the CK predictor."""
+        (Sec. 5.1's proposed extension, reading R20); 0 keeps the CK predictor."""
         xyz = np.asarray(elem_xyz, dtype=np.float64)
         vid = np.asarray(elem_vid, dtype=np.int64)
         # Reading R15: each element's reference map lists its vertices by

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -43,6 +44,7 @@ struct dg_ctx {
   int N = 0, L = 0, M = 1;
   int law = 0;                       // 0 = CDM, 1 = IVM, 2 = nonlinear shear
   int picard_iters = 0;              // Picard iterations after the CK predictor (0: CK alone)
+  int wait_limit = -1;               // polls of the tensor-core waits (-1: the kernels' default)
   int64_t E = 0;                     // mesh elements
   int64_t EV = 0;                    // element copies on the device: E x members, member fastest
   double cfl = 0.5;
@@ -705,6 +707,13 @@ dg_status dg_set_predictor(dg_ctx* ctx, int kind, int iterations) {
   return DG_OK;
 }
 
+dg_status dg_set_wait_limit(dg_ctx* ctx, int64_t polls) {
+  if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
+  if (polls > INT32_MAX) return fail(ctx, DG_E_ARG, "wait limit above 2^31 - 1 polls");
+  ctx->wait_limit = polls < 0 ? -1 : static_cast<int>(polls);
+  return DG_OK;
+}
+
 dg_status dg_set_rheology(dg_ctx* ctx, int law) {
   if (!ctx) return fail(ctx, DG_E_ARG, "NULL context");
   if (law != DG_LAW_CDM && law != DG_LAW_IVM && law != DG_LAW_NLSHEAR) return fail(ctx, DG_E_ARG, "unknown rheology");
@@ -1028,6 +1037,8 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
   a.grid_corr = ctx->grid_corr;
   a.law = ctx->law;
   a.picard_iters = ctx->picard_iters;
+  a.wait_limit = ctx->wait_limit;
+  a.wait_limit_set = ctx->wait_limit >= 0;
   a.geom = ctx->geom;
   a.mat = ctx->matf;
   a.nbr = ctx->nbr;
@@ -1152,6 +1163,8 @@ dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) 
   a.grid_corr = ctx->grid_corr;
   a.law = ctx->law;
   a.picard_iters = ctx->picard_iters;
+  a.wait_limit = ctx->wait_limit;
+  a.wait_limit_set = ctx->wait_limit >= 0;
   a.geom = ctx->geom;
   a.mat = ctx->matf;
   a.nbr = ctx->nbr;
@@ -1334,6 +1347,8 @@ dg_status dg_adjoint_gradient(dg_ctx* ctx, int64_t n_steps, double dt, const flo
   a.grid_corr = ctx->grid_corr;
   a.law = 0;
   a.picard_iters = 0;
+  a.wait_limit = ctx->wait_limit;
+  a.wait_limit_set = ctx->wait_limit >= 0;
   a.geom = ctx->geom;
   a.mat = ctx->matf;
   a.nbr = ctx->nbr;

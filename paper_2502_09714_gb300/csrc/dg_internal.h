@@ -150,6 +150,8 @@ struct StepArgs {
                           // 2 = nonlinear shear (Eq. "1d Riemann eqs")
   int has_boundary;       // nonzero when the mesh has absorbing or free-surface faces
   int picard_iters;       // Picard iterations after the CK predictor (0: the CK alone)
+  int wait_limit;         // polls of a bounded wait on the tensor cores, when wait_limit_set
+  int wait_limit_set;     // 0: the kernels' default limit
 };
 
 // Kernel launchers, one per compiled degree (dg_step_n<N>.cu), and their

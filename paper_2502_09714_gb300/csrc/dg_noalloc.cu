@@ -114,6 +114,7 @@ extern "C" dg_status dg_step_noalloc(dg_ctx* ctx, const float* q_in, float* q_ou
     return noalloc_error(ctx, DG_E_CUDA, (std::string("dg_step_noalloc: ") + cudaGetErrorString(e)).c_str());
   if (st & kStatusNonFinite) return noalloc_error(ctx, DG_E_NONFINITE, "non-finite value in the state");
   if (st & kStatusNonHyperbolic) return noalloc_error(ctx, DG_E_NONHYPERBOLIC, "effective moduli lost hyperbolicity");
+  if (st & kStatusIndex) return noalloc_error(ctx, DG_E_MESH, "neighbour index out of range");
   if (st & kStatusTimeout) return noalloc_error(ctx, DG_E_CUDA, "a bounded wait on the tensor cores timed out");
   return DG_OK;
 }

@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
 }
 
 // ===========================================================================
-// Picard predictor (the extension Sec. 6.1 proposes in place of the linearised
+// Picard predictor (the extension Sec. 5.1 proposes in place of the linearised
 // CK): starting from the CK output in a.d, each iteration evaluates the
 // element-local rate R(q) = -div F(q) + S(q) of the predictor's polynomial
 // q(t) = sum_o t^o/o! D^o at the N + 1 time nodes of the step, with the volume-
@@ -1525,6 +1525,8 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
   constexpr int NV = C::NV, NPC = C::NPC, NFC = C::NFC;
   constexpr TableLayout T = table_layout(N);
   constexpr int kWaitLimit = 1 << 24;
+  // the limit of the waits on the MMAs; the drain after a failure keeps the default
+  const int wait_limit = a.wait_limit_set ? a.wait_limit : kWaitLimit;
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
   __shared__ __align__(8) uint64_t mbar;
@@ -1779,7 +1781,7 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
         }
       }, tid, C::WORKERS, bar);
     }
-    const bool ok = tc::wait_parity(&mbar, phase, kWaitLimit);
+    const bool ok = tc::wait_parity(&mbar, phase, wait_limit);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
       failed = true;
@@ -1879,7 +1881,7 @@ __global__ void __launch_bounds__(CorrTcCfg<N>::THREADS, 1) k_corrector_tc(StepA
     }
     tc::cp_async_commit();
     {
-      const bool ok2 = tc::wait_parity(&mbar, phase, kWaitLimit);
+      const bool ok2 = tc::wait_parity(&mbar, phase, wait_limit);
       phase ^= 1u;
       if (__syncthreads_or(!ok2)) {
         failed = true;

@@ -24,7 +24,7 @@ EXPORTS = (
     "dg_set_state_device", "dg_get_state", "dg_get_state_f32", "dg_get_state_device", "dg_step",
     "dg_receivers", "dg_receivers_read", "dg_dt", "dg_time", "dg_n_modes", "dg_get_stats",
     "dg_profile_enable", "dg_profile_read", "dg_reference_table", "dg_last_error", "dg_destroy",
-    "dg_step_noalloc", "dg_set_rheology", "dg_set_predictor", "dg_step_host",
+    "dg_step_noalloc", "dg_set_rheology", "dg_set_predictor", "dg_set_wait_limit", "dg_step_host",
     "dg_adjoint_gradient", "dg_revolve_plan", "dg_revolve_cost",
 )
 
@@ -87,6 +87,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "dg_set_material": ([vp, C.POINTER(dbl), C.POINTER(dbl)], C.c_int),
         "dg_set_rheology": ([vp, C.c_int], C.c_int),
         "dg_set_predictor": ([vp, C.c_int, C.c_int], C.c_int),
+        "dg_set_wait_limit": ([vp, i64], C.c_int),
         "dg_step_host": ([vp, vp, vp, C.c_double], C.c_int),
         "dg_set_source": ([vp, C.POINTER(PointSource), i64], C.c_int),
         "dg_set_state": ([vp, C.POINTER(dbl), dbl], C.c_int),
@@ -216,8 +217,12 @@ class Solver:
 
     def set_predictor(self, kind="ck", iterations=0):
         """kind: "ck" (the linearised Cauchy-Kovalevskaya procedure) or "picard"
-        (`iterations` discrete Picard sweeps after it, Sec. 6.1's extension)."""
+        (`iterations` discrete Picard sweeps after it, Sec. 5.1's extension)."""
         self._chk(self.lib.dg_set_predictor(self.ctx, {"ck": 0, "picard": 1}[kind], int(iterations)))
+
+    def set_wait_limit(self, polls=-1):
+        """Polls per bounded wait of the tensor-core corrector (negative: default)."""
+        self._chk(self.lib.dg_set_wait_limit(self.ctx, int(polls)))
 
     # ------------------------------------------------------------------
     def _chk(self, status):

@@ -125,3 +125,62 @@ def submesh_oracle(mesh, material, order, rows, sources=(), law="cdm", cfl=0.5):
     if kept:
         o.set_sources(kept)
     return o, elems, pos[rows]
+
+
+# ---- a pool of oracle processes for long runs ----------------------------------
+# Each worker holds its own Oracle of the whole mesh and steps one chunk of the
+# elements; the parent gathers the chunks into the next state.  The pool is
+# started with "spawn" (a worker forked from a process that has touched CUDA can
+# hang), and each worker's BLAS is pinned to one thread.
+
+_POOL_ORACLE = None
+
+
+_ONE_THREAD = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _pool_init(args):
+    global _POOL_ORACLE
+    mesh_xyz, mesh_vid, face_bc, order, material, cfl, sources, receivers = args
+    _POOL_ORACLE = Oracle(mesh_xyz, mesh_vid, order, material, face_bc=face_bc, cfl=cfl)
+    if sources:
+        _POOL_ORACLE.set_sources(list(sources))
+    if receivers is not None:
+        _POOL_ORACLE.set_receivers(receivers)
+
+
+def _pool_step(job):
+    Q, dt, t, rows = job
+    return _POOL_ORACLE.step(Q, dt, t, rows=rows)
+
+
+def oracle_run_pool(mesh, material, order, Q0, dt, n_steps, t0=0.0, cfl=0.5, sources=(), receivers=None,
+                    workers=None):
+    """The oracle's run (the same Oracle.step per element, chunked over processes).
+    Returns the final state and, with receivers, the traces after every step."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    o = make_oracle(mesh, material, order, cfl=cfl, sources=sources, receivers=receivers)
+    chunks = np.array_split(np.arange(mesh.n_elem), workers)
+    init = (mesh.elem_xyz, mesh.elem_vid, _tags(mesh), order, material, cfl, list(sources), receivers)
+    Q, t, traces = np.array(Q0, dtype=np.float64), t0, []
+    saved = {k: os.environ.get(k) for k in _ONE_THREAD}
+    os.environ.update({k: "1" for k in _ONE_THREAD})       # inherited by the workers at spawn
+    try:
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"), initializer=_pool_init,
+                                    initargs=(init,)) as ex:
+            for _ in range(n_steps):
+                parts = list(ex.map(_pool_step, [(Q, dt, t, c) for c in chunks]))
+                Q = np.concatenate(parts, axis=0)
+                t += dt
+                if receivers is not None:
+                    traces.append(o.sample_receivers(Q))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return (Q, np.array(traces)) if receivers is not None else Q

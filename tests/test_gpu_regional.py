@@ -3,7 +3,8 @@ basin, layered background, free surface on top and absorbing elsewhere, about
 6000 sub-fault sources and 64 surface receivers, in the launch configuration of
 the benchmark.  20 GPU steps from the middle of the rupture, then one more GPU
 step against the oracle's step from the GPU state on sampled elements (near the
-hypocentre, on the free surface, on absorbing faces, in the basin, at random)."""
+hypocentre, on the free surface, on absorbing faces, in the basin, at random);
+the bar applies to the step's change of the state."""
 import numpy as np
 import pytest
 
@@ -57,8 +58,11 @@ def test_regional_sampled_step():
     qb, _ = s.get_state()
     Qa = from_abi(qa[elems])
     Qb = o.step(Qa, dt, ta, rows=rpos)
-    errs = rel_l2(qb[rows], Qb, o.detJ[rpos])
-    assert np.abs(Qb - Qa[rpos]).max() > 0
+    # compare the step's change of the state (what the step computes), per field group
+    dO = Qb - Qa[rpos]
+    dG = to_abi(from_abi(qb[rows]) - Qa[rpos])
+    assert np.abs(dO).max() > 0
+    errs = rel_l2(dG, dO, o.detJ[rpos])
     for name, e in errs.items():
         assert e <= TOL_REL_L2, (name, e)
     assert alpha_max_diff(qb[rows], Qb, N) <= TOL_ALPHA

@@ -1,5 +1,5 @@
 """Pins of the oracle's discrete Picard predictor (reading R20, the extension
-Sec. 6.1 proposes): for a linear flux the CK coefficients are its fixed point,
+Sec. 5.1 proposes): for a linear flux the CK coefficients are its fixed point,
 the iteration contracts on a nonlinear state, and the time fit reproduces the
 Taylor coefficients of a polynomial exactly."""
 import math

@@ -2,15 +2,17 @@
 cudaMalloc while they step: it must give the same state as dg_step, call
 after call, and refuse meshes larger than its fixed static scratch.
 
+Both entry points run the same predictor, face-flux and corrector kernels on
+the same FP32 input, element by element in the same order of operations, so
+their states must agree bit for bit; a stale or misplaced region of the
+shared static scratch would show up as a difference.
+
 This file is collected last on purpose, so that a run stopping at the first
 failure has already run every other test."""
 import numpy as np
 import pytest
 
-from oracle import from_abi
 from synthetic import periodic_cube_mesh, rock_material
-
-from parity_util import TOL_ALPHA, TOL_REL_L2, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -23,11 +25,8 @@ def _state(E, L, seed):
     return q.astype(np.float32)
 
 
-def _compare(q_new, q_ref, detJ):
-    errs = rel_l2(q_new, from_abi(q_ref), detJ)
-    for name, e in errs.items():
-        assert e <= TOL_REL_L2, (name, e)
-    assert np.abs(q_new[:, 9, :] - q_ref[:, 9, :]).max() <= TOL_ALPHA
+def _compare(q_new, q_ref):
+    np.testing.assert_array_equal(q_new, q_ref)
 
 
 def test_noalloc_step_matches_dg_step_on_two_calls_in_a_row():
@@ -51,16 +50,15 @@ def test_noalloc_step_matches_dg_step_on_two_calls_in_a_row():
     ref1, _ = s.get_state()
     s.step(1, dt)
     ref2, _ = s.get_state()
-    detJ = np.abs(np.linalg.det(np.stack([mesh.elem_xyz[:, k] - mesh.elem_xyz[:, 0] for k in (1, 2, 3)], axis=2)))
     qa = torch.from_numpy(q0).cuda()
     qb = torch.empty_like(qa)
     s.step_noalloc(qa, qb, dt)
     torch.cuda.synchronize()
-    _compare(qb.cpu().numpy().astype(np.float64), ref1, detJ)
+    _compare(qb.cpu().numpy().astype(np.float64), ref1)
     qa.copy_(qb)
     s.step_noalloc(qa, qb, dt)
     torch.cuda.synchronize()
-    _compare(qb.cpu().numpy().astype(np.float64), ref2, detJ)
+    _compare(qb.cpu().numpy().astype(np.float64), ref2)
     # the context's own state was not touched by the allocation-free calls
     cur, _ = s.get_state()
     np.testing.assert_array_equal(cur, ref2)
@@ -72,13 +70,13 @@ def test_noalloc_step_rejects_meshes_beyond_its_scratch():
 
     import paper_2502_09714_gb300 as dgpkg
     from paper_2502_09714_gb300 import DGError
-    mesh = periodic_cube_mesh(10, 4000.0)          # 6000 elements > 3968 at N = 4
+    mesh = periodic_cube_mesh(10, 4000.0)          # 6000 elements > 2772 at N = 4
     s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, 4, stream=torch.cuda.current_stream())
     s.set_material(rock_material(mesh.n_elem))
     q = torch.zeros((mesh.n_elem, 10, 35), dtype=torch.float32, device="cuda")
     with pytest.raises(DGError) as ei:
         s.step_noalloc(q, q, 0.0)
-    assert ei.value.name == "DG_E_ARG" and "capacity" in str(ei.value)
+    assert ei.value.name == "DG_E_ARG" and "2772-element capacity" in str(ei.value)
     s.close()
 
 
@@ -101,12 +99,11 @@ def test_noalloc_step_runs_the_picard_predictor():
     s.set_state(q0)
     s.step(1, dt)
     ref, _ = s.get_state()
-    detJ = np.abs(np.linalg.det(np.stack([mesh.elem_xyz[:, k] - mesh.elem_xyz[:, 0] for k in (1, 2, 3)], axis=2)))
     qa = torch.from_numpy(q0).cuda()
     qb = torch.empty_like(qa)
     s.step_noalloc(qa, qb, dt)
     torch.cuda.synchronize()
-    _compare(qb.cpu().numpy().astype(np.float64), ref, detJ)
+    _compare(qb.cpu().numpy().astype(np.float64), ref)
     # and the Picard result differs from the CK one (the iterations did run)
     s.set_predictor("ck")
     s.set_state(q0)
