@@ -1,15 +1,24 @@
 """Benchmark of the nonlinear-damage ADER-DG step on GB300.
 
-One bench step = one time step of the whole method (predictor, corrector with
-volume/source/face terms and update, point source, receivers) over the
-196,608-tet N=4 jittered two-layer periodic cube with a dip-slip point source
-and 64 receivers (synthetic, seeded).  Metric: element-updates/s.
+One bench step = one time step of the whole method (predictor, face fluxes,
+corrector with the volume, damage-source and face terms and the update, point
+sources, receivers).  The headline workload is the regional-shaped box: a
+120 x 80 x 40 km graded tetrahedral mesh of about 4.35 M elements at degree 4,
+with a soft ellipsoidal basin, a layered background, a free surface on top and
+absorbing faces elsewhere, about 6000 sub-fault point sources of a planar
+dipping fault and 64 surface receivers (synthetic, seeded).  Metric:
+element-updates/s.  The line also carries, as extra objects, the 196,608-tet
+jittered two-layer cube at degree 4 with one point source ("c2"), the 32-member
+ensemble on that cube at degree 3 ("ensemble") and the receiver-misfit gradient
+on the 82,944-tet cube at degree 3 ("adjoint").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N>1 (torchrun, one process per GPU) runs N independent replicas of the
 workload (the method is not sharded across GPUs here); value = all ranks'
-element updates / max-over-ranks time.
+element updates / max-over-ranks time.  --impl reference times the FP64 CPU
+oracle (the method has no other implementation) on all host cores, on a
+bounded sample of the same workload per step.
 """
 from __future__ import annotations
 
@@ -23,8 +32,9 @@ import sys
 import threading
 import time
 
-# The CPU baseline (the FP64 oracle) runs on one host thread: BLAS thread pools
-# are pinned before numpy loads so that the reported core count is exact.
+# The CPU baselines (the FP64 oracle) run one BLAS thread per process: the
+# thread pools are pinned before numpy loads so that the reported core counts
+# are exact; the all-core baseline runs one process per core.
 for _var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_var, "1")
 
@@ -35,7 +45,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "element-updates/s (FP32, N=4)"
 UNIT = "element-updates/s"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 
@@ -44,11 +53,11 @@ def n_modes(N):
 
 
 def algorithmic_flops(N):
-    """FLOPs per element update of each kernel of the method as this library
-    formulates it (FMA = 2 flops): Taylor terms on their nonzero modes (degree
-    <= N-i), (N+1)^3 volume nodes, (N+1)^2 face nodes and N+1 time nodes, each
-    interior face's flux once (a closed mesh has 2 faces per element).
-    Returns {"predictor", "faces", "corrector"}."""
+    """FLOPs per element update of each kernel as this library formulates it
+    (FMA = 2 flops): Taylor terms on their nonzero modes (degree <= N-i),
+    (N+1)^3 volume nodes, (N+1)^2 face nodes and N+1 time nodes, each interior
+    face's flux once (a closed mesh has 2 faces per element).  An informational
+    count; the roofline uses the dense count of hot_path_terms()."""
     L, NQ, NF, NT = n_modes(N), (N + 1) ** 3, (N + 1) ** 2, N + 1
     LR = [n_modes(N - i) for i in range(N + 1)]
     SH = sum(LR[1:])
@@ -66,6 +75,48 @@ def algorithmic_flops(N):
     return {"predictor": pred, "faces": faces, "corrector": corr}
 
 
+def hot_path_terms(N):
+    """Dense FLOP count per element update of each term of the step (FMA = 2;
+    reference matrices dense, time nodes and face traces once per element, each
+    interior Rusanov flux once per face pair), split into its contraction part
+    (products against reference matrices shared by all elements: dense GEMMs when
+    batched over elements, tensor-core work) and its pointwise part (FP32 ALU
+    work), and assigned to the kernel of this library that computes it.
+    Terms (L modes, Nq = (N+1)^3 volume nodes, Nf = (N+1)^2 face nodes,
+    Nt = N+1 time nodes):
+      CK predictor (Appendix A.1)            3N (20 L^2 + 200 L)
+      damage source at i = 1                 16 Nq L + 40 Nq
+      volume evaluation (A.2, 3rd term)      14 Nq L Nt + 14 L (N+1) Nt + 94 Nq Nt
+      volume projection                      20 L Nq + 54 Nq
+      face traces (A.2, 2nd term)            80 Nf L Nt
+      Rusanov flux                           580 Nf Nt
+      face projection                        80 L Nf
+      strain rows (linear in v)              18 L^2
+      time integration                       20 L (N+1)
+    Returns {term: (kernel, contraction flops, pointwise flops)}."""
+    L, NQ, NF, NT = n_modes(N), (N + 1) ** 3, (N + 1) ** 2, N + 1
+    return {
+        "ck_predictor": ("predictor", 3 * N * 20 * L * L, 3 * N * 200 * L),
+        "damage_source_i1": ("predictor", 16 * NQ * L, 40 * NQ),
+        "volume_evaluation": ("corrector", 14 * NQ * L * NT, 14 * L * (N + 1) * NT + 94 * NQ * NT),
+        "volume_projection": ("corrector", 20 * L * NQ, 54 * NQ),
+        "face_traces": ("faces", 80 * NF * L * NT, 0),
+        "rusanov_flux": ("faces", 0, 580 * NF * NT),
+        "face_projection": ("corrector", 80 * L * NF, 0),
+        "strain_rows": ("corrector", 18 * L * L, 0),
+        "time_integration": ("corrector", 0, 20 * L * (N + 1)),
+    }
+
+
+def kernel_flops(N):
+    """{kernel: (contraction flops, pointwise flops)} per element update."""
+    out = {}
+    for k, c, p in hot_path_terms(N).values():
+        a, b = out.get(k, (0, 0))
+        out[k] = (a + c, b + p)
+    return out
+
+
 def algorithmic_bytes(N):
     """Minimum HBM bytes per element update: read and write the FP32 state
     (10 L floats each) plus 176 B of geometry, material and connectivity."""
@@ -78,6 +129,34 @@ def _peaks():
         with open(p) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def roofline_peaks(sm_count):
+    """The composite roofline's three denominators: the 3xTF32 tensor rate (the
+    measured bf16 burst rate x the nominal TF32:BF16 ratio of 1:2, / 3 for the
+    three TF32 products of one FP32-accurate product), the FP32 ALU rate (SMs x
+    128 lanes x 2 flops x the maximum SM clock) and the measured HBM copy rate."""
+    peaks, kind = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    return {"tensor_3xtf32_tflops": float(peaks["bf16_tflops"]) / 2.0 / 3.0,
+            "alu_fp32_tflops": sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12,
+            "hbm_gbs": float(peaks["hbm_gbs"]), "kind": kind,
+            "source": (f"tensor: {kind} bf16 burst {peaks['bf16_tflops']} TFLOP/s / 2 (TF32) / 3 (3xTF32); "
+                       f"ALU: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz; "
+                       f"HBM: {kind} copy {peaks['hbm_gbs']} GB/s")}
+
+
+def composite(contraction, pointwise, n_units, ms, pk, bytes_=0.0):
+    """t_min = contraction / P_tensor + pointwise / P_ALU + bytes / BW_HBM for
+    n_units element updates, against the measured time ms."""
+    t_c = contraction * n_units / (pk["tensor_3xtf32_tflops"] * 1e12)
+    t_p = pointwise * n_units / (pk["alu_fp32_tflops"] * 1e12)
+    t_b = bytes_ * n_units / (pk["hbm_gbs"] * 1e9)
+    t_min = t_c + t_p + t_b
+    return {"t_min_ms": 1e3 * t_min, "ms": ms, "frac": 1e3 * t_min / ms if ms > 0 else None,
+            "t_tensor_ms": 1e3 * t_c, "t_alu_ms": 1e3 * t_p, "t_hbm_ms": 1e3 * t_b,
+            "contraction_flops_per_element": contraction, "pointwise_flops_per_element": pointwise,
+            "bytes_per_element": bytes_}
 
 
 class ClockSampler:
@@ -133,33 +212,178 @@ def _dist():
     return rank, world, local
 
 
-def cpu_baseline(workload, steps=1, max_seconds=None):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload: one
-    z-layer of hexahedral cells (6 n^2 elements) advanced one step from a
-    seeded state on the full mesh.  Returns (element-updates/s, sample text, threads)."""
-    from oracle import Oracle
-    mesh, mat, N = workload["mesh"], workload["material"], workload["order"]
-    n = mesh.cells[0]
-    rows = np.arange(6 * n * n * (n // 2), 6 * n * n * (n // 2 + 1))      # one z-layer of cells
-    t_setup = time.perf_counter()
-    o = Oracle(mesh.elem_xyz, mesh.elem_vid, N, mat, face_rows=rows)
-    o.set_sources(workload["sources"])
-    setup = time.perf_counter() - t_setup
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def load_workload(name, args):
+    if name == "c3":
+        from synthetic.regional import workload_c3
+        return workload_c3(order=args.order)
+    from synthetic import workload_c2
+    return workload_c2(n=args.n, order=args.order)
+
+
+# ---------------------------------------------------------------------------
+# CPU baselines: the FP64 oracle, as it stands, on bounded samples of a workload
+# ---------------------------------------------------------------------------
+
+def _face_neighbours_of(mesh, rows):
+    """[len(rows), 4] element across each face of the sample rows (-1 on boundary
+    faces), by matching vertex-id triples among the elements sharing a vertex
+    with the sample (host bookkeeping only)."""
+    vid = np.asarray(mesh.elem_vid)
+    rows = np.asarray(rows)
+    cand = np.nonzero(np.isin(vid, np.unique(vid[rows])).any(axis=1))[0]
+    owner = {}
+    for e in cand.tolist():
+        v = vid[e]
+        for f in range(4):
+            owner.setdefault(tuple(sorted(np.delete(v, f).tolist())), []).append(e)
+    nbr = -np.ones((rows.size, 4), dtype=np.int64)
+    for i, e in enumerate(rows.tolist()):
+        for f in range(4):
+            others = [x for x in owner[tuple(sorted(np.delete(vid[e], f).tolist()))] if x != e]
+            if others:
+                nbr[i, f] = others[0]
+    return nbr
+
+
+def _sample_spec(w, rows, nbr):
+    """The sub-mesh of the sample rows and their face neighbours (faces leaving it
+    tagged absorbing: they enter only the neighbours' own updates, which are not
+    timed), the sources inside it, and the rows' positions."""
+    mesh = w["mesh"]
+    elems = np.unique(np.concatenate([rows, nbr[nbr >= 0].ravel()]))
+    pos = -np.ones(mesh.n_elem, dtype=np.int64)
+    pos[elems] = np.arange(elems.size)
+    bc = np.array(mesh.face_bc[elems], dtype=np.int8)
+    inner = {int(e): i for i, e in enumerate(rows.tolist())}
+    vid = np.asarray(mesh.elem_vid)
+    elem_set = set(elems.tolist())
+    for k, e in enumerate(elems.tolist()):
+        if e in inner:
+            continue
+        for f in range(4):                       # a neighbour's faces towards elements outside
+            if bc[k, f] != 0:
+                continue
+            key = set(np.delete(vid[e], f).tolist())
+            shared = [x for x in elem_set if x != e and key <= set(vid[x].tolist())]
+            if not shared:
+                bc[k, f] = 2
+    lo, hi = mesh.elem_xyz[elems].min(axis=(0, 1)), mesh.elem_xyz[elems].max(axis=(0, 1))
+    srcs = [s for s in w["sources"] if np.all(s["x"] >= lo) and np.all(s["x"] <= hi)]
+    return {"xyz": mesh.elem_xyz[elems], "vid": mesh.elem_vid[elems], "bc": bc, "order": w["order"],
+            "mat": w["material"][elems], "cfl": w["cfl"], "sources": srcs, "rows": pos[rows]}
+
+
+def _sample_oracle(spec):
+    from oracle import MeshError, Oracle
+    o = Oracle(spec["xyz"], spec["vid"], spec["order"], spec["mat"], face_bc=spec["bc"], cfl=spec["cfl"],
+               face_rows=spec["rows"])
+    kept = []
+    for s in spec["sources"]:
+        try:
+            o.locate(s["x"])
+            kept.append(s)
+        except MeshError:
+            pass
+    if kept:
+        o.set_sources(kept)
     rng = np.random.default_rng(0)
-    Q = rng.normal(size=(mesh.n_elem, o.L, 10)) * 1e-6
+    Q = rng.normal(size=(o.E, o.L, 10)) * 1e-6
+    Q[..., 9] = 0.0
+    return o, Q
+
+
+_WORKER = None
+
+
+def _worker_init(spec):
+    global _WORKER
+    o, Q = _sample_oracle(spec)
+    _WORKER = (o, Q, spec["rows"], o.cfl_dt())
+
+
+def _worker_step(_):
+    o, Q, rows, dt = _WORKER
+    t0 = time.perf_counter()
+    o.step(Q, dt, t=0.8, rows=rows)
+    return time.perf_counter() - t0
+
+
+def _sample_rows(w, total):
+    E = w["mesh"].n_elem
+    start = max(0, E // 2 - total // 2)
+    return np.arange(start, min(E, start + total))
+
+
+class OraclePool:
+    """The oracle stepping `workers` disjoint chunks of `chunk` elements of a
+    workload, one chunk per process (started with "spawn": a process forked from
+    one that has used CUDA can hang; one BLAS thread each).  Set-up (the
+    sub-meshes and their reference tables) is outside the timed steps."""
+
+    def __init__(self, w, workers, chunk):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        rows = _sample_rows(w, workers * chunk)
+        nbr = _face_neighbours_of(w["mesh"], rows)
+        self.chunks = np.array_split(np.arange(rows.size), workers)
+        specs = [_sample_spec(w, rows[c], nbr[c]) for c in self.chunks]
+        self.rows = rows.size
+        self.workers = workers
+        ctx = mp.get_context("spawn")
+        self.ex = [cf.ProcessPoolExecutor(1, mp_context=ctx, initializer=_worker_init, initargs=(sp,))
+                   for sp in specs]
+        for f in [ex.submit(_worker_step, 0) for ex in self.ex]:     # builds the oracles, untimed
+            f.result()
+
+    def step(self):
+        """One step of every chunk, in parallel; returns the wall time in s."""
+        t0 = time.perf_counter()
+        for f in [ex.submit(_worker_step, 0) for ex in self.ex]:
+            f.result()
+        return time.perf_counter() - t0
+
+    def close(self):
+        for ex in self.ex:
+            ex.shutdown()
+
+
+def cpu_baseline_one_core(w, chunk=1024, steps=2):
+    """The oracle on one host core: `chunk` elements of the workload (and their
+    face neighbours' predictors), `steps` steps from a seeded state."""
+    rows = _sample_rows(w, chunk)
+    spec = _sample_spec(w, rows, _face_neighbours_of(w["mesh"], rows))
+    o, Q = _sample_oracle(spec)
     dt = o.cfl_dt()
+    o.step(Q, dt, t=0.8, rows=spec["rows"])                        # warm-up
     t0 = time.perf_counter()
     for _ in range(steps):
-        o.step(Q, dt, t=0.3, rows=rows)
+        o.step(Q, dt, t=0.8, rows=spec["rows"])
     el = time.perf_counter() - t0
+    sample = (f"{rows.size} contiguous elements of the {w['mesh'].n_elem}-element mesh (plus their face "
+              f"neighbours' predictors), {steps} step(s), numpy FP64, 1 process with 1 BLAS thread")
+    return rows.size * steps / el, sample, 1, el
+
+
+def cpu_baseline_all_cores(w, chunk=512, steps=2):
+    """The oracle on every host core: one process per core, each stepping its own
+    chunk of `chunk` contiguous elements of the workload."""
+    cores = _host_cores()
+    pool = OraclePool(w, cores, chunk)
     try:
-        from threadpoolctl import threadpool_info
-        threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:          # threadpoolctl absent: the pinned BLAS thread count
-        threads = int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
-    sample = (f"{rows.size} elements (one z-layer of cells of the {mesh.n_elem}-tet mesh), "
-              f"{steps} step(s), numpy FP64 with {threads} BLAS thread(s); setup {setup:.1f}s excluded")
-    return rows.size * steps / el, sample, threads, el
+        el = sum(pool.step() for _ in range(steps))
+    finally:
+        pool.close()
+    sample = (f"{pool.rows} contiguous elements of the {w['mesh'].n_elem}-element mesh in {cores} chunks of "
+              f"{chunk} (plus their face neighbours' predictors), {steps} step(s), numpy FP64, {cores} processes "
+              f"with 1 BLAS thread each")
+    return pool.rows * steps / el, sample, cores, el
 
 
 def cpu_adjoint_baseline():
@@ -168,7 +392,6 @@ def cpu_adjoint_baseline():
     cube at 4 cells per side (384 tets) and degree 3, one step each from a seeded
     damaged state.  Returns (adjoint element-steps/s, forward element-steps/s,
     sample text, threads)."""
-    import math
     from oracle import Oracle, mode_list
     from oracle.adjoint import step_vjp
     from synthetic import workload_adjoint
@@ -189,37 +412,38 @@ def cpu_adjoint_baseline():
     t1 = time.perf_counter()
     step_vjp(o, Q, dt, lam)
     t2 = time.perf_counter()
-    try:
-        from threadpoolctl import threadpool_info
-        threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:          # threadpoolctl absent: the pinned BLAS thread count
-        threads = int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
     sample = (f"{mesh.n_elem} tets of the adjoint workload's cube at n = 4, N = {N}, one forward step and one "
-              f"adjoint step, numpy FP64 with {threads} BLAS thread(s)")
-    return mesh.n_elem / (t2 - t1), mesh.n_elem / (t1 - t0), sample, threads
+              f"adjoint step, numpy FP64, 1 process with 1 BLAS thread")
+    return mesh.n_elem / (t2 - t1), mesh.n_elem / (t1 - t0), sample, 1
 
 
 def run_reference(args):
+    """The oracle on all host cores: each step is one step of a bounded sample
+    of the workload (one chunk of `--ref-chunk` contiguous elements per core)."""
     rank, world, _ = _dist()
     if rank != 0:
         return 0
-    from synthetic import workload_c2
-    w = workload_c2(n=args.n, order=args.order)
-    vals, total = [], 0.0
-    for _ in range(args.warmup):
-        cpu_baseline(w, steps=1)
-    for _ in range(args.steps):
-        v, sample, threads, el = cpu_baseline(w, steps=1)
-        vals.append(v)
-        total += el
-    value = statistics.median(vals)
+    w = load_workload(args.workload, args)
+    cores = _host_cores()
+    pool = OraclePool(w, cores, args.ref_chunk)
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        times = [pool.step() for _ in range(args.steps)]
+    finally:
+        pool.close()
+    total = sum(times)
+    value = pool.rows * args.steps / total
+    sample = (f"per step: {pool.rows} contiguous elements of the {w['mesh'].n_elem}-element mesh in {cores} "
+              f"chunks of {args.ref_chunk} (plus their face neighbours' predictors), numpy FP64, {cores} "
+              f"processes with 1 BLAS thread each")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * w["mesh"].n_elem / value, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(w, args),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": sample},
+            "ms_per_step": 1e3 * total / args.steps, "ms_per_step_is": "one step of the sample timed",
+            "ms_per_full_mesh_step_extrapolated": 1e3 * w["mesh"].n_elem / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(w, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -229,24 +453,110 @@ def _config(w, args):
     return {"workload": w["name"], "elements": w["mesh"].n_elem, "order": w["order"],
             "modes": n_modes(w["order"]), "fields": 10, "sources": len(w["sources"]),
             "receivers": int(len(w["receivers"])), "l2_policy": "inputs larger than L2 "
-            "(state 2x and predictor buffers > 129 MB at N=4); no flush", "parallelism": f"replicas{args.gpus}",
+            "(the state's two buffers and the predictor output exceed 129 MB); no flush",
+            "parallelism": f"replicas{args.gpus}",
             "predictor": f"picard{args.picard_iterations}" if getattr(args, "picard_iterations", 0) > 0 else "ck"}
+
+
+# ---------------------------------------------------------------------------
+# GPU runs
+# ---------------------------------------------------------------------------
+
+def run_forward(w, args, dgpkg, torch, stream, steps, warmup, e2e_steps, world=1, barrier=None, clocks_index=None):
+    """Time `steps` steps of the workload after `warmup` (CUDA events on the
+    library's stream, per-kernel events inside the library) and, if e2e_steps,
+    the end-to-end step through dg_step_host with pinned host buffers."""
+    mesh, mat, N = w["mesh"], w["material"], w["order"]
+    E, L = mesh.n_elem, n_modes(N)
+    bc = mesh.face_bc if np.any(mesh.face_bc != 0) else None
+    s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, N, face_bc=bc, cfl=w["cfl"], stream=stream)
+    s.set_material(mat)
+    if getattr(args, "picard_iterations", 0) > 0:
+        s.set_predictor("picard", args.picard_iterations)
+    s.set_sources(w["sources"])
+    s.set_receivers(w["receivers"])
+    s.set_state(np.zeros((E, 10, L), np.float32), 0.0)
+    barrier = barrier or torch.cuda.synchronize
+    s.step(warmup)
+    barrier()
+    s.profile(True)
+    launches0 = s.stats()["kernel_launches"]
+    clocks = ClockSampler(clocks_index) if clocks_index is not None else None
+    if clocks:
+        clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    barrier()
+    if clocks:
+        clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = s.profile_read()
+    s.profile(False)
+    out = {"E": E, "N": N, "ms": ms, "prof": prof, "launches": s.stats()["kernel_launches"] - launches0,
+           "clocks": clocks.summary() if clocks else None}
+    if e2e_steps > 0:
+        # end to end through the public API: pinned host state in, one step, state out
+        hq = torch.zeros((E, 10, L), dtype=torch.float32).pin_memory()
+        hq_np = hq.numpy()
+        res = torch.empty_like(hq).pin_memory()
+        res_np = res.numpy()
+        s.get_state(out=res_np)
+        hq_np[...] = res_np
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            s.step_host(hq_np, res_np)       # upload, one step, download (transfers overlap the step)
+        barrier()
+        out["e2e_s"] = time.perf_counter() - t0
+        out["e2e_bytes"] = (int(hq.numel() * 4), int(res.numel() * 4))
+        del hq, res
+    s.close()
+    return out
+
+
+def forward_report(r, pk, steps, world=1):
+    """Rates, per-kernel times and the composite roofline of a forward run."""
+    E, N, prof = r["E"], r["N"], r["prof"]
+    value = world * E * steps / (r["ms"] * 1e-3)
+    kavg = {k: v["total_ms"] / max(1, v["launches"]) for k, v in prof.items()}
+    kf = kernel_flops(N)
+    lib_flops = algorithmic_flops(N)
+    kernels = {}
+    for k, v in prof.items():
+        d = {"launches": v["launches"], "avg_ms": kavg[k]}
+        if k in kf and kavg[k] > 0:
+            c, p = kf[k]
+            d["roofline"] = composite(c, p, E, kavg[k], pk)
+            d["library_flops_per_element"] = lib_flops[k]
+        kernels[k] = d
+    ms_step = r["ms"] / steps
+    c_all = sum(c for c, _ in kf.values())
+    p_all = sum(p for _, p in kf.values())
+    step_roof = composite(c_all, p_all, E, ms_step, pk, algorithmic_bytes(N))
+    return value, kernels, step_roof, kavg
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=32, help="cells per cube side (32 -> 196,608 tets)")
+    ap.add_argument("--workload", default="c3", choices=["c2", "c3"],
+                    help="c3: the ~4.35 M-tet regional-shaped box (headline); c2: the 196,608-tet two-layer cube")
+    ap.add_argument("--n", type=int, default=32, help="cells per cube side of the two-layer cube (32 -> 196,608)")
     ap.add_argument("--order", type=int, default=4)
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cube-steps", type=int, default=200,
+                    help="steps of the two-layer cube timed as the extra 'c2' object (0 skips it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
-                    help="c2: 196,608-tet two-layer cube (the benchmark); c3: ~4.35 M-tet regional-shaped box")
-    ap.add_argument("--ensemble-members", type=int, default=0,
-                    help="also time the ensemble workload (N=3, this many members) against one member")
+    ap.add_argument("--ref-chunk", type=int, default=256,
+                    help="elements per host core in each step of --impl reference")
+    ap.add_argument("--ensemble-members", type=int, default=32,
+                    help="members of the ensemble workload (two-layer cube at N=3) timed against one member; "
+                         "0 skips it")
     ap.add_argument("--adjoint-steps", type=int, default=800,
                     help="steps of the adjoint workload (82,944 tets, N=3, 40 snapshots) whose gradient is "
                          "timed against its forward step; 0 skips it")
@@ -262,113 +572,78 @@ def main():
     import torch
     import torch.distributed as dist
     import paper_2502_09714_gb300 as dgpkg
-    from synthetic import workload_c2
 
     rank, world, local = _dist()
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dgpkg.build()
-    if args.workload == "c3":
-        from synthetic.regional import workload_c3
-        w = workload_c3(order=args.order)
-    else:
-        w = workload_c2(n=args.n, order=args.order)
-    mesh, mat, N = w["mesh"], w["material"], w["order"]
-    E, L = mesh.n_elem, n_modes(N)
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    pk = roofline_peaks(sm_count)
     stream = torch.cuda.current_stream()
-    bc = mesh.face_bc if np.any(mesh.face_bc != 0) else None
-    s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, N, face_bc=bc, cfl=w["cfl"], stream=stream)
-    s.set_material(mat)
-    if args.picard_iterations > 0:
-        s.set_predictor("picard", args.picard_iterations)
-    s.set_sources(w["sources"])
-    s.set_receivers(w["receivers"])
-    s.set_state(np.zeros((E, 10, L), np.float32), 0.0)
+    w = load_workload(args.workload, args)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    s.step(args.warmup)
-    barrier()
-    s.profile(True)
-    launches0 = s.stats()["kernel_launches"]
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    s.step(args.steps)
-    ev1.record(stream)
-    barrier()
-    clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    prof = s.profile_read()
-    s.profile(False)
-    launches = s.stats()["kernel_launches"] - launches0
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    r = run_forward(w, args, dgpkg, torch, stream, args.steps, args.warmup, args.e2e_steps, world, barrier,
+                    clocks_index=local)
+    t = torch.tensor([r["ms"], r.get("e2e_s", 0.0)], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * E * args.steps / (ms_max * 1e-3)
-
-    # end to end through the public API: pinned host state in, one step, state out
-    hq = torch.zeros((E, 10, L), dtype=torch.float32).pin_memory()
-    hq_np = hq.numpy()
-    out = torch.empty_like(hq).pin_memory()
-    out_np = out.numpy()
-    s.get_state(out=out_np)
-    hq_np[...] = out_np
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        s.step_host(hq_np, out_np)        # upload, one step, download (transfers overlap the step)
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * E * args.e2e_steps / float(te.item())
+    r["ms"], e2e_s = float(t[0].item()), float(t[1].item())
+    E, N = r["E"], r["N"]
+    value, kernels, step_roof, kavg = forward_report(r, pk, args.steps, world)
+    e2e_value = world * E * args.e2e_steps / e2e_s if e2e_s > 0 else None
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
 
-    peaks, peak_kind = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12    # TFLOP/s
-    flops = algorithmic_flops(N)
-    kavg = {k: v["total_ms"] / max(1, v["launches"]) for k, v in prof.items()}
-    dom = max(("predictor", "faces", "corrector"), key=lambda k: prof[k]["total_ms"])
-    dom_ms = kavg[dom]
-    achieved = flops[dom] * E / (dom_ms * 1e-3) / 1e12
-    traffic = _traffic_per_launch(dom, N, E)
+    peaks, _ = _peaks()
+    dom = max(("predictor", "faces", "corrector"), key=lambda k: r["prof"][k]["total_ms"])
+    dr = kernels[dom]["roofline"]
+    flops_dom = dr["contraction_flops_per_element"] + dr["pointwise_flops_per_element"]
+    achieved = flops_dom * E / (kavg[dom] * 1e-3) / 1e12
+    peak_eff = flops_dom * E / (dr["t_min_ms"] * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config(w, args),
-        "roofline": {"kernel": _kernel_name(dom, N), "bound": "alu", "achieved": achieved,
-                     "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                     "traffic": traffic,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (recipe unit counts, max clock)",
-                     "flops_per_element": flops[dom], "avg_ms": dom_ms},
-        "kernels": {k: {"launches": v["launches"], "avg_ms": kavg[k],
-                        "tflops": (flops[k] * E / (kavg[k] * 1e-3) / 1e12) if k in flops and kavg[k] > 0 else None}
-                    for k, v in prof.items()},
+        "roofline": {"kernel": _kernel_name(dom, N),
+                     "bound": "tensor" if dr["t_tensor_ms"] >= dr["t_alu_ms"] else "alu",
+                     "achieved": achieved, "peak": peak_eff, "unit": "TFLOP/s", "frac": achieved / peak_eff,
+                     "traffic": _traffic_per_launch(dom, N, E),
+                     "peak_is": ("composite: the kernel's dense flops / (contraction flops / P_tensor(3xTF32) + "
+                                 "pointwise flops / P_ALU(FP32)); frac = t_min / measured launch time"),
+                     "peak_source": pk["source"], "avg_ms": kavg[dom],
+                     "contraction_flops_per_element": dr["contraction_flops_per_element"],
+                     "pointwise_flops_per_element": dr["pointwise_flops_per_element"],
+                     "t_min_ms": dr["t_min_ms"]},
+        "step_roofline": step_roof,
+        "kernels": kernels,
         "hbm": {"algorithmic_bytes_per_element": algorithmic_bytes(N),
                 "achieved_gbs": algorithmic_bytes(N) * value / world / 1e9,
                 "peak_gbs": peaks.get("hbm_gbs"),
                 "frac": algorithmic_bytes(N) * value / world / 1e9 / float(peaks.get("hbm_gbs", 6800.0))},
-        "step_flops": dict(flops, per_element_total=sum(flops.values()),
-                           achieved_tflops=sum(flops.values()) * value / world / 1e12),
-        "gpu_launches": launches,
-        "clocks": clocks.summary(),
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(hq.numel() * 4),
-                "d2h_bytes_per_step": int(out.numel() * 4), "steps": args.e2e_steps},
+        "sm_count": sm_count,
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": r.get("e2e_bytes", (0, 0))[0],
+                "d2h_bytes_per_step": r.get("e2e_bytes", (0, 0))[1], "steps": args.e2e_steps},
     }
+    if args.workload == "c3" and args.cube_steps > 0:
+        wc = load_workload("c2", args)
+        rc = run_forward(wc, args, dgpkg, torch, stream, args.cube_steps, args.warmup, 0)
+        vc, kc, sc, _ = forward_report(rc, pk, args.cube_steps)
+        line["c2"] = {"workload": wc["name"], "elements": rc["E"], "order": rc["N"], "steps": args.cube_steps,
+                      "value": vc, "unit": UNIT, "ms_per_step": rc["ms"] / args.cube_steps,
+                      "step_roofline": sc, "kernels": kc, "gpu_launches": rc["launches"]}
+        del wc
     if args.ensemble_members > 1:
         line["ensemble"] = run_ensemble(args, dgpkg, torch, stream)
     if args.adjoint_steps > 0:
@@ -379,10 +654,12 @@ def main():
                 "value": va, "unit": "element-adjoint-steps/s", "forward_value": vf,
                 "adjoint_to_forward_step": vf / va, "cores": threads, "kind": "oracle", "sample": sample}
     if not args.no_cpu_baseline and world == 1:
-        v, sample, threads, _ = cpu_baseline(w, steps=1)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+        v1, s1, c1, _ = cpu_baseline_one_core(w)
+        va, sa, ca, _ = cpu_baseline_all_cores(w)
+        line["cpu_baseline"] = {"value": va, "unit": UNIT, "cores": ca, "kind": "oracle", "sample": sa,
+                                "one_core": {"value": v1, "unit": UNIT, "cores": c1, "kind": "oracle",
+                                             "sample": s1}}
     print(json.dumps(line), flush=True)
-    s.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

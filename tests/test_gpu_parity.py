@@ -172,9 +172,12 @@ def test_c2_shaped_full_run_500_steps():
     source and the 64 receivers, 500 steps from rest at the CFL step, through the
     whole wavelet and its reflections and periodic wrap-arounds.  The bar is the
     state after the run (relative L2 per field group, absolute on alpha) and the
-    receiver traces of every step."""
+    receiver traces of every step.  The peak moment rate is 4e13 N m/s (peak strain
+    about 2e-5, alpha up to 4.5e-4): on 1 km elements the point source's delta is
+    rough at the quadrature nodes, and from 4e14 on the nonlinear step runs away
+    next to the source near the wavelet's peak, in the FP64 oracle as well."""
     from parity_util import oracle_run_pool
-    w = workload_small_layered(n=4, order=4, m0=4e15)
+    w = workload_small_layered(n=4, order=4, m0=4e13)
     mesh, mat, N = w["mesh"], w["material"], 4
     steps = w["steps"]
     assert steps == 500
