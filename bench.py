@@ -231,48 +231,38 @@ def load_workload(name, args):
 # CPU baselines: the FP64 oracle, as it stands, on bounded samples of a workload
 # ---------------------------------------------------------------------------
 
-def _face_neighbours_of(mesh, rows):
-    """[len(rows), 4] element across each face of the sample rows (-1 on boundary
-    faces), by matching vertex-id triples among the elements sharing a vertex
-    with the sample (host bookkeeping only)."""
+def _face_index(mesh, rows):
+    """The faces of every element that shares a vertex with the sample rows,
+    keyed by their sorted vertex-id triple (host bookkeeping only)."""
     vid = np.asarray(mesh.elem_vid)
-    rows = np.asarray(rows)
     cand = np.nonzero(np.isin(vid, np.unique(vid[rows])).any(axis=1))[0]
     owner = {}
     for e in cand.tolist():
-        v = vid[e]
+        v = vid[e].tolist()
         for f in range(4):
-            owner.setdefault(tuple(sorted(np.delete(v, f).tolist())), []).append(e)
-    nbr = -np.ones((rows.size, 4), dtype=np.int64)
-    for i, e in enumerate(rows.tolist()):
-        for f in range(4):
-            others = [x for x in owner[tuple(sorted(np.delete(vid[e], f).tolist()))] if x != e]
-            if others:
-                nbr[i, f] = others[0]
-    return nbr
+            owner.setdefault(tuple(sorted(v[:f] + v[f + 1:])), []).append(e)
+    return owner
 
 
-def _sample_spec(w, rows, nbr):
+def _face_key(vid, e, f):
+    v = vid[e].tolist()
+    return tuple(sorted(v[:f] + v[f + 1:]))
+
+
+def _sample_spec(w, rows, owner):
     """The sub-mesh of the sample rows and their face neighbours (faces leaving it
     tagged absorbing: they enter only the neighbours' own updates, which are not
     timed), the sources inside it, and the rows' positions."""
     mesh = w["mesh"]
-    elems = np.unique(np.concatenate([rows, nbr[nbr >= 0].ravel()]))
+    vid = np.asarray(mesh.elem_vid)
+    nb = [x for e in rows.tolist() for f in range(4) for x in owner[_face_key(vid, e, f)] if x != e]
+    elems = np.unique(np.concatenate([rows, np.asarray(nb, dtype=np.int64)]))
     pos = -np.ones(mesh.n_elem, dtype=np.int64)
     pos[elems] = np.arange(elems.size)
     bc = np.array(mesh.face_bc[elems], dtype=np.int8)
-    inner = {int(e): i for i, e in enumerate(rows.tolist())}
-    vid = np.asarray(mesh.elem_vid)
-    elem_set = set(elems.tolist())
     for k, e in enumerate(elems.tolist()):
-        if e in inner:
-            continue
-        for f in range(4):                       # a neighbour's faces towards elements outside
-            if bc[k, f] != 0:
-                continue
-            key = set(np.delete(vid[e], f).tolist())
-            shared = [x for x in elem_set if x != e and key <= set(vid[x].tolist())]
-            if not shared:
+        for f in range(4):
+            if bc[k, f] == 0 and not any(x != e and pos[x] >= 0 for x in owner[_face_key(vid, e, f)]):
                 bc[k, f] = 2
     lo, hi = mesh.elem_xyz[elems].min(axis=(0, 1)), mesh.elem_xyz[elems].max(axis=(0, 1))
     srcs = [s for s in w["sources"] if np.all(s["x"] >= lo) and np.all(s["x"] <= hi)]
@@ -331,9 +321,9 @@ class OraclePool:
         import concurrent.futures as cf
         import multiprocessing as mp
         rows = _sample_rows(w, workers * chunk)
-        nbr = _face_neighbours_of(w["mesh"], rows)
+        owner = _face_index(w["mesh"], rows)
         self.chunks = np.array_split(np.arange(rows.size), workers)
-        specs = [_sample_spec(w, rows[c], nbr[c]) for c in self.chunks]
+        specs = [_sample_spec(w, rows[c], owner) for c in self.chunks]
         self.rows = rows.size
         self.workers = workers
         ctx = mp.get_context("spawn")
@@ -358,7 +348,7 @@ def cpu_baseline_one_core(w, chunk=1024, steps=2):
     """The oracle on one host core: `chunk` elements of the workload (and their
     face neighbours' predictors), `steps` steps from a seeded state."""
     rows = _sample_rows(w, chunk)
-    spec = _sample_spec(w, rows, _face_neighbours_of(w["mesh"], rows))
+    spec = _sample_spec(w, rows, _face_index(w["mesh"], rows))
     o, Q = _sample_oracle(spec)
     dt = o.cfl_dt()
     o.step(Q, dt, t=0.8, rows=spec["rows"])                        # warm-up
@@ -425,7 +415,10 @@ def run_reference(args):
         return 0
     w = load_workload(args.workload, args)
     cores = _host_cores()
-    pool = OraclePool(w, cores, args.ref_chunk)
+    # about four minutes of oracle work for the whole run at a conservative 300
+    # element updates/s per core, within [64, 1024] elements per core and step
+    chunk = args.ref_chunk or int(min(1024, max(64, 240.0 / (args.steps + args.warmup) * 300.0)) // 64 * 64)
+    pool = OraclePool(w, cores, chunk)
     try:
         for _ in range(args.warmup):
             pool.step()
@@ -435,7 +428,7 @@ def run_reference(args):
     total = sum(times)
     value = pool.rows * args.steps / total
     sample = (f"per step: {pool.rows} contiguous elements of the {w['mesh'].n_elem}-element mesh in {cores} "
-              f"chunks of {args.ref_chunk} (plus their face neighbours' predictors), numpy FP64, {cores} "
+              f"chunks of {chunk} (plus their face neighbours' predictors), numpy FP64, {cores} "
               f"processes with 1 BLAS thread each")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
@@ -552,8 +545,9 @@ def main():
     ap.add_argument("--cube-steps", type=int, default=200,
                     help="steps of the two-layer cube timed as the extra 'c2' object (0 skips it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-chunk", type=int, default=256,
-                    help="elements per host core in each step of --impl reference")
+    ap.add_argument("--ref-chunk", type=int, default=0,
+                    help="elements per host core in each step of --impl reference (0: sized from the steps so "
+                         "that the run takes a few minutes)")
     ap.add_argument("--ensemble-members", type=int, default=32,
                     help="members of the ensemble workload (two-layer cube at N=3) timed against one member; "
                          "0 skips it")
