@@ -708,15 +708,16 @@ def run_adjoint(args, dgpkg, torch, stream, snapshots=40, fwd_steps=50):
     E, L = mesh.n_elem, n_modes(N)
     s = dgpkg.Solver(mesh.elem_xyz, mesh.elem_vid, N, cfl=w["cfl"], stream=stream)
     zero = np.zeros((E, 10, L), np.float32)
+    t_start = w["t_start"]
     s.set_material(w["material_ref"])
     s.set_sources(w["sources"])
     s.set_receivers(w["receivers"])
-    s.set_state(zero, 0.0)
+    s.set_state(zero, t_start)
     dt = s.dt
     s.step(n, dt)
     ref = s.read_receivers()[:n]
     s.set_material(w["material"])
-    s.set_state(zero, 0.0)
+    s.set_state(zero, t_start)
     s.step(5, dt)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -725,7 +726,7 @@ def run_adjoint(args, dgpkg, torch, stream, snapshots=40, fwd_steps=50):
     ev1.record(stream)
     torch.cuda.synchronize()
     fwd_ms = ev0.elapsed_time(ev1) / fwd_steps
-    s.set_state(zero, 0.0)
+    s.set_state(zero, t_start)
     k = min(n, 20)
     s.adjoint_gradient(ref[:k], k, dt, snapshots=min(snapshots, k))
     torch.cuda.synchronize()
@@ -739,7 +740,7 @@ def run_adjoint(args, dgpkg, torch, stream, snapshots=40, fwd_steps=50):
     state_bytes = E * 4 * ((10 * L + 3) // 4 * 4)
     free, _ = torch.cuda.mem_get_info()
     if (n + 4) * state_bytes < 0.8 * free:
-        s.set_state(zero, 0.0)
+        s.set_state(zero, t_start)
         torch.cuda.synchronize()
         ev0.record(stream)
         J2, _, _, info2 = s.adjoint_gradient(ref, n, dt, snapshots=n + 1, info=True)
@@ -751,10 +752,15 @@ def run_adjoint(args, dgpkg, torch, stream, snapshots=40, fwd_steps=50):
                      "forward_steps_run": info2["forward_steps"], "misfit": J2}
     s.close()
     adj = info["adjoint_ms"] / info["adjoint_steps"]
+    # size of the residual behind J against the traces: J = dt/2 sum |v - v_ref|^2
+    res_rms = math.sqrt(2.0 * J / (dt * ref.size)) if J > 0 else 0.0
+    ref_rms = float(np.sqrt(np.mean(ref.astype(np.float64) ** 2)))
     return {"workload": w["name"], "elements": E, "order": N, "steps": n, "snapshots": snapshots,
             "forward_ms_per_step": fwd_ms, "adjoint_ms_per_step": adj, "adjoint_to_forward_step": adj / fwd_ms,
             "forward_steps_run": info["forward_steps"], "snapshot_copy_ms": info["copy_ms"],
             "gradient_ms": total, "gradient_to_forward_run": total / (n * fwd_ms), "misfit": J,
+            "t_start": t_start, "reference_trace_rms": ref_rms, "residual_rms": res_rms,
+            "residual_to_trace_rms": res_rms / ref_rms if ref_rms > 0 else None,
             "max_abs_grad_xi0": float(np.abs(gx).max()), "max_abs_grad_cd": float(np.abs(gc).max()),
             "store_all": store_all}
 

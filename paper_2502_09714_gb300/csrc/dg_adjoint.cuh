@@ -42,6 +42,14 @@ struct ADim {
   static constexpr int QS = q_stride(N), DS = d_stride(N), AOFF = d_alpha_offset(N);
   static constexpr int RS = adj_rec_stride(N);
   static constexpr int LDS = QS + DS;           // lam of D^0..D^N in the (Q, D) layout
+  // rows (i, k), k < L_{N-i}, of the forward CK products of the transposed recursion
+  __host__ __device__ static constexpr int gx_row(int i) {
+    int r = 0;
+    for (int j = 1; j < i; ++j) r += n_modes(N - j);
+    return r;
+  }
+  static constexpr int GXI = gx_row(N + 1);
+  static_assert(GXI * 27 <= NQ * 28, "forward CK products fit in the X region");
 };
 
 // sqrt(I2), xi = I1 / sqrt(I2) and their derivatives in the six strain entries
@@ -260,6 +268,42 @@ __device__ __forceinline__ int ld_index(int o, int l, int p) {
   return q_stride(N) + d_offset(N, o) + l * 9 + p;
 }
 
+// For two nodes x, x+1 of a basis table V[l][x] (row stride ldv) and field p: the mode
+// sums t[o] = sum_l V[l][x] D^o_lp of every Taylor order o (D^0 = the state Q, row
+// stride 10; D^o, o >= 1, row stride 9; alpha has orders 0 and 1 on all modes).  The
+// loops run over compile-time mode counts and share each table load between orders.
+template <int N>
+__device__ __forceinline__ void mode_sums(const float* vx, int ldv, const float* Qs, const float* Ds, int p,
+                                          float* t0, float* t1) {
+  constexpr int NT = N + 1, L = n_modes(N);
+#pragma unroll
+  for (int o = 0; o < NT; ++o) t0[o] = t1[o] = 0.f;
+  if (p == 9) {
+#pragma unroll 4
+    for (int l = 0; l < L; ++l) {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(vx + l * ldv));
+      const float c0 = Qs[l * 10 + 9], c1 = Ds[d_alpha_offset(N) + l];
+      t0[0] = fmaf(v.x, c0, t0[0]);
+      t1[0] = fmaf(v.y, c0, t1[0]);
+      t0[1] = fmaf(v.x, c1, t0[1]);
+      t1[1] = fmaf(v.y, c1, t1[1]);
+    }
+  } else {
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(vx + l * ldv));
+#pragma unroll
+      for (int o = 0; o < NT; ++o) {
+        if (l < n_modes(N - o)) {
+          const float c = o == 0 ? Qs[l * 10 + p] : Ds[d_offset(N, o) + l * 9 + p];
+          t0[o] = fmaf(v.x, c, t0[o]);
+          t1[o] = fmaf(v.y, c, t1[o]);
+        }
+      }
+    }
+  }
+}
+
 // For every node x of a basis table V[l][x] (row stride ldv, NX nodes) and field
 // p: the value of the predictor's polynomial at the NT time nodes,
 //     u[z][x][p] = sum_o c[z][o] sum_l V[l][x] D^o_lp,
@@ -273,21 +317,7 @@ __device__ __forceinline__ void node_values(const float* V, int ldv, const float
     const int xh = w / 10, p = w - xh * 10, x = 2 * xh;
     const float* vx = V + x;
     float t0[NT], t1[NT];
-#pragma unroll
-    for (int o = 0; o < NT; ++o) {
-      const int lim = order_modes<N>(o, p);
-      const float* src = o == 0 ? sQ + p : (p == 9 ? sD + d_alpha_offset(N) : sD + d_offset(N, o) + p);
-      const int st = o == 0 ? 10 : (p == 9 ? 1 : 9);
-      float a0 = 0.f, a1 = 0.f;
-      for (int l = 0; l < lim; ++l) {
-        const float2 v = __ldg(reinterpret_cast<const float2*>(vx + l * ldv));
-        const float c = src[l * st];
-        a0 = fmaf(v.x, c, a0);
-        a1 = fmaf(v.y, c, a1);
-      }
-      t0[o] = a0;
-      t1[o] = a1;
-    }
+    mode_sums<N>(vx, ldv, sQ, sD, p, t0, t1);
     const bool two = x + 1 < NX;
     if (out0 != nullptr && p < 6) {                           // the strains at t_n
       out0[x * 6 + p] = t0[0];
@@ -303,6 +333,36 @@ __device__ __forceinline__ void node_values(const float* V, int ldv, const float
       }
       out[(z * NX + x) * 10 + p] = u0;
       if (two) out[(z * NX + x + 1) * 10 + p] = u1;
+    }
+  }
+}
+
+// node_values for the two sides of a face in one pass (items over both sides): side s
+// takes its table V[s] and its element's state Q + s QS and predictor output D + s DS.
+template <int N, int NX>
+__device__ __forceinline__ void node_values_2side(const float* V0, const float* V1, int ldv, const float* sQ,
+                                                  const float* sD, const float* sC, float* out) {
+  constexpr int NT = N + 1, NXH = (NX + 1) / 2, QS = q_stride(N), DS = d_stride(N);
+  for (int w = threadIdx.x; w < 2 * NXH * 10; w += blockDim.x) {
+    const int sd = w / (NXH * 10), r = w - sd * NXH * 10;
+    const int xh = r / 10, p = r - xh * 10, x = 2 * xh;
+    const float* vx = (sd ? V1 : V0) + x;
+    const float* Qs = sQ + sd * QS;
+    const float* Ds = sD + sd * DS;
+    float t0[NT], t1[NT];
+    mode_sums<N>(vx, ldv, Qs, Ds, p, t0, t1);
+    const bool two = x + 1 < NX;
+    float* os = out + sd * NT * NX * 10;
+#pragma unroll
+    for (int z = 0; z < NT; ++z) {
+      float u0 = 0.f, u1 = 0.f;
+#pragma unroll
+      for (int o = 0; o < NT; ++o) {
+        u0 = fmaf(sC[z * NT + o], t0[o], u0);
+        u1 = fmaf(sC[z * NT + o], t1[o], u1);
+      }
+      os[(z * NX + x) * 10 + p] = u0;
+      if (two) os[(z * NX + x + 1) * 10 + p] = u1;
     }
   }
 }
@@ -358,15 +418,15 @@ __global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
     if (threadIdx.x < 6) sRed[threadIdx.x] = 0.0;
     __syncthreads();
     // traces of both sides at the space-time face nodes
-    for (int sd = 0; sd < 2; ++sd)
-      node_values<N, NF>(tb + T.VfT + (sd ? lf1 : lf0) * L * A::NFP, A::NFP, smem + S::oQ + sd * A::QS,
-                         smem + S::oD + sd * A::DS, sC, smem + S::oTr + sd * NT * NF * 10);
+    node_values_2side<N, NF>(tb + T.VfT + lf0 * L * A::NFP, tb + T.VfT + lf1 * L * A::NFP, A::NFP, smem + S::oQ,
+                             smem + S::oD, sC, smem + S::oTr);
     // lam of the time-integrated face flux:
     //   lff[i][p] = -(a0 sum_k Vfw[f0][i][k] lam0[k][p] - a1 sum_k Vfw[f1][i][k] lam1[k][p])
     const float a0 = a.geom[e0].face[lf0][3], a1 = bnd ? 0.f : a.geom[e1].face[lf1][3];
     for (int w = threadIdx.x; w < NF * 9; w += blockDim.x) {
       const int i = w / 9, p = w - i * 9;
       float s0 = 0.f, s1 = 0.f;
+#pragma unroll 4
       for (int k = 0; k < L; ++k) {
         s0 = fmaf(__ldg(tb + T.Vfw + (lf0 * NF + i) * A::LP + k), smem[S::oLam + k * 10 + p], s0);
         s1 = fmaf(__ldg(tb + T.Vfw + (lf1 * NF + i) * A::LP + k), smem[S::oLam + A::QS + k * 10 + p], s1);
@@ -458,6 +518,7 @@ __global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
       float a0[NT], a1[NT];
 #pragma unroll
       for (int o = 0; o < NT; ++o) a0[o] = a1[o] = 0.f;
+#pragma unroll 4
       for (int i = 0; i < NF; ++i) {
         const float v = __ldg(V + i);
 #pragma unroll
@@ -552,6 +613,7 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
       float g0[3] = {0.f, 0.f, 0.f}, g1[3] = {0.f, 0.f, 0.f};
       const float* gw = tb + T.Gw + q * A::LP;
       const float* vw = tb + T.Vw + q * A::LP;
+#pragma unroll 4
       for (int k = 0; k < L; ++k) {
         const float2 lk = *reinterpret_cast<const float2*>(smem + S::oLam + k * 10 + p0);
         const float ga = __ldg(gw + k), gb = __ldg(gw + NQ * A::LP + k), gc = __ldg(gw + 2 * NQ * A::LP + k);
@@ -612,6 +674,7 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
       float a0[NT], a1[NT];
 #pragma unroll
       for (int z = 0; z < NT; ++z) a0[z] = a1[z] = 0.f;
+#pragma unroll 4
       for (int q = 0; q < NQ; ++q) {
         const float v = __ldg(V + q);
 #pragma unroll
@@ -634,6 +697,35 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
 #pragma unroll
           for (int fl = 0; fl < 4; ++fl) s += smem[S::oR + fl * A::RS + idx];
           sLD[idx] = s;
+        }
+      }
+    }
+    // the forward CK products every order of the transposed recursion needs (they do not
+    // depend on lam), computed here with many items instead of inside the order loop:
+    // GX[i][k][q][d] = sum_e Theta^{-1}_ed sum_l Kt^e_kl D^{i-1}_lq, k < L_{N-i}, q < 9, in the
+    // X region (free since the flux phase)
+    {
+      float* sGX = smem + S::oX;
+      for (int w = threadIdx.x; w < A::GXI * 9; w += blockDim.x) {
+#pragma unroll
+        for (int i = 1; i <= N; ++i) {
+          const int r0 = 9 * A::gx_row(i), r1 = 9 * A::gx_row(i + 1);
+          if (w < r0 || w >= r1) continue;
+          const int k = (w - r0) / 9, q = (w - r0) - 9 * k;
+          const float* Dprev = i == 1 ? smem + S::oQ : smem + S::oD + d_offset(N, i - 1);
+          const int sp = i == 1 ? 10 : 9;
+          float gk0 = 0.f, gk1 = 0.f, gk2 = 0.f;
+          const float* kt = tb + T.KtA + k;
+#pragma unroll
+          for (int l = 0; l < n_modes(N - i + 1); ++l) {
+            const float dv = Dprev[l * sp + q];
+            gk0 = fmaf(__ldg(kt + (0 * L + l) * A::LP), dv, gk0);
+            gk1 = fmaf(__ldg(kt + (1 * L + l) * A::LP), dv, gk1);
+            gk2 = fmaf(__ldg(kt + (2 * L + l) * A::LP), dv, gk2);
+          }
+          float* g = sGX + w * 3;
+#pragma unroll
+          for (int d = 0; d < 3; ++d) g[d] = sGeo[0 * 3 + d] * gk0 + sGeo[1 * 3 + d] * gk1 + sGeo[2 * 3 + d] * gk2;
         }
       }
     }
@@ -673,16 +765,17 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
       sRed[3] = (static_cast<double>(2.f * dc) + sRed[5]) * m.rho;
     }
     __syncthreads();
-    // Cauchy-Kovalevskaya recursion transposed, order N down to 1
+    // Cauchy-Kovalevskaya recursion transposed, order N down to 1 (the forward products in
+    // GX; the lambda/rho and mu/rho parts summed per thread over all orders, reduced once)
     const float lr = sGeo[9], mr = sGeo[10];
+    float plr = 0.f, pmr = 0.f;
+#pragma unroll
     for (int i = N; i >= 1; --i) {
       const int Lout = n_modes(N - i), Lin = n_modes(N - i + 1);
       const float* lDi = sLD + A::QS + d_offset(N, i);       // [Lout][9]
-      const float* Dprev = i == 1 ? smem + S::oQ : smem + S::oD + d_offset(N, i - 1);
-      const int sp = i == 1 ? 10 : 9;
       float* lDprev = i == 1 ? sLD : sLD + A::QS + d_offset(N, i - 1);
       const int lsp = i == 1 ? 10 : 9;
-      float plr = 0.f, pmr = 0.f;
+      const float* gxi = smem + S::oX + 27 * A::gx_row(i);
       for (int w = threadIdx.x; w < Lout * 9; w += blockDim.x) {
         const int k = w / 9, q = w - k * 9;
         float lv[9];
@@ -711,17 +804,7 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
           smem[S::oH + (ee * L + k) * 9 + q] = sGeo[ee * 3 + 0] * ps[0] + sGeo[ee * 3 + 1] * ps[1] + sGeo[ee * 3 + 2] * ps[2];
         // the star matrices' dependence on lambda/rho and mu/rho:
         // Gx[d] = sum_e Theta^{-1}_ed sum_l Kt^e_kl D^{i-1}_lq
-        float gk0 = 0.f, gk1 = 0.f, gk2 = 0.f;
-        const float* kt = tb + T.KtA + k;
-        for (int l = 0; l < Lin; ++l) {
-          const float dv = Dprev[l * sp + q];
-          gk0 = fmaf(__ldg(kt + (0 * L + l) * A::LP), dv, gk0);
-          gk1 = fmaf(__ldg(kt + (1 * L + l) * A::LP), dv, gk1);
-          gk2 = fmaf(__ldg(kt + (2 * L + l) * A::LP), dv, gk2);
-        }
-        float gx[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) gx[d] = sGeo[0 * 3 + d] * gk0 + sGeo[1 * 3 + d] * gk1 + sGeo[2 * 3 + d] * gk2;
+        const float gx[3] = {gxi[w * 3], gxi[w * 3 + 1], gxi[w * 3 + 2]};
         // d/d(lam/rho): B^d_{6+d, q<3} = -lam/rho; d/d(mu/rho): B^d_{6+i, sym(i,d)} = -2 mu/rho
         if (q < 3) {
           plr += gx[0] * lv[6] + gx[1] * lv[7] + gx[2] * lv[8];
@@ -734,21 +817,22 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
           pmr += 2.f * (gx[0] * lv[8] + gx[2] * lv[6]);
         }
       }
-      block_add(&sRed[2], plr);
-      block_add(&sRed[3], pmr);
       __syncthreads();
       // lam D^{i-1}_lq -= sum_e sum_k Kt^e_kl H[e][k][q]
       for (int w = threadIdx.x; w < Lin * 9; w += blockDim.x) {
         const int l = w / 9, q = w - l * 9;
-        float s = 0.f;
+        float s3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
         for (int k = 0; k < Lout; ++k)
 #pragma unroll
           for (int ee = 0; ee < 3; ++ee)
-            s = fmaf(__ldg(tb + T.KtA + (ee * L + l) * A::LP + k), smem[S::oH + (ee * L + k) * 9 + q], s);
-        lDprev[l * lsp + q] -= s;
+            s3[ee] = fmaf(__ldg(tb + T.KtA + (ee * L + l) * A::LP + k), smem[S::oH + (ee * L + k) * 9 + q], s3[ee]);
+        lDprev[l * lsp + q] -= s3[0] + s3[1] + s3[2];
       }
       __syncthreads();
     }
+    block_add(&sRed[2], plr);   // read after the barriers of the damage-source phase below
+    block_add(&sRed[3], pmr);
     // damage-rate source of D^1 from the state at t_n: lam_r(q) = sum_k w_q phi_k(x_q) lam D^1_k9
     {
       float* sLu0 = smem + S::oLu;                           // [NQ][6] (reuses the nodal lam)
@@ -758,8 +842,10 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
 #pragma unroll
         for (int p = 0; p < 6; ++p) u[p] = smem[S::oU0 + q * 6 + p];
         u[6] = u[7] = u[8] = u[9] = 0.f;
-        float lrq = 0.f;
-        for (int l = 0; l < L; ++l) lrq = fmaf(__ldg(tb + T.Vw + q * A::LP + l), sLD[A::QS + A::AOFF + l], lrq);
+        float lr4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int l = 0; l < L; ++l) lr4[l & 3] = fmaf(__ldg(tb + T.Vw + q * A::LP + l), sLD[A::QS + A::AOFF + l], lr4[l & 3]);
+        const float lrq = (lr4[0] + lr4[1]) + (lr4[2] + lr4[3]);
         float lu[10];
 #pragma unroll
         for (int p = 0; p < 10; ++p) lu[p] = 0.f;
@@ -772,9 +858,10 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
       __syncthreads();
       for (int w = threadIdx.x; w < L * 6; w += blockDim.x) {
         const int l = w / 6, p = w - l * 6;
-        float s = 0.f;
-        for (int q = 0; q < NQ; ++q) s = fmaf(__ldg(tb + T.VvT + l * A::NQP + q), sLu0[q * 6 + p], s);
-        sLD[l * 10 + p] += s;
+        float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int q = 0; q < NQ; ++q) s4[q & 3] = fmaf(__ldg(tb + T.VvT + l * A::NQP + q), sLu0[q * 6 + p], s4[q & 3]);
+        sLD[l * 10 + p] += (s4[0] + s4[1]) + (s4[2] + s4[3]);
       }
       __syncthreads();
     }

@@ -184,3 +184,35 @@ def oracle_run_pool(mesh, material, order, Q0, dt, n_steps, t0=0.0, cfl=0.5, sou
             else:
                 os.environ[k] = v
     return (Q, np.array(traces)) if receivers is not None else Q
+
+
+def _misfit_job(job):
+    from oracle.adjoint import misfit
+    xyz, vid, order, mat, sources, receivers, Q0, dt, n, ref, t0 = job
+    o = Oracle(xyz, vid, order, mat)
+    if sources:
+        o.set_sources(list(sources))
+    o.set_receivers(receivers)
+    return misfit(o, Q0, dt, n, ref, t0=t0)[0]
+
+
+def misfit_pool(mesh, order, materials, sources, receivers, Q0, dt, n_steps, ref, t0=0.0, workers=None):
+    """The oracle's receiver misfit (oracle.adjoint.misfit) of one run per material
+    table, the runs spread over spawn-started processes with one BLAS thread each."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    workers = workers or max(1, min(16, os.cpu_count() or 1, len(materials)))
+    jobs = [(mesh.elem_xyz, mesh.elem_vid, order, m, list(sources), receivers, Q0, dt, n_steps, ref, t0)
+            for m in materials]
+    saved = {k: os.environ.get(k) for k in _ONE_THREAD}
+    os.environ.update({k: "1" for k in _ONE_THREAD})
+    try:
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_misfit_job, jobs))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
