@@ -42,6 +42,7 @@ struct ADim {
   static constexpr int QS = q_stride(N), DS = d_stride(N), AOFF = d_alpha_offset(N);
   static constexpr int RS = adj_rec_stride(N);
   static constexpr int LDS = QS + DS;           // lam of D^0..D^N in the (Q, D) layout
+  static constexpr int U0S = NQP + 4;           // row stride of the nodal lam of the damage source (off the bank period)
   // rows (i, k), k < L_{N-i}, of the forward CK products of the transposed recursion
   __host__ __device__ static constexpr int gx_row(int i) {
     int r = 0;
@@ -230,6 +231,13 @@ __device__ __forceinline__ void boundary_flux_vjp(int bc, const float* u, const 
   *dm += dmu;
 }
 
+__device__ __forceinline__ float dot4(const float4 a, const float4 b, float acc) {
+  acc = fmaf(a.x, b.x, acc);
+  acc = fmaf(a.y, b.y, acc);
+  acc = fmaf(a.z, b.z, acc);
+  return fmaf(a.w, b.w, acc);
+}
+
 // Block-wide sum of one float per thread into a shared double (atomic).
 __device__ __forceinline__ void block_add(double* acc, float v) {
 #pragma unroll
@@ -304,14 +312,74 @@ __device__ __forceinline__ void mode_sums(const float* vx, int ldv, const float*
   }
 }
 
+// The same for four nodes x..x+3 (ldv and x multiples of 4: one 16-byte table load per mode).
+template <int N>
+__device__ __forceinline__ void mode_sums4(const float* vx, int ldv, const float* Qs, const float* Ds, int p,
+                                           float (*t)[N + 1]) {
+  constexpr int NT = N + 1, L = n_modes(N);
+#pragma unroll
+  for (int n = 0; n < 4; ++n)
+#pragma unroll
+    for (int o = 0; o < NT; ++o) t[n][o] = 0.f;
+  if (p == 9) {
+#pragma unroll 4
+    for (int l = 0; l < L; ++l) {
+      const float4 v4 = __ldg(reinterpret_cast<const float4*>(vx + l * ldv));
+      const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+      const float c0 = Qs[l * 10 + 9], c1 = Ds[d_alpha_offset(N) + l];
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        t[n][0] = fmaf(v[n], c0, t[n][0]);
+        t[n][1] = fmaf(v[n], c1, t[n][1]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      const float4 v4 = __ldg(reinterpret_cast<const float4*>(vx + l * ldv));
+      const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+      for (int o = 0; o < NT; ++o) {
+        if (l < n_modes(N - o)) {
+          const float c = o == 0 ? Qs[l * 10 + p] : Ds[d_offset(N, o) + l * 9 + p];
+#pragma unroll
+          for (int n = 0; n < 4; ++n) t[n][o] = fmaf(v[n], c, t[n][o]);
+        }
+      }
+    }
+  }
+}
+
 // For every node x of a basis table V[l][x] (row stride ldv, NX nodes) and field
 // p: the value of the predictor's polynomial at the NT time nodes,
 //     u[z][x][p] = sum_o c[z][o] sum_l V[l][x] D^o_lp,
 // taking the sum over modes once per Taylor order.
-template <int N, int NX>
-__device__ __forceinline__ void node_values(const float* V, int ldv, const float* sQ, const float* sD,
-                                            const float* sC, float* out, float* out0 = nullptr) {
+template <int N, int NX, int LDV>
+__device__ __forceinline__ void node_values(const float* V, const float* sQ, const float* sD, const float* sC,
+                                            float* out, float* out0 = nullptr) {
   constexpr int NT = N + 1, NXH = (NX + 1) / 2;
+  constexpr int ldv = LDV;
+  if constexpr (LDV % 4 == 0) {
+    // four nodes per item (the table's rows are padded with zeros to LDV >= NX)
+    constexpr int NX4 = (NX + 3) / 4;
+    for (int w = threadIdx.x; w < NX4 * 10; w += blockDim.x) {
+      const int xq = w / 10, p = w - xq * 10, x = 4 * xq;
+      float t[4][NT];
+      mode_sums4<N>(V + x, ldv, sQ, sD, p, t);
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        if (x + n >= NX) continue;
+        if (out0 != nullptr && p < 6) out0[(x + n) * 6 + p] = t[n][0];   // the strains at t_n
+#pragma unroll
+        for (int z = 0; z < NT; ++z) {
+          float u = 0.f;
+#pragma unroll
+          for (int o = 0; o < NT; ++o) u = fmaf(sC[z * NT + o], t[n][o], u);
+          out[(z * NX + x + n) * 10 + p] = u;
+        }
+      }
+    }
+  } else {
   // two nodes per item: the table's rows are padded to an even length with zeros
   for (int w = threadIdx.x; w < NXH * 10; w += blockDim.x) {
     const int xh = w / 10, p = w - xh * 10, x = 2 * xh;
@@ -335,14 +403,37 @@ __device__ __forceinline__ void node_values(const float* V, int ldv, const float
       if (two) out[(z * NX + x + 1) * 10 + p] = u1;
     }
   }
+  }
 }
 
 // node_values for the two sides of a face in one pass (items over both sides): side s
 // takes its table V[s] and its element's state Q + s QS and predictor output D + s DS.
-template <int N, int NX>
-__device__ __forceinline__ void node_values_2side(const float* V0, const float* V1, int ldv, const float* sQ,
+template <int N, int NX, int LDV>
+__device__ __forceinline__ void node_values_2side(const float* V0, const float* V1, const float* sQ,
                                                   const float* sD, const float* sC, float* out) {
   constexpr int NT = N + 1, NXH = (NX + 1) / 2, QS = q_stride(N), DS = d_stride(N);
+  constexpr int ldv = LDV;
+  if constexpr (LDV % 4 == 0) {
+    constexpr int NX4 = (NX + 3) / 4;
+    for (int w = threadIdx.x; w < 2 * NX4 * 10; w += blockDim.x) {
+      const int sd = w / (NX4 * 10), r = w - sd * NX4 * 10;
+      const int xq = r / 10, p = r - xq * 10, x = 4 * xq;
+      float t[4][NT];
+      mode_sums4<N>((sd ? V1 : V0) + x, ldv, sQ + sd * QS, sD + sd * DS, p, t);
+      float* os = out + sd * NT * NX * 10;
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        if (x + n >= NX) continue;
+#pragma unroll
+        for (int z = 0; z < NT; ++z) {
+          float u = 0.f;
+#pragma unroll
+          for (int o = 0; o < NT; ++o) u = fmaf(sC[z * NT + o], t[n][o], u);
+          os[(z * NX + x + n) * 10 + p] = u;
+        }
+      }
+    }
+  } else {
   for (int w = threadIdx.x; w < 2 * NXH * 10; w += blockDim.x) {
     const int sd = w / (NXH * 10), r = w - sd * NXH * 10;
     const int xh = r / 10, p = r - xh * 10, x = 2 * xh;
@@ -365,6 +456,7 @@ __device__ __forceinline__ void node_values_2side(const float* V0, const float* 
       if (two) os[(z * NX + x + 1) * 10 + p] = u1;
     }
   }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -384,16 +476,18 @@ struct FaceSmem {
 };
 
 template <int N>
-__global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
+__global__ void __launch_bounds__(128, 7) k_adj_face(AdjArgs a) {
   using A = ADim<N>;
   using S = FaceSmem<N>;
   constexpr int L = A::L, NF = A::NF, NT = A::NT;
   extern __shared__ __align__(16) float smem[];
   __shared__ double sRed[6];
-  __shared__ float sC[NT * NT], sG[NT];
+  __shared__ float sC[NT * NT], sG[NT], sIB[NF];
   const TableLayout T = table_layout(N);
   const float* tb = a.tables;
   time_tables<N>(tb, T, a.dt, sC, sG);
+  // 1 / beta_i of the face rule: beta_i phi_0 is column 0 of any local face's weighted table
+  for (int i = threadIdx.x; i < NF; i += blockDim.x) sIB[i] = 2.449489742783178f / __ldg(tb + T.Vfw + i * A::LP);
   for (int64_t f = blockIdx.x; f < a.F; f += gridDim.x) {
     const int4 fc = a.faces[f];
     // a boundary face is (element, local face, -1, tag): its side 1 is a stand-in that
@@ -418,18 +512,29 @@ __global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
     if (threadIdx.x < 6) sRed[threadIdx.x] = 0.0;
     __syncthreads();
     // traces of both sides at the space-time face nodes
-    node_values_2side<N, NF>(tb + T.VfT + lf0 * L * A::NFP, tb + T.VfT + lf1 * L * A::NFP, A::NFP, smem + S::oQ,
-                             smem + S::oD, sC, smem + S::oTr);
+    // the traces and lam of the face flux (independent of each other) in one phase
+    node_values_2side<N, NF, A::NFP>(tb + T.VfT + lf0 * L * A::NFP, tb + T.VfT + lf1 * L * A::NFP, smem + S::oQ,
+                                     smem + S::oD, sC, smem + S::oTr);
     // lam of the time-integrated face flux:
     //   lff[i][p] = -(a0 sum_k Vfw[f0][i][k] lam0[k][p] - a1 sum_k Vfw[f1][i][k] lam1[k][p])
     const float a0 = a.geom[e0].face[lf0][3], a1 = bnd ? 0.f : a.geom[e1].face[lf1][3];
     for (int w = threadIdx.x; w < NF * 9; w += blockDim.x) {
       const int i = w / 9, p = w - i * 9;
+      const float4* v0 = reinterpret_cast<const float4*>(tb + T.Vfw + (lf0 * NF + i) * A::LP);
+      const float4* v1 = reinterpret_cast<const float4*>(tb + T.Vfw + (lf1 * NF + i) * A::LP);
+      const float* l0 = smem + S::oLam + p;
+      const float* l1 = smem + S::oLam + A::QS + p;
       float s0 = 0.f, s1 = 0.f;
-#pragma unroll 4
-      for (int k = 0; k < L; ++k) {
-        s0 = fmaf(__ldg(tb + T.Vfw + (lf0 * NF + i) * A::LP + k), smem[S::oLam + k * 10 + p], s0);
-        s1 = fmaf(__ldg(tb + T.Vfw + (lf1 * NF + i) * A::LP + k), smem[S::oLam + A::QS + k * 10 + p], s1);
+#pragma unroll
+      for (int kq = 0; kq < A::LP / 4; ++kq) {
+        const float4 x = __ldg(v0 + kq), y = __ldg(v1 + kq);
+        const int k = 4 * kq;
+        // the table's rows are zero beyond L; lam is read only at modes below L
+        s0 = fmaf(x.x, l0[k * 10], s0);
+        s1 = fmaf(y.x, l1[k * 10], s1);
+        if (k + 1 < L) { s0 = fmaf(x.y, l0[(k + 1) * 10], s0); s1 = fmaf(y.y, l1[(k + 1) * 10], s1); }
+        if (k + 2 < L) { s0 = fmaf(x.z, l0[(k + 2) * 10], s0); s1 = fmaf(y.z, l1[(k + 2) * 10], s1); }
+        if (k + 3 < L) { s0 = fmaf(x.w, l0[(k + 3) * 10], s0); s1 = fmaf(y.w, l1[(k + 3) * 10], s1); }
       }
       smem[S::oLff + w] = -(a0 * s0 - a1 * s1);
     }
@@ -494,9 +599,12 @@ __global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
     block_add(&sRed[1], px0);
     block_add(&sRed[2], px1);
     __syncthreads();
-    // fold the time nodes into Taylor orders in place: Lo[o][i][p] = sum_z c[z][o] Lu[z][i][p]
+    // fold the time nodes into Taylor orders in place, divided by the face weight of the
+    // node (the projection below runs over beta_i phi_l(x_i)):
+    //   Lo[o][i][p] = sum_z c[z][o] Lu[z][i][p] / beta_i,  beta_i = Vfw[.][i][0] / phi_0
     for (int w = threadIdx.x; w < 2 * NF * 10; w += blockDim.x) {
       const int sd = w / (NF * 10), r = w - sd * NF * 10;
+      const float ib = sIB[r / 10];
       float* base = smem + S::oLu + sd * NT * NF * 10 + r;
       float lz[NT];
 #pragma unroll
@@ -506,33 +614,56 @@ __global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
         float acc = 0.f;
 #pragma unroll
         for (int z = 0; z < NT; ++z) acc = fmaf(sC[z * NT + o], lz[z], acc);
-        base[o * NF * 10] = acc;
+        base[o * NF * 10] = acc * ib;
       }
     }
     __syncthreads();
-    // lam of D^o_lp of each side = sum_i phi_l(x_i) Lo[o][i][p]; one item per mode and pair of fields
-    for (int w = threadIdx.x; w < 2 * L * 5; w += blockDim.x) {
-      const int sd = w / (L * 5), r = w - sd * L * 5, l = r / 5, p0 = 2 * (r - l * 5);
-      const float* V = tb + T.VfT + ((sd ? lf1 : lf0) * L + l) * A::NFP;
+    // lam of D^o_lp of each side = sum_i beta_i phi_l(x_i) Lo[o][i][p]; one item per four
+    // modes and pair of fields (16-byte loads of the node-major weighted table)
+    constexpr int LQ = A::LP / 4, PITEMS = 2 * LQ * 5 * 2;   // (side, 4 modes, pair of fields, half of the nodes)
+    for (int base = 0; base < PITEMS; base += blockDim.x) {   // warp-uniform trip count (shuffles below)
+      const int w = base + threadIdx.x;
+      const bool live = w < PITEMS;
+      const int item = live ? w >> 1 : 0, ic = w & 1;
+      const int sd = item / (LQ * 5), r = item - sd * LQ * 5, lq = r / 5, p0 = 2 * (r - lq * 5);
+      const float4* V = reinterpret_cast<const float4*>(tb + T.Vfw + (sd ? lf1 : lf0) * NF * A::LP) + lq;
       const float* Lo = smem + S::oLu + sd * NT * NF * 10 + p0;
-      float a0[NT], a1[NT];
+      float acc[4][2][NT];
 #pragma unroll
-      for (int o = 0; o < NT; ++o) a0[o] = a1[o] = 0.f;
-#pragma unroll 4
-      for (int i = 0; i < NF; ++i) {
-        const float v = __ldg(V + i);
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int o = 0; o < NT; ++o) acc[j][0][o] = acc[j][1][o] = 0.f;
+#pragma unroll 2
+      for (int i = live ? ic : NF; i < NF; i += 2) {
+        const float4 v4 = __ldg(V + i * LQ);
+        const float v[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
         for (int o = 0; o < NT; ++o) {
           const float2 lo = *reinterpret_cast<const float2*>(Lo + (o * NF + i) * 10);
-          a0[o] = fmaf(v, lo.x, a0[o]);
-          a1[o] = fmaf(v, lo.y, a1[o]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[j][0][o] = fmaf(v[j], lo.x, acc[j][0][o]);
+            acc[j][1][o] = fmaf(v[j], lo.y, acc[j][1][o]);
+          }
         }
       }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int o = 0; o < NT; ++o) acc[j][h][o] += __shfl_xor_sync(0xffffffffu, acc[j][h][o], 1);
+      if (!live) continue;
       float* out = a.rec + (f * 2 + sd) * A::RS;
 #pragma unroll
-      for (int o = 0; o < NT; ++o) {
-        if (l < order_modes<N>(o, p0)) out[ld_index<N>(o, l, p0)] = a0[o];
-        if (l < order_modes<N>(o, p0 + 1)) out[ld_index<N>(o, l, p0 + 1)] = a1[o];
+      for (int j = 0; j < 4; ++j) {
+        const int l = 4 * lq + j;
+        if ((j >> 1) != ic || l >= L) continue;   // both lanes hold the sums: lane ic takes modes 2 ic, 2 ic + 1
+#pragma unroll
+        for (int o = 0; o < NT; ++o) {
+          if (l < order_modes<N>(o, p0)) out[ld_index<N>(o, l, p0)] = acc[j][0][o];
+          if (l < order_modes<N>(o, p0 + 1)) out[ld_index<N>(o, l, p0 + 1)] = acc[j][1][o];
+        }
       }
     }
     if (threadIdx.x < 2) {
@@ -563,9 +694,15 @@ struct ElemSmem {
   static constexpr int oLu = oU;                          //   (each node's lam replaces its value)
   static constexpr int oX = round4(oU + A::NT * A::NQ * 10);   // [NQ][28]: w_q dphi_k/dx_d lam_kp (27), w_q phi_k lam_k9
   static constexpr int oLD = oX + A::NQ * 28;             // [QS + DS] lam of D^0..D^N
-  static constexpr int oH = oLD + A::LDS;                 // [3][L][9]
-  static constexpr int oU0 = oH + 3 * A::L * 9;           // [NQ][6] strains at the volume nodes at t_n
-  static constexpr int oR = round4(oU0 + A::NQ * 6);      // [4][RS] the element's four face records
+  // [3][9][LP] H of the CK transpose, mode fastest: in the X region, after the forward CK
+  // products (both live only from the projection on)
+  static constexpr int oH = oX + round4(27 * A::GXI);
+  static_assert(round4(27 * A::GXI) + 27 * A::LP <= A::NQ * 28, "CK products and H inside the X region");
+  static constexpr int oR = round4(oLD + A::LDS);         // [4][RS] the element's four face records
+  // [10][LP] lam^{k+1}, mode fastest, in the lam of D^0..D^N region: read up to the X phase,
+  // before the projection first writes that region
+  static constexpr int oLamT = oLD;
+  static_assert(10 * A::LP <= A::LDS, "lam^T inside the lam-of-D region");
   static constexpr int total = oR + 4 * A::RS;
 };
 
@@ -575,16 +712,20 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
   using S = ElemSmem<N>;
   constexpr int L = A::L, NQ = A::NQ, NT = A::NT;
   extern __shared__ __align__(16) float smem[];
-  __shared__ double sRed[6];          // xi0, C_d, lam/rho, mu/rho, boundary d/dlam, d/dmu
+  // xi0, C_d, lam of cp, (unused), boundary d/dlam, d/dmu, CK d/d(lam/rho), CK d/d(mu/rho)
+  __shared__ double sRed[8];
   __shared__ float sGeo[16];          // Theta^{-1} [e][d], lambda_eff/rho, mu_eff/rho
-  __shared__ float sC[NT * NT], sG[NT];
+  __shared__ float sC[NT * NT], sG[NT], sIW[NQ];
   const TableLayout T = table_layout(N);
   const float* tb = a.tables;
   time_tables<N>(tb, T, a.dt, sC, sG);
+  // 1 / w_q of the volume rule: w_q phi_0 is column 0 of the weighted table
+  for (int q = threadIdx.x; q < NQ; q += blockDim.x) sIW[q] = 2.449489742783178f / __ldg(tb + T.Vw + q * A::LP);
   float* sLD = smem + S::oLD;
   for (int64_t e = blockIdx.x; e < a.E; e += gridDim.x) {
     __syncthreads();
-    // one batch of 16-byte asynchronous copies: lam, Q, D and the four face records
+    // two groups of 16-byte asynchronous copies: lam, Q and D, then the four face records
+    // (first needed by the projection, so that their gather overlaps the nodal phases)
     {
       const int4 ef4 = reinterpret_cast<const int4*>(a.elem_face)[e];
       for (int w = threadIdx.x; w < A::QS / 4; w += blockDim.x) {
@@ -593,35 +734,53 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
       }
       for (int w = threadIdx.x; w < A::DS / 4; w += blockDim.x)
         tc::cp_async16(smem + S::oD + 4 * w, a.d + e * A::DS + 4 * w);
+      // lam with the mode index fastest (zero beyond L), for 16-byte loads in the X phase:
+      // 4-byte asynchronous copies do the transpose
+      for (int w = threadIdx.x; w < 10 * A::LP; w += blockDim.x) {
+        const int p = w / A::LP, k = w - p * A::LP;
+        if (k < L) tc::cp_async4(smem + S::oLamT + w, a.lam_in + e * A::QS + k * 10 + p);
+        else smem[S::oLamT + w] = 0.f;
+      }
+      tc::cp_async_commit();
       for (int w = threadIdx.x; w < A::RS; w += blockDim.x) {
         const int fl = w / (A::RS / 4), c = 4 * (w - fl * (A::RS / 4));
         const int ef = fl == 0 ? ef4.x : (fl == 1 ? ef4.y : (fl == 2 ? ef4.z : ef4.w));
         tc::cp_async16(smem + S::oR + fl * A::RS + c, a.rec + static_cast<int64_t>(ef) * A::RS + c);
       }
     }
-    for (int w = threadIdx.x; w < A::LDS; w += blockDim.x) sLD[w] = 0.f;
-    tc::cp_async_wait_all();
+    tc::cp_async_commit();
+    // (sLD needs no zeroing: the projection assigns every entry that is read later)
+    tc::cp_async_wait<1>();                  // lam, Q, D have landed; the records may still be in flight
     const MatF m = a.mat[e];
     if (threadIdx.x < 9) sGeo[threadIdx.x] = a.geom[e].tinv[threadIdx.x];
-    if (threadIdx.x < 6) sRed[threadIdx.x] = 0.0;
+    if (threadIdx.x < 8) sRed[threadIdx.x] = 0.0;
     __syncthreads();
-    node_values<N, NQ>(tb + T.VvT, A::NQP, smem + S::oQ, smem + S::oD, sC, smem + S::oU, smem + S::oU0);
+    // the nodal values and X (independent of each other) in one phase
+    node_values<N, NQ, A::NQP>(tb + T.VvT, smem + S::oQ, smem + S::oD, sC, smem + S::oU);
     // per volume node q: X[q][d][p] = sum_k w_q dphi_k/dx_d(x_q) lam[k][p], X[q][27] = sum_k w_q phi_k lam[k][9];
     // one item per node and pair of fields (8, 9 pairs the last wave field with alpha)
     for (int w = threadIdx.x; w < NQ * 5; w += blockDim.x) {
       const int q = w / 5, pp = w - q * 5, p0 = 2 * pp;
       float g0[3] = {0.f, 0.f, 0.f}, g1[3] = {0.f, 0.f, 0.f};
-      const float* gw = tb + T.Gw + q * A::LP;
-      const float* vw = tb + T.Vw + q * A::LP;
-#pragma unroll 4
-      for (int k = 0; k < L; ++k) {
-        const float2 lk = *reinterpret_cast<const float2*>(smem + S::oLam + k * 10 + p0);
-        const float ga = __ldg(gw + k), gb = __ldg(gw + NQ * A::LP + k), gc = __ldg(gw + 2 * NQ * A::LP + k);
-        g0[0] = fmaf(ga, lk.x, g0[0]); g0[1] = fmaf(gb, lk.x, g0[1]); g0[2] = fmaf(gc, lk.x, g0[2]);
+      const float4* gA = reinterpret_cast<const float4*>(tb + T.Gw + q * A::LP);
+      const float4* gB = reinterpret_cast<const float4*>(tb + T.Gw + (NQ + q) * A::LP);
+      const float4* gC = reinterpret_cast<const float4*>(tb + T.Gw + (2 * NQ + q) * A::LP);
+      const float4* vW = reinterpret_cast<const float4*>(tb + T.Vw + q * A::LP);
+      const float4* lx = reinterpret_cast<const float4*>(smem + S::oLamT + p0 * A::LP);
+      const float4* ly = reinterpret_cast<const float4*>(smem + S::oLamT + (p0 + 1) * A::LP);
+#pragma unroll
+      for (int kq = 0; kq < A::LP / 4; ++kq) {
+        const float4 x = lx[kq], y = ly[kq];
+        const float4 ga = __ldg(gA + kq), gb = __ldg(gB + kq), gc = __ldg(gC + kq);
+        g0[0] = dot4(ga, x, g0[0]);
+        g0[1] = dot4(gb, x, g0[1]);
+        g0[2] = dot4(gc, x, g0[2]);
         if (pp < 4) {
-          g1[0] = fmaf(ga, lk.y, g1[0]); g1[1] = fmaf(gb, lk.y, g1[1]); g1[2] = fmaf(gc, lk.y, g1[2]);
+          g1[0] = dot4(ga, y, g1[0]);
+          g1[1] = dot4(gb, y, g1[1]);
+          g1[2] = dot4(gc, y, g1[2]);
         } else {
-          g1[0] = fmaf(__ldg(vw + k), lk.y, g1[0]);
+          g1[0] = dot4(__ldg(vW + kq), y, g1[0]);
         }
       }
       float* xq = smem + S::oX + q * 28;
@@ -660,43 +819,75 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
       for (int p = 0; p < 10; ++p) lu[p] = 0.f;
       px += flux_vjp(u, m, lF, lu);
       rate_vjp(u, m, lF[27], lu, &px, &pc);
+      // divided by the volume weight of the node: the projection runs over w_q phi_l(x_q)
+      const float iw = sIW[q];
       float* o = smem + S::oLu + w * 10;
 #pragma unroll
-      for (int p = 0; p < 10; p += 2) *reinterpret_cast<float2*>(o + p) = make_float2(lu[p], lu[p + 1]);
+      for (int p = 0; p < 10; p += 2) *reinterpret_cast<float2*>(o + p) = make_float2(lu[p] * iw, lu[p + 1] * iw);
     }
+    tc::cp_async_wait<0>();                  // the face records
     __syncthreads();
-    // lam of D^o_lp = sum_z c[z][o] sum_q phi_l(x_q) Lu[z][q][p], plus the four face records;
-    // one item per mode and pair of fields
-    for (int w = threadIdx.x; w < L * 5; w += blockDim.x) {
-      const int l = w / 5, p0 = 2 * (w - l * 5);
-      const float* V = tb + T.VvT + l * A::NQP;
+    // lam of D^o_lp = sum_z c[z][o] sum_q w_q phi_l(x_q) Lu[z][q][p] (Lu divided by w_q above),
+    // plus the four face records; one item per four modes and pair of fields (16-byte loads
+    // of the node-major weighted table)
+    constexpr int LQ = A::LP / 4, PITEMS = LQ * 5 * 4;   // (4 modes, pair of fields, quarter of the nodes)
+    for (int base = 0; base < PITEMS; base += blockDim.x) {   // warp-uniform trip count (shuffles below)
+      const int w = base + threadIdx.x;
+      const bool live = w < PITEMS;
+      const int item = live ? w >> 2 : 0, qc = w & 3;
+      const int lq = item / 5, p0 = 2 * (item - lq * 5);
+      const float4* V = reinterpret_cast<const float4*>(tb + T.Vw) + lq;
       const float* Lu = smem + S::oLu + p0;
-      float a0[NT], a1[NT];
+      float acc[4][2][NT];
 #pragma unroll
-      for (int z = 0; z < NT; ++z) a0[z] = a1[z] = 0.f;
-#pragma unroll 4
-      for (int q = 0; q < NQ; ++q) {
-        const float v = __ldg(V + q);
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int z = 0; z < NT; ++z) acc[j][0][z] = acc[j][1][z] = 0.f;
+#pragma unroll 2
+      for (int q = live ? qc : NQ; q < NQ; q += 4) {
+        const float4 v4 = __ldg(V + q * LQ);
+        const float v[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
         for (int z = 0; z < NT; ++z) {
           const float2 lz = *reinterpret_cast<const float2*>(Lu + (z * NQ + q) * 10);
-          a0[z] = fmaf(v, lz.x, a0[z]);
-          a1[z] = fmaf(v, lz.y, a1[z]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[j][0][z] = fmaf(v[j], lz.x, acc[j][0][z]);
+            acc[j][1][z] = fmaf(v[j], lz.y, acc[j][1][z]);
+          }
         }
       }
+      // the four node quarters of an item sit on consecutive lanes
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int p = p0 + h;
+      for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int o = 0; o < NT; ++o) {
-          if (l >= order_modes<N>(o, p)) continue;
-          float s = 0.f;
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int z = 0; z < NT; ++z) s = fmaf(sC[z * NT + o], h ? a1[z] : a0[z], s);
-          const int idx = ld_index<N>(o, l, p);
+          for (int z = 0; z < NT; ++z) {
+            float v = acc[j][h][z];
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            acc[j][h][z] = v;
+          }
+      if (!live) continue;
 #pragma unroll
-          for (int fl = 0; fl < 4; ++fl) s += smem[S::oR + fl * A::RS + idx];
-          sLD[idx] = s;
+      for (int j = 0; j < 4; ++j) {
+        const int l = 4 * lq + j;
+        if (j != qc || l >= L) continue;       // every lane holds the sums: lane qc takes mode 4 lq + qc
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int p = p0 + h;
+#pragma unroll
+          for (int o = 0; o < NT; ++o) {
+            if (l >= order_modes<N>(o, p)) continue;
+            float s = 0.f;
+#pragma unroll
+            for (int z = 0; z < NT; ++z) s = fmaf(sC[z * NT + o], acc[j][h][z], s);
+            const int idx = ld_index<N>(o, l, p);
+#pragma unroll
+            for (int fl = 0; fl < 4; ++fl) s += smem[S::oR + fl * A::RS + idx];
+            sLD[idx] = s;
+          }
         }
       }
     }
@@ -749,30 +940,44 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
       lam_eff = m.lam0 - ub[9] * m.gamma_r * v.xi * (1.f / 3.f);
       mu_eff = m.mu0 + ub[9] * m.xi0 * m.gamma_r - 0.5f * ub[9] * m.gamma_r * v.xi;
     }
-    if (threadIdx.x == 0) {
-      sGeo[9] = lam_eff * m.rho_inv;
-      sGeo[10] = mu_eff * m.rho_inv;
-    }
-    __syncthreads();
-    // the cp part: cp = sqrt((lambda + 2 mu) / rho)
-    const double lam_cp = sRed[2];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const float cp = a.cp[e];
-      const float dc = (lam_eff + 2.f * mu_eff > 0.f && cp > 0.f) ? static_cast<float>(lam_cp) * 0.5f * m.rho_inv / cp : 0.f;
-      // in units of lam/rho: d/d(lam/rho) = rho d/dlam
-      sRed[2] = (static_cast<double>(dc) + sRed[4]) * m.rho;
-      sRed[3] = (static_cast<double>(2.f * dc) + sRed[5]) * m.rho;
-    }
-    __syncthreads();
+    __syncthreads();                         // the projection's lam of D is complete
     // Cauchy-Kovalevskaya recursion transposed, order N down to 1 (the forward products in
     // GX; the lambda/rho and mu/rho parts summed per thread over all orders, reduced once)
-    const float lr = sGeo[9], mr = sGeo[10];
+    const float lr = lam_eff * m.rho_inv, mr = mu_eff * m.rho_inv;
     float plr = 0.f, pmr = 0.f;
+    // the damage-rate source of D^1 from the state at t_n runs alongside the first order: it
+    // reads only lam of D^1 of alpha (which the recursion does not change) and the strains at
+    // t_n, and leaves its result in sDS, added to lam of the strains at the end
+    //   lam_r(q) = sum_k w_q phi_k(x_q) lam D^1_k9;  lam Q_lp += sum_q phi_l(x_q) (d r / d eps_p)(q) lam_r(q)
+    float* sLu0 = smem + S::oLu;               // [6][U0S] (reuses the nodal lam), node fastest
+    float* sDS = smem + S::oLu + 6 * A::U0S;   // [L][6]
+    float pxr = 0.f, pcr = 0.f;
 #pragma unroll
     for (int i = N; i >= 1; --i) {
       const int Lout = n_modes(N - i), Lin = n_modes(N - i + 1);
       const float* lDi = sLD + A::QS + d_offset(N, i);       // [Lout][9]
+      if (i == N) {
+        for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
+          // the strains at t_n at node q
+          float u[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+          for (int l = 0; l < L; ++l) {
+            const float v = __ldg(tb + T.VvT + l * A::NQP + q);
+#pragma unroll
+            for (int p = 0; p < 6; ++p) u[p] = fmaf(v, smem[S::oQ + l * 10 + p], u[p]);
+          }
+          float lr4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int l = 0; l < L; ++l) lr4[l & 3] = fmaf(__ldg(tb + T.Vw + q * A::LP + l), sLD[A::QS + A::AOFF + l], lr4[l & 3]);
+          const float lrq = (lr4[0] + lr4[1]) + (lr4[2] + lr4[3]);
+          float lu[10];
+#pragma unroll
+          for (int p = 0; p < 10; ++p) lu[p] = 0.f;
+          rate_vjp(u, m, lrq, lu, &pxr, &pcr);
+#pragma unroll
+          for (int p = 0; p < 6; ++p) sLu0[p * A::U0S + q] = lu[p];
+        }
+      }
       float* lDprev = i == 1 ? sLD : sLD + A::QS + d_offset(N, i - 1);
       const int lsp = i == 1 ? 10 : 9;
       const float* gxi = smem + S::oX + 27 * A::gx_row(i);
@@ -801,7 +1006,7 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
         }
 #pragma unroll
         for (int ee = 0; ee < 3; ++ee)
-          smem[S::oH + (ee * L + k) * 9 + q] = sGeo[ee * 3 + 0] * ps[0] + sGeo[ee * 3 + 1] * ps[1] + sGeo[ee * 3 + 2] * ps[2];
+          smem[S::oH + (ee * 9 + q) * A::LP + k] = sGeo[ee * 3 + 0] * ps[0] + sGeo[ee * 3 + 1] * ps[1] + sGeo[ee * 3 + 2] * ps[2];
         // the star matrices' dependence on lambda/rho and mu/rho:
         // Gx[d] = sum_e Theta^{-1}_ed sum_l Kt^e_kl D^{i-1}_lq
         const float gx[3] = {gxi[w * 3], gxi[w * 3 + 1], gxi[w * 3 + 2]};
@@ -823,48 +1028,43 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
         const int l = w / 9, q = w - l * 9;
         float s3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < Lout; ++k)
+        for (int ee = 0; ee < 3; ++ee) {
+          const float* kt = tb + T.KtA + (ee * L + l) * A::LP;
+          const float* hq = smem + S::oH + (ee * 9 + q) * A::LP;
 #pragma unroll
-          for (int ee = 0; ee < 3; ++ee)
-            s3[ee] = fmaf(__ldg(tb + T.KtA + (ee * L + l) * A::LP + k), smem[S::oH + (ee * L + k) * 9 + q], s3[ee]);
+          for (int kq = 0; kq < Lout / 4; ++kq)
+            s3[ee] = dot4(__ldg(reinterpret_cast<const float4*>(kt) + kq), reinterpret_cast<const float4*>(hq)[kq], s3[ee]);
+#pragma unroll
+          for (int k = Lout / 4 * 4; k < Lout; ++k) s3[ee] = fmaf(__ldg(kt + k), hq[k], s3[ee]);
+        }
         lDprev[l * lsp + q] -= s3[0] + s3[1] + s3[2];
       }
-      __syncthreads();
-    }
-    block_add(&sRed[2], plr);   // read after the barriers of the damage-source phase below
-    block_add(&sRed[3], pmr);
-    // damage-rate source of D^1 from the state at t_n: lam_r(q) = sum_k w_q phi_k(x_q) lam D^1_k9
-    {
-      float* sLu0 = smem + S::oLu;                           // [NQ][6] (reuses the nodal lam)
-      float pxr = 0.f, pcr = 0.f;
-      for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
-        float u[10];
+      if (i == N) {
+        for (int w = threadIdx.x; w < L * 6; w += blockDim.x) {
+          const int l = w / 6, p = w - l * 6;
+          float s4[4] = {0.f, 0.f, 0.f, 0.f};
+          const float* vl = tb + T.VvT + l * A::NQP;
+          const float* up = sLu0 + p * A::U0S;
+          if constexpr (A::NQP % 4 == 0) {
+#pragma unroll 4
+            for (int qq = 0; qq < NQ / 4; ++qq)
+              s4[qq & 3] = dot4(__ldg(reinterpret_cast<const float4*>(vl) + qq), reinterpret_cast<const float4*>(up)[qq], s4[qq & 3]);
 #pragma unroll
-        for (int p = 0; p < 6; ++p) u[p] = smem[S::oU0 + q * 6 + p];
-        u[6] = u[7] = u[8] = u[9] = 0.f;
-        float lr4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int l = 0; l < L; ++l) lr4[l & 3] = fmaf(__ldg(tb + T.Vw + q * A::LP + l), sLD[A::QS + A::AOFF + l], lr4[l & 3]);
-        const float lrq = (lr4[0] + lr4[1]) + (lr4[2] + lr4[3]);
-        float lu[10];
-#pragma unroll
-        for (int p = 0; p < 10; ++p) lu[p] = 0.f;
-        rate_vjp(u, m, lrq, lu, &pxr, &pcr);
-#pragma unroll
-        for (int p = 0; p < 6; ++p) sLu0[q * 6 + p] = lu[p];
-      }
-      block_add(&sRed[0], pxr);
-      block_add(&sRed[1], pcr);
-      __syncthreads();
-      for (int w = threadIdx.x; w < L * 6; w += blockDim.x) {
-        const int l = w / 6, p = w - l * 6;
-        float s4[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int q = NQ / 4 * 4; q < NQ; ++q) s4[0] = fmaf(__ldg(vl + q), up[q], s4[0]);
+          } else {
 #pragma unroll 8
-        for (int q = 0; q < NQ; ++q) s4[q & 3] = fmaf(__ldg(tb + T.VvT + l * A::NQP + q), sLu0[q * 6 + p], s4[q & 3]);
-        sLD[l * 10 + p] += (s4[0] + s4[1]) + (s4[2] + s4[3]);
+            for (int q = 0; q < NQ; ++q) s4[q & 3] = fmaf(__ldg(vl + q), up[q], s4[q & 3]);
+          }
+          sDS[w] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+        }
       }
       __syncthreads();
     }
+    block_add(&sRed[6], plr);
+    block_add(&sRed[7], pmr);
+    block_add(&sRed[0], pxr);
+    block_add(&sRed[1], pcr);
+    __syncthreads();
     // the cell mean: lambda_eff and mu_eff (and through them cp) at ubar = sqrt(6) Q_0
     if (threadIdx.x == 0) {
       const float r6 = 2.449489742783178f;
@@ -872,8 +1072,14 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
 #pragma unroll
       for (int p = 0; p < 10; ++p) ub[p] = smem[S::oQ + p] * r6;
       const Inv v = invariants(ub);
-      const float al = static_cast<float>(sRed[2]) * m.rho_inv;   // d/dlambda_eff
-      const float am = static_cast<float>(sRed[3]) * m.rho_inv;   // d/dmu_eff
+      // the cp part (cp = sqrt((lambda + 2 mu) / rho)), the boundary fluxes and the CK
+      // recursion, in units of lam/rho (d/d(lam/rho) = rho d/dlam)
+      const float cp = a.cp[e];
+      const float dc = (lam_eff + 2.f * mu_eff > 0.f && cp > 0.f) ? static_cast<float>(sRed[2]) * 0.5f * m.rho_inv / cp : 0.f;
+      const double a_lr = (static_cast<double>(dc) + sRed[4]) * m.rho + sRed[6];
+      const double a_mr = (static_cast<double>(2.f * dc) + sRed[5]) * m.rho + sRed[7];
+      const float al = static_cast<float>(a_lr) * m.rho_inv;   // d/dlambda_eff
+      const float am = static_cast<float>(a_mr) * m.rho_inv;   // d/dmu_eff
       const float wv = al * (1.f / 3.f) + 0.5f * am;
       const float ag = ub[9] * m.gamma_r;
 #pragma unroll
@@ -882,8 +1088,10 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
       sRed[0] += static_cast<double>(am * ag);
     }
     __syncthreads();
-    for (int w = threadIdx.x; w < A::QS; w += blockDim.x)
-      a.lam_out[e * A::QS + w] = w < L * 10 ? smem[S::oLam + w] + sLD[w] : 0.f;
+    for (int w = threadIdx.x; w < A::QS; w += blockDim.x) {
+      const int l = w / 10, p = w - 10 * l;
+      a.lam_out[e * A::QS + w] = w < L * 10 ? smem[S::oLam + w] + sLD[w] + (p < 6 ? sDS[l * 6 + p] : 0.f) : 0.f;
+    }
     if (threadIdx.x == 0) {
       a.g_xi0[e] += sRed[0];
       a.g_cd[e] += sRed[1];
