@@ -699,10 +699,6 @@ struct ElemSmem {
   static constexpr int oH = oX + round4(27 * A::GXI);
   static_assert(round4(27 * A::GXI) + 27 * A::LP <= A::NQ * 28, "CK products and H inside the X region");
   static constexpr int oR = round4(oLD + A::LDS);         // [4][RS] the element's four face records
-  // [10][LP] lam^{k+1}, mode fastest, in the lam of D^0..D^N region: read up to the X phase,
-  // before the projection first writes that region
-  static constexpr int oLamT = oLD;
-  static_assert(10 * A::LP <= A::LDS, "lam^T inside the lam-of-D region");
   static constexpr int total = oR + 4 * A::RS;
 };
 
@@ -734,13 +730,6 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
       }
       for (int w = threadIdx.x; w < A::DS / 4; w += blockDim.x)
         tc::cp_async16(smem + S::oD + 4 * w, a.d + e * A::DS + 4 * w);
-      // lam with the mode index fastest (zero beyond L), for 16-byte loads in the X phase:
-      // 4-byte asynchronous copies do the transpose
-      for (int w = threadIdx.x; w < 10 * A::LP; w += blockDim.x) {
-        const int p = w / A::LP, k = w - p * A::LP;
-        if (k < L) tc::cp_async4(smem + S::oLamT + w, a.lam_in + e * A::QS + k * 10 + p);
-        else smem[S::oLamT + w] = 0.f;
-      }
       tc::cp_async_commit();
       for (int w = threadIdx.x; w < A::RS; w += blockDim.x) {
         const int fl = w / (A::RS / 4), c = 4 * (w - fl * (A::RS / 4));
@@ -766,11 +755,18 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
       const float4* gB = reinterpret_cast<const float4*>(tb + T.Gw + (NQ + q) * A::LP);
       const float4* gC = reinterpret_cast<const float4*>(tb + T.Gw + (2 * NQ + q) * A::LP);
       const float4* vW = reinterpret_cast<const float4*>(tb + T.Vw + q * A::LP);
-      const float4* lx = reinterpret_cast<const float4*>(smem + S::oLamT + p0 * A::LP);
-      const float4* ly = reinterpret_cast<const float4*>(smem + S::oLamT + (p0 + 1) * A::LP);
 #pragma unroll
       for (int kq = 0; kq < A::LP / 4; ++kq) {
-        const float4 x = lx[kq], y = ly[kq];
+        // lam at modes 4 kq .. 4 kq + 3 of fields p0, p0 + 1 (zero beyond L, where the tables are zero too)
+        float xv[4], yv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = 4 * kq + j;
+          const float2 lk = k < L ? *reinterpret_cast<const float2*>(smem + S::oLam + k * 10 + p0) : make_float2(0.f, 0.f);
+          xv[j] = lk.x;
+          yv[j] = lk.y;
+        }
+        const float4 x = make_float4(xv[0], xv[1], xv[2], xv[3]), y = make_float4(yv[0], yv[1], yv[2], yv[3]);
         const float4 ga = __ldg(gA + kq), gb = __ldg(gB + kq), gc = __ldg(gC + kq);
         g0[0] = dot4(ga, x, g0[0]);
         g0[1] = dot4(gb, x, g0[1]);
