@@ -737,6 +737,378 @@ __global__ void __launch_bounds__(512, 1) k_picard(StepArgs a) {
 }
 
 // ===========================================================================
+// Picard predictor with its two contractions on the tensor cores (degrees 2..4).
+// Per time node t_z of an iteration: the node values of the predictor's
+// polynomial, U[q][(e, c)] = sum_l phi_l(x_q) q_l(t_z) (A = phi_l(x_q) in tensor
+// memory, lane = node; B = the modal values at t_z, columns (element, field)),
+// and the projection of the nodal reference fluxes Theta^{-1}_{e'd} F^d and the
+// damage rate, Fh[l][(e, e' x field | rate)] = sum_q w_q phi_l(x_q) F[q][.]
+// (A = w_q phi_l(x_q) in tensor memory, lane = mode; B = the nodal terms), both
+// in 3xTF32 as in the corrector.  The pointwise flux reads the node values
+// straight from tensor memory; the divergence through the Kt tables and the time
+// fit stay SIMT.  Four elements per tile (one warp group each in the flux phase),
+// 512 threads, one CTA per SM; the last warp issues the MMAs.
+// ===========================================================================
+template <int N>
+struct PicTcCfg : Dim<N> {
+  using D = Dim<N>;
+  static constexpr int TE = 4;
+  static constexpr int THREADS = 512;
+  static constexpr int KP = tc_kp(N), KQ = tc_kq(N);
+  static constexpr int NU = (TE * 12 + 15) / 16 * 16;      // node-value MMA N: (element, 12 channels), padded
+  static constexpr int CF = TE * 28;                       // nodal-term columns (element, e' x 9 fields, rate)
+  static constexpr int NPF = (CF + 15) / 16 * 16;          // projection MMA N
+  // the projection's B operand: core matrices 36 floats apart along K, so that the 32
+  // nodes one warp writes land in 32 banks
+  static constexpr int PLBO = 36, PGS = KQ / 4 * PLBO, BF = NPF / 8 * PGS;
+  static constexpr int COL_U = 0;                          // node values: lane q, NU columns
+  static constexpr int COL_F = NU;                         // projections: lane l, NPF columns
+  static constexpr int COL_AH = COL_F + NPF, COL_AL = COL_AH + KQ;   // projection A (w phi), lane = mode
+  static constexpr int COL_PH = COL_AL + KQ, COL_PL = COL_PH + KP;   // node-value A (phi), lane = node
+  static constexpr int TMEM_NEED = COL_PL + KP;
+  static constexpr int TMEM_COLS = TMEM_NEED <= 128 ? 128 : (TMEM_NEED <= 256 ? 256 : 512);
+  static constexpr int QSP = D::QS % 32 == 0 ? D::QS + 4 : D::QS;
+  static constexpr int oKtA = 0;                                       // [3][L][LP]
+  static constexpr int oQ = round4(oKtA + 3 * D::L * D::LP);           // [TE][QSP] state at t_n
+  static constexpr int oD = oQ + TE * QSP;                             // [TE][DS] coefficients being refined
+  static constexpr int oDn = oD + TE * D::DS;                          // [TE][DS] new coefficients
+  static constexpr int oGeo = round4(oDn + TE * D::DS);                // [TE][40] GeomF, MatF
+  static constexpr int oBuH = round4(oGeo + TE * 40);                  // [NU x KP] canonical K-major
+  static constexpr int oBuL = oBuH + NU * KP;
+  static constexpr int oBfH = oBuL + NU * KP;                          // [NPF x KQ] padded K-major
+  static constexpr int oBfL = oBfH + BF;
+  static constexpr int oFh = oBfL + BF;                                // [LP][CF] projections
+  static constexpr int oC = oFh + D::LP * CF;                          // [CF] nodal terms at node 0
+  static constexpr int oTc = round4(oC + CF);                          // [NT][N+1] t_z^o / o!, [NT][NT] fit
+  static constexpr int SMEM = round4(oTc + D::NT * (N + 1) + D::NT * D::NT);
+  static constexpr int ISSUER = THREADS - 32;
+  static_assert(D::NQ <= 128 && KQ <= 128 && KP <= 40 && TMEM_NEED <= 512, "tensor-core shapes");
+  static_assert(TE * 12 <= NU && NU % 16 == 0 && NPF % 16 == 0 && NPF <= 256 && CF % 16 == 0, "MMA N and read-out");
+  static_assert(4 * TE <= THREADS / 32, "one warp group per element in the flux phase");
+  static_assert(SMEM * 4 <= 227 * 1024, "Picard tensor-core shared memory");
+  __host__ __device__ static constexpr int prj_canon(int n, int q) {
+    return (n >> 3) * PGS + (q >> 2) * PLBO + (n & 7) * 4 + (q & 3);
+  }
+};
+
+template <int N, int LAW>
+__global__ void __launch_bounds__(PicTcCfg<N>::THREADS, 1) k_picard_tc(StepArgs a) {
+  using C = PicTcCfg<N>;
+  constexpr int L = C::L, NQ = C::NQ, LP = C::LP, NT = C::NT, QS = C::QS, DS = C::DS, AOFF = C::AOFF;
+  constexpr int TE = C::TE, KP = C::KP, KQ = C::KQ, NU = C::NU, CF = C::CF, NPF = C::NPF, QSP = C::QSP;
+  constexpr int L1 = n_modes(N - 1);
+  constexpr TableLayout T = table_layout(N);
+  constexpr int kWaitLimit = 1 << 24;
+  const int wait_limit = a.wait_limit_set ? a.wait_limit : kWaitLimit;
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  float* sKtA = sm + C::oKtA;
+  float* sQ = sm + C::oQ;
+  float* sD = sm + C::oD;
+  float* sDn = sm + C::oDn;
+  float* sGM = sm + C::oGeo;
+  float* sBuH = sm + C::oBuH;
+  float* sBuL = sm + C::oBuL;
+  float* sBfH = sm + C::oBfH;
+  float* sBfL = sm + C::oBfL;
+  float* sFh = sm + C::oFh;
+  float* sC = sm + C::oC;
+  float* sCz = sm + C::oTc;                                // [NT][N+1]
+  float* sFit = sCz + NT * (N + 1);                        // [NT][NT], sFit[j][z]
+  const float* tb = a.tables;
+  const float dt = a.dt;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  copy_to_smem(sKtA, tb + T.KtA, 3 * L * LP);
+  for (int w = tid; w < 2 * C::BF; w += blockDim.x) sBfH[w] = 0.f;   // rows beyond CF stay zero
+  if (tid < NT) {
+    const int z = tid;
+    const float tz = __ldg(tb + T.tz + z) * dt;
+    float c = 1.f;
+    for (int o = 0; o <= N; ++o) {
+      sCz[z * (N + 1) + o] = c;
+      c *= tz / static_cast<float>(o + 1);
+    }
+    float sc = 1.f;
+    for (int j = 0; j < NT; ++j) {
+      sFit[j * NT + z] = __ldg(tb + T.Tfit + j * NT + z) * sc;
+      sc /= dt;
+    }
+  }
+  if (warp == 0) tc::alloc(&tmem_base, C::TMEM_COLS);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base;
+  // constant A operands into tensor memory: w_q phi_l(x_q) (lane l, columns q) on warps 0-3,
+  // phi_l(x_q) (lane q, columns l) on warps 4-7, TF32 parts and remainders
+  if (warp < 4) {
+    const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      const float* src = tb + (part ? T.PrjL : T.PrjH) + (32 * warp + lane) * KQ;
+#pragma unroll 1
+      for (int c0 = 0; c0 < KQ; c0 += 32) {
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 x = __ldg(reinterpret_cast<const float4*>(src + c0) + j);
+          v[4 * j] = x.x; v[4 * j + 1] = x.y; v[4 * j + 2] = x.z; v[4 * j + 3] = x.w;
+        }
+        tc::st_x32(tmem + lane_base + (part ? C::COL_AL : C::COL_AH) + c0, v);
+      }
+    }
+  } else if (warp < 8) {
+    const int q = 32 * (warp - 4) + lane;
+    const uint32_t lane_base = static_cast<uint32_t>(32 * (warp - 4)) << 16;
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      const float* src = tb + (part ? T.PhiL : T.PhiH);
+      float v[KP];
+#pragma unroll
+      for (int j = 0; j < KP / 4; ++j) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(src + tc_canon(q, 4 * j, KP)));
+        v[4 * j] = x.x; v[4 * j + 1] = x.y; v[4 * j + 2] = x.z; v[4 * j + 3] = x.w;
+      }
+      tc::st_cols<KP>(tmem + lane_base + (part ? C::COL_PL : C::COL_PH), v);
+    }
+  }
+  if (warp < 8) tc::wait_st();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  uint32_t phase = 0;
+  bool failed = false;
+
+  const int64_t ntiles = (a.E + TE - 1) / TE;
+  for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    const int64_t e0 = tile * TE;
+    const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
+    __syncthreads();
+    for (int w = tid; w < TE * QS / 4; w += blockDim.x) {
+      const int e = w / (QS / 4), c = w - e * (QS / 4);
+      if (e < ne) tc::cp_async16(sQ + e * QSP + 4 * c, a.q_in + (e0 + e) * QS + 4 * c);
+      else *reinterpret_cast<float4*>(sQ + e * QSP + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int w = tid; w < TE * DS / 4; w += blockDim.x) {
+      const int e = w / (DS / 4), c = w - e * (DS / 4);
+      if (e < ne) tc::cp_async16(sD + e * DS + 4 * c, a.d + (e0 + e) * DS + 4 * c);
+      else *reinterpret_cast<float4*>(sD + e * DS + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int w = tid; w < ne * 10; w += blockDim.x) {
+      const int e = w / 10, k = w - 10 * e;
+      if (k < 8) tc::cp_async16(sGM + e * 40 + 4 * k, reinterpret_cast<const float*>(a.geom + e0 + e) + 4 * k);
+      else tc::cp_async16(sGM + e * 40 + 32 + 4 * (k - 8), reinterpret_cast<const float*>(a.mat + e0 + e) + 4 * (k - 8));
+    }
+    tc::cp_async_wait_all();
+    __syncthreads();
+
+#pragma unroll 1
+    for (int iter = 0; iter < a.picard_iters && !failed; ++iter) {
+      for (int w = tid; w < TE * DS; w += blockDim.x) sDn[w] = 0.f;
+#pragma unroll 1
+      for (int z = 0; z < NT; ++z) {
+        // modal values of q(t_z) as the node-value MMA's B operand (row (element, field),
+        // column mode); alpha to first order.  Lane (l mod 4, row mod 8): one core matrix per warp
+        for (int w = tid; w < NU * KP; w += blockDim.x) {
+          const int l4 = w & 3, n7 = (w >> 2) & 7, r = w >> 5;
+          const int lq = r % (KP / 4), ng = r / (KP / 4);
+          const int l = 4 * lq + l4, n = 8 * ng + n7, e = n / 12, c = n - 12 * e;
+          float x = 0.f;
+          if (e < TE && c < 10 && l < L) {
+            const float* de = sD + e * DS;
+            x = sQ[e * QSP + l * 10 + c];
+            if (c < 9) {
+#pragma unroll
+              for (int o = 1; o <= N; ++o)
+                if (l < n_modes(N - o)) x = fmaf(sCz[z * (N + 1) + o], de[d_offset(N, o) + l * 9 + c], x);
+            } else {
+              x = fmaf(sCz[z * (N + 1) + 1], de[AOFF + l], x);
+            }
+          }
+          const int idx = tc_canon(n, l, KP);
+          const float h = tc::tf32_hi(x);
+          sBuH[idx] = h;
+          sBuL[idx] = tc::tf32_hi(x - h);
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before();
+        __syncthreads();
+        if (tid == C::ISSUER) {
+          tc::fence_after();
+          constexpr uint32_t idesc = tc::idesc_tf32(128, NU);
+          const uint32_t bH = tc::smem_u32(sBuH), bL = tc::smem_u32(sBuL);
+#pragma unroll
+          for (int ks = 0; ks < KP / 8; ++ks) {
+            const uint32_t off = ks * 256;   // 8 K-elements = 2 core matrices
+            const uint32_t aH = tmem + C::COL_PH + 8 * ks, aL = tmem + C::COL_PL + 8 * ks;
+            tc::mma_tf32_ta(tmem + C::COL_U, aH, tc::desc_kmajor(bH + off, KP), idesc, ks > 0 ? 1u : 0u);
+            tc::mma_tf32_ta(tmem + C::COL_U, aH, tc::desc_kmajor(bL + off, KP), idesc, 1u);
+            tc::mma_tf32_ta(tmem + C::COL_U, aL, tc::desc_kmajor(bH + off, KP), idesc, 1u);
+          }
+          tc::commit(&mbar);
+        }
+        {
+          const bool ok = tc::wait_parity(&mbar, phase, wait_limit);
+          phase ^= 1u;
+          if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+          }
+        }
+        tc::fence_after();
+        // reference fluxes Theta^{-1}_{e'd} F^d and the damage rate at every node: warp group e
+        // (warps 4e..4e+3) takes element e, thread q its volume node; the terms become the
+        // projection's B operand less their value at node 0 (which returns through the row
+        // sums of w_q phi_l(x_q))
+        if (warp < 4 * TE) {
+          const int e = warp >> 2, q = 32 * (warp & 3) + lane;
+          const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
+          float v[16];
+          tc::ld_cols<16>(tmem + lane_base + C::COL_U + e * 12, v);
+          tc::wait_ld();
+          float out[28];
+#pragma unroll
+          for (int p = 0; p < 28; ++p) out[p] = 0.f;
+          if (q < NQ && e < ne) {
+            const float* gm = sGM + e * 40;
+            const MatF m = *reinterpret_cast<const MatF*>(gm + 32);
+            float sig[6], rr;
+            law_point<LAW>(a.law, v, v[9], m, sig, &rr);
+            const float S[3][3] = {{sig[0], sig[3], sig[5]}, {sig[3], sig[1], sig[4]}, {sig[5], sig[4], sig[2]}};
+            const float vv[3] = {v[6], v[7], v[8]};
+#pragma unroll
+            for (int ep = 0; ep < 3; ++ep) {
+              const float th[3] = {gm[ep * 3 + 0], gm[ep * 3 + 1], gm[ep * 3 + 2]};   // Theta^{-1}[e'][d]
+              float* fe = out + ep * 9;
+              fe[0] = -vv[0] * th[0];
+              fe[1] = -vv[1] * th[1];
+              fe[2] = -vv[2] * th[2];
+              fe[3] = -0.5f * (vv[0] * th[1] + vv[1] * th[0]);
+              fe[4] = -0.5f * (vv[1] * th[2] + vv[2] * th[1]);
+              fe[5] = -0.5f * (vv[2] * th[0] + vv[0] * th[2]);
+#pragma unroll
+              for (int i = 0; i < 3; ++i) fe[6 + i] = -m.rho_inv * (S[i][0] * th[0] + S[i][1] * th[1] + S[i][2] * th[2]);
+            }
+            out[27] = rr;
+          }
+          if (q == 0) {
+#pragma unroll
+            for (int p = 0; p < 28; ++p) sC[e * 28 + p] = out[p];
+          }
+          tc::named_barrier(1 + e, 128);
+          if (q < KQ) {
+#pragma unroll
+            for (int p = 0; p < 28; ++p) {
+              const float x = q < NQ ? out[p] - sC[e * 28 + p] : 0.f;
+              const int idx = C::prj_canon(e * 28 + p, q);
+              const float h = tc::tf32_hi(x);
+              sBfH[idx] = h;
+              sBfL[idx] = tc::tf32_hi(x - h);
+            }
+          }
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before();
+        __syncthreads();
+        if (tid == C::ISSUER) {
+          tc::fence_after();
+          constexpr uint32_t idesc = tc::idesc_tf32(128, NPF);
+          const uint32_t bH = tc::smem_u32(sBfH), bL = tc::smem_u32(sBfL);
+          constexpr uint32_t lbo = 4u * C::PLBO, sbo = 4u * C::PGS;
+#pragma unroll
+          for (int ks = 0; ks < KQ / 8; ++ks) {
+            const uint32_t off = ks * 2 * lbo;   // 8 K-elements = 2 core matrices
+            const uint32_t aH = tmem + C::COL_AH + 8 * ks, aL = tmem + C::COL_AL + 8 * ks;
+            tc::mma_tf32_ta(tmem + C::COL_F, aH, tc::desc_kmajor_strided(bH + off, lbo, sbo), idesc, ks > 0 ? 1u : 0u);
+            tc::mma_tf32_ta(tmem + C::COL_F, aH, tc::desc_kmajor_strided(bL + off, lbo, sbo), idesc, 1u);
+            tc::mma_tf32_ta(tmem + C::COL_F, aL, tc::desc_kmajor_strided(bH + off, lbo, sbo), idesc, 1u);
+          }
+          tc::commit(&mbar);
+        }
+        {
+          const bool ok = tc::wait_parity(&mbar, phase, wait_limit);
+          phase ^= 1u;
+          if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+          }
+        }
+        tc::fence_after();
+        // read-out: warps 0-3, lane = mode l; the node-0 values come back through the row sums
+        if (warp < 4) {
+          const int l = 32 * warp + lane;
+          const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
+          const float sl = l < L ? __ldg(tb + T.PrjS + l) : 0.f;
+#pragma unroll
+          for (int c0 = 0; c0 < CF; c0 += 32) {
+            float v[32];
+            if (CF - c0 >= 32) tc::ld_x32(tmem + lane_base + C::COL_F + c0, v);
+            else tc::ld_x16(tmem + lane_base + C::COL_F + c0, v);
+            tc::wait_ld();
+            if (l < L) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (c0 + j < CF) sFh[l * CF + c0 + j] = fmaf(sC[c0 + j], sl, v[j]);
+            }
+          }
+        }
+        tc::fence_before();
+        __syncthreads();
+        // R(t_z) = -sum_e' Kt^{e'} Fh_{e'} + Shat, folded into the Taylor fit of every order;
+        // items (mode, element, group of 3 fields)
+        for (int w = tid; w < L * TE * 3; w += blockDim.x) {
+          const int pg = w % 3, ke = w / 3;
+          const int k = ke / TE, e = ke - k * TE;
+          float* dn = sDn + e * DS;
+          if (k < L1) {
+            float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll 5
+            for (int l = 0; l < L; ++l) {
+              const float* fh = sFh + l * CF + e * 28 + 3 * pg;
+#pragma unroll
+              for (int ep = 0; ep < 3; ++ep) {
+                const float kt = sKtA[(ep * L + l) * LP + k];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) acc[j] = fmaf(kt, fh[ep * 9 + j], acc[j]);
+              }
+            }
+#pragma unroll
+            for (int o = 1; o <= N; ++o) {
+              if (k < n_modes(N - o)) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) dn[d_offset(N, o) + k * 9 + 3 * pg + j] -= sFit[(o - 1) * NT + z] * acc[j];
+              }
+            }
+          }
+          if (pg == 0) dn[AOFF + k] += sFit[z] * sFh[k * CF + e * 28 + 27];
+        }
+        __syncthreads();
+      }
+      if (failed) break;
+      for (int w = tid; w < TE * DS; w += blockDim.x) sD[w] = sDn[w];
+      __syncthreads();
+    }
+    if (failed) break;
+    bool bad = false;
+    for (int w = tid; w < ne * DS; w += blockDim.x) {
+      bad |= !isfinite(sD[w]);
+      a.d[e0 * DS + w] = sD[w];
+    }
+    if (bad) atomicOr(a.status, kStatusNonFinite);
+  }
+  if (failed) {
+    if (tid == 0) atomicOr(a.status, kStatusTimeout);
+    tc::wait_parity(&mbar, phase ^ 1u, kWaitLimit);   // let the MMAs in flight finish before freeing TMEM
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::dealloc(tmem, C::TMEM_COLS);
+}
+
+// ===========================================================================
 // Faces: Rusanov flux at the space-time nodes of each interior face, once per
 // face; boundary faces (side 1 absent, tag in the fourth entry) take the
 // absorbing or free-surface flux.  Persistent CTAs of 256 threads, two per SM.  Per tile of
@@ -1958,7 +2330,7 @@ cudaError_t launch_persistent(Kern kern, int64_t tiles, int grid_hint, const Ste
 
 // Kernel variants (bit 0: predictor with shared-memory tables on a persistent
 // grid; bit 2: SIMT corrector likewise; bit 3: SIMT corrector instead of the
-// tensor-core one).  Clear bits read the tables
+// tensor-core one; bit 4: SIMT Picard predictor instead of the tensor-core one).  Clear bits read the tables
 // through the L1 cache with one CTA per tile.  The default is the fastest
 // measured combination on GB300; DG_KERNEL_VARIANT overrides it for tuning.
 inline int table_residency_mask() {
@@ -2017,10 +2389,18 @@ cudaError_t launch_corrector_law(const StepArgs& a, cudaStream_t s) {
 
 template <int N, int LAW>
 cudaError_t launch_picard_law(const StepArgs& a, cudaStream_t s) {
-  static bool cfg = false;
-  static int blocks = 1;
+  static bool cfg[2] = {false, false};
+  static int blocks[2] = {1, 1};
+  if constexpr (tc_volume(N)) {
+    if (!(table_residency_mask() & 16)) {
+      const int64_t tiles = (a.E + PicTcCfg<N>::TE - 1) / PicTcCfg<N>::TE;
+      // resident CTAs of an SM share its 512 tensor-memory columns
+      return launch_persistent<PicTcCfg<N>>(k_picard_tc<N, LAW>, tiles, a.grid_corr > 0 ? a.grid_corr : 148, a, s,
+                                            &cfg[1], &blocks[1], 512 / PicTcCfg<N>::TMEM_COLS);
+    }
+  }
   const int64_t tiles = (a.E + PicardCfg<N>::TE - 1) / PicardCfg<N>::TE;
-  return launch_persistent<PicardCfg<N>>(k_picard<N, LAW>, tiles, 148, a, s, &cfg, &blocks);
+  return launch_persistent<PicardCfg<N>>(k_picard<N, LAW>, tiles, 148, a, s, &cfg[0], &blocks[0]);
 }
 
 // The CDM runs on kernels compiled for it alone; the other laws on the dispatching ones.
