@@ -212,6 +212,23 @@ def _dist():
     return rank, world, local
 
 
+def max_over_ranks(values, world, device="cpu"):
+    """The per-rank timings reduced to their maximum over the ranks (the job
+    ends when its slowest replica does); identity for one rank."""
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(world, units_per_rank, steps, ms):
+    """Element updates per second of the whole job: every rank advances its own
+    replica of units_per_rank elements for `steps` steps in at most ms."""
+    return world * units_per_rank * steps / (ms * 1e-3)
+
+
 def _host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -512,7 +529,7 @@ def run_forward(w, args, dgpkg, torch, stream, steps, warmup, e2e_steps, world=1
 def forward_report(r, pk, steps, world=1):
     """Rates, per-kernel times and the composite roofline of a forward run."""
     E, N, prof = r["E"], r["N"], r["prof"]
-    value = world * E * steps / (r["ms"] * 1e-3)
+    value = whole_job_rate(world, E, steps, r["ms"])
     kavg = {k: v["total_ms"] / max(1, v["launches"]) for k, v in prof.items()}
     kf = kernel_flops(N)
     lib_flops = algorithmic_flops(N)
@@ -584,13 +601,10 @@ def main():
 
     r = run_forward(w, args, dgpkg, torch, stream, args.steps, args.warmup, args.e2e_steps, world, barrier,
                     clocks_index=local)
-    t = torch.tensor([r["ms"], r.get("e2e_s", 0.0)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    r["ms"], e2e_s = float(t[0].item()), float(t[1].item())
+    r["ms"], e2e_s = max_over_ranks([r["ms"], r.get("e2e_s", 0.0)], world, device="cuda")
     E, N = r["E"], r["N"]
     value, kernels, step_roof, kavg = forward_report(r, pk, args.steps, world)
-    e2e_value = world * E * args.e2e_steps / e2e_s if e2e_s > 0 else None
+    e2e_value = whole_job_rate(world, E, args.e2e_steps, 1e3 * e2e_s) if e2e_s > 0 else None
 
     if rank != 0:
         if world > 1:
