@@ -38,6 +38,22 @@ struct FaceKeyHash {
   }
 };
 
+// dg_step_host streams the state through the device in element chunks: multiples
+// of 16 elements, at least 4096 each, at most 8 of them (16 measured slower).
+int64_t host_chunk_size(int64_t E) {
+  const int64_t chunk = std::max<int64_t>(4096, (E + 7) / 8);
+  return (chunk + 15) / 16 * 16;
+}
+
+// The faces of one such chunk: the interior faces first seen from its elements
+// (the flux list holds them in ascending order of that element), the last chunk
+// whose predictor they read (the other side's chunk), and its boundary faces.
+struct HostChunkFaces {
+  int64_t fi0 = 0, fi1 = 0;
+  int64_t fb0 = 0, fb1 = 0;
+  int need = 0;
+};
+
 }  // namespace
 
 struct dg_ctx {
@@ -76,6 +92,7 @@ struct dg_ctx {
   int grid_pred = 0, grid_face = 0, grid_corr = 0;
   cudaStream_t copy_stream = nullptr;     // host transfers of dg_step_host (created on first use)
   std::vector<cudaEvent_t> xfer_events;   // [2 x chunks + 1] for dg_step_host
+  std::vector<HostChunkFaces> host_faces;  // per chunk of dg_step_host (one member only)
   GeomF* geom = nullptr;
   MatF* matf = nullptr;
   int* nbr = nullptr;
@@ -597,6 +614,26 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
   if (ctx->F * M >= (int64_t(1) << 30)) {
     dg_destroy(ctx);
     return fail(nullptr, DG_E_ARG, "too many faces x members");
+  }
+  if (M == 1) {
+    // the face ranges that dg_step_host launches as soon as their predictors are done
+    const int64_t chunk = host_chunk_size(E);
+    const int C = static_cast<int>((E + chunk - 1) / chunk);
+    ctx->host_faces.assign(static_cast<size_t>(C), HostChunkFaces{});
+    int64_t fi = 0, fb = ctx->F_interior;
+    for (int k = 0; k < C; ++k) {
+      const int64_t e1 = std::min<int64_t>(E, (k + 1) * chunk);
+      HostChunkFaces& h = ctx->host_faces[static_cast<size_t>(k)];
+      int64_t reach = k * chunk;
+      h.fi0 = fi;
+      for (; fi < ctx->F_interior && faces[static_cast<size_t>(fi)].x < e1; ++fi)
+        reach = std::max<int64_t>(reach, faces[static_cast<size_t>(fi)].z);
+      h.fi1 = fi;
+      h.need = static_cast<int>(reach / chunk);
+      h.fb0 = fb;
+      for (; fb < ctx->F && faces[static_cast<size_t>(fb)].x < e1; ++fb) {}
+      h.fb1 = fb;
+    }
   }
 
   // ensemble: copy v = e * M + m of element e for member m, and copy fid * M + m of face fid;
@@ -1130,10 +1167,9 @@ dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) 
     dg_status st = ensure_staging(ctx, sizeof(float) * row * E);
     if (st != DG_OK) return st;
   }
-  // chunks of a multiple of 16 elements, at least 4096 each, at most 8 (16 measured slower)
-  int64_t chunk = std::max<int64_t>(4096, (E + 7) / 8);
-  chunk = (chunk + 15) / 16 * 16;
+  const int64_t chunk = host_chunk_size(E);
   const int C = static_cast<int>((E + chunk - 1) / chunk);
+  const bool face_ranges = ctx->host_faces.size() == static_cast<size_t>(C);
   if (!ctx->copy_stream) DG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
   while (ctx->xfer_events.size() < static_cast<size_t>(2 * C + 1)) {
     cudaEvent_t ev;
@@ -1195,7 +1231,17 @@ dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) 
                                  cudaMemcpyHostToDevice, ctx->copy_stream));
     DG_CUDA(ctx, cudaEventRecord(evH[k], ctx->copy_stream));
   }
+  // a range of the flux list (element indices in its records stay global); every range runs
+  // the kernel of the whole list, so that the fluxes are bitwise those of dg_step
+  auto faces_part = [&](int64_t f0, int64_t f1) {
+    StepArgs c = a;
+    c.faces = a.faces + f0;
+    c.ff = a.ff + f0 * ff_stride(ctx->N);
+    c.F = f1 - f0;
+    return c;
+  };
   int64_t launches = 0;
+  int faces_done = 0;                       // chunks whose interior faces are launched
   for (int k = 0; k < C; ++k) {
     const StepArgs c = part(k);
     const int64_t e0 = k * chunk;
@@ -1207,9 +1253,25 @@ dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) 
       DG_CUDA(ctx, launch_picard(ctx->N, c, ctx->stream));
       ++launches;
     }
+    if (!face_ranges) continue;
+    // the faces whose both sides are predicted run while later chunks are still uploading
+    const HostChunkFaces& hk = ctx->host_faces[static_cast<size_t>(k)];
+    if (hk.fb1 > hk.fb0) {
+      DG_CUDA(ctx, launch_faces(ctx->N, faces_part(hk.fb0, hk.fb1), ctx->stream));
+      ++launches;
+    }
+    for (; faces_done < C && ctx->host_faces[static_cast<size_t>(faces_done)].need <= k; ++faces_done) {
+      const HostChunkFaces& hj = ctx->host_faces[static_cast<size_t>(faces_done)];
+      if (hj.fi1 > hj.fi0) {
+        DG_CUDA(ctx, launch_faces(ctx->N, faces_part(hj.fi0, hj.fi1), ctx->stream));
+        ++launches;
+      }
+    }
   }
-  DG_CUDA(ctx, launch_faces(ctx->N, a, ctx->stream));
-  ++launches;
+  if (!face_ranges) {
+    DG_CUDA(ctx, launch_faces(ctx->N, a, ctx->stream));
+    ++launches;
+  }
   for (int k = 0; k < C; ++k) {
     const StepArgs c = part(k);
     const int64_t e0 = k * chunk;

@@ -1332,83 +1332,107 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
       issue_records(tile + 2 * static_cast<int64_t>(gridDim.x), it & 1, tid, C::THREADS);
     tc::cp_async_commit();
 
-    // flux at the face nodes, time-integrated: two threads per (face, node), each
-    // over half of the time nodes, combined by a shuffle
+    // flux at the face nodes, time-integrated.  The strain rows of the normal flux, the
+    // Rusanov term and the whole boundary flux are linear in the state: their time integral
+    // is their value at the time-integrated trace (the time rule integrates the degree-N
+    // Taylor polynomial exactly).  Only the stress of the velocity rows is taken at the time
+    // nodes.  Every part splits by side: of the two threads of a (face, node) pair, each
+    // takes one side over all time nodes, and a shuffle adds the two.
     for (int w0 = 0; w0 < 2 * TF * NF; w0 += C::THREADS) {
       const int w = w0 + tid;
-      const int pair = w >> 1, half = w & 1;
+      const int pair = w >> 1, side = w & 1;
       const int fc = pair / NF, i = pair - fc * NF;
       float Fb[9];
 #pragma unroll
       for (int p = 0; p < 9; ++p) Fb[p] = 0.f;
-      if (fc < nf) {
-        const float* mt = sMeta + fc * META;
+      const float* mt = sMeta + fc * META;
+      const int bc = (BND && fc < nf) ? static_cast<int>(mt[6]) : 0;
+      if (fc < nf && (bc == 0 || side == 0)) {
         const float n[3] = {mt[0], mt[1], mt[2]};
-        const int bc = BND ? static_cast<int>(mt[6]) : 0;
-        MatF mm, mp;
+        MatF m;
         {
-          const float* m0 = mt + 8;
-          mm.rho = m0[0]; mm.lam0 = m0[1]; mm.mu0 = m0[2]; mm.gamma_r = m0[3];
-          mm.xi0 = m0[4]; mm.cd = m0[5]; mm.rho_inv = m0[6]; mm.pad = 0.f;
-          const float* m1 = mt + 16;
-          mp.rho = m1[0]; mp.lam0 = m1[1]; mp.mu0 = m1[2]; mp.gamma_r = m1[3];
-          mp.xi0 = m1[4]; mp.cd = m1[5]; mp.rho_inv = m1[6]; mp.pad = 0.f;
+          const float* m0 = mt + 8 + 8 * side;
+          m.rho = m0[0]; m.lam0 = m0[1]; m.mu0 = m0[2]; m.gamma_r = m0[3];
+          m.xi0 = m0[4]; m.cd = m0[5]; m.rho_inv = m0[6]; m.pad = 0.f;
         }
-        float lam = 0.f, mu = 0.f, cpb = 0.f, csb = 0.f, k_p = 0.f;
-        if (bc != 0) {
-          effective_lame<LAW>(a.law, mt + 28, mm, &lam, &mu);   // side 0's cell-mean modes
-          cpb = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * mm.rho_inv);
-          csb = sqrtf(fmaxf(mu, 0.f) * mm.rho_inv);
-          k_p = lam + 2.f * mu > 0.f ? cpb / (lam + 2.f * mu) : 0.f;
-        }
-        const float Cs = fmaxf(mt[4], mt[5]);
-        const float* Tm = sTr + (2 * fc) * (N + 1) * NGG * 12 + i * 12;
-        const float* Tp = Tm + (N + 1) * NGG * 12;
-        constexpr int ZH = (NT + 1) / 2;
-        for (int z = half * ZH; z < (half ? NT : ZH); ++z) {
-          const float tau = __ldg(tb + T.tz + z) * dt, gam = __ldg(tb + T.gz + z) * dt;
-          float um[10], up[10];
+        const float* Tr = sTr + (2 * fc + side) * (N + 1) * NGG * 12 + i * 12;
+        // the strain's Taylor coefficients, alpha and its rate, and the time-integrated
+        // trace ub = sum_o D^o dt^(o+1) / (o+1)!
+        float eo[N + 1][6], ub[9];
+        float al, dal;
+        {
+          const float4 a0 = *reinterpret_cast<const float4*>(Tr);
+          const float4 a1 = *reinterpret_cast<const float4*>(Tr + 4);
+          const float4 a2 = *reinterpret_cast<const float4*>(Tr + 8);
+          eo[0][0] = a0.x; eo[0][1] = a0.y; eo[0][2] = a0.z; eo[0][3] = a0.w; eo[0][4] = a1.x; eo[0][5] = a1.y;
+          al = a2.y;
+          dal = a2.z;
+          const float u0[9] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, a2.x};
 #pragma unroll
-          for (int sd = 0; sd < 2; ++sd) {
-            const float* t0 = sd ? Tp : Tm;
-            float* u = sd ? up : um;
-            const float4 a0 = *reinterpret_cast<const float4*>(t0);
-            const float4 a1 = *reinterpret_cast<const float4*>(t0 + 4);
-            const float4 a2 = *reinterpret_cast<const float4*>(t0 + 8);
-            u[0] = a0.x; u[1] = a0.y; u[2] = a0.z; u[3] = a0.w;
-            u[4] = a1.x; u[5] = a1.y; u[6] = a1.z; u[7] = a1.w;
-            u[8] = a2.x; u[9] = fmaf(tau, a2.z, a2.y);
+          for (int p = 0; p < 9; ++p) ub[p] = dt * u0[p];
+        }
+        float cw = dt;
+#pragma unroll
+        for (int o = 1; o <= N; ++o) {
+          cw *= dt * (1.f / static_cast<float>(o + 1));   // constant after unrolling: no division
+          const float* to = Tr + o * NGG * 12;
+          const float4 b0 = *reinterpret_cast<const float4*>(to);
+          const float4 b1 = *reinterpret_cast<const float4*>(to + 4);
+          const float b2 = to[8];
+          eo[o][0] = b0.x; eo[o][1] = b0.y; eo[o][2] = b0.z; eo[o][3] = b0.w; eo[o][4] = b1.x; eo[o][5] = b1.y;
+          const float uo[9] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w, b2};
+#pragma unroll
+          for (int p = 0; p < 9; ++p) ub[p] = fmaf(cw, uo[p], ub[p]);
+        }
+        if (BND && bc != 0) {
+          float lam, mu;
+          effective_lame<LAW>(a.law, mt + 28, m, &lam, &mu);   // side 0's cell-mean modes
+          const float cpb = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * m.rho_inv);
+          const float csb = sqrtf(fmaxf(mu, 0.f) * m.rho_inv);
+          const float k_p = lam + 2.f * mu > 0.f ? cpb / (lam + 2.f * mu) : 0.f;
+          boundary_flux(bc, ub, n, lam, mu, m.rho_inv, cpb, csb, k_p, Fb);
+        } else {
+          // this side's half of the strain rows and of the Rusanov term (+ for side 0)
+          const float hc = (side ? -0.5f : 0.5f) * fmaxf(mt[4], mt[5]);
+          Fb[0] = fmaf(hc, ub[0], -0.5f * ub[6] * n[0]);
+          Fb[1] = fmaf(hc, ub[1], -0.5f * ub[7] * n[1]);
+          Fb[2] = fmaf(hc, ub[2], -0.5f * ub[8] * n[2]);
+          Fb[3] = fmaf(hc, ub[3], -0.25f * (ub[6] * n[1] + ub[7] * n[0]));
+          Fb[4] = fmaf(hc, ub[4], -0.25f * (ub[7] * n[2] + ub[8] * n[1]));
+          Fb[5] = fmaf(hc, ub[5], -0.25f * (ub[8] * n[0] + ub[6] * n[2]));
+          Fb[6] = hc * ub[6];
+          Fb[7] = hc * ub[7];
+          Fb[8] = hc * ub[8];
+          // this side's half of the velocity rows, -sigma n / rho, at the time nodes
+          float sn[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+          for (int z = 0; z < NT; ++z) {
+            const float tau = __ldg(tb + T.tz + z) * dt, gam = __ldg(tb + T.gz + z) * dt;
+            float e[6];
+#pragma unroll
+            for (int p = 0; p < 6; ++p) e[p] = eo[0][p];
             float c = 1.f;
 #pragma unroll
             for (int o = 1; o <= N; ++o) {
-              c *= tau * (1.f / static_cast<float>(o));   // constant after unrolling: no division
-              const float* to = t0 + o * NGG * 12;
-              const float4 b0 = *reinterpret_cast<const float4*>(to);
-              const float4 b1 = *reinterpret_cast<const float4*>(to + 4);
-              const float b2 = to[8];
-              u[0] = fmaf(c, b0.x, u[0]); u[1] = fmaf(c, b0.y, u[1]); u[2] = fmaf(c, b0.z, u[2]);
-              u[3] = fmaf(c, b0.w, u[3]); u[4] = fmaf(c, b1.x, u[4]); u[5] = fmaf(c, b1.y, u[5]);
-              u[6] = fmaf(c, b1.z, u[6]); u[7] = fmaf(c, b1.w, u[7]); u[8] = fmaf(c, b2, u[8]);
+              c *= tau * (1.f / static_cast<float>(o));
+#pragma unroll
+              for (int p = 0; p < 6; ++p) e[p] = fmaf(c, eo[o][p], e[p]);
             }
-            if (bc != 0) break;                 // a boundary face has no side 1
+            float sig[6], r;
+            law_point<LAW>(a.law, e, fmaf(tau, dal, al), m, sig, &r);
+            sn[0] = fmaf(gam, sig[0] * n[0] + sig[3] * n[1] + sig[5] * n[2], sn[0]);
+            sn[1] = fmaf(gam, sig[3] * n[0] + sig[1] * n[1] + sig[4] * n[2], sn[1]);
+            sn[2] = fmaf(gam, sig[5] * n[0] + sig[4] * n[1] + sig[2] * n[2], sn[2]);
           }
-          float F[9];
-          if (bc != 0) {
-            boundary_flux(bc, um, n, lam, mu, mm.rho_inv, cpb, csb, k_p, F);
-          } else {
-            float Fm[9], Fp[9];
-            normal_flux<LAW>(a.law, um, mm, n, Fm);
-            normal_flux<LAW>(a.law, up, mp, n, Fp);
-#pragma unroll
-            for (int p = 0; p < 9; ++p) F[p] = 0.5f * (Fm[p] + Fp[p]) + 0.5f * Cs * (um[p] - up[p]);
-          }
-#pragma unroll
-          for (int p = 0; p < 9; ++p) Fb[p] = fmaf(gam, F[p], Fb[p]);
+          const float k = -0.5f * m.rho_inv;
+          Fb[6] = fmaf(k, sn[0], Fb[6]);
+          Fb[7] = fmaf(k, sn[1], Fb[7]);
+          Fb[8] = fmaf(k, sn[2], Fb[8]);
         }
       }
 #pragma unroll
       for (int p = 0; p < 9; ++p) Fb[p] += __shfl_down_sync(0xffffffffu, Fb[p], 1);
-      if (fc < nf && half == 0) {
+      if (fc < nf && side == 0) {
         float* out = a.ff + (f0 + fc) * FFS + i * 9;
 #pragma unroll
         for (int p = 0; p < 9; ++p) out[p] = Fb[p];
