@@ -64,8 +64,8 @@ def algorithmic_flops(N):
     pred = (2 * 6 * NQ * L + 20 * NQ + 2 * NQ * L                       # damage rate at t_n, projection
             + sum(2 * 27 * LR[i] * LR[i - 1] + 192 * LR[i] for i in range(1, N + 1)))   # CK
     per_face = (2 * NF * 2 * (11 * L + 9 * SH)                          # traces, both sides, all orders
-                + 2 * NF * NT * (18 * N + 2)                            # Taylor sums at the time nodes
-                + NF * NT * 165)                                        # two normal fluxes + Rusanov
+                + 2 * NF * (18 * (N + 1) + NT * (12 * N + 2))           # time-integrated trace; strain, alpha
+                + NF * (NT * 2 * 61 + 2 * 30))                          # stress n at the time nodes; linear part
     faces = 2 * per_face
     corr = (2 * NQ * (8 * L + 6 * SH) + 2 * NQ * NT * (6 * N + 1)       # strains, damage at the nodes
             + NQ * NT * 50 + NQ * 63                                    # CDM stress/rate, stress terms
@@ -514,6 +514,10 @@ def run_forward(w, args, dgpkg, torch, stream, steps, warmup, e2e_steps, world=1
         res_np = res.numpy()
         s.get_state(out=res_np)
         hq_np[...] = res_np
+        # W untimed calls, like the device run: the first call allocates the staging buffer,
+        # and the first transfers after the device run are slow
+        for _ in range(warmup):
+            s.step_host(hq_np, res_np)
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
