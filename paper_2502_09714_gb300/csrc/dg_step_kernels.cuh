@@ -20,6 +20,7 @@
 // with 4x4 register tiles.
 #pragma once
 
+#include <algorithm>
 #include <cstdlib>
 
 #include "dg_internal.h"
@@ -514,6 +515,291 @@ __global__ void __launch_bounds__(256) k_predictor(StepArgs a) {
       __syncthreads();
     }
   }
+}
+
+// ===========================================================================
+// Predictor with the strains and alpha at the volume nodes on the tensor cores
+// (degrees 2..4).  D[q][(e, c)] = sum_l phi_l(x_q) C_e[l][c], c = the six strains and
+// alpha at t_n: 3xTF32 MMAs with A = phi_l(x_q) in tensor memory (lane q, column l,
+// loaded once) and B = the tile's coefficients in shared memory (row (e, c), K = l),
+// issued before the CK recursion, which runs on the SIMT cores meanwhile; then the
+// damage rate at the nodes from D and its projection (D^1 of alpha).  Two CTAs of 256
+// threads per SM, each with 256 tensor-memory columns.
+// ===========================================================================
+template <int N>
+struct PredTcCfg : Dim<N> {
+  using D = Dim<N>;
+  static constexpr int TE = N >= 4 ? 8 : 16;
+  static constexpr int THREADS = 256;
+  static constexpr int CW = 12 * TE;                       // CK column width: (element, 9 fields + 3 pad)
+  static constexpr int KS_SRC = N >= 4 ? 8 : 4;
+  static constexpr int KP = tc_kp(N);
+  static constexpr int NB = 8 * TE;                        // MMA N: (element, 6 strains, alpha, 0)
+  // B's 8-row groups (one per element) BSBO floats apart: 4 floats off the bank period, so
+  // that the lanes of a warp writing one coefficient of eight elements hit distinct banks
+  static constexpr int BSBO = 8 * KP + 4;
+  static constexpr int COL_D = 0, COL_AH = NB, COL_AL = NB + KP;
+  static constexpr int TMEM_NEED = COL_AL + KP;
+  static constexpr int TMEM_COLS = TMEM_NEED <= 128 ? 128 : 256;
+  static constexpr int QSP = D::QS % 32 == 0 ? D::QS + 4 : D::QS;
+  static constexpr int oVw = 0;                            // [NQ][LP]
+  static constexpr int oKtA = round4(oVw + D::NQ * D::LP); // [3][L][LP]
+  static constexpr int oQ = round4(oKtA + 3 * D::L * D::LP);   // [TE][QSP] staged state rows
+  static constexpr int oBH = oQ + TE * QSP;                // B, TF32 high part
+  static constexpr int oBL = oBH + TE * BSBO;              // B, remainder
+  static constexpr int oR = oBL + TE * BSBO;               // [NQ][TE] damage rate at the nodes
+  static constexpr int oP0 = round4(oR + D::NQ * TE);      // [L][CW] CK input
+  static constexpr int oP1 = oP0 + D::L * CW;              // [L][CW] CK output
+  static constexpr int oPart = oP1 + D::L * CW;            // split-K partial sums
+  static constexpr int PART = KS_SRC * D::LP * TE;
+  static constexpr int oCoef = oPart + PART;               // [TE][16]
+  static constexpr int oGM = round4(oCoef + 16 * TE);      // [TE][40] GeomF, MatF as copied
+  static constexpr int SMEM = oGM + 40 * TE;
+  static constexpr int ISSUER = THREADS - 32;
+  __host__ __device__ static constexpr int b_index(int e, int c, int l) {
+    return e * BSBO + (l >> 2) * 32 + c * 4 + (l & 3);
+  }
+  static_assert(NB % 16 == 0 && NB <= 256 && D::NQ <= 128 && KP % 8 == 0 && KP <= 40, "tensor-core shapes");
+  static_assert(oQ % 4 == 0 && (TE * QSP) % 4 == 0 && BSBO % 4 == 0, "16-byte aligned operands");
+  static_assert(TMEM_NEED <= 256, "two CTAs per SM share the 512 tensor-memory columns");
+  static_assert(2 * (SMEM * 4 + 1024) <= 228 * 1024, "two CTAs per SM");
+  static_assert(TE % 8 == 0 && THREADS == 256, "read-out: warps 0-3 and 4-7 take half the elements each");
+  static_assert(TE * n_modes(N - 1) <= ISSUER, "the issuing warp has no CK work at order 1");
+};
+
+template <int N, int LAW>
+__global__ void __launch_bounds__(256, 2) k_predictor_tc(StepArgs a) {
+  using C = PredTcCfg<N>;
+  constexpr int L = C::L, NQ = C::NQ, LP = C::LP, QS = C::QS, DS = C::DS, TE = C::TE, KP = C::KP;
+  constexpr int CW = C::CW, NB = C::NB;
+  constexpr TableLayout T = table_layout(N);
+  constexpr int kWaitLimit = 1 << 24;
+  const int wait_limit = a.wait_limit_set ? a.wait_limit : kWaitLimit;
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const float* sVw = sm + C::oVw;
+  const float* sKtA = sm + C::oKtA;
+  float* sQ = sm + C::oQ;
+  float* sBH = sm + C::oBH;
+  float* sBL = sm + C::oBL;
+  float* sR = sm + C::oR;
+  float* sP0 = sm + C::oP0;
+  float* sP1 = sm + C::oP1;
+  float* sPart = sm + C::oPart;
+  float* sCoef = sm + C::oCoef;
+  float* sGM = sm + C::oGM;
+  const float* tb = a.tables;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  copy_to_smem(sm + C::oVw, tb + T.Vw, NQ * LP);
+  copy_to_smem(sm + C::oKtA, tb + T.KtA, 3 * L * LP);
+  // B's K padding (modes L .. KP-1) stays zero
+  if constexpr (KP > L) {
+    for (int w = tid; w < TE * 8 * (KP - L); w += blockDim.x) {
+      const int l = L + w % (KP - L), ec = w / (KP - L);
+      sBH[C::b_index(ec >> 3, ec & 7, l)] = 0.f;
+      sBL[C::b_index(ec >> 3, ec & 7, l)] = 0.f;
+    }
+  }
+  if (warp == 0) tc::alloc(&tmem_base, C::TMEM_COLS);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base;
+  // A = phi_l(x_q) (TF32 part, remainder) into tensor memory once: lane q, columns l, read
+  // from the canonical tables (rows q >= NQ are zero)
+  if (warp < 4) {
+    const int q = 32 * warp + lane;
+    const uint32_t lane_base = static_cast<uint32_t>(32 * warp) << 16;
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+      const float* src = tb + (part ? T.PhiL : T.PhiH);
+      float v[KP];
+#pragma unroll
+      for (int j = 0; j < KP / 4; ++j) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(src + tc_canon(q, 4 * j, KP)));
+        v[4 * j] = x.x; v[4 * j + 1] = x.y; v[4 * j + 2] = x.z; v[4 * j + 3] = x.w;
+      }
+      tc::st_cols<KP>(tmem + lane_base + (part ? C::COL_AL : C::COL_AH), v);
+    }
+    tc::wait_st();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  uint32_t phase = 0;
+  bool failed = false;
+
+  const int64_t ntiles = (a.E + TE - 1) / TE;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e0 = tile * TE;
+    const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
+    __syncthreads();
+    // one batch of asynchronous copies: the tile's state rows, GeomF and MatF
+    for (int w = tid; w < TE * QS / 4; w += blockDim.x) {
+      const int e = w / (QS / 4), c = w - e * (QS / 4);
+      if (e < ne) tc::cp_async16(sQ + e * C::QSP + 4 * c, a.q_in + (e0 + e) * QS + 4 * c);
+      else *reinterpret_cast<float4*>(sQ + e * C::QSP + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int w = tid; w < ne * 10; w += blockDim.x) {
+      const int e = w / 10, k = w - 10 * e;
+      if (k < 8) tc::cp_async16(sGM + e * 40 + 4 * k, reinterpret_cast<const float*>(a.geom + e0 + e) + 4 * k);
+      else tc::cp_async16(sGM + e * 40 + 32 + 4 * (k - 8), reinterpret_cast<const float*>(a.mat + e0 + e) + 4 * (k - 8));
+    }
+    tc::cp_async_wait_all();
+    __syncthreads();
+    // per element: effective moduli at the cell mean (Eq. "effective-cdb", mu sign from Eq. "cdb-model")
+    if (tid < ne) {
+      const int e = tid;
+      const int64_t ge = e0 + e;
+      const MatF m = *reinterpret_cast<const MatF*>(sGM + e * 40 + 32);
+      float lam, mu;
+      effective_lame<LAW>(a.law, sQ + e * C::QSP, m, &lam, &mu);
+      if (!(mu > 0.f) || !(lam + 2.f * mu > 0.f)) atomicOr(a.status, kStatusNonHyperbolic);
+      a.cp[ge] = sqrtf(fmaxf(lam + 2.f * mu, 0.f) * m.rho_inv);
+      float* c = sCoef + e * 16;
+      c[0] = lam * m.rho_inv;
+      c[1] = mu * m.rho_inv;
+      const float* g = sGM + e * 40;           // GeomF starts with Theta^{-1}
+      for (int k = 0; k < 9; ++k) c[2 + k] = g[k];
+    }
+    // the MMA's B operand (strains and alpha at t_n, split) and the CK input [l][e*12 + p]
+    for (int w = tid; w < L * TE; w += blockDim.x) {
+      const int l = w / TE, e = w - l * TE;
+      const float2* q2 = reinterpret_cast<const float2*>(sQ + e * C::QSP + l * 10);
+      const float2 q01 = q2[0], q23 = q2[1], q45 = q2[2], q67 = q2[3], q89 = q2[4];
+      const float x[8] = {q01.x, q01.y, q23.x, q23.y, q45.x, q45.y, q89.y, 0.f};
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float h = tc::tf32_hi(x[c]);
+        sBH[C::b_index(e, c, l)] = h;
+        sBL[C::b_index(e, c, l)] = tc::tf32_hi(x[c] - h);
+      }
+      float4* p0 = reinterpret_cast<float4*>(sP0 + l * CW + e * 12);
+      p0[0] = make_float4(q01.x, q01.y, q23.x, q23.y);
+      p0[1] = make_float4(q45.x, q45.y, q67.x, q67.y);
+      p0[2] = make_float4(q89.x, 0.f, 0.f, 0.f);
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before();
+    __syncthreads();
+    // issued from the last warp, which has no CK work at order 1 (the issuing thread waits
+    // for the tensor pipe)
+    if (tid == C::ISSUER) {
+      tc::fence_after();
+      constexpr uint32_t idesc = tc::idesc_tf32(128, NB);
+      const uint32_t bH = tc::smem_u32(sBH), bL = tc::smem_u32(sBL);
+      constexpr uint32_t sbo = 4u * C::BSBO;
+#pragma unroll
+      for (int ks = 0; ks < KP / 8; ++ks) {
+        const uint32_t off = ks * 256;   // 8 K-elements = 2 core matrices
+        const uint32_t aH = tmem + C::COL_AH + 8 * ks, aL = tmem + C::COL_AL + 8 * ks;
+        tc::mma_tf32_ta(tmem + C::COL_D, aH, tc::desc_kmajor_strided(bH + off, 128u, sbo), idesc, ks > 0 ? 1u : 0u);
+        tc::mma_tf32_ta(tmem + C::COL_D, aH, tc::desc_kmajor_strided(bL + off, 128u, sbo), idesc, 1u);
+        tc::mma_tf32_ta(tmem + C::COL_D, aL, tc::desc_kmajor_strided(bH + off, 128u, sbo), idesc, 1u);
+      }
+      tc::commit(&mbar);
+    }
+
+    // Cauchy-Kovalevskaya while the MMAs run: D^i_kp = -sum_e Kt^e_kl D^{i-1}_lq
+    // (Theta^{-1}_ed B^d_pq); the order loop is unrolled so that the mode counts are constants
+#pragma unroll
+    for (int i = 1; i <= N; ++i) {
+      const int Lin = n_modes(N - i + 1), Lout = n_modes(N - i);
+      const float* pin = (i & 1) ? sP0 : sP1;
+      float* pout = (i & 1) ? sP1 : sP0;
+      const int doff = d_offset(N, i);
+      for (int w = tid; w < TE * Lout; w += blockDim.x) {
+        const int k = w / TE, e = w - k * TE;
+        float g[3][9];
+#pragma unroll
+        for (int f = 0; f < 9; ++f) g[0][f] = g[1][f] = g[2][f] = 0.f;
+#pragma unroll 4
+        for (int l = 0; l < Lin; ++l) {
+          const float k0 = sKtA[(0 * L + l) * LP + k], k1 = sKtA[(1 * L + l) * LP + k], k2 = sKtA[(2 * L + l) * LP + k];
+          const float4 p0 = *reinterpret_cast<const float4*>(pin + l * CW + e * 12);
+          const float4 p1 = *reinterpret_cast<const float4*>(pin + l * CW + e * 12 + 4);
+          const float p8 = pin[l * CW + e * 12 + 8];
+          const float pv[9] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w, p8};
+#pragma unroll
+          for (int f = 0; f < 9; ++f) {
+            g[0][f] = fmaf(k0, pv[f], g[0][f]);
+            g[1][f] = fmaf(k1, pv[f], g[1][f]);
+            g[2][f] = fmaf(k2, pv[f], g[2][f]);
+          }
+        }
+        const float* c = sCoef + e * 16;
+        float gd[3][9];   // d/dx_d of field f, projected
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int f = 0; f < 9; ++f) gd[d][f] = c[2 + d] * g[0][f] + c[5 + d] * g[1][f] + c[8 + d] * g[2][f];
+        const float lr_ = c[0], mr = c[1];
+        float Di[9];
+        Di[0] = gd[0][6];
+        Di[1] = gd[1][7];
+        Di[2] = gd[2][8];
+        Di[3] = 0.5f * (gd[1][6] + gd[0][7]);
+        Di[4] = 0.5f * (gd[2][7] + gd[1][8]);
+        Di[5] = 0.5f * (gd[0][8] + gd[2][6]);
+        Di[6] = lr_ * (gd[0][0] + gd[0][1] + gd[0][2]) + 2.f * mr * (gd[0][0] + gd[1][3] + gd[2][5]);
+        Di[7] = lr_ * (gd[1][0] + gd[1][1] + gd[1][2]) + 2.f * mr * (gd[0][3] + gd[1][1] + gd[2][4]);
+        Di[8] = lr_ * (gd[2][0] + gd[2][1] + gd[2][2]) + 2.f * mr * (gd[0][5] + gd[1][4] + gd[2][2]);
+        float* po = pout + k * CW + e * 12;
+        *reinterpret_cast<float4*>(po) = make_float4(Di[0], Di[1], Di[2], Di[3]);
+        *reinterpret_cast<float4*>(po + 4) = make_float4(Di[4], Di[5], Di[6], Di[7]);
+        *reinterpret_cast<float4*>(po + 8) = make_float4(Di[8], 0.f, 0.f, 0.f);
+        if (e < ne) {
+          float* gout = a.d + (e0 + e) * DS + doff + k * 9;
+#pragma unroll
+          for (int f = 0; f < 9; ++f) gout[f] = Di[f];
+        }
+      }
+      __syncthreads();
+    }
+
+    // damage rate at the volume nodes from the MMA's result: thread (warp w, lane) holds
+    // node q = 32 (w mod 4) + lane of elements [TE/2 (w / 4), TE/2 (w / 4 + 1))
+    const bool ok = tc::wait_parity(&mbar, phase, wait_limit);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after();
+    {
+      const int q = 32 * (warp & 3) + lane;
+      const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
+#pragma unroll 1
+      for (int e4 = 0; e4 < TE / 2; e4 += 4) {
+        const int eb = (warp >> 2) * (TE / 2) + e4;
+        float v[32];
+        tc::ld_cols<32>(tmem + lane_base + C::COL_D + 8 * eb, v);
+        tc::wait_ld();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int e = eb + j;
+          const MatF m = *reinterpret_cast<const MatF*>(sGM + (e < ne ? e : 0) * 40 + 32);
+          if (q < NQ) sR[q * TE + e] = e < ne ? law_rate<LAW>(a.law, v + 8 * j, v[8 * j + 6], m) : 0.f;
+        }
+      }
+    }
+    tc::fence_before();
+    __syncthreads();
+    // D^1 of alpha = projection of the rate (mass matrix = identity)
+    block_gemm<C::KS_SRC>(sVw, LP, sR, TE, LP, TE, NQ, sPart, [&](int k, int e, float v) {
+      if (k < L && e < ne) a.d[(e0 + e) * DS + C::AOFF + k] = v;
+    });
+  }
+  if (failed) {
+    if (tid == 0) atomicOr(a.status, kStatusTimeout);
+    tc::wait_parity(&mbar, phase ^ 1u, kWaitLimit);   // let the MMAs in flight finish before freeing TMEM
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::dealloc(tmem, C::TMEM_COLS);
 }
 
 // ===========================================================================
@@ -2338,10 +2624,34 @@ cudaError_t launch_persistent(Kern kern, int64_t tiles, int grid_hint, const Ste
   if (!*configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, smem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    if (cap_per_sm > 0 && per_sm > cap_per_sm) per_sm = cap_per_sm;
+    int per_sm = 0;
+    if (cap_per_sm > 0) {
+      // Kernels holding tensor memory: the occupancy query counts one block per SM for any
+      // kernel that allocates it, whatever it allocates.  The blocks that shared memory,
+      // registers and threads allow are resident; of those, cap_per_sm fit in the SM's
+      // 512 columns (a block that finds too few waits in its allocation, it cannot deadlock).
+      cudaFuncAttributes fa{};
+      e = cudaFuncGetAttributes(&fa, kern);
+      if (e != cudaSuccess) return e;
+      int dev = 0, sm_smem = 0, reserved = 0, sm_regs = 0, sm_threads = 0;
+      if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+          (e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+          (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+          (e = cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
+          (e = cudaDeviceGetAttribute(&sm_threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev)) != cudaSuccess)
+        return e;
+      const int warps = (Cfg::THREADS + 31) / 32;
+      const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;      // allocated per warp in units of 256
+      const int by_smem = static_cast<int>(static_cast<size_t>(sm_smem) / (smem + fa.sharedSizeBytes + reserved));
+      const int by_regs = regs_warp > 0 ? sm_regs / (regs_warp * warps) : cap_per_sm;
+      const int by_threads = sm_threads / Cfg::THREADS;
+      per_sm = std::min(std::min(by_smem, by_regs), std::min(by_threads, cap_per_sm));
+    } else {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, smem);
+      if (e != cudaSuccess) return e;
+    }
     *max_blocks = per_sm > 0 ? per_sm : 1;
     *configured = true;
   }
@@ -2354,7 +2664,8 @@ cudaError_t launch_persistent(Kern kern, int64_t tiles, int grid_hint, const Ste
 
 // Kernel variants (bit 0: predictor with shared-memory tables on a persistent
 // grid; bit 2: SIMT corrector likewise; bit 3: SIMT corrector instead of the
-// tensor-core one; bit 4: SIMT Picard predictor instead of the tensor-core one).  Clear bits read the tables
+// tensor-core one; bit 4: SIMT Picard predictor instead of the tensor-core one;
+// bit 5: SIMT predictor instead of the tensor-core one).  Clear bits read the tables
 // through the L1 cache with one CTA per tile.  The default is the fastest
 // measured combination on GB300; DG_KERNEL_VARIANT overrides it for tuning.
 inline int table_residency_mask() {
@@ -2368,8 +2679,16 @@ inline int table_residency_mask() {
 
 template <int N, int LAW>
 cudaError_t launch_predictor_law(const StepArgs& a, cudaStream_t s) {
-  static bool cfg[2] = {false, false};
-  static int blocks[2] = {1, 1};
+  static bool cfg[3] = {false, false, false};
+  static int blocks[3] = {1, 1, 1};
+  if constexpr (tc_volume(N)) {
+    if (!(table_residency_mask() & 32)) {
+      const int64_t tiles = (a.E + PredTcCfg<N>::TE - 1) / PredTcCfg<N>::TE;
+      // resident CTAs of an SM share its 512 tensor-memory columns
+      return launch_persistent<PredTcCfg<N>>(k_predictor_tc<N, LAW>, tiles, a.grid_pred > 0 ? a.grid_pred : 148, a,
+                                             s, &cfg[2], &blocks[2], 512 / PredTcCfg<N>::TMEM_COLS);
+    }
+  }
   const int64_t tiles = (a.E + PredCfg<N, true>::TE - 1) / PredCfg<N, true>::TE;
   if constexpr (PredCfg<N, true>::FITS) {
     if (table_residency_mask() & 1)

@@ -1,9 +1,9 @@
-"""The failure path of the tensor-core corrector's bounded waits, run without any
-fault: with a wait limit of 0 polls, the first wait on the matrix products gives
-up at once.  The corrector must then stop, drain its products in flight with the
-default limit, free its tensor memory and return; dg_step reports DG_E_CUDA
-("timed out") and the context stays usable: the next step at the default limit
-matches the oracle."""
+"""The failure path of the bounded waits of the tensor-core kernels (predictor and
+corrector), run without any fault: with a wait limit of 0 polls, the first wait on
+the matrix products gives up at once.  Each kernel must then stop, drain its
+products in flight with the default limit, free its tensor memory and return;
+dg_step reports DG_E_CUDA ("timed out") and the context stays usable: the next step
+at the default limit matches the oracle."""
 import numpy as np
 import pytest
 
