@@ -138,11 +138,11 @@ dg_status dg_set_rheology(dg_ctx* ctx, int law);
 enum { DG_PREDICTOR_CK = 0, DG_PREDICTOR_PICARD = 1 };
 dg_status dg_set_predictor(dg_ctx* ctx, int kind, int iterations);
 
-/* Limit of the bounded waits with which the tensor-core corrector (degrees 2..4)
- * waits for its matrix products: `polls` polls of the completion barrier per wait
- * (0 .. 2^31 - 1), or the library's default (2^24) for a negative value.  A wait
- * that runs out makes the corrector stop its work, wait (with the default limit)
- * for the products in flight, free its tensor memory and return; the step then
+/* Limit of the bounded waits with which the tensor-core predictor and corrector
+ * (degrees 2..4) wait for their matrix products: `polls` polls of the completion
+ * barrier per wait (0 .. 2^31 - 1), or the library's default (2^24) for a negative
+ * value.  A wait that runs out makes the kernel stop its work, wait (with the
+ * default limit) for the products in flight, free its tensor memory and return; the step then
  * returns DG_E_CUDA ("timed out") and the state is left as computed, so the caller
  * restores it with dg_set_state.  A limit of 0 gives up at the first wait, which
  * is how the failure path is tested without any fault.  Not a passage of the
@@ -211,8 +211,9 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt);
  * dg_set_state_f32(q_in, current time), dg_step(1, dt), dg_get_state_f32(q_out),
  * with the same arithmetic, but with one member the transfers overlap the
  * step: the elements are cut into chunks, the upload of one chunk runs while the
- * previous one is predicted and the download of one chunk while the corrector
- * works on the next (page-locked host arrays are needed for the overlap;
+ * previous one is predicted, the faces run as soon as both their sides are
+ * predicted, and the download of one chunk runs while the corrector works on the
+ * next (page-locked host arrays are needed for the overlap;
  * pageable ones work without it).  Advances the time by dt.  Requires the
  * material (DG_E_STATE); errors as dg_step. */
 dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt);
