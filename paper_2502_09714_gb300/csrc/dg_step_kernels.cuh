@@ -1959,8 +1959,8 @@ template <int N, bool TSM, int LAW>
 __global__ void __launch_bounds__(256) k_corrector(StepArgs a) {
   using C = CorrCfg<N, TSM>;
   constexpr int L = C::L, NQ = C::NQ, NQP = C::NQP, NF = C::NF, NT = C::NT, LP = C::LP;
-  constexpr int QS = C::QS, DS = C::DS, AOFF = C::AOFF, FFS = C::FFS, TE = C::TE;
-  constexpr int NV = C::NV, NB = C::NB, NM = C::NM, NFC = C::NFC;
+  constexpr int QS = C::QS, DS = C::DS, AOFF = C::AOFF, TE = C::TE;
+  constexpr int NM = C::NM;
   constexpr TableLayout T = table_layout(N);
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
