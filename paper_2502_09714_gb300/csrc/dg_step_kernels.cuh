@@ -633,22 +633,28 @@ __global__ void __launch_bounds__(256, 2) k_predictor_tc(StepArgs a) {
   bool failed = false;
 
   const int64_t ntiles = (a.E + TE - 1) / TE;
+  // one batch of asynchronous copies of a tile: its state rows, GeomF and MatF (rows of
+  // elements beyond the mesh are zero)
+  auto issue = [&](int64_t tl) {
+    const int64_t t0 = tl * TE;
+    const int nt = static_cast<int>(min(static_cast<int64_t>(TE), a.E - t0));
+    for (int w = tid; w < TE * QS / 4; w += blockDim.x) {
+      const int e = w / (QS / 4), c = w - e * (QS / 4);
+      if (e < nt) tc::cp_async16(sQ + e * C::QSP + 4 * c, a.q_in + (t0 + e) * QS + 4 * c);
+      else *reinterpret_cast<float4*>(sQ + e * C::QSP + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int w = tid; w < nt * 10; w += blockDim.x) {
+      const int e = w / 10, k = w - 10 * e;
+      if (k < 8) tc::cp_async16(sGM + e * 40 + 4 * k, reinterpret_cast<const float*>(a.geom + t0 + e) + 4 * k);
+      else tc::cp_async16(sGM + e * 40 + 32 + 4 * (k - 8), reinterpret_cast<const float*>(a.mat + t0 + e) + 4 * (k - 8));
+    }
+    tc::cp_async_commit();
+  };
+  if (static_cast<int64_t>(blockIdx.x) < ntiles) issue(blockIdx.x);
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e0 = tile * TE;
     const int ne = static_cast<int>(min(static_cast<int64_t>(TE), a.E - e0));
-    __syncthreads();
-    // one batch of asynchronous copies: the tile's state rows, GeomF and MatF
-    for (int w = tid; w < TE * QS / 4; w += blockDim.x) {
-      const int e = w / (QS / 4), c = w - e * (QS / 4);
-      if (e < ne) tc::cp_async16(sQ + e * C::QSP + 4 * c, a.q_in + (e0 + e) * QS + 4 * c);
-      else *reinterpret_cast<float4*>(sQ + e * C::QSP + 4 * c) = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    for (int w = tid; w < ne * 10; w += blockDim.x) {
-      const int e = w / 10, k = w - 10 * e;
-      if (k < 8) tc::cp_async16(sGM + e * 40 + 4 * k, reinterpret_cast<const float*>(a.geom + e0 + e) + 4 * k);
-      else tc::cp_async16(sGM + e * 40 + 32 + 4 * (k - 8), reinterpret_cast<const float*>(a.mat + e0 + e) + 4 * (k - 8));
-    }
-    tc::cp_async_wait_all();
+    tc::cp_async_wait<0>();                  // this tile's copies (issued during the previous tile's CK)
     __syncthreads();
     // per element: effective moduli at the cell mean (Eq. "effective-cdb", mu sign from Eq. "cdb-model")
     if (tid < ne) {
@@ -664,6 +670,13 @@ __global__ void __launch_bounds__(256, 2) k_predictor_tc(StepArgs a) {
       c[1] = mu * m.rho_inv;
       const float* g = sGM + e * 40;           // GeomF starts with Theta^{-1}
       for (int k = 0; k < 9; ++k) c[2 + k] = g[k];
+      // what the damage rate at the nodes needs of the material (GeomF and MatF are
+      // overwritten by the next tile's copies meanwhile)
+      c[11] = m.lam0;
+      c[12] = m.mu0;
+      c[13] = m.gamma_r;
+      c[14] = m.xi0;
+      c[15] = m.cd;
     }
     // the MMA's B operand (strains and alpha at t_n, split) and the CK input [l][e*12 + p]
     for (int w = tid; w < L * TE; w += blockDim.x) {
@@ -685,6 +698,8 @@ __global__ void __launch_bounds__(256, 2) k_predictor_tc(StepArgs a) {
     tc::fence_smem_to_async();
     tc::fence_before();
     __syncthreads();
+    // the next tile's copies: the state rows, GeomF and MatF are no longer read
+    if (tile + gridDim.x < ntiles) issue(tile + gridDim.x);
     // issued from the last warp, which has no CK work at order 1 (the issuing thread waits
     // for the tensor pipe)
     if (tid == C::ISSUER) {
@@ -781,7 +796,9 @@ __global__ void __launch_bounds__(256, 2) k_predictor_tc(StepArgs a) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int e = eb + j;
-          const MatF m = *reinterpret_cast<const MatF*>(sGM + (e < ne ? e : 0) * 40 + 32);
+          const float* c = sCoef + (e < ne ? e : 0) * 16;
+          MatF m{};
+          m.lam0 = c[11]; m.mu0 = c[12]; m.gamma_r = c[13]; m.xi0 = c[14]; m.cd = c[15];
           if (q < NQ) sR[q * TE + e] = e < ne ? law_rate<LAW>(a.law, v + 8 * j, v[8 * j + 6], m) : 0.f;
         }
       }
@@ -793,6 +810,7 @@ __global__ void __launch_bounds__(256, 2) k_predictor_tc(StepArgs a) {
       if (k < L && e < ne) a.d[(e0 + e) * DS + C::AOFF + k] = v;
     });
   }
+  tc::cp_async_wait<0>();                    // no copy may still be in flight at exit
   if (failed) {
     if (tid == 0) atomicOr(a.status, kStatusTimeout);
     tc::wait_parity(&mbar, phase ^ 1u, kWaitLimit);   // let the MMAs in flight finish before freeing TMEM
