@@ -38,11 +38,34 @@ struct FaceKeyHash {
   }
 };
 
-// dg_step_host streams the state through the device in element chunks: multiples
-// of 16 elements, at least 4096 each, at most 8 of them (16 measured slower).
-int64_t host_chunk_size(int64_t E) {
-  const int64_t chunk = std::max<int64_t>(4096, (E + 7) / 8);
-  return (chunk + 15) / 16 * 16;
+// dg_step_host streams the state through the device in element chunks, whose
+// boundaries (multiples of 16 elements) this returns: about 1/16 of the elements in
+// the first chunk and in the last, whose upload and download nothing hides, and the
+// rest in seven equal chunks; at least 4096 elements per chunk, so small meshes take
+// fewer (more than about nine chunks measured slower).
+std::vector<int64_t> host_chunk_bounds(int64_t E) {
+  auto r16 = [](int64_t x) { return (x + 15) / 16 * 16; };
+  std::vector<int64_t> b{0};
+  const int64_t edge = r16(std::max<int64_t>(4096, E / 16));
+  if (E <= 2 * edge + 4096) {                 // uniform chunks of at least 4096
+    const int64_t chunk = r16(std::max<int64_t>(4096, (E + 7) / 8));
+    for (int64_t e = chunk; e < E; e += chunk) b.push_back(e);
+  } else {
+    const int64_t last = (E - edge) / 16 * 16;  // start of the last chunk
+    b.push_back(edge);
+    const int64_t mid = last - edge;
+    const int64_t parts = std::max<int64_t>(1, std::min<int64_t>(7, mid / 4096));
+    const int64_t chunk = r16((mid + parts - 1) / parts);
+    for (int64_t e = edge + chunk; e < last; e += chunk) b.push_back(e);
+    b.push_back(last);
+  }
+  b.push_back(E);
+  return b;
+}
+
+// the chunk of element e
+int host_chunk_of(const std::vector<int64_t>& b, int64_t e) {
+  return static_cast<int>(std::upper_bound(b.begin(), b.end(), e) - b.begin()) - 1;
 }
 
 // The faces of one such chunk: the interior faces first seen from its elements
@@ -617,19 +640,19 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
   }
   if (M == 1) {
     // the face ranges that dg_step_host launches as soon as their predictors are done
-    const int64_t chunk = host_chunk_size(E);
-    const int C = static_cast<int>((E + chunk - 1) / chunk);
+    const std::vector<int64_t> cb = host_chunk_bounds(E);
+    const int C = static_cast<int>(cb.size()) - 1;
     ctx->host_faces.assign(static_cast<size_t>(C), HostChunkFaces{});
     int64_t fi = 0, fb = ctx->F_interior;
     for (int k = 0; k < C; ++k) {
-      const int64_t e1 = std::min<int64_t>(E, (k + 1) * chunk);
+      const int64_t e1 = cb[static_cast<size_t>(k) + 1];
       HostChunkFaces& h = ctx->host_faces[static_cast<size_t>(k)];
-      int64_t reach = k * chunk;
+      int64_t reach = cb[static_cast<size_t>(k)];
       h.fi0 = fi;
       for (; fi < ctx->F_interior && faces[static_cast<size_t>(fi)].x < e1; ++fi)
         reach = std::max<int64_t>(reach, faces[static_cast<size_t>(fi)].z);
       h.fi1 = fi;
-      h.need = static_cast<int>(reach / chunk);
+      h.need = host_chunk_of(cb, reach);
       h.fb0 = fb;
       for (; fb < ctx->F && faces[static_cast<size_t>(fb)].x < e1; ++fb) {}
       h.fb1 = fb;
@@ -669,7 +692,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, dg_ctx** out) {
   }
 
   // device allocation and upload
-  const int N = ctx->N, L = ctx->L;
+  const int N = ctx->N;
   const size_t qs = static_cast<size_t>(q_stride(N)), ds = static_cast<size_t>(d_stride(N));
   const int64_t EV = ctx->EV;
   ctx->q[0] = static_cast<float*>(dev_alloc(ctx, sizeof(float) * qs * EV));
@@ -1139,10 +1162,11 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt) {
 }
 
 // One step from a host state to a host state, with the transfers overlapped: the
-// element range is cut into chunks; the host-to-device copy of chunk k+1 runs
-// (on a copy stream) while chunk k is converted and predicted, and the
-// device-to-host copy of chunk k while the corrector works on chunk k+1.  Every
-// element's arithmetic is the same as dg_step's.
+// element range is cut into chunks (host_chunk_bounds); the host-to-device copy of
+// chunk k+1 runs (on a copy stream) while chunk k is converted and predicted, the
+// faces run as soon as their two sides are predicted, and the device-to-host copy of
+// chunk k runs while the corrector works on chunk k+1.  Every element's arithmetic
+// is the same as dg_step's.
 dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) {
   if (!ctx || !q_in || !q_out) return fail(ctx, DG_E_ARG, "NULL argument");
   if (!ctx->has_material) return fail(ctx, DG_E_STATE, "material must be set before dg_step_host");
@@ -1167,8 +1191,8 @@ dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) 
     dg_status st = ensure_staging(ctx, sizeof(float) * row * E);
     if (st != DG_OK) return st;
   }
-  const int64_t chunk = host_chunk_size(E);
-  const int C = static_cast<int>((E + chunk - 1) / chunk);
+  const std::vector<int64_t> cb = host_chunk_bounds(E);
+  const int C = static_cast<int>(cb.size()) - 1;
   const bool face_ranges = ctx->host_faces.size() == static_cast<size_t>(C);
   if (!ctx->copy_stream) DG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
   while (ctx->xfer_events.size() < static_cast<size_t>(2 * C + 1)) {
@@ -1208,9 +1232,9 @@ dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) 
   a.dt = static_cast<float>(dt);
   a.status = ctx->status;
   auto part = [&](int k) {
-    const int64_t e0 = k * chunk;
+    const int64_t e0 = cb[static_cast<size_t>(k)];
     StepArgs c = a;
-    c.E = std::min<int64_t>(chunk, E - e0);
+    c.E = cb[static_cast<size_t>(k) + 1] - e0;
     c.q_in = qi + e0 * qs;
     c.q_out = qo + e0 * qs;
     c.d = a.d + e0 * ds;
@@ -1226,7 +1250,7 @@ dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) 
   DG_CUDA(ctx, cudaEventRecord(evStart, ctx->stream));
   DG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, evStart, 0));
   for (int k = 0; k < C; ++k) {
-    const int64_t e0 = k * chunk, ne = std::min<int64_t>(chunk, E - e0);
+    const int64_t e0 = cb[static_cast<size_t>(k)], ne = cb[static_cast<size_t>(k) + 1] - e0;
     DG_CUDA(ctx, cudaMemcpyAsync(staging + e0 * row, q_in + e0 * row, sizeof(float) * row * ne,
                                  cudaMemcpyHostToDevice, ctx->copy_stream));
     DG_CUDA(ctx, cudaEventRecord(evH[k], ctx->copy_stream));
@@ -1244,7 +1268,7 @@ dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) 
   int faces_done = 0;                       // chunks whose interior faces are launched
   for (int k = 0; k < C; ++k) {
     const StepArgs c = part(k);
-    const int64_t e0 = k * chunk;
+    const int64_t e0 = cb[static_cast<size_t>(k)];
     DG_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, evH[k], 0));
     DG_CUDA(ctx, launch_state_in(ctx->N, c.E, 1, staging + e0 * row, 0, qi + e0 * qs, ctx->stream));
     DG_CUDA(ctx, launch_predictor(ctx->N, c, ctx->stream));
@@ -1274,7 +1298,7 @@ dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) 
   }
   for (int k = 0; k < C; ++k) {
     const StepArgs c = part(k);
-    const int64_t e0 = k * chunk;
+    const int64_t e0 = cb[static_cast<size_t>(k)];
     DG_CUDA(ctx, launch_corrector(ctx->N, c, ctx->stream));
     ++launches;
     if (nsrc > 0) {
@@ -1285,7 +1309,7 @@ dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt) 
     DG_CUDA(ctx, cudaEventRecord(evC[k], ctx->stream));
   }
   for (int k = 0; k < C; ++k) {
-    const int64_t e0 = k * chunk, ne = std::min<int64_t>(chunk, E - e0);
+    const int64_t e0 = cb[static_cast<size_t>(k)], ne = cb[static_cast<size_t>(k) + 1] - e0;
     DG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, evC[k], 0));
     DG_CUDA(ctx, cudaMemcpyAsync(q_out + e0 * row, staging + e0 * row, sizeof(float) * row * ne,
                                  cudaMemcpyDeviceToHost, ctx->copy_stream));
