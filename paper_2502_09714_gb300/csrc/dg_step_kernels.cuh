@@ -253,7 +253,7 @@ template <int KS, int NJ = 4, class Out, class Bar>
 __device__ __forceinline__ void block_gemm_part(const float* __restrict__ A, int lda,
                                                 const float* __restrict__ B, int ldb, int M, int Nc,
                                                 int K, float* partial, Out out, int t, int nt, Bar bar) {
-  static_assert(NJ == 4 || NJ == 2, "4 rows x 4 or 2 columns per work item");
+  static_assert(NJ == 4 || NJ == 3 || NJ == 2, "4 rows x 4, 3 or 2 columns per work item");
   const int mq = M >> 2, nq = Nc / NJ, tiles = mq * nq;
   const int kchunk = (K + KS - 1) / KS;
   for (int w = t; w < tiles * KS; w += nt) {
@@ -275,6 +275,8 @@ __device__ __forceinline__ void block_gemm_part(const float* __restrict__ A, int
       if constexpr (NJ == 4) {
         const float4 b = *reinterpret_cast<const float4*>(bp + k * ldb);
         bv[0] = b.x; bv[1] = b.y; bv[2] = b.z; bv[3] = b.w;
+      } else if constexpr (NJ == 3) {
+        bv[0] = bp[k * ldb]; bv[1] = bp[k * ldb + 1]; bv[2] = bp[k * ldb + 2];
       } else {
         const float2 b = *reinterpret_cast<const float2*>(bp + k * ldb);
         bv[0] = b.x; bv[1] = b.y;
@@ -295,6 +297,7 @@ __device__ __forceinline__ void block_gemm_part(const float* __restrict__ A, int
       for (int i = 0; i < 4; ++i) {
         float* pp = partial + (ks * M + 4 * mi + i) * Nc + NJ * ni;
         if constexpr (NJ == 4) *reinterpret_cast<float4*>(pp) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        else if constexpr (NJ == 3) { pp[0] = acc[i][0]; pp[1] = acc[i][1]; pp[2] = acc[i][2]; }
         else *reinterpret_cast<float2*>(pp) = make_float2(acc[i][0], acc[i][1]);
       }
     }
@@ -2165,7 +2168,7 @@ struct CorrTcCfg : Dim<N> {
   static constexpr int NBC = TE * NCOL;                    // MMA N of the volume evaluation
   static constexpr int NV = 3 * TE, NB = 10 * TE, NM = 2 * NV, NFC = 9 * TE;
   static constexpr int NPC = (NB + 15) / 16 * 16;          // MMA N of the projection
-  static constexpr int KS_FACE = N >= 4 ? 2 : 1, NJ_FACE = 2;   // face GEMM: k-split, columns per item
+  static constexpr int KS_FACE = N >= 4 ? 4 : 1, NJ_FACE = N >= 4 ? 3 : 2;   // face GEMM: k-split, columns per item
   // tensor memory: volume-node values (then the projection's D) | projection A (TF32
   // high part, remainder) | volume A phi_l(x_q) (TF32 high part, remainder)
   static constexpr int COL_DP = 0;
