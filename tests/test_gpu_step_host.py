@@ -34,8 +34,10 @@ def _state(E, L, seed):
 def _mesh(case):
     if case == "periodic4":                       # 384 elements: one chunk
         return periodic_cube_mesh(4, 4000.0, jitter=0.1, seed=3)
-    if case == "periodic13":                      # 13182 elements: four chunks, the last ragged
+    if case == "periodic13":                      # 13182 elements: three chunks, the last ragged
         return periodic_cube_mesh(13, 4000.0, jitter=0.1, seed=13)
+    if case == "periodic32":                      # 196608 elements: nine chunks, the first and last halved
+        return periodic_cube_mesh(32, 4000.0, jitter=0.1, seed=32)
     g = np.linspace(0.0, 4000.0, 13)              # 10368 elements: three chunks, boundary faces in each
     mesh = kuhn_box_mesh(g, g, g, periodic=(False, True, False), jitter=0.1, seed=5)
     if case == "box_shuffled":
@@ -43,7 +45,7 @@ def _mesh(case):
     return mesh
 
 
-@pytest.mark.parametrize("case", ["periodic4", "periodic13", "box", "box_shuffled"])
+@pytest.mark.parametrize("case", ["periodic4", "periodic13", "periodic32", "box", "box_shuffled"])
 def test_step_host_equals_the_plain_sequence(case):
     import paper_2502_09714_gb300 as dgpkg
     N = 2
