@@ -1487,6 +1487,12 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
   const float* tb = a.tables;
   const float dt = a.dt;
   const int tid = threadIdx.x;
+  float tzs[NT], gzs[NT];                       // the time nodes and weights, scaled by dt
+#pragma unroll
+  for (int z = 0; z < NT; ++z) {
+    tzs[z] = __ldg(tb + T.tz + z) * dt;
+    gzs[z] = __ldg(tb + T.gz + z) * dt;
+  }
   // face basis table regrouped by node groups (zero beyond the NF face nodes)
   for (int w = tid; w < 4 * L * NG * GP; w += C::THREADS) {
     const int n = w % GP, r = w / GP;
@@ -1714,7 +1720,7 @@ __global__ void __launch_bounds__(FluxCfg<N>::THREADS, 512 / FluxCfg<N>::THREADS
           float sn[3] = {0.f, 0.f, 0.f};
 #pragma unroll
           for (int z = 0; z < NT; ++z) {
-            const float tau = __ldg(tb + T.tz + z) * dt, gam = __ldg(tb + T.gz + z) * dt;
+            const float tau = tzs[z], gam = gzs[z];
             float e[6];
 #pragma unroll
             for (int p = 0; p < 6; ++p) e[p] = eo[0][p];
