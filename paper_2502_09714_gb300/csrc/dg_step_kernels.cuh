@@ -546,8 +546,8 @@ struct PredTcCfg : Dim<N> {
   static constexpr int TMEM_COLS = TMEM_NEED <= 128 ? 128 : 256;
   static constexpr int QSP = D::QS % 32 == 0 ? D::QS + 4 : D::QS;
   static constexpr int oVw = 0;                            // [NQ][LP]
-  static constexpr int oKtA = round4(oVw + D::NQ * D::LP); // [3][L][LP]
-  static constexpr int oQ = round4(oKtA + 3 * D::L * D::LP);   // [TE][QSP] staged state rows
+  static constexpr int oKtA = round4(oVw + D::NQ * D::LP); // [L][LP][4]: Kt^e_lk of e = 0..2 (and 0) in one 16-byte word
+  static constexpr int oQ = round4(oKtA + 4 * D::L * D::LP);   // [TE][QSP] staged state rows
   static constexpr int oBH = oQ + TE * QSP;                // B, TF32 high part
   static constexpr int oBL = oBH + TE * BSBO;              // B, remainder
   static constexpr int oR = oBL + TE * BSBO;               // [NQ][TE] damage rate at the nodes
@@ -596,7 +596,12 @@ __global__ void __launch_bounds__(256, 2) k_predictor_tc(StepArgs a) {
   const float* tb = a.tables;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   copy_to_smem(sm + C::oVw, tb + T.Vw, NQ * LP);
-  copy_to_smem(sm + C::oKtA, tb + T.KtA, 3 * L * LP);
+  for (int w = tid; w < L * LP; w += blockDim.x) {
+    const int l = w / LP, k = w - l * LP;
+    *reinterpret_cast<float4*>(sm + C::oKtA + 4 * w) =
+        make_float4(__ldg(tb + T.KtA + (0 * L + l) * LP + k), __ldg(tb + T.KtA + (1 * L + l) * LP + k),
+                    __ldg(tb + T.KtA + (2 * L + l) * LP + k), 0.f);
+  }
   // B's K padding (modes L .. KP-1) stays zero
   if constexpr (KP > L) {
     for (int w = tid; w < TE * 8 * (KP - L); w += blockDim.x) {
@@ -736,7 +741,8 @@ __global__ void __launch_bounds__(256, 2) k_predictor_tc(StepArgs a) {
         for (int f = 0; f < 9; ++f) g[0][f] = g[1][f] = g[2][f] = 0.f;
 #pragma unroll 4
         for (int l = 0; l < Lin; ++l) {
-          const float k0 = sKtA[(0 * L + l) * LP + k], k1 = sKtA[(1 * L + l) * LP + k], k2 = sKtA[(2 * L + l) * LP + k];
+          const float4 kk = *reinterpret_cast<const float4*>(sKtA + 4 * (l * LP + k));
+          const float k0 = kk.x, k1 = kk.y, k2 = kk.z;
           const float4 p0 = *reinterpret_cast<const float4*>(pin + l * CW + e * 12);
           const float4 p1 = *reinterpret_cast<const float4*>(pin + l * CW + e * 12 + 4);
           const float p8 = pin[l * CW + e * 12 + 8];
