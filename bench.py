@@ -794,11 +794,18 @@ def _kernel_name(kind, N):
     return f"k_{kind}<{N}, 0>"
 
 
-def _kernel_source_digest():
+def _kernel_source_digest(path=None):
+    """Digest of the step kernels' code: comments and spacing are left out, so that
+    a change of wording keeps the DRAM counters taken on the same code."""
     import hashlib
-    p = os.path.join(ROOT, "paper_2502_09714_gb300", "csrc", "dg_step_kernels.cuh")
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    import re
+    p = path or os.path.join(ROOT, "paper_2502_09714_gb300", "csrc", "dg_step_kernels.cuh")
+    with open(p, encoding="utf-8") as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    src = " ".join(src.split())
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def _traffic_per_launch(kernel, N, E):

@@ -2,22 +2,24 @@
 // (CDM of Eq. "cdb-model", IVM of Eq. "ivm-model"; Appendix A), FP32, templated
 // on the degree N.
 //
-//   k_predictor  cell-mean effective Jacobian, Cauchy-Kovalevskaya recursion
-//                (Eq. "CKIter-ref-matrix") and damage-rate source at i = 1
-//                (Eq. "CKIter-ref-source")                       -> D, cp
-//   k_face_flux  Rusanov flux (Eq. "rusanov-flux") at the space-time nodes of
-//                every interior face, once per face, time-integrated; absorbing
-//                and free-surface fluxes (Appendix A) on boundary faces -> FF
+//   k_predictor_tc (degrees 2..4) / k_predictor (1, 5): cell-mean effective
+//                Jacobian, Cauchy-Kovalevskaya recursion (Eq. "CKIter-ref-matrix")
+//                and damage-rate source at i = 1 (Eq. "CKIter-ref-source") -> D, cp
+//   k_face_flux  Rusanov flux (Eq. "rusanov-flux") of every interior face, once
+//                per face, time-integrated (the stress at the space-time nodes,
+//                the linear terms from the time-integrated trace); absorbing and
+//                free-surface fluxes (Appendix A) on boundary faces -> FF
 //   k_corrector_tc (degrees 2..4) / k_corrector (1, 5): volume flux and damage
 //                source (Eqs. "3rd term", "rhs term"), face term (Eq. "2nd
 //                term") from FF, update (Eq. "time-integrated")
 //
 // Each kernel is persistent: a CTA loads the reference tables it needs into
-// shared memory once, then walks over tiles of elements (or faces).  The
-// evaluation of the Taylor expansion at the volume nodes runs on the tensor
-// cores (tcgen05, 3xTF32) for degrees 2..4 and feeds the pointwise law from
-// tensor memory; the other contractions with the shared tables are block GEMMs
-// with 4x4 register tiles.
+// shared memory once, then walks over tiles of elements (or faces).  For degrees
+// 2..4 the evaluations at the volume nodes (the predictor's strains and alpha,
+// the corrector's Taylor expansion, which feeds the pointwise law from tensor
+// memory) and the corrector's projection run on the tensor cores (tcgen05,
+// 3xTF32); the other contractions with the shared tables are block GEMMs with
+// register tiles.
 #pragma once
 
 #include <algorithm>
@@ -1430,8 +1432,8 @@ __global__ void __launch_bounds__(PicTcCfg<N>::THREADS, 1) k_picard_tc(StepArgs 
 // materials; the traces as register-tiled products with the face basis table
 // (G face nodes x 4 or 3 columns per thread, loops fully unrolled, warps 0-3
 // on order 0 and warps 4-7 on orders >= 1, whose mode counts add up to about
-// the same work); the flux at the face nodes with two threads per node, each
-// over half of the time nodes.
+// the same work); the flux at the face nodes with two threads per node, one per
+// side.
 // ===========================================================================
 template <int N>
 struct FluxCfg : Dim<N> {
