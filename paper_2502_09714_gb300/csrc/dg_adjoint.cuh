@@ -1106,8 +1106,11 @@ cudaError_t launch_adjoint_t(const AdjArgs& a, cudaStream_t s) {
   if (err != cudaSuccess) return err;
   err = cudaFuncSetAttribute(adj::k_adj_elem<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(be));
   if (err != cudaSuccess) return err;
-  const int gf = static_cast<int>(a.F < 152 * 64 ? a.F : 152 * 64);
-  const int ge = static_cast<int>(a.E < 152 * 64 ? a.E : 152 * 64);
+  // one CTA per face and per element (the hardware's dynamic scheduling of short CTAs
+  // balances the SMs' load to the end of the launch)
+  constexpr int64_t kMaxGrid = (int64_t(1) << 31) - 1;
+  const int gf = static_cast<int>(a.F < kMaxGrid ? a.F : kMaxGrid);
+  const int ge = static_cast<int>(a.E < kMaxGrid ? a.E : kMaxGrid);
   if (gf > 0) adj::k_adj_face<N><<<gf, 128, bf, s>>>(a);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
