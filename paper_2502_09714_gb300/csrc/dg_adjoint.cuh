@@ -350,6 +350,13 @@ __device__ __forceinline__ void mode_sums4(const float* vx, int ldv, const float
   }
 }
 
+// Work items of node_values (per side): four nodes per item when the table's row
+// stride is a multiple of 4, else two, times the ten fields.
+template <int NX, int LDV>
+__host__ __device__ constexpr int node_value_items() {
+  return (LDV % 4 == 0 ? (NX + 3) / 4 : (NX + 1) / 2) * 10;
+}
+
 // For every node x of a basis table V[l][x] (row stride ldv, NX nodes) and field
 // p: the value of the predictor's polynomial at the NT time nodes,
 //     u[z][x][p] = sum_o c[z][o] sum_l V[l][x] D^o_lp,
@@ -518,7 +525,10 @@ __global__ void __launch_bounds__(128, 7) k_adj_face(AdjArgs a) {
     // lam of the time-integrated face flux:
     //   lff[i][p] = -(a0 sum_k Vfw[f0][i][k] lam0[k][p] - a1 sum_k Vfw[f1][i][k] lam1[k][p])
     const float a0 = a.geom[e0].face[lf0][3], a1 = bnd ? 0.f : a.geom[e1].face[lf1][3];
-    for (int w = threadIdx.x; w < NF * 9; w += blockDim.x) {
+    // the items continue the traces' round-robin over the threads, so that the threads
+    // without a trace item take the first ones
+    constexpr int NVI = 2 * node_value_items<NF, A::NFP>();
+    for (int w = (threadIdx.x + blockDim.x - NVI % blockDim.x) % blockDim.x; w < NF * 9; w += blockDim.x) {
       const int i = w / 9, p = w - i * 9;
       const float4* v0 = reinterpret_cast<const float4*>(tb + T.Vfw + (lf0 * NF + i) * A::LP);
       const float4* v1 = reinterpret_cast<const float4*>(tb + T.Vfw + (lf1 * NF + i) * A::LP);
@@ -647,22 +657,29 @@ __global__ void __launch_bounds__(128, 7) k_adj_face(AdjArgs a) {
           }
         }
       }
+      // the two node halves of an item sit on adjacent lanes: their sums, with lane ic left
+      // holding modes 4 lq + 2 ic and 4 lq + 2 ic + 1 (each sends the pair it does not keep)
+      float s2[2][2][NT];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int jj = 0; jj < 2; ++jj)
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int o = 0; o < NT; ++o) acc[j][h][o] += __shfl_xor_sync(0xffffffffu, acc[j][h][o], 1);
+          for (int o = 0; o < NT; ++o) {
+            const float keep = ic ? acc[2 + jj][h][o] : acc[jj][h][o];
+            const float send = ic ? acc[jj][h][o] : acc[2 + jj][h][o];
+            s2[jj][h][o] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+          }
       if (!live) continue;
       float* out = a.rec + (f * 2 + sd) * A::RS;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int l = 4 * lq + j;
-        if ((j >> 1) != ic || l >= L) continue;   // both lanes hold the sums: lane ic takes modes 2 ic, 2 ic + 1
+      for (int jj = 0; jj < 2; ++jj) {
+        const int l = 4 * lq + 2 * ic + jj;
+        if (l >= L) continue;
 #pragma unroll
         for (int o = 0; o < NT; ++o) {
-          if (l < order_modes<N>(o, p0)) out[ld_index<N>(o, l, p0)] = acc[j][0][o];
-          if (l < order_modes<N>(o, p0 + 1)) out[ld_index<N>(o, l, p0 + 1)] = acc[j][1][o];
+          if (l < order_modes<N>(o, p0)) out[ld_index<N>(o, l, p0)] = s2[jj][0][o];
+          if (l < order_modes<N>(o, p0 + 1)) out[ld_index<N>(o, l, p0 + 1)] = s2[jj][1][o];
         }
       }
     }
@@ -703,14 +720,14 @@ struct ElemSmem {
 };
 
 template <int N>
-__global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
+__global__ void __launch_bounds__(128, 7) k_adj_elem(AdjArgs a) {
   using A = ADim<N>;
   using S = ElemSmem<N>;
   constexpr int L = A::L, NQ = A::NQ, NT = A::NT;
   extern __shared__ __align__(16) float smem[];
   // xi0, C_d, lam of cp, (unused), boundary d/dlam, d/dmu, CK d/d(lam/rho), CK d/d(mu/rho)
   __shared__ double sRed[8];
-  __shared__ float sGeo[16];          // Theta^{-1} [e][d], lambda_eff/rho, mu_eff/rho
+  __shared__ float sGeo[16];          // Theta^{-1} [e][d]
   __shared__ float sC[NT * NT], sG[NT], sIW[NQ];
   const TableLayout T = table_layout(N);
   const float* tb = a.tables;
@@ -747,8 +764,10 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
     // the nodal values and X (independent of each other) in one phase
     node_values<N, NQ, A::NQP>(tb + T.VvT, smem + S::oQ, smem + S::oD, sC, smem + S::oU);
     // per volume node q: X[q][d][p] = sum_k w_q dphi_k/dx_d(x_q) lam[k][p], X[q][27] = sum_k w_q phi_k lam[k][9];
-    // one item per node and pair of fields (8, 9 pairs the last wave field with alpha)
-    for (int w = threadIdx.x; w < NQ * 5; w += blockDim.x) {
+    // one item per node and pair of fields (8, 9 pairs the last wave field with alpha); the
+    // items continue the nodal values' round-robin over the threads
+    constexpr int NVI = node_value_items<NQ, A::NQP>();
+    for (int w = (threadIdx.x + blockDim.x - NVI % blockDim.x) % blockDim.x; w < NQ * 5; w += blockDim.x) {
       const int q = w / 5, pp = w - q * 5, p0 = 2 * pp;
       float g0[3] = {0.f, 0.f, 0.f}, g1[3] = {0.f, 0.f, 0.f};
       const float4* gA = reinterpret_cast<const float4*>(tb + T.Gw + q * A::LP);
@@ -853,37 +872,44 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
           }
         }
       }
-      // the four node quarters of an item sit on consecutive lanes
+      // the four node quarters of an item sit on consecutive lanes: their sums, with lane
+      // qc left holding mode 4 lq + qc (each exchange sends the half a lane does not keep)
+      const bool hi2 = (qc & 2) != 0, hi1 = (qc & 1) != 0;
+      float t2[2][2][NT];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int jj = 0; jj < 2; ++jj)
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
           for (int z = 0; z < NT; ++z) {
-            float v = acc[j][h][z];
-            v += __shfl_xor_sync(0xffffffffu, v, 1);
-            v += __shfl_xor_sync(0xffffffffu, v, 2);
-            acc[j][h][z] = v;
+            const float keep = hi2 ? acc[2 + jj][h][z] : acc[jj][h][z];
+            const float send = hi2 ? acc[jj][h][z] : acc[2 + jj][h][z];
+            t2[jj][h][z] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
           }
-      if (!live) continue;
+      float t1[2][NT];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int l = 4 * lq + j;
-        if (j != qc || l >= L) continue;       // every lane holds the sums: lane qc takes mode 4 lq + qc
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int p = p0 + h;
+        for (int z = 0; z < NT; ++z) {
+          const float keep = hi1 ? t2[1][h][z] : t2[0][h][z];
+          const float send = hi1 ? t2[0][h][z] : t2[1][h][z];
+          t1[h][z] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+        }
+      const int l = 4 * lq + qc;
+      if (!live || l >= L) continue;
 #pragma unroll
-          for (int o = 0; o < NT; ++o) {
-            if (l >= order_modes<N>(o, p)) continue;
-            float s = 0.f;
+      for (int h = 0; h < 2; ++h) {
+        const int p = p0 + h;
 #pragma unroll
-            for (int z = 0; z < NT; ++z) s = fmaf(sC[z * NT + o], acc[j][h][z], s);
-            const int idx = ld_index<N>(o, l, p);
+        for (int o = 0; o < NT; ++o) {
+          if (l >= order_modes<N>(o, p)) continue;
+          float s = 0.f;
 #pragma unroll
-            for (int fl = 0; fl < 4; ++fl) s += smem[S::oR + fl * A::RS + idx];
-            sLD[idx] = s;
-          }
+          for (int z = 0; z < NT; ++z) s = fmaf(sC[z * NT + o], t1[h][z], s);
+          const int idx = ld_index<N>(o, l, p);
+#pragma unroll
+          for (int fl = 0; fl < 4; ++fl) s += smem[S::oR + fl * A::RS + idx];
+          sLD[idx] = s;
         }
       }
     }
@@ -953,7 +979,9 @@ __global__ void __launch_bounds__(128, 8) k_adj_elem(AdjArgs a) {
       const int Lout = n_modes(N - i), Lin = n_modes(N - i + 1);
       const float* lDi = sLD + A::QS + d_offset(N, i);       // [Lout][9]
       if (i == N) {
-        for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
+        // from the first warp without an H item below
+        constexpr int Q0 = (9 * n_modes(0) + 31) / 32 * 32;
+        for (int q = (threadIdx.x + blockDim.x - Q0 % blockDim.x) % blockDim.x; q < NQ; q += blockDim.x) {
           // the strains at t_n at node q
           float u[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
