@@ -727,7 +727,7 @@ __global__ void __launch_bounds__(128, 7) k_adj_elem(AdjArgs a) {
   extern __shared__ __align__(16) float smem[];
   // xi0, C_d, lam of cp, (unused), boundary d/dlam, d/dmu, CK d/d(lam/rho), CK d/d(mu/rho)
   __shared__ double sRed[8];
-  __shared__ float sGeo[16];          // Theta^{-1} [e][d]
+  __shared__ float sGeo[16];          // Theta^{-1} [e][d]; lambda_eff, mu_eff of the cell mean at [9], [10]
   __shared__ float sC[NT * NT], sG[NT], sIW[NQ];
   const TableLayout T = table_layout(N);
   const float* tb = a.tables;
@@ -951,18 +951,19 @@ __global__ void __launch_bounds__(128, 7) k_adj_elem(AdjArgs a) {
     }
     block_add(&sRed[0], px);
     block_add(&sRed[1], pc);
-    // effective Lame parameters of the cell mean (the forward predictor's rule)
-    float lam_eff, mu_eff;
-    {
+    // effective Lame parameters of the cell mean (the forward predictor's rule), on the last
+    // thread (one item of the forward CK products at most)
+    if (threadIdx.x == blockDim.x - 1) {
       const float r6 = 2.449489742783178f;
       float ub[10];
 #pragma unroll
       for (int p = 0; p < 10; ++p) ub[p] = smem[S::oQ + p] * r6;
       const Inv v = invariants(ub);
-      lam_eff = m.lam0 - ub[9] * m.gamma_r * v.xi * (1.f / 3.f);
-      mu_eff = m.mu0 + ub[9] * m.xi0 * m.gamma_r - 0.5f * ub[9] * m.gamma_r * v.xi;
+      sGeo[9] = m.lam0 - ub[9] * m.gamma_r * v.xi * (1.f / 3.f);
+      sGeo[10] = m.mu0 + ub[9] * m.xi0 * m.gamma_r - 0.5f * ub[9] * m.gamma_r * v.xi;
     }
     __syncthreads();                         // the projection's lam of D is complete
+    const float lam_eff = sGeo[9], mu_eff = sGeo[10];
     // Cauchy-Kovalevskaya recursion transposed, order N down to 1 (the forward products in
     // GX; the lambda/rho and mu/rho parts summed per thread over all orders, reduced once)
     const float lr = lam_eff * m.rho_inv, mr = mu_eff * m.rho_inv;
@@ -982,18 +983,18 @@ __global__ void __launch_bounds__(128, 7) k_adj_elem(AdjArgs a) {
         // from the first warp without an H item below
         constexpr int Q0 = (9 * n_modes(0) + 31) / 32 * 32;
         for (int q = (threadIdx.x + blockDim.x - Q0 % blockDim.x) % blockDim.x; q < NQ; q += blockDim.x) {
-          // the strains at t_n at node q
+          // the strains at t_n at node q, and lam of the damage rate there,
+          //   w_q sum_k phi_k(x_q) lam D^1_k9
           float u[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          float lsum = 0.f;
 #pragma unroll 4
           for (int l = 0; l < L; ++l) {
             const float v = __ldg(tb + T.VvT + l * A::NQP + q);
 #pragma unroll
             for (int p = 0; p < 6; ++p) u[p] = fmaf(v, smem[S::oQ + l * 10 + p], u[p]);
+            lsum = fmaf(v, sLD[A::QS + A::AOFF + l], lsum);
           }
-          float lr4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-          for (int l = 0; l < L; ++l) lr4[l & 3] = fmaf(__ldg(tb + T.Vw + q * A::LP + l), sLD[A::QS + A::AOFF + l], lr4[l & 3]);
-          const float lrq = (lr4[0] + lr4[1]) + (lr4[2] + lr4[3]);
+          const float lrq = lsum / sIW[q];
           float lu[10];
 #pragma unroll
           for (int p = 0; p < 10; ++p) lu[p] = 0.f;
