@@ -952,7 +952,7 @@ __global__ void __launch_bounds__(128, 7) k_adj_elem(AdjArgs a) {
     block_add(&sRed[0], px);
     block_add(&sRed[1], pc);
     // effective Lame parameters of the cell mean (the forward predictor's rule), on the last
-    // thread (one item of the forward CK products at most)
+    // thread (no more items of the forward CK products than any other), shared after the barrier
     if (threadIdx.x == blockDim.x - 1) {
       const float r6 = 2.449489742783178f;
       float ub[10];
