@@ -71,7 +71,7 @@ def _solver(w, N, Q0):
     return s
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
 def test_adjoint_parity_with_oracle(N):
     n = 6
     w, o, Q0, dt, ref = _case(N, n)
