@@ -90,7 +90,7 @@ def test_adjoint_parity_with_oracle(N):
     assert errs["xi0"] <= TOL_GRAD and errs["cd"] <= TOL_GRAD and errs["q0"] <= TOL_GRAD, errs
 
 
-@pytest.mark.parametrize("N", [2, 3])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
 def test_adjoint_parity_with_boundary_faces(N):
     """A closed jittered box (162 tets) with a free-surface top and absorbing
     sides: the GPU gradient against the oracle's adjoint, whose boundary part is
