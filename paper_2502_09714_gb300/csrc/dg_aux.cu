@@ -7,38 +7,62 @@
 namespace dg {
 namespace {
 
+// The conversions give each element copy one warp: it reads the copy's row in the source
+// layout with coalesced loads into its own shared-memory row, and writes the row in the
+// destination layout with coalesced stores.
+constexpr int kConvWarps = 8;
+
 // internal q[v][l*10+p] <- ABI src[m][e][p][l], v = e*M + m
 template <int L>
-__global__ void k_state_in(int64_t E, int M, const void* src, int src_is_double, float* q, int qs) {
-  const int64_t v = blockIdx.x;
+__global__ void __launch_bounds__(32 * kConvWarps) k_state_in(int64_t E, int M, const void* src,
+                                                              int src_is_double, float* q, int qs) {
+  constexpr int R = kFields * L;
+  __shared__ float t[kConvWarps][R];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int64_t v = static_cast<int64_t>(blockIdx.x) * kConvWarps + wp;
   if (v >= E * M) return;
   const int64_t e = v / M, m = v - e * M;
-  const int64_t base = (m * E + e) * kFields * L;
-  for (int w = threadIdx.x; w < qs; w += blockDim.x) {
+  const int64_t base = (m * E + e) * R;
+  float* tw = t[wp];
+#pragma unroll
+  for (int r = lane; r < R; r += 32)
+    tw[r] = src_is_double ? static_cast<float>(static_cast<const double*>(src)[base + r])
+                          : static_cast<const float*>(src)[base + r];
+  __syncwarp();
+  float* qv = q + v * qs;
+#pragma unroll
+  for (int w = lane; w < round4(R); w += 32) {
     float val = 0.f;
-    if (w < kFields * L) {
-      const int k = w / kFields, p = w % kFields;
-      const int64_t idx = base + p * L + k;
-      val = src_is_double ? static_cast<float>(static_cast<const double*>(src)[idx])
-                          : static_cast<const float*>(src)[idx];
+    if (w < R) {
+      const int k = w / kFields, p = w - k * kFields;
+      val = tw[p * L + k];
     }
-    q[v * qs + w] = val;
+    if (w < qs) qv[w] = val;
   }
 }
 
 // ABI dst[m][e][p][l] <- internal q[v], v = e*M + m
 template <int L>
-__global__ void k_state_out(int64_t E, int M, const float* q, int qs, void* dst, int dst_is_double) {
-  const int64_t vi = blockIdx.x;
-  if (vi >= E * M) return;
-  const int64_t e = vi / M, m = vi - e * M;
-  const int64_t base = (m * E + e) * kFields * L;
-  for (int w = threadIdx.x; w < kFields * L; w += blockDim.x) {
-    const int p = w / L, l = w % L;
-    const float v = q[vi * qs + l * kFields + p];
-    const int64_t idx = base + w;
-    if (dst_is_double) static_cast<double*>(dst)[idx] = static_cast<double>(v);
-    else static_cast<float*>(dst)[idx] = v;
+__global__ void __launch_bounds__(32 * kConvWarps) k_state_out(int64_t E, int M, const float* q, int qs,
+                                                               void* dst, int dst_is_double) {
+  constexpr int R = kFields * L;
+  __shared__ float t[kConvWarps][R];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int64_t v = static_cast<int64_t>(blockIdx.x) * kConvWarps + wp;
+  if (v >= E * M) return;
+  const int64_t e = v / M, m = v - e * M;
+  const int64_t base = (m * E + e) * R;
+  float* tw = t[wp];
+  const float* qv = q + v * qs;
+#pragma unroll
+  for (int r = lane; r < R; r += 32) tw[r] = qv[r];
+  __syncwarp();
+#pragma unroll
+  for (int w = lane; w < R; w += 32) {
+    const int p = w / L, l = w - p * L;
+    const float val = tw[l * kFields + p];
+    if (dst_is_double) static_cast<double*>(dst)[base + w] = static_cast<double>(val);
+    else static_cast<float*>(dst)[base + w] = val;
   }
 }
 
@@ -68,13 +92,17 @@ __global__ void k_receivers(int L, int qs, int n_rec, const ReceiverDev* rec, co
 
 template <int N>
 cudaError_t state_in_t(int64_t E, int M, const void* src, int dbl, float* q, cudaStream_t s) {
-  k_state_in<n_modes(N)><<<static_cast<unsigned>(E * M), 128, 0, s>>>(E, M, src, dbl, q, q_stride(N));
+  const int64_t blocks = (E * M + kConvWarps - 1) / kConvWarps;
+  if (blocks == 0) return cudaSuccess;
+  k_state_in<n_modes(N)><<<static_cast<unsigned>(blocks), 32 * kConvWarps, 0, s>>>(E, M, src, dbl, q, q_stride(N));
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t state_out_t(int64_t E, int M, const float* q, void* dst, int dbl, cudaStream_t s) {
-  k_state_out<n_modes(N)><<<static_cast<unsigned>(E * M), 128, 0, s>>>(E, M, q, q_stride(N), dst, dbl);
+  const int64_t blocks = (E * M + kConvWarps - 1) / kConvWarps;
+  if (blocks == 0) return cudaSuccess;
+  k_state_out<n_modes(N)><<<static_cast<unsigned>(blocks), 32 * kConvWarps, 0, s>>>(E, M, q, q_stride(N), dst, dbl);
   return cudaGetLastError();
 }
 
