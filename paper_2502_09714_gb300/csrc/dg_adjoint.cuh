@@ -483,7 +483,7 @@ struct FaceSmem {
 };
 
 template <int N>
-__global__ void __launch_bounds__(128, 7) k_adj_face(AdjArgs a) {
+__global__ void __launch_bounds__(128, 8) k_adj_face(AdjArgs a) {
   using A = ADim<N>;
   using S = FaceSmem<N>;
   constexpr int L = A::L, NF = A::NF, NT = A::NT;
