@@ -218,6 +218,18 @@ dg_status dg_step(dg_ctx* ctx, int64_t n_steps, double dt);
  * material (DG_E_STATE); errors as dg_step. */
 dg_status dg_step_host(dg_ctx* ctx, const float* q_in, float* q_out, double dt);
 
+/* The element chunks of dg_step_host with one member, for inspection (host only,
+ * no device needed): chunk k holds elements [bounds[k], bounds[k + 1]) of a mesh
+ * of n_elem elements.  Every chunk start is a multiple of 16.  Meshes of at most
+ * 12,288 elements take chunks of 4096 elements (the last one shorter).  Larger
+ * ones take a first chunk of max(4096, n_elem / 16) elements rounded up to 16
+ * and a last chunk of that size plus up to 15 (nothing hides these chunks'
+ * transfers), with one to seven chunks between, all of one size (a multiple of
+ * 16, at least 4096) but the last of them, which is not larger.  Writes the first
+ * min(cap, count + 1) entries of bounds and returns the chunk count; -1 for
+ * n_elem < 1, cap < 0, or a NULL bounds with cap > 0. */
+int dg_host_chunks(int64_t n_elem, int64_t* bounds, int cap);
+
 /* One step that allocates no memory, for callers that cannot call
  * cudaMalloc while they step (a host process under a fixed device-memory
  * budget, code running between the capture of other work, or an embedding

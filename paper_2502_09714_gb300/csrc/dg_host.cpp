@@ -443,6 +443,14 @@ extern "C" {
 
 int64_t dg_n_modes(int order) { return order < 0 ? 0 : n_modes(order); }
 
+int dg_host_chunks(int64_t n_elem, int64_t* bounds, int cap) {
+  if (n_elem < 1 || cap < 0 || (cap > 0 && !bounds)) return -1;
+  const std::vector<int64_t> b = host_chunk_bounds(n_elem);
+  const int n = static_cast<int>(b.size());
+  for (int i = 0; i < n && i < cap; ++i) bounds[i] = b[static_cast<size_t>(i)];
+  return n - 1;
+}
+
 const char* dg_last_error(const dg_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_last_error.c_str();
 }

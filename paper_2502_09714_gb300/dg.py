@@ -25,7 +25,7 @@ EXPORTS = (
     "dg_receivers", "dg_receivers_read", "dg_dt", "dg_time", "dg_n_modes", "dg_get_stats",
     "dg_profile_enable", "dg_profile_read", "dg_reference_table", "dg_last_error", "dg_destroy",
     "dg_step_noalloc", "dg_set_rheology", "dg_set_predictor", "dg_set_wait_limit", "dg_step_host",
-    "dg_adjoint_gradient", "dg_revolve_plan", "dg_revolve_cost",
+    "dg_adjoint_gradient", "dg_revolve_plan", "dg_revolve_cost", "dg_host_chunks",
 )
 
 
@@ -89,6 +89,7 @@ def load_library(path: str | None = None) -> C.CDLL:
         "dg_set_predictor": ([vp, C.c_int, C.c_int], C.c_int),
         "dg_set_wait_limit": ([vp, i64], C.c_int),
         "dg_step_host": ([vp, vp, vp, C.c_double], C.c_int),
+        "dg_host_chunks": ([i64, vp, C.c_int], C.c_int),
         "dg_set_source": ([vp, C.POINTER(PointSource), i64], C.c_int),
         "dg_set_state": ([vp, C.POINTER(dbl), dbl], C.c_int),
         "dg_set_state_f32": ([vp, C.POINTER(C.c_float), dbl], C.c_int),
@@ -155,6 +156,18 @@ def revolve_plan(n_steps: int, snapshots: int):
 
 def revolve_cost(n_steps: int, snapshots: int) -> int:
     return int(load_library().dg_revolve_cost(int(n_steps), int(snapshots)))
+
+
+def host_chunks(n_elem: int):
+    """Chunk boundaries [count + 1] of the host-to-host step on a mesh of n_elem
+    elements (chunk k holds elements [b[k], b[k + 1]))."""
+    lib = load_library()
+    n = lib.dg_host_chunks(int(n_elem), None, 0)
+    if n < 0:
+        raise DGError(1, "dg_host_chunks: n_elem must be >= 1")
+    b = np.empty(n + 1, dtype=np.int64)
+    lib.dg_host_chunks(int(n_elem), b.ctypes.data_as(C.c_void_p), n + 1)
+    return b
 
 
 def _check(lib, ctx, status):

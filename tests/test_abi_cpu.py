@@ -27,13 +27,49 @@ def lib():
 
 def test_library_exports_every_declared_symbol(lib):
     header = open(os.path.join(ROOT, "include", "dg.h")).read()
-    declared = set(re.findall(r"^\s*(?:dg_status|double|int64_t|const char\s*\*|void)\s+(dg_\w+)\s*\(",
+    declared = set(re.findall(r"^\s*(?:dg_status|double|int64_t|int|const char\s*\*|void)\s+(dg_\w+)\s*\(",
                               header, flags=re.M))
     assert declared, "no declarations found"
     assert declared == set(EXPORTS)
     raw = ctypes.CDLL(dgpkg.LIB_PATH)
     for name in declared:
         assert hasattr(raw, name), name
+
+
+def _check_chunk_plan(E, b):
+    r16 = lambda x: (x + 15) // 16 * 16
+    sizes = np.diff(b)
+    assert b[0] == 0 and b[-1] == E, (E, b)
+    assert np.all(sizes > 0), (E, b)
+    assert np.all(b[1:-1] % 16 == 0), (E, b)
+    assert len(sizes) <= 9, (E, b)
+    if E <= 3 * 4096:                                 # chunks of 4096, the last shorter
+        assert np.all(sizes[:-1] == 4096) and sizes[-1] <= 4096, (E, b)
+        return
+    edge = r16(max(4096, E // 16))
+    assert sizes[0] == edge and edge <= sizes[-1] <= edge + 15, (E, b)
+    mid = sizes[1:-1]
+    assert 1 <= len(mid) <= 7, (E, b)
+    assert np.all(mid[:-1] == mid[0]) and mid[0] % 16 == 0 and mid[0] >= 4096 and mid[-1] <= mid[0], (E, b)
+
+
+def test_host_step_chunk_plan(lib):
+    """The element chunks of dg_step_host: they tile the mesh in order, start on
+    multiples of 16, and take the documented sizes (small first and last chunks,
+    up to seven equal ones between), over sizes around every branch and random
+    ones up to the 2^29 copies the library admits."""
+    for E in (1, 15, 16, 17, 4095, 4096, 4097, 8192, 12287, 12288, 12289, 13182, 65535, 65536, 65537,
+              196608, 4350240, (1 << 29) - 1):
+        _check_chunk_plan(E, dgpkg.host_chunks(E))
+    rng = np.random.default_rng(1)
+    for E in rng.integers(1, 1 << 29, size=2000):
+        _check_chunk_plan(int(E), dgpkg.host_chunks(int(E)))
+    # the count comes back without a buffer, and bad arguments are refused
+    assert lib.dg_host_chunks(4350240, None, 0) == 9
+    assert lib.dg_host_chunks(0, None, 0) == -1
+    assert lib.dg_host_chunks(100, None, 3) == -1
+    with pytest.raises(DGError):
+        dgpkg.host_chunks(0)
 
 
 def test_n_modes(lib):
